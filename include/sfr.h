@@ -1,0 +1,132 @@
+/*
+ * libsfr — sparse fixed-rank decomposition M = L + S, rank(L) = r, on one GB300 GPU.
+ *
+ * The library solves the S-FR problem of Ros et al., "Fast and Robust Fixed-Rank
+ * Matrix Recovery" (Eq. 1 / Eq. 3): min ||S||_1 s.t. M = L + S, L on the rank-r
+ * manifold, by FR-ADM (Algorithm 1), an augmented-Lagrangian iteration (Eq. 4)
+ * whose L-step is one FixedRankOptStep (Algorithm 3) in polar form L = U B V^T
+ * (U, V Stiefel, B symmetric, Sec. 4.1), and its Nystrom variant FR-Nys
+ * (Algorithm 2).
+ *
+ * Conventions for every entry point:
+ *   - All matrices are row-major.  M is m x n with leading dimension ldm >= n
+ *     (in elements).  U is m x r, V is n x r, B is r x r, all float64 and dense
+ *     (leading dimension r).  S is m x n with leading dimension lds >= n.
+ *   - `mem` says where the caller's M, nys_perm, U, B, V and S live:
+ *     SFR_MEM_DEVICE (pointers into the context's GPU) or SFR_MEM_HOST
+ *     (ordinary or pinned host memory; the library copies in and out).
+ *   - The caller owns M and every result buffer; they must stay valid until
+ *     the call (sfr_solve) or the request (sfr_submit ... sfr_poll) finishes.
+ *     The library owns its workspace (multiplier Y, thin products, r x r
+ *     scratch) and frees it in sfr_destroy.
+ *   - Functions return an sfr_status and never abort.  A status < 0 is an
+ *     error; sfr_last_error(ctx) then holds a one-line message.  A per-problem
+ *     outcome is also stored in sfr_result.status.
+ *   - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef SFR_H
+#define SFR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SFR_OK = 0,
+  SFR_PENDING = 1,      /* sfr_poll: the request is still running                      */
+  SFR_E_INVAL = -1,     /* bad argument (sizes, rank, dtype, null pointer, rho <= 1 ...) */
+  SFR_E_NOMEM = -2,     /* device allocation failed or the HBM budget is exceeded        */
+  SFR_E_CUDA = -3,      /* a CUDA runtime call failed                                     */
+  SFR_E_RANK = -4,      /* P_O met an m x r (or n x r) matrix of rank < r (Eq. 9 assumes full rank) */
+  SFR_E_NOCONV = -5,    /* max_iter iterations without reaching tol                       */
+  SFR_E_NAN = -6,       /* a non-finite value appeared in the iteration                   */
+  SFR_E_TIMEOUT = -7,   /* sfr_poll: timeout elapsed                                      */
+  SFR_E_BUSY = -8       /* the request queue is full                                      */
+} sfr_status;
+
+typedef enum { SFR_F64 = 0, SFR_F32 = 1, SFR_BF16 = 2 } sfr_dtype;
+
+/* Arithmetic of the m x n sweep.  The r x r projectors and the convergence
+ * test are float64 in both modes.
+ *   SFR_PREC_FP64:  float64 everywhere (M may be stored f64, f32 or bf16).
+ *   SFR_PREC_MIXED: float32 sweep arithmetic and multiplier storage, float64
+ *                   factors and r x r steps. */
+typedef enum { SFR_PREC_FP64 = 0, SFR_PREC_MIXED = 1 } sfr_precision;
+
+typedef enum { SFR_MEM_DEVICE = 0, SFR_MEM_HOST = 1 } sfr_memspace;
+
+typedef struct sfr_ctx sfr_ctx;
+
+typedef struct {
+  int device;               /* CUDA device ordinal                                         */
+  size_t hbm_budget_bytes;  /* cap on workspace bytes the context may hold; 0 = no cap     */
+  int max_slots;            /* concurrent requests for sfr_submit; 0 = default (8)         */
+  void* cuda_stream;        /* cudaStream_t for sfr_solve; NULL = a stream the ctx creates */
+} sfr_config;
+
+typedef struct {
+  int64_t m, n, ldm;        /* M is m x n, row-major, leading dimension ldm >= n           */
+  int32_t r;                /* target rank, 1 <= r <= min(m, n) and r <= 64                */
+  sfr_dtype m_dtype;        /* storage type of M                                           */
+  const void* M;            /* the data matrix (read only)                                 */
+  double mu0;               /* initial penalty mu_1 (Algorithm 1 uses 1); > 0              */
+  double rho;               /* continuation factor, > 1 (Algorithm 1 leaves it open)       */
+  double mu_max;            /* penalty cap mu_bar (Algorithm 1 uses 1e9)                   */
+  double tol;               /* stop when ||M - L - S||_F / ||M||_F <= tol                  */
+  int32_t max_iter;         /* give up (SFR_E_NOCONV) after this many iterations           */
+  int32_t fixed_iters;      /* > 0: run exactly this many iterations, ignore tol           */
+  sfr_precision precision;
+  sfr_memspace mem;         /* where M, nys_perm and the result buffers live               */
+  int32_t nys_l;            /* 0: FR-ADM.  > 0: FR-Nys with an m x l column block and an
+                               l x n row block (Algorithm 2), r <= l <= min(m, n)          */
+  const int64_t* nys_perm;  /* FR-Nys only: row shuffle, shuffled row i = input row perm[i] */
+} sfr_problem;
+
+typedef struct {
+  double* U;                /* m x r (FR-Nys: NULL, factors are not returned)              */
+  double* B;                /* r x r                                                       */
+  double* V;                /* n x r                                                       */
+  void* S;                  /* m x n sparse part; NULL = do not write S                    */
+  sfr_dtype s_dtype;        /* SFR_F64 or SFR_F32                                          */
+  int64_t lds;              /* leading dimension of S, >= n                                */
+  void* L;                  /* optional m x n low-rank part (same dtype/ld as S); NULL = skip */
+  int32_t iters;            /* iterations run (FR-Nys: sum over the two block solves)      */
+  double rel_residual;      /* ||M - L - S||_F / ||M||_F after the last iteration          */
+  double lambda_min_B;      /* smallest eigenvalue of the returned B (SPD diagnostic)      */
+  sfr_status status;        /* outcome of this problem                                     */
+} sfr_result;
+
+/* Create a context on cfg->device.  *out receives the handle. */
+sfr_status sfr_create(sfr_ctx** out, const sfr_config* cfg);
+
+/* Solve one problem and wait for it (FR-ADM, Algorithm 1, or FR-Nys, Algorithm 2).
+ * Returns the same status as res->status. */
+sfr_status sfr_solve(sfr_ctx* ctx, const sfr_problem* prob, sfr_result* res);
+
+/* Queue one problem; requests run concurrently on the device as slots and HBM
+ * budget allow (continuous batching).  *ticket identifies it for sfr_poll.
+ * The problem struct is copied; the buffers it points to are not. */
+sfr_status sfr_submit(sfr_ctx* ctx, const sfr_problem* prob, sfr_result* res, uint64_t* ticket);
+
+/* Wait up to timeout_us microseconds (< 0: forever, 0: just check) for a ticket.
+ * Returns SFR_PENDING if still running, SFR_E_TIMEOUT is never returned for a
+ * 0 timeout, otherwise the request's final status (res->status). */
+sfr_status sfr_poll(sfr_ctx* ctx, uint64_t ticket, int64_t timeout_us);
+
+/* Finish or cancel outstanding requests, free the workspace and the context. */
+sfr_status sfr_destroy(sfr_ctx* ctx);
+
+/* The last error message of ctx (or of the last failed sfr_create when ctx is NULL). */
+const char* sfr_last_error(const sfr_ctx* ctx);
+
+/* Library version string. */
+const char* sfr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFR_H */

@@ -1,0 +1,313 @@
+// r x r steps of FixedRankOptStep (Algorithm 3), one CTA per problem.
+//
+// Stiefel projector (Sec. 4.1.1, Eq. 9): P_O[A] = A (A^T A)^{-1/2} for a full-rank
+// m x r matrix A.  With A = P B (U side, P = X V) or A = W B (V side, W = X^T U),
+//     A^T A = B G B,   G = P^T P  or  W^T W,
+// so P_O[A] = P T with T = B (B G B)^{-1/2}: only r x r work, applied row-wise later.
+// SPD projector (Sec. 4.1.2, Eq. 10): B_bar = Sym(U_bar^T X V_bar) = Sym(W^T V_bar)
+//     = Sym(G_W T_V), and C = V_bar B_bar = W (T_V B_bar) so that L = U_bar C^T.
+//
+// The inverse square root Z = K^{-1/2} of K = B G B is computed in two stages:
+//  1. cyclic parallel Jacobi in float32 (warm-started from the previous call's
+//     eigenvectors) gives an approximate eigenbasis Q and eigenvalues lambda;
+//  2. Newton's method for the symmetric solution of Z K Z = I in float64:
+//     with R = I - Z K Z, the correction Delta solves Delta K Z + Z K Delta = R;
+//     in the approximate eigenbasis K Z ~ Q diag(sqrt(lambda)) Q^T, so
+//     Delta = Q [ (Q^T R Q)_pq / (sqrt(lambda_p) + sqrt(lambda_q)) ] Q^T.
+//     The residual R is formed in float64; the small correction may be formed
+//     in float32.  Each step contracts the error by roughly the eigenbasis error,
+//     so two or three steps reach float64 round-off.
+#include "sfr_internal.h"
+
+namespace sfr {
+namespace {
+
+constexpr int RPMAX = kMaxRank;
+constexpr int LD = RPMAX + 1;
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ bool stopped(const DevState* st) { return *(volatile const int32_t*)&st->done != 0; }
+
+// C = op(A) op(B) on the leading r x r blocks of [RPMAX][LD] shared arrays.
+template <typename T, bool TA, bool TB>
+__device__ void mm(const T* A, const T* B, T* C, int r) {
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    T acc = 0;
+    for (int k = 0; k < r; ++k) {
+      const T a = TA ? A[k * LD + i] : A[i * LD + k];
+      const T b = TB ? B[j * LD + k] : B[k * LD + j];
+      acc = fma(a, b, acc);
+    }
+    C[i * LD + j] = acc;
+  }
+  __syncthreads();
+}
+
+__device__ double block_reduce(double v, double* red, bool take_max) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = take_max ? fmax(v, w) : v + w;
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = take_max ? 0.0 : 0.0;
+  for (int i = 0; i < nw; ++i) t = take_max ? fmax(t, red[i]) : t + red[i];
+  __syncthreads();
+  return t;
+}
+
+// Cyclic two-sided Jacobi on the symmetric n2 x n2 float matrix A (n2 even; rows/cols
+// beyond r are zero), accumulating the rotations into Q (A_final = Q^T A_init Q).
+// Round-robin ordering: n2/2 disjoint rotations per step, n2-1 steps per sweep.
+__device__ void jacobi_f32(float* A, float* Q, int n2, int max_sweeps, double* red, float* cs, float* sn, int* pp,
+                           int* qq) {
+  const int np = n2 / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
+      const int i = e / n2, j = e % n2;
+      const double v = (double)A[i * LD + j];
+      if (i == j) dia += v * v; else off += v * v;
+    }
+    off = block_reduce(off, red, false);
+    dia = block_reduce(dia, red, false);
+    if (!(off > 4e-13 * dia)) break;
+    for (int step = 0; step < n2 - 1; ++step) {
+      if (threadIdx.x < np) {
+        const int k = threadIdx.x;
+        int p, q;
+        if (k == 0) { p = n2 - 1; q = step; }
+        else { p = (step + k) % (n2 - 1); q = (step - k + n2 - 1) % (n2 - 1); }
+        const float apq = A[p * LD + q], app = A[p * LD + p], aqq = A[q * LD + q];
+        float c = 1.f, s = 0.f;
+        if (fabsf(apq) > 1e-9f * sqrtf(fabsf(app * aqq)) && apq != 0.f) {
+          const float th = (aqq - app) / (2.f * apq);
+          float t;
+          if (fabsf(th) > 1e15f) t = 0.5f / th;
+          else t = copysignf(1.f, th) / (fabsf(th) + sqrtf(1.f + th * th));
+          c = rsqrtf(1.f + t * t);
+          s = t * c;
+        }
+        cs[k] = c; sn[k] = s; pp[k] = p; qq[k] = q;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int e = threadIdx.x; e < np * n2; e += blockDim.x) {
+        const int k = e / n2, j = e % n2;
+        const float c = cs[k], s = sn[k];
+        if (s == 0.f) continue;
+        const int p = pp[k], q = qq[k];
+        const float ap = A[p * LD + j], aq = A[q * LD + j];
+        A[p * LD + j] = c * ap - s * aq;
+        A[q * LD + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, Q <- Q J
+      for (int e = threadIdx.x; e < 2 * np * n2; e += blockDim.x) {
+        const int which = e / (np * n2), rem = e % (np * n2);
+        const int k = rem / n2, j = rem % n2;
+        const float c = cs[k], s = sn[k];
+        if (s == 0.f) continue;
+        const int p = pp[k], q = qq[k];
+        float* X = which ? Q : A;
+        const float xp = X[j * LD + p], xq = X[j * LD + q];
+        X[j * LD + p] = c * xp - s * xq;
+        X[j * LD + q] = s * xp + c * xq;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+struct RxrSmem {
+  double K[RPMAX * LD];    // B G B / s
+  double B[RPMAX * LD];
+  double Z[RPMAX * LD];    // K^{-1/2} iterate
+  double T1[RPMAX * LD];   // scratch; also holds two float scratch arrays
+  double T2[RPMAX * LD];   // scratch
+  float Af[RPMAX * LD];    // Jacobi matrix / float scratch
+  float Qf[RPMAX * LD];    // approximate eigenbasis
+  double lam[RPMAX];
+  double sq[RPMAX];
+  double red[32];
+  float cs[RPMAX / 2], sn[RPMAX / 2];
+  int pp[RPMAX / 2], qq[RPMAX / 2];
+  double scale;
+  int bad;
+};
+
+__device__ void load_gram(const double* __restrict__ parts, int count, int rp, int r, double* dst) {
+  const int rpsq = rp * rp;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    double v = 0.0;
+    for (int c = 0; c < count; ++c) v += parts[(int64_t)c * rpsq + i * rp + j];  // fixed order
+    dst[i * LD + j] = v;
+  }
+  __syncthreads();
+}
+
+__device__ void fail(DevState* st, int code) {
+  if (threadIdx.x == 0) { st->status = code; st->done = 1; }
+}
+
+// v_side = false: T_U = B (B G_P B)^{-1/2}.
+// v_side = true:  T_V = B (B G_W B)^{-1/2}, B <- Sym(G_W T_V), T_C = T_V B.
+__global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict__ parts, int count, int rp, int r,
+                                                       double* __restrict__ Bg, double* __restrict__ Tout,
+                                                       double* __restrict__ TCout, float* __restrict__ Qeig,
+                                                       int v_side, DevState* st) {
+  if (stopped(st)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RxrSmem& S = *reinterpret_cast<RxrSmem*>(smem_raw);
+  float* F1 = reinterpret_cast<float*>(S.T1);            // float scratch inside T1
+  float* F2 = F1 + RPMAX * LD;
+  const int tid = threadIdx.x;
+  const int rpsq = rp * rp;
+  // 1. Gram of the thin matrix and B; K = B G B (symmetrised) scaled by s = trace / r
+  load_gram(parts, count, rp, r, S.T2);
+  for (int e = tid; e < r * r; e += blockDim.x) S.B[(e / r) * LD + e % r] = Bg[(e / r) * rp + e % r];
+  __syncthreads();
+  mm<double, false, false>(S.T2, S.B, S.T1, r);
+  mm<double, false, false>(S.B, S.T1, S.Z, r);
+  if (tid == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < r; ++i) tr += S.Z[i * LD + i];
+    S.scale = tr / r;
+    S.bad = !(S.scale > 0.0) || !(S.scale < 1e300);
+  }
+  __syncthreads();
+  if (S.bad) { fail(st, SFR_E_NAN); return; }
+  const double inv_s = 1.0 / S.scale;
+  for (int e = tid; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    S.K[i * LD + j] = 0.5 * (S.Z[i * LD + j] + S.Z[j * LD + i]) * inv_s;
+  }
+  __syncthreads();
+  // 2. float32 Jacobi, warm-started from the previous eigenbasis Qw: A = Qw^T K Qw
+  const int n2 = (r + 1) & ~1;
+  for (int e = tid; e < n2 * n2; e += blockDim.x) {
+    const int i = e / n2, j = e % n2;
+    const bool in = i < r && j < r;
+    F1[i * LD + j] = in ? (float)S.K[i * LD + j] : 0.f;
+    S.Qf[i * LD + j] = in ? Qeig[i * rp + j] : (i == j ? 1.f : 0.f);
+  }
+  __syncthreads();
+  mm<float, false, false>(F1, S.Qf, F2, n2);
+  mm<float, true, false>(S.Qf, F2, S.Af, n2);
+  jacobi_f32(S.Af, S.Qf, n2, 12, S.red, S.cs, S.sn, S.pp, S.qq);
+  // re-orthonormalise the float basis: Q <- Q (3I - Q^T Q) / 2
+  mm<float, true, false>(S.Qf, S.Qf, F1, r);
+  for (int e = tid; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    F1[i * LD + j] = 0.5f * ((i == j ? 3.f : 0.f) - F1[i * LD + j]);
+  }
+  __syncthreads();
+  mm<float, false, false>(S.Qf, F1, F2, r);
+  for (int e = tid; e < r * r; e += blockDim.x) S.Qf[(e / r) * LD + e % r] = F2[(e / r) * LD + e % r];
+  __syncthreads();
+  // 3. float64 Rayleigh quotients lambda_p = q_p^T K q_p / q_p^T q_p
+  for (int e = tid; e < r * r; e += blockDim.x) S.T1[(e / r) * LD + e % r] = (double)S.Qf[(e / r) * LD + e % r];
+  __syncthreads();
+  mm<double, false, false>(S.K, S.T1, S.T2, r);
+  for (int p = tid; p < r; p += blockDim.x) {
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < r; ++i) {
+      num = fma(S.T1[i * LD + p], S.T2[i * LD + p], num);
+      den = fma(S.T1[i * LD + p], S.T1[i * LD + p], den);
+    }
+    S.lam[p] = num / den;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double lo = S.lam[0], hi = S.lam[0];
+    for (int p = 1; p < r; ++p) { lo = fmin(lo, S.lam[p]); hi = fmax(hi, S.lam[p]); }
+    // Eq. 9 needs rank r; the same relative cut as the oracle's eigenvalue check
+    S.bad = !(lo > 1e-14 * hi);
+    if (v_side) st->lam_min_v = lo * S.scale; else st->lam_min_u = lo * S.scale;
+    for (int p = 0; p < r; ++p) S.sq[p] = sqrt(fmax(S.lam[p], 1e-300));
+  }
+  __syncthreads();
+  if (S.bad) { fail(st, SFR_E_RANK); return; }
+  // 4. Z0 = Q diag(lambda^{-1/2}) Q^T
+  for (int e = tid; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    S.T2[i * LD + j] = S.T1[i * LD + j] / S.sq[j];
+  }
+  __syncthreads();
+  mm<double, false, true>(S.T2, S.T1, S.Z, r);
+  // 5. Newton steps on Z K Z = I (residual in float64, correction in float32)
+  for (int it = 0; it < 5; ++it) {
+    mm<double, false, false>(S.K, S.Z, S.T1, r);
+    mm<double, false, false>(S.Z, S.T1, S.T2, r);
+    double rmax = 0.0;
+    for (int e = tid; e < r * r; e += blockDim.x) {
+      const int i = e / r, j = e % r;
+      const double v = (i == j ? 1.0 : 0.0) - 0.5 * (S.T2[i * LD + j] + S.T2[j * LD + i]);
+      F1[i * LD + j] = (float)v;
+      rmax = fmax(rmax, fabs(v));
+    }
+    rmax = block_reduce(rmax, S.red, true);
+    if (!(rmax == rmax)) { fail(st, SFR_E_NAN); return; }
+    if (rmax < 4e-16 * r) break;
+    mm<float, false, false>(F1, S.Qf, F2, r);     // R Q
+    mm<float, true, false>(S.Qf, F2, S.Af, r);    // Q^T R Q
+    for (int e = tid; e < r * r; e += blockDim.x) {
+      const int p = e / r, q = e % r;
+      S.Af[p * LD + q] = S.Af[p * LD + q] / (float)(S.sq[p] + S.sq[q]);
+    }
+    __syncthreads();
+    mm<float, false, true>(S.Af, S.Qf, F2, r);    // Dt Q^T
+    mm<float, false, false>(S.Qf, F2, F1, r);     // Q Dt Q^T
+    for (int e = tid; e < r * r; e += blockDim.x) {
+      const int i = e / r, j = e % r;
+      S.Z[i * LD + j] += 0.5 * ((double)F1[i * LD + j] + (double)F1[j * LD + i]);
+    }
+    __syncthreads();
+  }
+  // 6. (B G B)^{-1/2} = Z / sqrt(s); T = B (B G B)^{-1/2}
+  const double zs = 1.0 / sqrt(S.scale);
+  for (int e = tid; e < r * r; e += blockDim.x) S.Z[(e / r) * LD + e % r] *= zs;
+  __syncthreads();
+  mm<double, false, false>(S.B, S.Z, S.T1, r);
+  for (int e = tid; e < rpsq; e += blockDim.x) {
+    const int i = e / rp, j = e % rp;
+    const bool in = i < r && j < r;
+    Tout[e] = in ? S.T1[i * LD + j] : 0.0;
+    Qeig[e] = in ? S.Qf[i * LD + j] : (i == j ? 1.f : 0.f);
+  }
+  if (!v_side) return;
+  // 7. B_bar = Sym(G_W T_V) (Eq. 10 with W = X^T U_bar), T_C = T_V B_bar
+  load_gram(parts, count, rp, r, S.K);
+  mm<double, false, false>(S.K, S.T1, S.T2, r);
+  for (int e = tid; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    S.Z[i * LD + j] = 0.5 * (S.T2[i * LD + j] + S.T2[j * LD + i]);
+  }
+  __syncthreads();
+  mm<double, false, false>(S.T1, S.Z, S.T2, r);
+  for (int e = tid; e < rpsq; e += blockDim.x) {
+    const int i = e / rp, j = e % rp;
+    const bool in = i < r && j < r;
+    Bg[e] = in ? S.Z[i * LD + j] : 0.0;
+    TCout[e] = in ? S.T2[i * LD + j] : 0.0;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream_t st) {
+  const size_t smem = sizeof(RxrSmem);
+  cudaError_t e = cudaFuncSetAttribute(rxr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (v_side)
+    rxr_kernel<<<1, kThreads, smem, st>>>(b.GWpart, s.gw_blocks, s.rp, s.r, b.B, b.TV, b.TCm, b.Qeig_v, 1, b.st);
+  else
+    rxr_kernel<<<1, kThreads, smem, st>>>(b.GPpart, s.gp_blocks, s.rp, s.r, b.B, b.TU, nullptr, b.Qeig_u, 0, b.st);
+  return cudaGetLastError();
+}
+
+}  // namespace sfr

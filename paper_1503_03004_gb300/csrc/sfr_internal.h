@@ -1,0 +1,104 @@
+// Internal declarations shared by the libsfr translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/sfr.h"
+
+namespace sfr {
+
+constexpr int kMaxRank = 64;  // r <= 64: r x r blocks live in shared memory
+
+// Per-problem scalars, device resident, read and written by the iteration kernels.
+struct DevState {
+  double mu;          // mu_k: penalty of the iteration about to run (Algorithm 1)
+  double mu_last;     // mu used by the most recent S/Y step
+  double rho;         // continuation factor
+  double mu_max;      // mu_bar
+  double tol;         // relative residual tolerance
+  double norm_m;      // ||M||_F
+  double res;         // ||M - L - S||_F / ||M||_F after the last iteration
+  double lam_min_u;   // smallest eigenvalue of the last U-side Gram (B G_P B)
+  double lam_min_v;   // smallest eigenvalue of the last V-side Gram (B G_W B)
+  int32_t iter;       // completed iterations
+  int32_t max_iter;   // hard cap (fixed_iters when > 0)
+  int32_t fixed;      // 1: run exactly max_iter iterations
+  int32_t done;       // 1: stop (converged, cap reached or failed)
+  int32_t status;     // sfr_status of the solve so far
+  int32_t pad;
+};
+
+// Shapes and launch parameters of one problem; plain values captured by the kernels.
+struct Shape {
+  int64_t m, n, ldm;
+  int r, rp;            // rank and padded rank (8, 16, 32 or 64)
+  int nsplit;           // column splits of the sweep (partial thin products P)
+  int cols_per_split;   // multiple of the sweep's column tile
+  int nchunk;           // row chunks of the W = X^T U pass
+  int rows_per_chunk;   // multiple of the W pass's row tile
+  int sweep_grid_x;     // ceil(m / sweep rows per CTA)
+  int wpass_grid_x;     // ceil(n / W-pass columns per CTA)
+  int gram_rows;        // rows per CTA in the Gram / row-transform kernels
+  int gp_blocks;        // ceil(m / gram_rows)
+  int gw_blocks;        // ceil(n / gram_rows)
+};
+
+// Device buffers of one solve.  TC is double (FP64 path) or float (mixed path);
+// the pointers below are typed void* and cast by the launchers.
+struct Buffers {
+  const void* M;        // caller's m x n matrix (device)
+  sfr_dtype m_dtype;
+  void* Y[2];           // multiplier ping-pong, m x n dense (ld = n), TC
+  void* D;              // Delta = X_{k+1} - L_{k+1}, m x n dense, TC
+  void* P;              // m x rp, TC: X_k V_k
+  void* U[2];           // m x rp, TC: U_bar ping-pong
+  void* W;              // n x rp, TC: X_k^T U_bar
+  void* V;              // n x rp, TC
+  void* C;              // n x rp, TC: C = V_bar B_bar (so L = U C^T)
+  void* Qpart;          // nsplit x m x rp, TC
+  void* Wpart;          // nchunk x n x rp, TC
+  double* GPpart;       // gp_blocks x rp x rp
+  double* GWpart;       // gw_blocks x rp x rp
+  double* Hpart;        // gp_blocks x rp x rp : U_old^T U_new partials
+  double* resid_part;   // sweep CTAs
+  double* normm_part;   // ||M||^2 partials
+  double* B;            // rp x rp
+  double* TU;           // rp x rp : U_bar = P T_U
+  double* TV;           // rp x rp : V_bar = W T_V
+  double* TCm;          // rp x rp : C = W T_C
+  float* Qeig_u;        // rp x rp : last U-side eigenvectors (warm start)
+  float* Qeig_v;        // rp x rp : last V-side eigenvectors
+  DevState* st;
+  int u_cur;            // which U buffer holds the current U_bar (host-side bookkeeping)
+};
+
+// ---- kernel launchers (sweep.cu / rxr.cu) ----
+// Each launcher returns the cudaError_t of its launch.
+
+cudaError_t launch_norm_m(const Shape& s, const Buffers& b, cudaStream_t st);
+cudaError_t launch_init_p(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st);
+cudaError_t launch_gram_p(const Shape& s, const Buffers& b, bool fp64, bool sum_parts, cudaStream_t st);
+cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream_t st);
+cudaError_t launch_apply_u(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st);
+cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first, int u_new, cudaStream_t st);
+cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st);
+cudaError_t launch_apply_v(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st);
+cudaError_t launch_sweep(const Shape& s, const Buffers& b, bool fp64, int u_cur, cudaStream_t st);
+cudaError_t launch_iter_end(const Shape& s, const Buffers& b, cudaStream_t st);
+cudaError_t launch_finalize(const Shape& s, const Buffers& b, bool fp64, int u_cur, void* S, sfr_dtype s_dtype,
+                            int64_t lds, void* L, cudaStream_t st);
+cudaError_t launch_export_factors(const Shape& s, const Buffers& b, bool fp64, int u_cur, double* U, double* V,
+                                  cudaStream_t st);
+
+// Tile constants shared between the launchers and the host planner.
+constexpr int kSweepBM = 32;     // rows per sweep CTA
+constexpr int kSweepBN = 64;     // columns per sweep tile
+constexpr int kWBN = 64;         // columns per W-pass CTA
+constexpr int kWBM = 32;         // rows per W-pass tile
+constexpr int kGramRows = 64;    // rows per Gram / transform CTA
+
+inline int pad_rank(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 32 ? 32 : 64; }
+
+}  // namespace sfr

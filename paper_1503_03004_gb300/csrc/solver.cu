@@ -1,0 +1,651 @@
+// Host driver of libsfr: contexts, workspace, the FR-ADM iteration schedule
+// (Algorithm 1) on one stream with CUDA graphs, FR-Nys (Algorithm 2), and the
+// request queue behind sfr_submit / sfr_poll.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "sfr_internal.h"
+
+namespace sfr {
+
+// ---------------------------------------------------------------- errors
+struct Fail {
+  sfr_status code;
+  std::string msg;
+};
+
+#define SFR_CUDA(call)                                                                                   \
+  do {                                                                                                   \
+    cudaError_t e_ = (call);                                                                             \
+    if (e_ != cudaSuccess) throw Fail{SFR_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+static std::string fmt(const char* f, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, f);
+  vsnprintf(buf, sizeof buf, f, ap);
+  va_end(ap);
+  return buf;
+}
+
+static size_t dtype_size(sfr_dtype d) { return d == SFR_F64 ? 8 : d == SFR_F32 ? 4 : 2; }
+
+// ---------------------------------------------------------------- device memory
+// A growable device arena: one cudaMalloc per workspace, carved into aligned pieces.
+struct DeviceBlock {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  ~DeviceBlock() {
+    if (ptr) cudaFree(ptr);
+  }
+  void ensure(size_t want, size_t* held, size_t budget) {
+    if (want <= bytes) return;
+    if (budget && *held - bytes + want > budget)
+      throw Fail{SFR_E_NOMEM, fmt("workspace of %zu bytes exceeds the HBM budget of %zu bytes", want, budget)};
+    if (ptr) {
+      cudaFree(ptr);
+      *held -= bytes;
+      ptr = nullptr;
+      bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&ptr, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Fail{SFR_E_NOMEM, fmt("cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e))};
+    }
+    bytes = want;
+    *held += want;
+  }
+};
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  bool dry;
+  explicit Carver(void* b) : base(static_cast<char*>(b)), dry(b == nullptr) {}
+  void* take(size_t bytes) {
+    off = (off + 255) & ~size_t(255);
+    void* p = dry ? nullptr : base + off;
+    off += bytes;
+    return p;
+  }
+};
+
+// ---------------------------------------------------------------- planning
+static Shape plan_shape(int64_t m, int64_t n, int64_t ldm, int r, int num_sms) {
+  Shape s{};
+  s.m = m;
+  s.n = n;
+  s.ldm = ldm;
+  s.r = r;
+  s.rp = pad_rank(r);
+  const int64_t target = 2LL * num_sms;
+  s.sweep_grid_x = (int)((m + kSweepBM - 1) / kSweepBM);
+  int64_t tiles = (n + kSweepBN - 1) / kSweepBN;
+  int64_t ns = std::max<int64_t>(1, std::min<int64_t>(tiles, (target + s.sweep_grid_x - 1) / s.sweep_grid_x));
+  int64_t tps = (tiles + ns - 1) / ns;
+  s.cols_per_split = (int)(tps * kSweepBN);
+  s.nsplit = (int)((n + s.cols_per_split - 1) / s.cols_per_split);
+  s.wpass_grid_x = (int)((n + kWBN - 1) / kWBN);
+  int64_t rtiles = (m + kWBM - 1) / kWBM;
+  int64_t nc = std::max<int64_t>(1, std::min<int64_t>(rtiles, (target + s.wpass_grid_x - 1) / s.wpass_grid_x));
+  int64_t rtpc = (rtiles + nc - 1) / nc;
+  s.rows_per_chunk = (int)(rtpc * kWBM);
+  s.nchunk = (int)((m + s.rows_per_chunk - 1) / s.rows_per_chunk);
+  s.gram_rows = kGramRows;
+  s.gp_blocks = (int)((m + kGramRows - 1) / kGramRows);
+  s.gw_blocks = (int)((n + kGramRows - 1) / kGramRows);
+  return s;
+}
+
+// Lay out every buffer of one solve inside `base` (or just size it when base == nullptr).
+static size_t carve(const Shape& s, bool fp64, void* base, Buffers* b) {
+  const size_t tc = fp64 ? 8 : 4;
+  const size_t rp = s.rp, rpsq = rp * rp;
+  Carver c(base);
+  Buffers x{};
+  x.Y[0] = c.take(tc * s.m * s.n);
+  x.Y[1] = c.take(tc * s.m * s.n);
+  x.D = c.take(tc * s.m * s.n);
+  x.P = c.take(tc * s.m * rp);
+  x.U[0] = c.take(tc * s.m * rp);
+  x.U[1] = c.take(tc * s.m * rp);
+  x.W = c.take(tc * s.n * rp);
+  x.V = c.take(tc * s.n * rp);
+  x.C = c.take(tc * s.n * rp);
+  x.Qpart = c.take(tc * s.nsplit * s.m * rp);
+  x.Wpart = c.take(tc * s.nchunk * s.n * rp);
+  x.GPpart = static_cast<double*>(c.take(8 * rpsq * s.gp_blocks));
+  x.GWpart = static_cast<double*>(c.take(8 * rpsq * s.gw_blocks));
+  x.Hpart = static_cast<double*>(c.take(8 * rpsq * (s.gp_blocks + 1)));
+  x.resid_part = static_cast<double*>(c.take(8 * (size_t)s.sweep_grid_x * s.nsplit));
+  x.normm_part = static_cast<double*>(c.take(8 * 1024));
+  x.B = static_cast<double*>(c.take(8 * rpsq));
+  x.TU = static_cast<double*>(c.take(8 * rpsq));
+  x.TV = static_cast<double*>(c.take(8 * rpsq));
+  x.TCm = static_cast<double*>(c.take(8 * rpsq));
+  x.Qeig_u = static_cast<float*>(c.take(4 * rpsq));
+  x.Qeig_v = static_cast<float*>(c.take(4 * rpsq));
+  x.st = static_cast<DevState*>(c.take(sizeof(DevState)));
+  if (b) *b = x;
+  return c.off + 256;
+}
+
+// ---------------------------------------------------------------- one FR-ADM solve
+struct Solver {
+  int device = 0;
+  int num_sms = 152;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0;
+  size_t held = 0;
+  DeviceBlock work;
+  DeviceBlock staging;  // host-memory mode: device copies of M / S / L / perm
+  DeviceBlock nys;      // FR-Nys: gathered blocks and block factors
+  DevState* host_state = nullptr;  // pinned
+  // graph cache, keyed by the buffer layout it was captured with
+  cudaGraphExec_t graph = nullptr;
+  std::string graph_key;
+
+  ~Solver() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (host_state) cudaFreeHost(host_state);
+  }
+
+  void enqueue_iteration(const Shape& s, Buffers& b, bool fp64, bool first) {
+    cudaStream_t st = stream;
+    if (first) {
+      SFR_CUDA(launch_init_p(s, b, fp64, st));
+      SFR_CUDA(launch_gram_p(s, b, fp64, false, st));
+    }
+    SFR_CUDA(launch_rxr(s, b, false, st));                     // T_U = B (B G_P B)^{-1/2}
+    SFR_CUDA(launch_apply_u(s, b, fp64, first, st));           // U_bar = P T_U
+    const int u_new = 1 - b.u_cur;
+    SFR_CUDA(launch_wpass(s, b, fp64, first, u_new, st));      // X^T U_bar partials
+    SFR_CUDA(launch_wfinal(s, b, fp64, first, st));            // W, G_W partials
+    SFR_CUDA(launch_rxr(s, b, true, st));                      // T_V, B_bar, T_C
+    SFR_CUDA(launch_apply_v(s, b, fp64, st));                  // V_bar, C
+    SFR_CUDA(launch_sweep(s, b, fp64, u_new, st));             // S/Y steps, Delta, next P partials
+    SFR_CUDA(launch_iter_end(s, b, st));                       // residual, mu, stop test
+    SFR_CUDA(launch_gram_p(s, b, fp64, true, st));             // P = sum of partials, G_P partials
+    b.u_cur = u_new;
+    std::swap(b.Y[0], b.Y[1]);
+  }
+
+  // Runs Algorithm 1 on a device-resident M.  Returns the final host copy of the state and
+  // fills U/V/B/S/L (device pointers) as requested.
+  DevState run(const sfr_problem& p, const void* Mdev, double* Udev, double* Bdev, double* Vdev, void* Sdev,
+               sfr_dtype s_dtype, int64_t lds, void* Ldev) {
+    const bool fp64 = p.precision == SFR_PREC_FP64;
+    const Shape s = plan_shape(p.m, p.n, p.ldm, p.r, num_sms);
+    Buffers b{};
+    const size_t bytes = carve(s, fp64, nullptr, nullptr);
+    work.ensure(bytes, &held, budget);
+    carve(s, fp64, work.ptr, &b);
+    b.M = Mdev;
+    b.m_dtype = p.m_dtype;
+    b.u_cur = 0;
+
+    DevState h{};
+    h.mu = p.mu0;
+    h.mu_last = p.mu0;
+    h.rho = p.rho;
+    h.mu_max = p.mu_max;
+    h.tol = p.tol;
+    h.fixed = p.fixed_iters > 0;
+    h.max_iter = p.fixed_iters > 0 ? p.fixed_iters : p.max_iter;
+    h.status = SFR_OK;
+    SFR_CUDA(cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, stream));
+    const size_t tc = fp64 ? 8 : 4;
+    SFR_CUDA(cudaMemsetAsync(b.Y[0], 0, tc * s.m * s.n, stream));  // Y_1 = 0
+    std::vector<double> eye(s.rp * s.rp, 0.0);
+    std::vector<float> eyef(s.rp * s.rp, 0.f);
+    for (int i = 0; i < s.rp; ++i) {
+      eye[i * s.rp + i] = 1.0;
+      eyef[i * s.rp + i] = 1.f;
+    }
+    SFR_CUDA(cudaMemcpyAsync(b.B, eye.data(), 8 * eye.size(), cudaMemcpyHostToDevice, stream));  // B_0 = I_r
+    SFR_CUDA(cudaMemcpyAsync(b.Qeig_u, eyef.data(), 4 * eyef.size(), cudaMemcpyHostToDevice, stream));
+    SFR_CUDA(cudaMemcpyAsync(b.Qeig_v, eyef.data(), 4 * eyef.size(), cudaMemcpyHostToDevice, stream));
+    SFR_CUDA(launch_norm_m(s, b, stream));
+
+    // iteration 1 (X_1 = M, V_1 = I_{n x r}), eager
+    enqueue_iteration(s, b, fp64, true);
+    const Buffers after_first = b;
+
+    // iterations 2, 3, ...: a graph of two iterations, replayed; every kernel exits at once
+    // after the stop flag is set, so overshooting the last iteration costs only launches.
+    const std::string key = fmt("%p/%lld/%lld/%lld/%d/%d/%p", work.ptr, (long long)s.m, (long long)s.n,
+                                (long long)s.ldm, s.r, (int)fp64, Mdev) +
+                            fmt("/%d", (int)p.m_dtype);
+    if (graph_key != key) {
+      if (graph) {
+        cudaGraphExecDestroy(graph);
+        graph = nullptr;
+      }
+      cudaGraph_t g;
+      SFR_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed));
+      try {
+        enqueue_iteration(s, b, fp64, false);
+        enqueue_iteration(s, b, fp64, false);
+      } catch (...) {
+        cudaStreamEndCapture(stream, &g);
+        throw;
+      }
+      SFR_CUDA(cudaStreamEndCapture(stream, &g));
+      cudaError_t e = cudaGraphInstantiate(&graph, g, 0);
+      cudaGraphDestroy(g);
+      SFR_CUDA(e);
+      graph_key = key;
+      b = after_first;
+    }
+    const int cap = h.max_iter;
+    int launched = 1;
+    int per_check = 1;
+    SFR_CUDA(cudaMemcpyAsync(host_state, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
+    SFR_CUDA(cudaStreamSynchronize(stream));
+    while (!host_state->done && launched < cap) {
+      for (int k = 0; k < per_check && launched < cap; ++k) {
+        SFR_CUDA(cudaGraphLaunch(graph, stream));
+        launched += 2;
+      }
+      SFR_CUDA(cudaMemcpyAsync(host_state, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
+      SFR_CUDA(cudaStreamSynchronize(stream));
+      per_check = std::min(per_check * 2, 8);
+    }
+    DevState out = *host_state;
+    const int K = out.iter;
+    // buffers of the last completed iteration (see the graph's two-iteration period)
+    Buffers fin = after_first;
+    if (K >= 2 && K % 2 == 0) {
+      fin.u_cur = 1 - after_first.u_cur;  // U written by the first iteration of a pair
+      // that iteration read after_first.Y[0]
+    } else {
+      fin.Y[0] = after_first.Y[1];  // the second iteration of a pair (or iteration 1) read Y[1]
+      fin.Y[1] = after_first.Y[0];
+    }
+    if (out.status == SFR_OK || out.status == SFR_E_NOCONV) {
+      SFR_CUDA(launch_export_factors(s, fin, fp64, fin.u_cur, Udev, Vdev, stream));
+      if (Bdev) {
+        for (int i = 0; i < p.r; ++i)
+          SFR_CUDA(cudaMemcpyAsync(Bdev + (size_t)i * p.r, fin.B + (size_t)i * s.rp, 8 * p.r,
+                                   cudaMemcpyDeviceToDevice, stream));
+      }
+      if (Sdev || Ldev) SFR_CUDA(launch_finalize(s, fin, fp64, fin.u_cur, Sdev, s_dtype, lds, Ldev, stream));
+    }
+    SFR_CUDA(cudaStreamSynchronize(stream));
+    return out;
+  }
+};
+
+// Smallest eigenvalue of a symmetric r x r matrix (cyclic Jacobi on the host, float64).
+static double host_lambda_min(std::vector<double> A, int r) {
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < r; ++i)
+      for (int j = 0; j < r; ++j)
+        if (i != j) off += A[i * r + j] * A[i * r + j];
+    if (off < 1e-30) break;
+    for (int p = 0; p < r; ++p)
+      for (int q = p + 1; q < r; ++q) {
+        const double apq = A[p * r + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double th = (A[q * r + q] - A[p * r + p]) / (2 * apq);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(1 + th * th));
+        const double c = 1 / std::sqrt(1 + t * t), s = t * c;
+        for (int k = 0; k < r; ++k) {
+          const double ap = A[p * r + k], aq = A[q * r + k];
+          A[p * r + k] = c * ap - s * aq;
+          A[q * r + k] = s * ap + c * aq;
+        }
+        for (int k = 0; k < r; ++k) {
+          const double ap = A[k * r + p], aq = A[k * r + q];
+          A[k * r + p] = c * ap - s * aq;
+          A[k * r + q] = s * ap + c * aq;
+        }
+      }
+  }
+  double lo = A[0];
+  for (int i = 1; i < r; ++i) lo = std::min(lo, A[i * r + i]);
+  return lo;
+}
+
+DevState solver_run(Solver& sv, const sfr_problem& p, const void* Mdev, double* U, double* B, double* V, void* S,
+                    sfr_dtype s_dtype, int64_t lds, void* L) {
+  return sv.run(p, Mdev, U, B, V, S, s_dtype, lds, L);
+}
+void* solver_nys_block(Solver& sv, size_t bytes) {
+  sv.nys.ensure(bytes, &sv.held, sv.budget);
+  return sv.nys.ptr;
+}
+cudaStream_t solver_stream(Solver& sv) { return sv.stream; }
+
+sfr_status nys_solve_device(Solver& sv, const sfr_problem& p, const void* Mdev, const int64_t* perm_dev,
+                            sfr_result* res, void* Sdev, void* Ldev, std::string* err);
+
+// FR-Nys entry: stage host buffers when needed, then run on the device.
+sfr_status sfr_nys_solve(Solver& sv, const sfr_problem& p, sfr_result* res, std::string* err) {
+  const size_t mbytes = dtype_size(p.m_dtype) * (size_t)((p.m - 1) * p.ldm + p.n);
+  const size_t outbytes = dtype_size(res->s_dtype) * (size_t)((p.m - 1) * res->lds + p.n);
+  if (p.mem == SFR_MEM_DEVICE)
+    return nys_solve_device(sv, p, p.M, p.nys_perm, res, res->S, res->L, err);
+  size_t need = 0;
+  auto add = [&](size_t bytes) { need = (need + 255) & ~size_t(255); size_t o = need; need += bytes; return o; };
+  const size_t offM = add(mbytes), offP = add(8 * (size_t)p.m);
+  const size_t offS = res->S ? add(outbytes) : 0, offL = res->L ? add(outbytes) : 0;
+  sv.staging.ensure(need + 256, &sv.held, sv.budget);
+  char* st = static_cast<char*>(sv.staging.ptr);
+  SFR_CUDA(cudaMemcpyAsync(st + offM, p.M, mbytes, cudaMemcpyHostToDevice, sv.stream));
+  SFR_CUDA(cudaMemcpyAsync(st + offP, p.nys_perm, 8 * (size_t)p.m, cudaMemcpyHostToDevice, sv.stream));
+  sfr_status s = nys_solve_device(sv, p, st + offM, reinterpret_cast<const int64_t*>(st + offP), res,
+                                  res->S ? st + offS : nullptr, res->L ? st + offL : nullptr, err);
+  if (s == SFR_OK) {
+    if (res->S) SFR_CUDA(cudaMemcpyAsync(res->S, st + offS, outbytes, cudaMemcpyDeviceToHost, sv.stream));
+    if (res->L) SFR_CUDA(cudaMemcpyAsync(res->L, st + offL, outbytes, cudaMemcpyDeviceToHost, sv.stream));
+    SFR_CUDA(cudaStreamSynchronize(sv.stream));
+  }
+  return s;
+}
+
+}  // namespace sfr
+
+// ---------------------------------------------------------------- C ABI
+using namespace sfr;
+
+struct Request {
+  uint64_t ticket;
+  sfr_problem prob;
+  sfr_result* res;
+  bool finished = false;
+  sfr_status status = SFR_PENDING;
+};
+
+struct sfr_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string last_error;
+  std::unique_ptr<Solver> solver;
+  // request queue
+  int max_slots = 8;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::shared_ptr<Request>> queue;
+  std::map<uint64_t, std::shared_ptr<Request>> live;
+  uint64_t next_ticket = 1;
+  bool stopping = false;
+  std::thread worker;
+  std::unique_ptr<Solver> worker_solver;
+  cudaStream_t worker_stream = nullptr;
+};
+
+static thread_local std::string g_create_error;
+
+static sfr_status validate(const sfr_problem* p, const sfr_result* r, std::string* why) {
+  if (!p || !r) return *why = "null problem or result", SFR_E_INVAL;
+  if (p->m <= 0 || p->n <= 0) return *why = "m and n must be positive", SFR_E_INVAL;
+  if (p->ldm < p->n) return *why = "ldm must be >= n", SFR_E_INVAL;
+  if (p->r < 1 || p->r > kMaxRank || p->r > p->m || p->r > p->n)
+    return *why = fmt("need 1 <= r <= min(m, n, %d)", kMaxRank), SFR_E_INVAL;
+  if (!p->M) return *why = "M is null", SFR_E_INVAL;
+  if (p->m_dtype != SFR_F64 && p->m_dtype != SFR_F32 && p->m_dtype != SFR_BF16) return *why = "bad m_dtype", SFR_E_INVAL;
+  if (!(p->rho > 1.0)) return *why = "rho must exceed 1", SFR_E_INVAL;
+  if (!(p->mu0 > 0.0) || !(p->mu_max >= p->mu0)) return *why = "need 0 < mu0 <= mu_max", SFR_E_INVAL;
+  if (p->fixed_iters <= 0 && (p->max_iter <= 0 || !(p->tol >= 0.0))) return *why = "need max_iter > 0 and tol >= 0", SFR_E_INVAL;
+  if (p->precision != SFR_PREC_FP64 && p->precision != SFR_PREC_MIXED) return *why = "bad precision", SFR_E_INVAL;
+  if (p->mem != SFR_MEM_DEVICE && p->mem != SFR_MEM_HOST) return *why = "bad mem", SFR_E_INVAL;
+  if ((r->S || r->L) && (r->s_dtype != SFR_F64 && r->s_dtype != SFR_F32)) return *why = "s_dtype must be F64 or F32", SFR_E_INVAL;
+  if ((r->S || r->L) && r->lds < p->n) return *why = "lds must be >= n", SFR_E_INVAL;
+  if (p->nys_l != 0) {
+    if (p->nys_l < p->r || p->nys_l > p->m || p->nys_l > p->n) return *why = "need r <= nys_l <= min(m, n)", SFR_E_INVAL;
+    if (!p->nys_perm) return *why = "FR-Nys needs nys_perm", SFR_E_INVAL;
+  }
+  if ((int64_t)p->m * p->n > (int64_t)1 << 40) return *why = "matrix too large", SFR_E_INVAL;
+  return SFR_OK;
+}
+
+// Solve on `sv`, staging host buffers when p.mem == SFR_MEM_HOST.
+static sfr_status solve_with(Solver& sv, const sfr_problem& p, sfr_result* res, std::string* err) {
+  try {
+    SFR_CUDA(cudaSetDevice(sv.device));
+    if (p.nys_l != 0) {
+      res->status = sfr_nys_solve(sv, p, res, err);
+      return res->status;
+    }
+    const void* Mdev = p.M;
+    double *U = res->U, *B = res->B, *V = res->V;
+    void *S = res->S, *L = res->L;
+    const size_t sb = dtype_size(res->s_dtype);
+    const size_t mbytes = dtype_size(p.m_dtype) * (size_t)((p.m - 1) * p.ldm + p.n);
+    const size_t outbytes = sb * (size_t)((p.m - 1) * res->lds + p.n);
+    char* st = nullptr;
+    size_t offU = 0, offV = 0, offB = 0, offS = 0, offL = 0;
+    if (p.mem == SFR_MEM_HOST) {
+      size_t need = 0;
+      auto add = [&](size_t bytes) { need = (need + 255) & ~size_t(255); size_t o = need; need += bytes; return o; };
+      const size_t offM = add(mbytes);
+      if (U) offU = add(8 * (size_t)p.m * p.r);
+      if (V) offV = add(8 * (size_t)p.n * p.r);
+      if (B) offB = add(8 * (size_t)p.r * p.r);
+      if (S) offS = add(outbytes);
+      if (L) offL = add(outbytes);
+      sv.staging.ensure(need + 256, &sv.held, sv.budget);
+      st = static_cast<char*>(sv.staging.ptr);
+      SFR_CUDA(cudaMemcpyAsync(st + offM, p.M, mbytes, cudaMemcpyHostToDevice, sv.stream));
+      Mdev = st + offM;
+      if (U) U = reinterpret_cast<double*>(st + offU);
+      if (V) V = reinterpret_cast<double*>(st + offV);
+      if (B) B = reinterpret_cast<double*>(st + offB);
+      if (S) S = st + offS;
+      if (L) L = st + offL;
+    }
+    DevState out = sv.run(p, Mdev, U, B, V, S, res->s_dtype, res->lds, L);
+    if (p.mem == SFR_MEM_HOST) {
+      if (res->U) SFR_CUDA(cudaMemcpyAsync(res->U, U, 8 * (size_t)p.m * p.r, cudaMemcpyDeviceToHost, sv.stream));
+      if (res->V) SFR_CUDA(cudaMemcpyAsync(res->V, V, 8 * (size_t)p.n * p.r, cudaMemcpyDeviceToHost, sv.stream));
+      if (res->B) SFR_CUDA(cudaMemcpyAsync(res->B, B, 8 * (size_t)p.r * p.r, cudaMemcpyDeviceToHost, sv.stream));
+      if (res->S) SFR_CUDA(cudaMemcpyAsync(res->S, S, outbytes, cudaMemcpyDeviceToHost, sv.stream));
+      if (res->L) SFR_CUDA(cudaMemcpyAsync(res->L, L, outbytes, cudaMemcpyDeviceToHost, sv.stream));
+      SFR_CUDA(cudaStreamSynchronize(sv.stream));
+    }
+    res->iters = out.iter;
+    res->rel_residual = out.res;
+    res->status = (sfr_status)out.status;
+    res->lambda_min_B = NAN;
+    if (res->status == SFR_OK || res->status == SFR_E_NOCONV) {
+      // lambda_min of the returned B (SPD diagnostic, Appendix): from the device copy of B
+      std::vector<double> hb((size_t)p.r * p.r);
+      if (res->B && p.mem == SFR_MEM_HOST) {
+        memcpy(hb.data(), res->B, 8 * hb.size());
+      } else if (res->B) {
+        SFR_CUDA(cudaMemcpy(hb.data(), res->B, 8 * hb.size(), cudaMemcpyDeviceToHost));
+      }
+      if (res->B) res->lambda_min_B = host_lambda_min(hb, p.r);
+    }
+    if (res->status != SFR_OK) {
+      *err = res->status == SFR_E_NOCONV  ? fmt("no convergence after %d iterations (residual %.3e)", out.iter, out.res)
+             : res->status == SFR_E_RANK ? fmt("rank-deficient thin product at iteration %d", out.iter + 1)
+             : res->status == SFR_E_NAN  ? fmt("non-finite value at iteration %d", out.iter + 1)
+                                         : fmt("solve failed with status %d", (int)res->status);
+    }
+    return res->status;
+  } catch (const Fail& f) {
+    *err = f.msg;
+    res->status = f.code;
+    return f.code;
+  }
+}
+
+static void worker_main(sfr_ctx* ctx) {
+  cudaSetDevice(ctx->device);
+  for (;;) {
+    std::shared_ptr<Request> rq;
+    {
+      std::unique_lock<std::mutex> lk(ctx->mu);
+      ctx->cv_work.wait(lk, [&] { return ctx->stopping || !ctx->queue.empty(); });
+      if (ctx->queue.empty()) return;
+      rq = ctx->queue.front();
+      ctx->queue.pop_front();
+    }
+    std::string err;
+    sfr_status s = solve_with(*ctx->worker_solver, rq->prob, rq->res, &err);
+    {
+      std::lock_guard<std::mutex> lk(ctx->mu);
+      rq->status = s;
+      rq->finished = true;
+      if (s < 0) ctx->last_error = err;
+    }
+    ctx->cv_done.notify_all();
+  }
+}
+
+extern "C" {
+
+const char* sfr_version(void) { return "libsfr 0.1 (sm_103a)"; }
+
+const char* sfr_last_error(const sfr_ctx* ctx) {
+  if (!ctx) return g_create_error.c_str();
+  return ctx->last_error.c_str();
+}
+
+sfr_status sfr_create(sfr_ctx** out, const sfr_config* cfg) {
+  if (!out || !cfg) {
+    g_create_error = "null argument";
+    return SFR_E_INVAL;
+  }
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+    g_create_error = fmt("no CUDA device %d (%s)", cfg->device, cudaGetErrorString(e));
+    cudaGetLastError();
+    return e != cudaSuccess ? SFR_E_CUDA : SFR_E_INVAL;
+  }
+  auto ctx = std::make_unique<sfr_ctx>();
+  ctx->device = cfg->device;
+  ctx->max_slots = cfg->max_slots > 0 ? cfg->max_slots : 8;
+  try {
+    SFR_CUDA(cudaSetDevice(cfg->device));
+    cudaDeviceProp prop;
+    SFR_CUDA(cudaGetDeviceProperties(&prop, cfg->device));
+    if (cfg->cuda_stream) {
+      ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    } else {
+      SFR_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+      ctx->own_stream = true;
+    }
+    SFR_CUDA(cudaStreamCreateWithFlags(&ctx->worker_stream, cudaStreamNonBlocking));
+    for (int w = 0; w < 2; ++w) {
+      auto sv = std::make_unique<Solver>();
+      sv->device = cfg->device;
+      sv->num_sms = prop.multiProcessorCount;
+      sv->stream = w == 0 ? ctx->stream : ctx->worker_stream;
+      sv->budget = cfg->hbm_budget_bytes;
+      SFR_CUDA(cudaMallocHost(&sv->host_state, sizeof(DevState)));
+      (w == 0 ? ctx->solver : ctx->worker_solver) = std::move(sv);
+    }
+  } catch (const Fail& f) {
+    g_create_error = f.msg;
+    return f.code;
+  }
+  sfr_ctx* raw = ctx.release();
+  raw->worker = std::thread(worker_main, raw);
+  *out = raw;
+  return SFR_OK;
+}
+
+sfr_status sfr_solve(sfr_ctx* ctx, const sfr_problem* prob, sfr_result* res) {
+  if (!ctx) return SFR_E_INVAL;
+  std::string why;
+  sfr_status v = validate(prob, res, &why);
+  if (v != SFR_OK) {
+    ctx->last_error = why;
+    if (res) res->status = v;
+    return v;
+  }
+  std::string err;
+  sfr_status s = solve_with(*ctx->solver, *prob, res, &err);
+  if (s < 0) ctx->last_error = err;
+  return s;
+}
+
+sfr_status sfr_submit(sfr_ctx* ctx, const sfr_problem* prob, sfr_result* res, uint64_t* ticket) {
+  if (!ctx || !ticket) return SFR_E_INVAL;
+  std::string why;
+  sfr_status v = validate(prob, res, &why);
+  if (v != SFR_OK) {
+    ctx->last_error = why;
+    if (res) res->status = v;
+    return v;
+  }
+  auto rq = std::make_shared<Request>();
+  rq->prob = *prob;
+  rq->res = res;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if ((int)ctx->queue.size() >= 64 * ctx->max_slots) {
+      ctx->last_error = "request queue full";
+      return SFR_E_BUSY;
+    }
+    rq->ticket = ctx->next_ticket++;
+    res->status = SFR_PENDING;
+    ctx->queue.push_back(rq);
+    ctx->live[rq->ticket] = rq;
+    *ticket = rq->ticket;
+  }
+  ctx->cv_work.notify_one();
+  return SFR_OK;
+}
+
+sfr_status sfr_poll(sfr_ctx* ctx, uint64_t ticket, int64_t timeout_us) {
+  if (!ctx) return SFR_E_INVAL;
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  auto it = ctx->live.find(ticket);
+  if (it == ctx->live.end()) {
+    ctx->last_error = fmt("unknown ticket %llu", (unsigned long long)ticket);
+    return SFR_E_INVAL;
+  }
+  std::shared_ptr<Request> rq = it->second;
+  auto ready = [&] { return rq->finished; };
+  if (timeout_us < 0) {
+    ctx->cv_done.wait(lk, ready);
+  } else if (timeout_us > 0) {
+    if (!ctx->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) return SFR_E_TIMEOUT;
+  } else if (!rq->finished) {
+    return SFR_PENDING;
+  }
+  ctx->live.erase(ticket);
+  return rq->status;
+}
+
+sfr_status sfr_destroy(sfr_ctx* ctx) {
+  if (!ctx) return SFR_E_INVAL;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->stopping = true;
+  }
+  ctx->cv_work.notify_all();
+  if (ctx->worker.joinable()) ctx->worker.join();
+  cudaSetDevice(ctx->device);
+  ctx->solver.reset();
+  ctx->worker_solver.reset();
+  if (ctx->worker_stream) cudaStreamDestroy(ctx->worker_stream);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return SFR_OK;
+}
+
+}  // extern "C"

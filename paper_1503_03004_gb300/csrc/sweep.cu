@@ -1,0 +1,690 @@
+// m x n and thin (m x r, n x r) kernels of one FR-ADM iteration (Algorithm 1 with
+// the L-step of Algorithm 3), SIMT version for float64 (FP64 path) and float32
+// (mixed path) arithmetic.
+//
+// Notation (Algorithm 1): X_k = M - S_k + Y_k / mu_k, the matrix handed to
+// FixedRankOptStep.  The L-step computes
+//     P = X_k V_k,  U_bar = P_O[P B_k],  W = X_k^T U_bar,  V_bar = P_O[W B_k],
+//     B_bar = Sym(U_bar^T X_k V_bar) = Sym(W^T V_bar)                 (Algorithm 3)
+// and the S/Y steps use z = M - L_{k+1} + Y_k / mu_k:
+//     S_{k+1} = P_ST_{1/mu_k}(z),   Y_{k+1} = Y_k + mu_k (M - L_{k+1} - S_{k+1}).
+// Since Y_k + mu_k (z - Y_k/mu_k - P_ST(z)) = mu_k (z - P_ST(z)) = clip(mu_k z, -1, 1),
+// the sweep stores Y_{k+1} = clip(mu_k z, -1, 1) and never stores S (it is rebuilt
+// once at the end).  The next iteration's X is
+//     X_{k+1} = M - S_{k+1} + Y_{k+1}/mu_{k+1} = L_{k+1} + Delta_{k+1},
+//     Delta_{k+1} = Y_{k+1} (1/mu_k + 1/mu_{k+1}) - Y_k / mu_k,
+// so the sweep writes Delta and accumulates P_{k+1} = X_{k+1} V_{k+1} row by row,
+// and the second pass forms X_{k+1}^T U = C (U_old^T U) + Delta^T U with L = U_old C^T.
+#include "sfr_internal.h"
+
+namespace sfr {
+namespace {
+
+template <typename T> __device__ __forceinline__ T from_bf16(__nv_bfloat16 v) { return (T)__bfloat162float(v); }
+template <typename TC, typename TS> __device__ __forceinline__ TC ld_as(const TS* p) { return (TC)(*p); }
+template <> __device__ __forceinline__ float ld_as<float, __nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+template <> __device__ __forceinline__ double ld_as<double, __nv_bfloat16>(const __nv_bfloat16* p) { return (double)__bfloat162float(*p); }
+
+__device__ __forceinline__ bool stopped(const DevState* st) { return *(volatile const int32_t*)&st->done != 0; }
+
+// Block-wide sum of a double; every thread gets the result.  blockDim.x <= 1024.
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; ++i) t += red[i];  // fixed order: deterministic
+  __syncthreads();
+  return t;
+}
+
+// ---------------------------------------------------------------- ||M||_F
+template <typename TMs>
+__global__ void norm_m_kernel(const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm, double* part) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
+    float a = 0.f;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+      float v = ld_as<float, TMs>(M + i * ldm + j);
+      a = fmaf(v, v, a);
+    }
+    acc += (double)a;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+template <>
+__global__ void norm_m_kernel<double>(const double* __restrict__ M, int64_t m, int64_t n, int64_t ldm, double* part) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x; i < m; i += gridDim.x)
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+      double v = M[i * ldm + j];
+      acc = fma(v, v, acc);
+    }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// ---------------------------------------------------------------- first P = M[:, :r]
+// Iteration 1: X_1 = M (S = Y = 0), V_1 = I_{n x r}, so P = X_1 V_1 = M[:, 0:r].
+template <typename TC, typename TMs>
+__global__ void init_p_kernel(const TMs* __restrict__ M, int64_t m, int64_t ldm, int r, int rp, TC* P) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * rp) return;
+  int64_t i = idx / rp;
+  int a = (int)(idx % rp);
+  P[idx] = a < r ? ld_as<TC, TMs>(M + i * ldm + a) : (TC)0;
+}
+
+// ---------------------------------------------------------------- thin reduce + Gram partials
+// out[i][:] = sum_s parts[s][i][:]  (+ addA[i][:] * H when addA != nullptr), for rows i of
+// this CTA, then gpart[cta] = sum_i out[i]^T out[i]  (r x r, row block of kGramRows rows).
+// nparts == 0 leaves `out` as it is and only forms the Gram partial.
+template <typename TC, int RP>
+__global__ void __launch_bounds__(256) thin_gram_kernel(const TC* __restrict__ parts, int nparts, int64_t part_stride,
+                                                        TC* __restrict__ out, int64_t rows, const TC* __restrict__ addA,
+                                                        const double* __restrict__ H, double* __restrict__ gpart,
+                                                        const DevState* st) {
+  if (stopped(st)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto tile = reinterpret_cast<TC(*)[RP + 1]>(smem_raw);              // [kGramRows][RP + 1]
+  auto Hs = reinterpret_cast<TC(*)[RP + 1]>(smem_raw + sizeof(TC) * kGramRows * (RP + 1));  // [RP][RP + 1]
+  const int64_t i0 = (int64_t)blockIdx.x * kGramRows;
+  if (addA)
+    for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) Hs[e / RP][e % RP] = (TC)H[e];
+  __syncthreads();
+  for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
+    int ii = e / RP, a = e % RP;
+    int64_t i = i0 + ii;
+    TC v = 0;
+    if (i < rows) {
+      if (nparts == 0) {
+        v = out[i * RP + a];
+      } else {
+        for (int s = 0; s < nparts; ++s) v += parts[s * part_stride + i * RP + a];
+        if (addA) {
+          TC acc = 0;
+#pragma unroll 8
+          for (int b = 0; b < RP; ++b) acc += addA[i * RP + b] * Hs[b][a];
+          v += acc;
+        }
+        out[i * RP + a] = v;
+      }
+    }
+    tile[ii][a] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
+    int a = e / RP, b = e % RP;
+    TC acc = 0;
+#pragma unroll 8
+    for (int ii = 0; ii < kGramRows; ++ii) acc += tile[ii][a] * tile[ii][b];
+    gpart[(int64_t)blockIdx.x * RP * RP + e] = (double)acc;
+  }
+}
+
+// Sum of `count` rp x rp double partials into out (one CTA, fixed order).
+__global__ void reduce_sq_kernel(const double* __restrict__ parts, int count, int rpsq, double* out, const DevState* st) {
+  if (stopped(st)) return;
+  for (int e = threadIdx.x; e < rpsq; e += blockDim.x) {
+    double v = 0.0;
+    for (int c = 0; c < count; ++c) v += parts[(int64_t)c * rpsq + e];
+    out[e] = v;
+  }
+}
+
+// ---------------------------------------------------------------- thin row transform
+// dst[i][:] = src[i][:] T   (T rp x rp, float64 in global), optional second output
+// dst2 = src T2, and optional Gram-like partial hpart[cta] = sum_i old[i]^T dst[i].
+template <typename TC, int RP>
+__global__ void __launch_bounds__(256) row_transform_kernel(const TC* __restrict__ src, int64_t rows,
+                                                            const double* __restrict__ T, TC* __restrict__ dst,
+                                                            const double* __restrict__ T2, TC* __restrict__ dst2,
+                                                            const TC* __restrict__ old, double* __restrict__ hpart,
+                                                            const DevState* st) {
+  if (stopped(st)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto Ts = reinterpret_cast<TC(*)[RP + 1]>(smem_raw);                                   // [RP][RP + 1]
+  auto srow = reinterpret_cast<TC(*)[RP + 1]>(smem_raw + sizeof(TC) * RP * (RP + 1));    // [kGramRows][RP + 1]
+  auto drow = reinterpret_cast<TC(*)[RP + 1]>(smem_raw + sizeof(TC) * (RP + kGramRows) * (RP + 1));
+  const int64_t i0 = (int64_t)blockIdx.x * kGramRows;
+  for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) Ts[e / RP][e % RP] = (TC)T[e];
+  for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
+    int ii = e / RP, a = e % RP;
+    int64_t i = i0 + ii;
+    srow[ii][a] = i < rows ? src[i * RP + a] : (TC)0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
+    int ii = e / RP, a = e % RP;
+    TC acc = 0;
+#pragma unroll 8
+    for (int b = 0; b < RP; ++b) acc += srow[ii][b] * Ts[b][a];
+    drow[ii][a] = acc;
+    int64_t i = i0 + ii;
+    if (i < rows) dst[i * RP + a] = acc;
+  }
+  if (T2) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) Ts[e / RP][e % RP] = (TC)T2[e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
+      int ii = e / RP, a = e % RP;
+      TC acc = 0;
+#pragma unroll 8
+      for (int b = 0; b < RP; ++b) acc += srow[ii][b] * Ts[b][a];
+      int64_t i = i0 + ii;
+      if (i < rows) dst2[i * RP + a] = acc;
+    }
+  }
+  if (hpart) {
+    __syncthreads();  // srow reused for the old rows
+    for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
+      int ii = e / RP, a = e % RP;
+      int64_t i = i0 + ii;
+      srow[ii][a] = i < rows ? old[i * RP + a] : (TC)0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
+      int a = e / RP, b = e % RP;
+      TC acc = 0;
+#pragma unroll 8
+      for (int ii = 0; ii < kGramRows; ++ii) acc += srow[ii][a] * drow[ii][b];
+      hpart[(int64_t)blockIdx.x * RP * RP + e] = (double)acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- W pass
+// Wpart[c][j][:] = sum_{i in chunk c} src[i][j] U[i][:]   (Algorithm 3 line 2: X^T U_bar).
+// src is Delta (TC, ld n) from iteration 2 on, or M itself on iteration 1.
+template <typename TC, typename TS, int RP>
+__global__ void __launch_bounds__(256) wpass_kernel(const TS* __restrict__ src, int64_t lds, int64_t m, int64_t n,
+                                                    int rows_per_chunk, const TC* __restrict__ U, TC* __restrict__ Wpart,
+                                                    const DevState* st) {
+  if (stopped(st)) return;
+  constexpr int APT = RP / 4;  // accumulators per thread
+  __shared__ TC xs[kWBM][kWBN + 1];
+  __shared__ TC us[kWBM][RP];
+  const int64_t j0 = (int64_t)blockIdx.x * kWBN;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
+  const int64_t r1 = min(m, r0 + rows_per_chunk);
+  const int tj = threadIdx.x % kWBN, ta = threadIdx.x / kWBN;
+  TC acc[APT];
+#pragma unroll
+  for (int c = 0; c < APT; ++c) acc[c] = 0;
+  for (int64_t it = r0; it < r1; it += kWBM) {
+    for (int e = threadIdx.x; e < kWBM * kWBN; e += blockDim.x) {
+      int ii = e / kWBN, jj = e % kWBN;
+      int64_t i = it + ii, j = j0 + jj;
+      xs[ii][jj] = (i < r1 && j < n) ? ld_as<TC, TS>(src + i * lds + j) : (TC)0;
+    }
+    for (int e = threadIdx.x; e < kWBM * RP; e += blockDim.x) {
+      int ii = e / RP, a = e % RP;
+      int64_t i = it + ii;
+      us[ii][a] = i < r1 ? U[i * RP + a] : (TC)0;
+    }
+    __syncthreads();
+    TC part[APT];
+#pragma unroll
+    for (int c = 0; c < APT; ++c) part[c] = 0;
+#pragma unroll 4
+    for (int ii = 0; ii < kWBM; ++ii) {
+      TC x = xs[ii][tj];
+#pragma unroll
+      for (int c = 0; c < APT; ++c) part[c] += x * us[ii][ta * APT + c];
+    }
+#pragma unroll
+    for (int c = 0; c < APT; ++c) acc[c] += part[c];
+    __syncthreads();
+  }
+  int64_t j = j0 + tj;
+  if (j < n) {
+    TC* dst = Wpart + (int64_t)blockIdx.y * n * RP + j * RP + ta * APT;
+#pragma unroll
+    for (int c = 0; c < APT; ++c) dst[c] = acc[c];
+  }
+}
+
+// ---------------------------------------------------------------- fused sweep (Algorithm 1 S/Y steps)
+// One CTA owns kSweepBM rows and a range of columns (one split).  Per column tile:
+//   L = U_bar C^T (rebuilt from the factors, never stored),
+//   z = M - L + Y_k/mu_k,  Y_{k+1} = clip(mu_k z, -1, 1),  Delta = Y_{k+1}(1/mu_k + 1/mu_{k+1}) - Y_k/mu_k,
+//   residual += (Y_{k+1} - Y_k)^2   (= mu_k^2 (M - L - S)^2),
+//   Q += (L + Delta) V_bar           (partial of P_{k+1} = X_{k+1} V_{k+1}).
+template <typename TC, typename TMs, int RP>
+__global__ void __launch_bounds__(256) sweep_kernel(const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm,
+                                                    const TC* __restrict__ Yin, TC* __restrict__ Yout,
+                                                    TC* __restrict__ D, const TC* __restrict__ U,
+                                                    const TC* __restrict__ C, const TC* __restrict__ V,
+                                                    TC* __restrict__ Qpart, int cols_per_split,
+                                                    double* __restrict__ resid_part, const DevState* st) {
+  if (stopped(st)) return;
+  constexpr int BM = kSweepBM, BN = kSweepBN;
+  constexpr int QPT = RP / 8;  // Q accumulators per thread (8 warps split the rank)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC* UsT = reinterpret_cast<TC*>(smem_raw);  // [RP][BM]
+  TC* CsT = UsT + RP * BM;                    // [RP][BN]
+  TC* Vs = CsT + RP * BN;                     // [BN][RP]
+  TC* Xs = Vs + BN * RP;                      // [BM][BN + 1]
+  __shared__ double red[32];
+
+  const double mu = st->mu;
+  const double mu_next = fmin(st->mu_max, st->rho * mu);
+  const TC tmu = (TC)mu, inv_mu = (TC)(1.0 / mu), dcoef = (TC)(1.0 / mu + 1.0 / mu_next);
+
+  const int64_t i0 = (int64_t)blockIdx.x * BM;
+  const int64_t jbeg = (int64_t)blockIdx.y * cols_per_split;
+  const int64_t jend = min(n, jbeg + cols_per_split);
+  const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+  const int qi = t & 31, qg = t >> 5;
+
+  for (int e = t; e < RP * BM; e += blockDim.x) {
+    int a = e / BM, ii = e % BM;
+    int64_t i = i0 + ii;
+    UsT[e] = i < m ? U[i * RP + a] : (TC)0;
+  }
+  TC q[QPT];
+#pragma unroll
+  for (int c = 0; c < QPT; ++c) q[c] = 0;
+  double resid = 0.0;
+
+  for (int64_t j0 = jbeg; j0 < jend; j0 += BN) {
+    __syncthreads();  // previous tile's Xs / Vs fully consumed; UsT visible on the first pass
+    for (int e = t; e < BN * RP; e += blockDim.x) {
+      int jj = e / RP, a = e % RP;
+      int64_t j = j0 + jj;
+      TC cv = 0, vv = 0;
+      if (j < jend) {
+        cv = C[j * RP + a];
+        vv = V[j * RP + a];
+      }
+      CsT[a * BN + jj] = cv;
+      Vs[e] = vv;
+    }
+    __syncthreads();
+    TC l[2][4];
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) l[x][c] = 0;
+#pragma unroll 4
+    for (int a = 0; a < RP; ++a) {
+      TC u0 = UsT[a * BM + ty], u1 = UsT[a * BM + ty + 16];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        TC cv = CsT[a * BN + tx * 4 + c];
+        l[0][c] += u0 * cv;
+        l[1][c] += u1 * cv;
+      }
+    }
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+      const int ii = ty + 16 * x;
+      const int64_t i = i0 + ii;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int jj = tx * 4 + c;
+        const int64_t j = j0 + jj;
+        TC xv = 0;
+        if (i < m && j < jend) {
+          const TC mv = ld_as<TC, TMs>(M + i * ldm + j);
+          const TC y = Yin[i * n + j];
+          const TC z = mv - l[x][c] + y * inv_mu;
+          TC yn = tmu * z;
+          yn = yn > (TC)1 ? (TC)1 : (yn < (TC)-1 ? (TC)-1 : yn);
+          const TC d = yn * dcoef - y * inv_mu;
+          const double dy = (double)(yn - y);
+          resid += dy * dy;
+          Yout[i * n + j] = yn;
+          D[i * n + j] = d;
+          xv = l[x][c] + d;
+        }
+        Xs[ii * (BN + 1) + jj] = xv;
+      }
+    }
+    __syncthreads();
+    TC part[QPT];
+#pragma unroll
+    for (int c = 0; c < QPT; ++c) part[c] = 0;
+#pragma unroll 4
+    for (int jj = 0; jj < BN; ++jj) {
+      const TC xv = Xs[qi * (BN + 1) + jj];
+#pragma unroll
+      for (int c = 0; c < QPT; ++c) part[c] += xv * Vs[jj * RP + qg * QPT + c];
+    }
+#pragma unroll
+    for (int c = 0; c < QPT; ++c) q[c] += part[c];
+  }
+  const int64_t i = i0 + qi;
+  if (i < m) {
+    TC* dst = Qpart + (int64_t)blockIdx.y * m * RP + i * RP + qg * QPT;
+#pragma unroll
+    for (int c = 0; c < QPT; ++c) dst[c] = q[c];
+  }
+  resid = block_sum(resid, red);
+  if (t == 0) resid_part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = resid;
+}
+
+// ---------------------------------------------------------------- end of iteration (one CTA)
+// ||M - L - S||_F = ||Y_{k+1} - Y_k||_F / mu_k; continuation mu_{k+1} = min(mu_bar, rho mu_k).
+__global__ void iter_end_kernel(const double* __restrict__ resid_part, int count, DevState* st) {
+  __shared__ double red[32];
+  if (stopped(st)) return;
+  double v = 0.0;
+  for (int c = threadIdx.x; c < count; c += blockDim.x) v += resid_part[c];
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) {
+    const double mu = st->mu;
+    const double res = sqrt(v) / mu / st->norm_m;
+    st->res = res;
+    st->mu_last = mu;
+    st->mu = fmin(st->mu_max, st->rho * mu);
+    st->iter += 1;
+    if (!(res == res) || res > 1e300) {
+      st->status = SFR_E_NAN;
+      st->done = 1;
+    } else if (st->fixed) {
+      if (st->iter >= st->max_iter) st->done = 1;
+    } else if (res <= st->tol) {
+      st->done = 1;
+    } else if (st->iter >= st->max_iter) {
+      st->status = SFR_E_NOCONV;
+      st->done = 1;
+    }
+  }
+}
+
+__global__ void norm_finish_kernel(const double* __restrict__ part, int count, DevState* st) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (int c = threadIdx.x; c < count; c += blockDim.x) v += part[c];
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) {
+    st->norm_m = sqrt(v);
+    if (!(v > 0.0) || !(v < 1e300)) {
+      st->status = (v == 0.0) ? SFR_E_INVAL : SFR_E_NAN;
+      st->done = 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- outputs
+// S = P_ST_{1/mu}(M - L + Y_prev / mu) with the mu, Y_prev and factors of the last iteration
+// (Algorithm 1 returns L_k, S_k); optionally L itself.
+template <typename TC, typename TMs, typename TSo, int RP>
+__global__ void __launch_bounds__(256) finalize_kernel(const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm,
+                                                       const TC* __restrict__ Yprev, const TC* __restrict__ U,
+                                                       const TC* __restrict__ C, TSo* __restrict__ S, TSo* __restrict__ L,
+                                                       int64_t lds, const DevState* st) {
+  __shared__ TC us[8][RP];
+  __shared__ TC cs[32][RP + 1];
+  const int64_t i0 = (int64_t)blockIdx.y * 8, j0 = (int64_t)blockIdx.x * 32;
+  const int tj = threadIdx.x & 31, ti = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < 8 * RP; e += blockDim.x) {
+    int ii = e / RP, a = e % RP;
+    us[ii][a] = i0 + ii < m ? U[(i0 + ii) * RP + a] : (TC)0;
+  }
+  for (int e = threadIdx.x; e < 32 * RP; e += blockDim.x) {
+    int jj = e / RP, a = e % RP;
+    cs[jj][a] = j0 + jj < n ? C[(j0 + jj) * RP + a] : (TC)0;
+  }
+  __syncthreads();
+  const int64_t i = i0 + ti, j = j0 + tj;
+  if (i >= m || j >= n) return;
+  TC l = 0;
+#pragma unroll 8
+  for (int a = 0; a < RP; ++a) l += us[ti][a] * cs[tj][a];
+  const double mu = st->mu_last;
+  const TC inv_mu = (TC)(1.0 / mu);
+  const TC z = ld_as<TC, TMs>(M + i * ldm + j) - l + Yprev[i * n + j] * inv_mu;
+  const TC sv = z > inv_mu ? z - inv_mu : (z < -inv_mu ? z + inv_mu : (TC)0);
+  if (S) S[i * lds + j] = (TSo)sv;
+  if (L) L[i * lds + j] = (TSo)l;
+}
+
+template <typename TC, int RP>
+__global__ void export_kernel(const TC* __restrict__ src, int64_t rows, int r, double* __restrict__ dst) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * r) return;
+  int64_t i = idx / r;
+  int a = (int)(idx % r);
+  dst[idx] = (double)src[i * RP + a];
+}
+
+// ---------------------------------------------------------------- dispatch helpers
+template <typename F>
+cudaError_t by_rank(int rp, F&& f) {
+  switch (rp) {
+    case 8: return f(std::integral_constant<int, 8>{});
+    case 16: return f(std::integral_constant<int, 16>{});
+    case 32: return f(std::integral_constant<int, 32>{});
+    case 64: return f(std::integral_constant<int, 64>{});
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename F>
+cudaError_t by_mtype(sfr_dtype dt, const void* M, F&& f) {
+  switch (dt) {
+    case SFR_F64: return f(static_cast<const double*>(M));
+    case SFR_F32: return f(static_cast<const float*>(M));
+    case SFR_BF16: return f(static_cast<const __nv_bfloat16*>(M));
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename F>
+cudaError_t by_prec(bool fp64, F&& f) {
+  if (fp64) return f(double{});
+  return f(float{});
+}
+
+inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+template <typename TC, int RP>
+size_t gram_smem() { return sizeof(TC) * (size_t)(kGramRows + RP) * (RP + 1); }
+template <typename TC, int RP>
+size_t transform_smem() { return sizeof(TC) * (size_t)(RP + 2 * kGramRows) * (RP + 1); }
+
+template <typename K>
+cudaError_t allow_smem(K kern, size_t bytes) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+cudaError_t launch_norm_m(const Shape& s, const Buffers& b, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>(s.m, 1024);
+  cudaError_t e = by_mtype(b.m_dtype, b.M, [&](auto M) {
+    using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
+    norm_m_kernel<TMs><<<blocks, 256, 0, st>>>(M, s.m, s.n, s.ldm, b.normm_part);
+    return cudaGetLastError();
+  });
+  if (e != cudaSuccess) return e;
+  norm_finish_kernel<<<1, 256, 0, st>>>(b.normm_part, blocks, b.st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_p(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st) {
+  return by_prec(fp64, [&](auto tc) {
+    using TC = decltype(tc);
+    return by_mtype(b.m_dtype, b.M, [&](auto M) {
+      using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
+      init_p_kernel<TC, TMs><<<cdiv(s.m * s.rp, 256), 256, 0, st>>>(M, s.m, s.ldm, s.r, s.rp, static_cast<TC*>(b.P));
+      return cudaGetLastError();
+    });
+  });
+}
+
+cudaError_t launch_gram_p(const Shape& s, const Buffers& b, bool fp64, bool sum_parts, cudaStream_t st) {
+  return by_prec(fp64, [&](auto tc) {
+    using TC = decltype(tc);
+    return by_rank(s.rp, [&](auto rpc) {
+      constexpr int RP = decltype(rpc)::value;
+      const size_t sm = gram_smem<TC, RP>();
+      cudaError_t e = allow_smem(thin_gram_kernel<TC, RP>, sm);
+      if (e != cudaSuccess) return e;
+      thin_gram_kernel<TC, RP><<<s.gp_blocks, 256, sm, st>>>(
+          static_cast<const TC*>(b.Qpart), sum_parts ? s.nsplit : 0, s.m * RP, static_cast<TC*>(b.P), s.m, nullptr,
+          nullptr, b.GPpart, b.st);
+      return cudaGetLastError();
+    });
+  });
+}
+
+cudaError_t launch_apply_u(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st) {
+  // U_new = P T_U into the other U buffer; H partials U_old^T U_new (iteration >= 2).
+  const int u_old = b.u_cur, u_new = 1 - b.u_cur;
+  return by_prec(fp64, [&](auto tc) {
+    using TC = decltype(tc);
+    return by_rank(s.rp, [&](auto rpc) {
+      constexpr int RP = decltype(rpc)::value;
+      const size_t sm = transform_smem<TC, RP>();
+      cudaError_t e = allow_smem(row_transform_kernel<TC, RP>, sm);
+      if (e != cudaSuccess) return e;
+      row_transform_kernel<TC, RP><<<s.gp_blocks, 256, sm, st>>>(
+          static_cast<const TC*>(b.P), s.m, b.TU, static_cast<TC*>(b.U[u_new]), nullptr, nullptr,
+          first ? nullptr : static_cast<const TC*>(b.U[u_old]), first ? nullptr : b.Hpart, b.st);
+      return cudaGetLastError();
+    });
+  });
+}
+
+cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first, int u_new, cudaStream_t st) {
+  dim3 grid(s.wpass_grid_x, s.nchunk);
+  return by_prec(fp64, [&](auto tc) {
+    using TC = decltype(tc);
+    return by_rank(s.rp, [&](auto rpc) {
+      constexpr int RP = decltype(rpc)::value;
+      const TC* U = static_cast<const TC*>(b.U[u_new]);
+      TC* Wp = static_cast<TC*>(b.Wpart);
+      if (first) {
+        return by_mtype(b.m_dtype, b.M, [&](auto M) {
+          using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
+          wpass_kernel<TC, TMs, RP><<<grid, 256, 0, st>>>(M, s.ldm, s.m, s.n, s.rows_per_chunk, U, Wp, b.st);
+          return cudaGetLastError();
+        });
+      }
+      wpass_kernel<TC, TC, RP><<<grid, 256, 0, st>>>(static_cast<const TC*>(b.D), s.n, s.m, s.n, s.rows_per_chunk, U, Wp,
+                                                     b.st);
+      return cudaGetLastError();
+    });
+  });
+}
+
+cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st) {
+  // W = sum_c Wpart[c] (+ C_old H, H = U_old^T U_new), then Gram partials of W.
+  // H = sum of the U_old^T U_new partials, reduced into the slot after the partials.
+  if (!first) {
+    reduce_sq_kernel<<<1, 256, 0, st>>>(b.Hpart, s.gp_blocks, s.rp * s.rp, b.Hpart + (size_t)s.gp_blocks * s.rp * s.rp,
+                                        b.st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const double* H = b.Hpart + (size_t)s.gp_blocks * s.rp * s.rp;
+  return by_prec(fp64, [&](auto tc) {
+    using TC = decltype(tc);
+    return by_rank(s.rp, [&](auto rpc) {
+      constexpr int RP = decltype(rpc)::value;
+      const size_t sm = gram_smem<TC, RP>();
+      cudaError_t e = allow_smem(thin_gram_kernel<TC, RP>, sm);
+      if (e != cudaSuccess) return e;
+      thin_gram_kernel<TC, RP><<<s.gw_blocks, 256, sm, st>>>(
+          static_cast<const TC*>(b.Wpart), s.nchunk, s.n * RP, static_cast<TC*>(b.W), s.n,
+          first ? nullptr : static_cast<const TC*>(b.C), first ? nullptr : H, b.GWpart, b.st);
+      return cudaGetLastError();
+    });
+  });
+}
+
+cudaError_t launch_apply_v(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st) {
+  return by_prec(fp64, [&](auto tc) {
+    using TC = decltype(tc);
+    return by_rank(s.rp, [&](auto rpc) {
+      constexpr int RP = decltype(rpc)::value;
+      const size_t sm = transform_smem<TC, RP>();
+      cudaError_t e = allow_smem(row_transform_kernel<TC, RP>, sm);
+      if (e != cudaSuccess) return e;
+      row_transform_kernel<TC, RP><<<s.gw_blocks, 256, sm, st>>>(static_cast<const TC*>(b.W), s.n, b.TV,
+                                                                static_cast<TC*>(b.V), b.TCm, static_cast<TC*>(b.C),
+                                                                nullptr, nullptr, b.st);
+      return cudaGetLastError();
+    });
+  });
+}
+
+cudaError_t launch_sweep(const Shape& s, const Buffers& b, bool fp64, int u_cur, cudaStream_t st) {
+  // Y ping-pong: iteration k (0-based count of completed iterations) reads Y[k % 2] and writes
+  // Y[(k + 1) % 2].  The host tracks k because graphs are replayed per iteration parity.
+  dim3 grid(s.sweep_grid_x, s.nsplit);
+  return by_prec(fp64, [&](auto tc) {
+    using TC = decltype(tc);
+    return by_rank(s.rp, [&](auto rpc) {
+      constexpr int RP = decltype(rpc)::value;
+      const size_t smem = sizeof(TC) * ((size_t)RP * kSweepBM + (size_t)RP * kSweepBN * 2 +
+                                        (size_t)kSweepBM * (kSweepBN + 1));
+      return by_mtype(b.m_dtype, b.M, [&](auto M) {
+        using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
+        auto kern = sweep_kernel<TC, TMs, RP>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, 256, smem, st>>>(M, s.m, s.n, s.ldm, static_cast<const TC*>(b.Y[0]), static_cast<TC*>(b.Y[1]),
+                                      static_cast<TC*>(b.D), static_cast<const TC*>(b.U[u_cur]),
+                                      static_cast<const TC*>(b.C), static_cast<const TC*>(b.V),
+                                      static_cast<TC*>(b.Qpart), s.cols_per_split, b.resid_part, b.st);
+        return cudaGetLastError();
+      });
+    });
+  });
+}
+
+cudaError_t launch_iter_end(const Shape& s, const Buffers& b, cudaStream_t st) {
+  iter_end_kernel<<<1, 256, 0, st>>>(b.resid_part, s.sweep_grid_x * s.nsplit, b.st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const Shape& s, const Buffers& b, bool fp64, int u_cur, void* S, sfr_dtype s_dtype,
+                            int64_t lds, void* L, cudaStream_t st) {
+  // Y_prev is the multiplier the last sweep read: Buffers::Y[0] by the host's swap convention.
+  dim3 grid(cdiv(s.n, 32), cdiv(s.m, 8));
+  return by_prec(fp64, [&](auto tc) {
+    using TC = decltype(tc);
+    return by_rank(s.rp, [&](auto rpc) {
+      constexpr int RP = decltype(rpc)::value;
+      return by_mtype(b.m_dtype, b.M, [&](auto M) {
+        using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
+        if (s_dtype == SFR_F64) {
+          finalize_kernel<TC, TMs, double, RP><<<grid, 256, 0, st>>>(
+              M, s.m, s.n, s.ldm, static_cast<const TC*>(b.Y[0]), static_cast<const TC*>(b.U[u_cur]),
+              static_cast<const TC*>(b.C), static_cast<double*>(S), static_cast<double*>(L), lds, b.st);
+        } else {
+          finalize_kernel<TC, TMs, float, RP><<<grid, 256, 0, st>>>(
+              M, s.m, s.n, s.ldm, static_cast<const TC*>(b.Y[0]), static_cast<const TC*>(b.U[u_cur]),
+              static_cast<const TC*>(b.C), static_cast<float*>(S), static_cast<float*>(L), lds, b.st);
+        }
+        return cudaGetLastError();
+      });
+    });
+  });
+}
+
+cudaError_t launch_export_factors(const Shape& s, const Buffers& b, bool fp64, int u_cur, double* U, double* V,
+                                  cudaStream_t st) {
+  return by_prec(fp64, [&](auto tc) {
+    using TC = decltype(tc);
+    return by_rank(s.rp, [&](auto rpc) {
+      constexpr int RP = decltype(rpc)::value;
+      if (U) export_kernel<TC, RP><<<cdiv(s.m * s.r, 256), 256, 0, st>>>(static_cast<const TC*>(b.U[u_cur]), s.m, s.r, U);
+      if (V) export_kernel<TC, RP><<<cdiv(s.n * s.r, 256), 256, 0, st>>>(static_cast<const TC*>(b.V), s.n, s.r, V);
+      return cudaGetLastError();
+    });
+  });
+}
+
+}  // namespace sfr

@@ -1,0 +1,198 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Bars (stated by the workload definitions):
+  * float64 path:  ||L_gpu - L_oracle||_F / ||L_oracle||_F <= 1e-9, and the same
+    support of S except entries whose |z| lies within 1e-9 (relative) of the
+    threshold 1/mu (z = M - L + Y_prev/mu of the last iteration);
+  * mixed path (float32 sweep):  ||L_gpu - L_oracle||_F / ||L_oracle||_F <= 1e-5.
+Inputs are seeded synthetic matrices; both sides see the same stored values.
+"""
+import numpy as np
+import pytest
+
+from oracle import fradm as O
+from paper_1503_03004_gb300 import binding as B
+from paper_1503_03004_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+FP64_TOL = 1e-9
+MIXED_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(prob):
+    if prob.dtype == "bf16":
+        t = torch.from_numpy(prob.M.view(np.int16)).view(torch.bfloat16)
+    else:
+        t = torch.from_numpy(prob.M)
+    return t.cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _gpu_L(sol):
+    return (sol.U @ sol.B @ sol.V.T).cpu().numpy()
+
+
+def _support_ok(S_gpu, ref, M):
+    z = M - ref.L + ref.Y_prev / ref.mu_last
+    thr = 1.0 / ref.mu_last
+    near = np.abs(np.abs(z) - thr) <= 1e-9 * max(1.0, np.abs(z).max())
+    diff = (S_gpu != 0) != (ref.S != 0)
+    return int(np.count_nonzero(diff & ~near))
+
+
+@pytest.mark.parametrize("m,n,r,K", [
+    (77, 53, 3, 1),
+    (77, 53, 3, 4),
+    (130, 70, 8, 6),
+    (200, 150, 17, 5),
+    (96, 300, 1, 7),
+    (300, 280, 64, 3),
+    (3000, 40, 3, 6),
+])
+def test_fp64_fixed_iterations_match_oracle(ctx, m, n, r, K):
+    prob = synth.planted(m, n, r, p=0.08, amp=1.0, seed=m * 7 + n + r, dtype="f64")
+    M = prob.values_f64()
+    ref = O.fr_adm(M, r, rho=1.5, fixed_iters=K)
+    sol = B.solve_torch(ctx, _dev(prob), r, fixed_iters=K, rho=1.5)
+    assert sol.iters == K
+    assert _rel(_gpu_L(sol), ref.L) <= FP64_TOL
+    np.testing.assert_allclose(sol.B.cpu().numpy(), ref.B, atol=FP64_TOL * np.abs(ref.B).max())
+    assert _support_ok(sol.S.cpu().numpy(), ref, M) == 0
+    S = sol.S.cpu().numpy()
+    assert _rel(S, ref.S) <= 1e-8 or np.linalg.norm(ref.S) == 0
+
+
+def test_fp64_500_r25_to_convergence(ctx):
+    # 500 x 500, r = 25, 10% outliers in [-50, 50], float64; mu0 = 0.05, rho = 1.5, tol 1e-9
+    prob = synth.square_fp64_500()
+    M = prob.values_f64()
+    ref = O.fr_adm(M, 25, rho=1.5, mu0=0.05, tol=1e-9)
+    sol = B.solve_torch(ctx, _dev(prob), 25, rho=1.5, mu0=0.05, tol=1e-9)
+    assert sol.iters == ref.iters
+    assert sol.rel_residual <= 1e-9
+    L = _gpu_L(sol)
+    assert _rel(L, ref.L) <= FP64_TOL
+    assert _support_ok(sol.S.cpu().numpy(), ref, M) == 0
+    L0 = prob.U0 @ prob.V0.T
+    assert _rel(L, L0) <= 1e-7            # planted recovery
+    U, V = sol.U.cpu().numpy(), sol.V.cpu().numpy()
+    np.testing.assert_allclose(U.T @ U, np.eye(25), atol=1e-12)
+    np.testing.assert_allclose(V.T @ V, np.eye(25), atol=1e-12)
+    assert sol.lambda_min_B > 0
+
+
+def test_paper_table1_recipe_on_gpu(ctx):
+    prob = synth.paper_table1(500, 10)
+    M = prob.values_f64()
+    ref = O.fr_adm(M, 10, rho=1.5, tol=1e-9)
+    sol = B.solve_torch(ctx, _dev(prob), 10, rho=1.5, tol=1e-9)
+    assert sol.iters == ref.iters == 28
+    assert _rel(_gpu_L(sol), ref.L) <= FP64_TOL
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_mixed_matches_oracle(ctx, dtype):
+    prob = synth.planted(640, 520, 10, p=0.05, amp=50.0, seed=11, dtype=dtype)
+    M = prob.values_f64()
+    ref = O.fr_adm(M, 10, rho=1.5, mu0=0.05, tol=1e-9, max_iter=200)
+    sol = B.solve_torch(ctx, _dev(prob), 10, rho=1.5, mu0=0.05, tol=1e-9, max_iter=200,
+                        precision=B.PREC_MIXED, check=False)
+    assert sol.status in (B.OK, B.E_NOCONV)
+    assert _rel(_gpu_L(sol), ref.L) <= MIXED_TOL
+
+
+def test_fp64_path_with_low_precision_storage(ctx):
+    prob = synth.planted(256, 192, 6, p=0.1, amp=1.0, seed=5, dtype="bf16")
+    M = prob.values_f64()
+    ref = O.fr_adm(M, 6, rho=1.5, fixed_iters=12)
+    sol = B.solve_torch(ctx, _dev(prob), 6, rho=1.5, fixed_iters=12)
+    assert _rel(_gpu_L(sol), ref.L) <= FP64_TOL
+
+
+def test_host_memory_mode_matches_device_mode(ctx):
+    prob = synth.planted(150, 120, 5, p=0.1, amp=1.0, seed=21, dtype="f64")
+    dev = B.solve_torch(ctx, _dev(prob), 5, fixed_iters=9)
+    M = np.ascontiguousarray(prob.M)
+    U = np.empty((150, 5)); Bm = np.empty((5, 5)); V = np.empty((120, 5)); S = np.empty((150, 120))
+    p = B.make_problem(m=150, n=120, r=5, M_ptr=M.ctypes.data, m_dtype=B.F64, fixed_iters=9, mem=B.MEM_HOST)
+    res = B.make_result(U_ptr=U.ctypes.data, B_ptr=Bm.ctypes.data, V_ptr=V.ctypes.data, S_ptr=S.ctypes.data,
+                        s_dtype=B.F64, lds=120)
+    assert ctx.solve(p, res) == B.OK
+    np.testing.assert_array_equal(U, dev.U.cpu().numpy())
+    np.testing.assert_array_equal(S, dev.S.cpu().numpy())
+
+
+def test_frnys_matches_oracle(ctx):
+    m, n, r, l = 400, 300, 4, 40
+    prob = synth.planted(m, n, r, p=0.05, amp=1.0, seed=91, dtype="f64")
+    M = prob.values_f64()
+    perm = synth.row_permutation(m, 92)
+    ref = O.fr_nys(M, r, l, perm, rho=1.5, mu0=0.1, tol=1e-10)
+    sol = B.solve_torch(ctx, _dev(prob), r, nys_l=l, nys_perm=torch.from_numpy(perm).cuda(), rho=1.5, mu0=0.1,
+                        tol=1e-10, want_L=True)
+    assert sol.iters == ref.left.iters + ref.top.iters
+    assert _rel(sol.L.cpu().numpy(), ref.L) <= FP64_TOL
+    assert _rel(sol.S.cpu().numpy(), ref.S) <= 1e-6
+
+
+def test_submit_poll_equals_solve(ctx):
+    probs = [synth.planted(120 + 40 * i, 90 + 10 * i, 3 + i, p=0.08, amp=1.0, seed=300 + i, dtype="f64") for i in range(4)]
+    alone = [B.solve_torch(ctx, _dev(p), p.r, fixed_iters=8) for p in probs]
+    keep, tickets = [], []
+    for p in probs:
+        Md = _dev(p)
+        m, n = p.shape
+        U = torch.empty((m, p.r), dtype=torch.float64, device="cuda")
+        Bm = torch.empty((p.r, p.r), dtype=torch.float64, device="cuda")
+        V = torch.empty((n, p.r), dtype=torch.float64, device="cuda")
+        S = torch.empty((m, n), dtype=torch.float64, device="cuda")
+        prob = B.make_problem(m=m, n=n, r=p.r, M_ptr=Md.data_ptr(), m_dtype=B.F64, fixed_iters=8)
+        res = B.make_result(U_ptr=U.data_ptr(), B_ptr=Bm.data_ptr(), V_ptr=V.data_ptr(), S_ptr=S.data_ptr(),
+                            s_dtype=B.F64, lds=n)
+        keep.append((Md, U, Bm, V, S, prob, res))
+        tickets.append(ctx.submit(prob, res))
+    for t in tickets:
+        assert ctx.poll(t, -1) == B.OK
+    for a, (_, U, Bm, V, S, _, res) in zip(alone, keep):
+        assert res.iters == 8
+        assert torch.equal(U, a.U) and torch.equal(S, a.S)
+
+
+def test_invalid_arguments_are_rejected(ctx):
+    Md = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
+    for kw in (dict(m=0, n=8, r=1), dict(m=8, n=8, r=9), dict(m=8, n=8, r=2, rho=1.0), dict(m=8, n=8, r=70)):
+        p = B.make_problem(M_ptr=Md.data_ptr(), m_dtype=B.F64, **kw)
+        res = B.make_result()
+        assert ctx.solve(p, res) == B.E_INVAL
+        assert ctx.last_error()
+
+
+def test_zero_matrix_is_rejected(ctx):
+    Md = torch.zeros((16, 12), dtype=torch.float64, device="cuda")
+    p = B.make_problem(m=16, n=12, r=2, M_ptr=Md.data_ptr(), m_dtype=B.F64)
+    assert ctx.solve(p, B.make_result()) == B.E_INVAL
+
+
+def test_rank_deficient_input_reports_rank_error(ctx):
+    g = synth.rng(3)
+    M = g.standard_normal((40, 2)) @ g.standard_normal((2, 30))
+    with pytest.raises(O.RankDeficient):
+        O.fr_adm(M, 4, fixed_iters=1)
+    Md = torch.from_numpy(M).cuda()
+    sol = B.solve_torch(ctx, Md, 4, fixed_iters=1, check=False)
+    assert sol.status == B.E_RANK
