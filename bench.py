@@ -1,0 +1,294 @@
+#!/usr/bin/env python3
+"""FR-ADM throughput on one GB300: solves/s of the 16384 x 16384, r = 64 workload.
+
+One step = one full FR-ADM solve (Algorithm 1 to ||M - L - S||_F / ||M||_F <= 1e-9)
+of a seeded 16384 x 16384 rank-64 matrix with 5% outliers in [-50, 50], stored in
+bfloat16, on the mixed path (float32 sweep, float64 r x r projectors), through
+the libsfr C ABI with inputs resident in HBM.  Inputs (512 MB M, 2 x 1 GB
+multiplier buffers) are larger than the 129 MB L2, so no flush is needed.
+
+Printed (rank 0, one JSON line): value = solves/s over all ranks; roofline of the
+fused sweep kernel (algorithmic bytes / event-timed duration, against the measured
+HBM copy bandwidth); e2e = the same metric through the C ABI with host buffers
+(host -> device copy of M and device -> host copy of S inside the timed region);
+cpu_baseline = the FP64 CPU oracle on a bounded sample of the same recipe.
+
+--impl reference times that oracle alone (the slow reference program).
+Multi-GPU (torchrun): replicas only, each rank solves its own problem; no collective
+on the data path (barrier + max of the elapsed time only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="square16384_r64_bf16_mixed", m=16384, n=16384, r=64, storage="bf16", precision="mixed",
+                outlier_fraction=0.05, outlier_range=[-50, 50], mu0=0.05, rho=1.5, tol=1e-9, max_iter=300,
+                l2="inputs larger than L2 (M 512 MB, multipliers 2 x 1 GB); no flush")
+SAMPLE = dict(m=2048, n=2048)          # CPU oracle sample of the same recipe (about 10 s of CPU work)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[4 + k].lower().startswith("active")})
+        pw = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
+
+
+def make_workload(seed: int):
+    from paper_1503_03004_gb300 import synth
+    return synth.square_large(WORKLOAD["m"], WORKLOAD["r"], dtype="bf16", seed=seed)
+
+
+def oracle_sample_rate(seed: int = 1001):
+    """FP64 CPU oracle on a 2048 x 2048 sample of the same recipe, scaled to full-size solves/s.
+
+    FR-ADM costs O(m n r) per iteration and needs a similar iteration count at both sizes,
+    so the full-size time is taken as the sample's solve time x (16384^2 / 2048^2).
+    """
+    import numpy as np
+    from oracle import fradm as O
+    from paper_1503_03004_gb300 import synth
+    p = synth.planted(SAMPLE["m"], SAMPLE["n"], WORKLOAD["r"], p=WORKLOAD["outlier_fraction"], amp=50.0, seed=seed,
+                      dtype="bf16")
+    M = p.values_f64()
+    t0 = time.perf_counter()
+    res = O.fr_adm(M, WORKLOAD["r"], rho=WORKLOAD["rho"], mu0=WORKLOAD["mu0"], tol=WORKLOAD["tol"],
+                   max_iter=WORKLOAD["max_iter"])
+    dt = time.perf_counter() - t0
+    scale = (WORKLOAD["m"] * WORKLOAD["n"]) / (SAMPLE["m"] * SAMPLE["n"])
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": 1.0 / (dt * scale), "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": (f"one FP64 oracle solve of a {SAMPLE['m']}x{SAMPLE['n']} r=64 sample of the same recipe "
+                       f"({res.iters} iterations, {dt:.1f} s), scaled by m*n to 16384x16384"),
+            "sample_iters": res.iters, "sample_seconds": dt, "converged": bool(res.converged)}, np
+
+
+def dist_setup():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = dist_setup()
+    if rank != 0:
+        return 0
+    rates = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        info, _ = oracle_sample_rate()
+        if i >= args.warmup:
+            rates.append(info["value"])
+    value = args.steps / sum(1.0 / r for r in rates)
+    line = {"impl": "reference", "metric": "solves/s", "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": WORKLOAD,
+            "cpu_baseline": {k: info[k] for k in ("kind", "cores", "sample")} | {"value": value, "unit": "solves/s"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    from paper_1503_03004_gb300 import binding as B
+
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_base, _ = oracle_sample_rate()  # before any CUDA work of the library (host cores only)
+
+    prob = make_workload(seed=1001 + rank)
+    m, n, r = WORKLOAD["m"], WORKLOAD["n"], WORKLOAD["r"]
+    M_dev = torch.from_numpy(prob.M.view(np.int16)).view(torch.bfloat16).cuda()
+    U = torch.empty((m, r), dtype=torch.float64, device="cuda")
+    Bm = torch.empty((r, r), dtype=torch.float64, device="cuda")
+    V = torch.empty((n, r), dtype=torch.float64, device="cuda")
+    S = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()           # the library and the timing events share this stream
+    ctx = B.Context(local, stream=stream.cuda_stream, profile=True)
+    kw = dict(m=m, n=n, r=r, m_dtype=B.BF16, mu0=WORKLOAD["mu0"], rho=WORKLOAD["rho"], tol=WORKLOAD["tol"],
+              max_iter=WORKLOAD["max_iter"], precision=B.PREC_MIXED)
+    p = B.make_problem(M_ptr=M_dev.data_ptr(), **kw)
+    res = B.make_result(U_ptr=U.data_ptr(), B_ptr=Bm.data_ptr(), V_ptr=V.data_ptr(), S_ptr=S.data_ptr(),
+                        s_dtype=B.F32, lds=n)
+    torch.cuda.synchronize()
+
+    def one_solve():
+        st = ctx.solve(p, res)
+        if st != B.OK:
+            raise RuntimeError(f"solve failed: {B.STATUS_NAMES.get(st)} {ctx.last_error()}")
+        return res.iters
+
+    for _ in range(args.warmup):
+        one_solve()
+    iters_seen = res.iters
+    ctx.stats(reset=True)
+
+    # ---- timed region: K device-resident solves
+    barrier()
+    torch.cuda.synchronize()
+    lat = []
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for _ in range(args.steps):
+            a = time.perf_counter()
+            one_solve()  # synchronous: the library waits for its stream before returning
+            lat.append(time.perf_counter() - a)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    stats = ctx.stats(reset=True)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = world * args.steps / (elapsed_ms / 1000.0)
+    clocks = clk.summary()
+
+    # roofline of the fused sweep kernel: algorithmic bytes per launch / event-timed duration
+    sw = stats[B.STAT_SWEEP]
+    bytes_per_elem = 2 + 4 + 4 + 4       # read M (bf16) and Y_k (f32); write Y_{k+1} and Delta (f32)
+    alg_bytes = bytes_per_elem * m * n
+    avg_ms = sw["total_ms"] / max(1, sw["timed"])
+    achieved = alg_bytes / (avg_ms / 1000.0) / 1e9
+    peak, peak_kind = peaks()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "sweep_kernel<float,bf16,64>", "bytes_per_launch": alg_bytes,
+                "avg_launch_ms": avg_ms, "timed_launches": sw["timed"], "peak_source": peak_kind + " hbm_gbs",
+                "wpass_avg_ms": stats[B.STAT_WPASS]["total_ms"] / max(1, stats[B.STAT_WPASS]["timed"]),
+                "rxr_avg_ms": stats[B.STAT_RXR]["total_ms"] / max(1, stats[B.STAT_RXR]["timed"])}
+
+    # ---- e2e: the same solve through the C ABI with pinned host buffers (copies inside the region)
+    M_host = torch.from_numpy(prob.M.view(np.int16)).pin_memory()
+    S_host = torch.empty((m, n), dtype=torch.float32).pin_memory()
+    U_h = np.empty((m, r)); B_h = np.empty((r, r)); V_h = np.empty((n, r))
+    ph = B.make_problem(M_ptr=M_host.data_ptr(), mem=B.MEM_HOST, **kw)
+    rh = B.make_result(U_ptr=U_h.ctypes.data, B_ptr=B_h.ctypes.data, V_ptr=V_h.ctypes.data, S_ptr=S_host.data_ptr(),
+                       s_dtype=B.F32, lds=n)
+    if ctx.solve(ph, rh) != B.OK:
+        raise RuntimeError(ctx.last_error())
+    barrier()
+    a = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        if ctx.solve(ph, rh) != B.OK:
+            raise RuntimeError(ctx.last_error())
+    e2e_s = time.perf_counter() - a
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * args.e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 2 * m * n,
+           "d2h_bytes_per_step": 4 * m * n + 8 * (m * r + r * r + n * r)}
+
+    lat_ms = sorted(x * 1000.0 for x in lat)
+    line = {"metric": "solves/s", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+            "config": WORKLOAD | {"parallelism": f"replicas x{world}", "iters_per_solve": iters_seen},
+            "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
+                                                                                int(0.99 * len(lat_ms)))]},
+            "roofline": roofline, "clocks": clocks, "e2e": e2e,
+            "gpu_launches": stats[B.STAT_ALL]["launches"],
+            "cpu_baseline": cpu_base and {k: cpu_base[k] for k in ("value", "unit", "cores", "kind", "sample")}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

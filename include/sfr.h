@@ -65,7 +65,24 @@ typedef struct {
   size_t hbm_budget_bytes;  /* cap on workspace bytes the context may hold; 0 = no cap     */
   int max_slots;            /* concurrent requests for sfr_submit; 0 = default (8)         */
   void* cuda_stream;        /* cudaStream_t for sfr_solve; NULL = a stream the ctx creates */
+  int profile;              /* nonzero: time the sweep, W-pass and r x r kernels of sfr_solve
+                               with CUDA events on the solve stream (see sfr_stats)        */
 } sfr_config;
+
+/* Kernel classes counted by sfr_stats. */
+typedef enum {
+  SFR_STAT_SWEEP = 0,       /* fused sweep: L rebuild, S- and Y-steps of Algorithm 1, Delta, next X V */
+  SFR_STAT_WPASS = 1,       /* X^T U_bar pass (V-step product of Algorithm 3)                      */
+  SFR_STAT_RXR = 2,         /* r x r projector kernels (Eq. 9, Eq. 10)                           */
+  SFR_STAT_ALL = 3,         /* every kernel launch of the library (total_ms unused)              */
+  SFR_STAT_COUNT = 4
+} sfr_stat_kind;
+
+typedef struct {
+  int64_t launches;         /* kernel launches (including launches that found the stop flag set) */
+  int64_t timed;            /* launches that did work and were timed (profile != 0)              */
+  double total_ms;          /* summed event-to-event duration of the timed launches              */
+} sfr_kernel_stat;
 
 typedef struct {
   int64_t m, n, ldm;        /* M is m x n, row-major, leading dimension ldm >= n           */
@@ -118,6 +135,11 @@ sfr_status sfr_poll(sfr_ctx* ctx, uint64_t ticket, int64_t timeout_us);
 
 /* Finish or cancel outstanding requests, free the workspace and the context. */
 sfr_status sfr_destroy(sfr_ctx* ctx);
+
+/* Copy the per-kernel-class counters of sfr_solve calls on ctx into out[0 .. count)
+ * (indexed by sfr_stat_kind); reset != 0 zeroes them afterwards.  Counts cover
+ * sfr_solve only, not requests run through sfr_submit. */
+sfr_status sfr_stats(sfr_ctx* ctx, sfr_kernel_stat* out, int32_t count, int32_t reset);
 
 /* The last error message of ctx (or of the last failed sfr_create when ctx is NULL). */
 const char* sfr_last_error(const sfr_ctx* ctx);

@@ -30,7 +30,15 @@ DTYPE_CODES = {"f64": F64, "f32": F32, "bf16": BF16}
 
 class Config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("profile", ctypes.c_int)]
+
+
+# sfr_stat_kind
+STAT_SWEEP, STAT_WPASS, STAT_RXR, STAT_ALL, STAT_COUNT = 0, 1, 2, 3, 4
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("timed", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
 class Problem(ctypes.Structure):
@@ -56,6 +64,7 @@ SIGNATURES = [
                                   ctypes.POINTER(ctypes.c_uint64)]),
     ("sfr_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64]),
     ("sfr_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("sfr_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(KernelStat), ctypes.c_int32, ctypes.c_int32]),
     ("sfr_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("sfr_version", ctypes.c_char_p, []),
 ]
@@ -88,11 +97,12 @@ class SfrError(RuntimeError):
 class Context:
     """An sfr_ctx on one device (sfr_create / sfr_destroy)."""
 
-    def __init__(self, device: int = 0, stream: int | None = None, hbm_budget_bytes: int = 0, max_slots: int = 0):
+    def __init__(self, device: int = 0, stream: int | None = None, hbm_budget_bytes: int = 0, max_slots: int = 0,
+                 profile: bool = False):
         self.lib = load()
         self.handle = ctypes.c_void_p()
         cfg = Config(device=device, hbm_budget_bytes=hbm_budget_bytes, max_slots=max_slots,
-                     cuda_stream=ctypes.c_void_p(stream) if stream else None)
+                     cuda_stream=ctypes.c_void_p(stream) if stream else None, profile=int(profile))
         st = self.lib.sfr_create(ctypes.byref(self.handle), ctypes.byref(cfg))
         if st != OK:
             raise SfrError(st, self.lib.sfr_last_error(None).decode())
@@ -112,6 +122,13 @@ class Context:
 
     def poll(self, ticket: int, timeout_us: int = -1) -> int:
         return self.lib.sfr_poll(self.handle, ticket, timeout_us)
+
+    def stats(self, reset: bool = False) -> list:
+        arr = (KernelStat * STAT_COUNT)()
+        st = self.lib.sfr_stats(self.handle, arr, STAT_COUNT, int(reset))
+        if st != OK:
+            raise SfrError(st, self.last_error())
+        return [dict(launches=a.launches, timed=a.timed, total_ms=a.total_ms) for a in arr]
 
     def close(self):
         if self.handle:

@@ -159,30 +159,89 @@ struct Solver {
   // graph cache, keyed by the buffer layout it was captured with
   cudaGraphExec_t graph = nullptr;
   std::string graph_key;
+  int graph_kernels = 0;
+  // profiling: kernel counters and events (slot 0: eager iteration, slots 1-2: the graph's two)
+  bool profile = false;
+  bool count_stats = false;
+  bool capturing = false;
+  int64_t launches[SFR_STAT_COUNT] = {};
+  int64_t timed[SFR_STAT_COUNT] = {};
+  double total_ms[SFR_STAT_COUNT] = {};
+  cudaEvent_t ev[3][4][2] = {};
 
   ~Solver() {
     if (graph) cudaGraphExecDestroy(graph);
     if (host_state) cudaFreeHost(host_state);
+    for (auto& a : ev)
+      for (auto& b : a)
+        for (auto& e : b)
+          if (e) cudaEventDestroy(e);
   }
 
-  void enqueue_iteration(const Shape& s, Buffers& b, bool fp64, bool first) {
+  void make_events() {
+    for (auto& a : ev)
+      for (auto& b : a)
+        for (auto& e : b)
+          if (!e) SFR_CUDA(cudaEventCreate(&e));
+  }
+
+  // Timed launch of one kernel class: events around it when profiling.
+  template <typename F>
+  void timed_launch(int slot, int k, F&& f) {
+    // inside stream capture an event record becomes a graph node only with the external flag,
+    // and that flag is refused outside capture
+    const unsigned flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (profile) SFR_CUDA(cudaEventRecordWithFlags(ev[slot][k][0], stream, flags));
+    SFR_CUDA(f());
+    if (profile) SFR_CUDA(cudaEventRecordWithFlags(ev[slot][k][1], stream, flags));
+  }
+
+  // Accumulate the event durations of the iterations that ran in `slot`s [first, first + count).
+  void harvest(int first, int count) {
+    if (!profile || !count_stats) return;
+    for (int sl = first; sl < first + count; ++sl) {
+      float ms;
+      SFR_CUDA(cudaEventElapsedTime(&ms, ev[sl][0][0], ev[sl][0][1]));
+      total_ms[SFR_STAT_SWEEP] += ms;
+      timed[SFR_STAT_SWEEP] += 1;
+      SFR_CUDA(cudaEventElapsedTime(&ms, ev[sl][1][0], ev[sl][1][1]));
+      total_ms[SFR_STAT_WPASS] += ms;
+      timed[SFR_STAT_WPASS] += 1;
+      for (int k = 2; k < 4; ++k) {
+        SFR_CUDA(cudaEventElapsedTime(&ms, ev[sl][k][0], ev[sl][k][1]));
+        total_ms[SFR_STAT_RXR] += ms;
+        timed[SFR_STAT_RXR] += 1;
+      }
+    }
+  }
+
+  void count(int kind, int64_t n) {
+    if (count_stats) launches[kind] += n;
+  }
+
+  // Enqueue one FR-ADM iteration; returns the number of kernels it launches.
+  int enqueue_iteration(const Shape& s, Buffers& b, bool fp64, bool first, int slot) {
     cudaStream_t st = stream;
+    int kernels = 0;
     if (first) {
       SFR_CUDA(launch_init_p(s, b, fp64, st));
       SFR_CUDA(launch_gram_p(s, b, fp64, false, st));
+      kernels += 2;
     }
-    SFR_CUDA(launch_rxr(s, b, false, st));                     // T_U = B (B G_P B)^{-1/2}
-    SFR_CUDA(launch_apply_u(s, b, fp64, first, st));           // U_bar = P T_U
+    timed_launch(slot, 2, [&] { return launch_rxr(s, b, false, st); });      // T_U = B (B G_P B)^{-1/2}
+    SFR_CUDA(launch_apply_u(s, b, fp64, first, st));                          // U_bar = P T_U
     const int u_new = 1 - b.u_cur;
-    SFR_CUDA(launch_wpass(s, b, fp64, first, u_new, st));      // X^T U_bar partials
-    SFR_CUDA(launch_wfinal(s, b, fp64, first, st));            // W, G_W partials
-    SFR_CUDA(launch_rxr(s, b, true, st));                      // T_V, B_bar, T_C
-    SFR_CUDA(launch_apply_v(s, b, fp64, st));                  // V_bar, C
-    SFR_CUDA(launch_sweep(s, b, fp64, u_new, st));             // S/Y steps, Delta, next P partials
-    SFR_CUDA(launch_iter_end(s, b, st));                       // residual, mu, stop test
-    SFR_CUDA(launch_gram_p(s, b, fp64, true, st));             // P = sum of partials, G_P partials
+    timed_launch(slot, 1, [&] { return launch_wpass(s, b, fp64, first, u_new, st); });  // X^T U_bar partials
+    SFR_CUDA(launch_wfinal(s, b, fp64, first, st));                           // W, G_W partials
+    timed_launch(slot, 3, [&] { return launch_rxr(s, b, true, st); });       // T_V, B_bar, T_C
+    SFR_CUDA(launch_apply_v(s, b, fp64, st));                                 // V_bar, C
+    timed_launch(slot, 0, [&] { return launch_sweep(s, b, fp64, u_new, st); });  // S/Y steps, Delta, next P
+    SFR_CUDA(launch_iter_end(s, b, st));                                      // residual, mu, stop test
+    SFR_CUDA(launch_gram_p(s, b, fp64, true, st));                            // P = sum of partials, G_P
+    kernels += first ? 9 : 10;
     b.u_cur = u_new;
     std::swap(b.Y[0], b.Y[1]);
+    return kernels;
   }
 
   // Runs Algorithm 1 on a device-resident M.  Returns the final host copy of the state and
@@ -221,35 +280,44 @@ struct Solver {
     SFR_CUDA(cudaMemcpyAsync(b.Qeig_u, eyef.data(), 4 * eyef.size(), cudaMemcpyHostToDevice, stream));
     SFR_CUDA(cudaMemcpyAsync(b.Qeig_v, eyef.data(), 4 * eyef.size(), cudaMemcpyHostToDevice, stream));
     SFR_CUDA(launch_norm_m(s, b, stream));
+    count(SFR_STAT_ALL, 2);
+    if (profile) make_events();
 
     // iteration 1 (X_1 = M, V_1 = I_{n x r}), eager
-    enqueue_iteration(s, b, fp64, true);
+    count(SFR_STAT_ALL, enqueue_iteration(s, b, fp64, true, 0));
+    count(SFR_STAT_SWEEP, 1);
+    count(SFR_STAT_WPASS, 1);
+    count(SFR_STAT_RXR, 2);
     const Buffers after_first = b;
 
     // iterations 2, 3, ...: a graph of two iterations, replayed; every kernel exits at once
     // after the stop flag is set, so overshooting the last iteration costs only launches.
-    const std::string key = fmt("%p/%lld/%lld/%lld/%d/%d/%p", work.ptr, (long long)s.m, (long long)s.n,
+    const std::string key0 = fmt("%p/%lld/%lld/%lld/%d/%d/%p", work.ptr, (long long)s.m, (long long)s.n,
                                 (long long)s.ldm, s.r, (int)fp64, Mdev) +
                             fmt("/%d", (int)p.m_dtype);
-    if (graph_key != key) {
+    const std::string key = key0;
+    if (graph_key != key + (profile ? "/p" : "")) {
       if (graph) {
         cudaGraphExecDestroy(graph);
         graph = nullptr;
       }
       cudaGraph_t g;
       SFR_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed));
+      capturing = true;
       try {
-        enqueue_iteration(s, b, fp64, false);
-        enqueue_iteration(s, b, fp64, false);
+        graph_kernels = enqueue_iteration(s, b, fp64, false, 1);
+        graph_kernels += enqueue_iteration(s, b, fp64, false, 2);
       } catch (...) {
+        capturing = false;
         cudaStreamEndCapture(stream, &g);
         throw;
       }
+      capturing = false;
       SFR_CUDA(cudaStreamEndCapture(stream, &g));
       cudaError_t e = cudaGraphInstantiate(&graph, g, 0);
       cudaGraphDestroy(g);
       SFR_CUDA(e);
-      graph_key = key;
+      graph_key = key + (profile ? "/p" : "");
       b = after_first;
     }
     const int cap = h.max_iter;
@@ -257,14 +325,21 @@ struct Solver {
     int per_check = 1;
     SFR_CUDA(cudaMemcpyAsync(host_state, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
     SFR_CUDA(cudaStreamSynchronize(stream));
+    harvest(0, host_state->iter >= 1 ? 1 : 0);
     while (!host_state->done && launched < cap) {
+      const int before = host_state->iter;
       for (int k = 0; k < per_check && launched < cap; ++k) {
         SFR_CUDA(cudaGraphLaunch(graph, stream));
         launched += 2;
+        count(SFR_STAT_ALL, graph_kernels);
+        count(SFR_STAT_SWEEP, 2);
+        count(SFR_STAT_WPASS, 2);
+        count(SFR_STAT_RXR, 4);
       }
       SFR_CUDA(cudaMemcpyAsync(host_state, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
       SFR_CUDA(cudaStreamSynchronize(stream));
-      per_check = std::min(per_check * 2, 8);
+      harvest(1, host_state->iter - before);  // profiling keeps per_check at 1
+      if (!profile) per_check = std::min(per_check * 2, 8);
     }
     DevState out = *host_state;
     const int K = out.iter;
@@ -279,6 +354,7 @@ struct Solver {
     }
     if (out.status == SFR_OK || out.status == SFR_E_NOCONV) {
       SFR_CUDA(launch_export_factors(s, fin, fp64, fin.u_cur, Udev, Vdev, stream));
+      count(SFR_STAT_ALL, (Udev ? 1 : 0) + (Vdev ? 1 : 0) + ((Sdev || Ldev) ? 1 : 0));
       if (Bdev) {
         for (int i = 0; i < p.r; ++i)
           SFR_CUDA(cudaMemcpyAsync(Bdev + (size_t)i * p.r, fin.B + (size_t)i * s.rp, 8 * p.r,
@@ -554,6 +630,8 @@ sfr_status sfr_create(sfr_ctx** out, const sfr_config* cfg) {
       sv->num_sms = prop.multiProcessorCount;
       sv->stream = w == 0 ? ctx->stream : ctx->worker_stream;
       sv->budget = cfg->hbm_budget_bytes;
+      sv->profile = w == 0 && cfg->profile != 0;
+      sv->count_stats = w == 0;
       SFR_CUDA(cudaMallocHost(&sv->host_state, sizeof(DevState)));
       (w == 0 ? ctx->solver : ctx->worker_solver) = std::move(sv);
     }
@@ -629,6 +707,23 @@ sfr_status sfr_poll(sfr_ctx* ctx, uint64_t ticket, int64_t timeout_us) {
   }
   ctx->live.erase(ticket);
   return rq->status;
+}
+
+sfr_status sfr_stats(sfr_ctx* ctx, sfr_kernel_stat* out, int32_t count, int32_t reset) {
+  if (!ctx || (count > 0 && !out)) return SFR_E_INVAL;
+  Solver& sv = *ctx->solver;
+  for (int k = 0; k < count && k < SFR_STAT_COUNT; ++k) {
+    out[k].launches = sv.launches[k];
+    out[k].timed = sv.timed[k];
+    out[k].total_ms = sv.total_ms[k];
+  }
+  if (reset)
+    for (int k = 0; k < SFR_STAT_COUNT; ++k) {
+      sv.launches[k] = 0;
+      sv.timed[k] = 0;
+      sv.total_ms[k] = 0.0;
+    }
+  return SFR_OK;
 }
 
 sfr_status sfr_destroy(sfr_ctx* ctx) {

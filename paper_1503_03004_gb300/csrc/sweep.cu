@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) row_transform_kernel(const TC* __restrict
 }
 
 // ---------------------------------------------------------------- W pass
-// Wpart[c][j][:] = sum_{i in chunk c} src[i][j] U[i][:]   (Algorithm 3 line 2: X^T U_bar).
+// Wpart[c][j][:] = sum_{i in chunk c} src[i][j] U[i][:]   (the V-step product X^T U_bar of Algorithm 3).
 // src is Delta (TC, ld n) from iteration 2 on, or M itself on iteration 1.
 template <typename TC, typename TS, int RP>
 __global__ void __launch_bounds__(256) wpass_kernel(const TS* __restrict__ src, int64_t lds, int64_t m, int64_t n,

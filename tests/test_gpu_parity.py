@@ -116,6 +116,18 @@ def test_mixed_matches_oracle(ctx, dtype):
     assert _rel(_gpu_L(sol), ref.L) <= MIXED_TOL
 
 
+def test_mixed_square_r64_bf16_recipe(ctx):
+    # the 16384 x 16384 r = 64 recipe (5% outliers in [-50, 50], bf16 storage) at 1024 x 1024
+    prob = synth.planted(1024, 1024, 64, p=0.05, amp=50.0, seed=1001, dtype="bf16")
+    M = prob.values_f64()
+    ref = O.fr_adm(M, 64, rho=1.5, mu0=0.05, tol=1e-9, max_iter=300)
+    sol = B.solve_torch(ctx, _dev(prob), 64, rho=1.5, mu0=0.05, tol=1e-9, max_iter=300, precision=B.PREC_MIXED,
+                        s_dtype=B.F32)
+    assert abs(sol.iters - ref.iters) <= 2
+    assert _rel(_gpu_L(sol), ref.L) <= MIXED_TOL
+    assert _rel(sol.S.cpu().numpy().astype(np.float64), ref.S) <= 1e-4
+
+
 def test_fp64_path_with_low_precision_storage(ctx):
     prob = synth.planted(256, 192, 6, p=0.1, amp=1.0, seed=5, dtype="bf16")
     M = prob.values_f64()
