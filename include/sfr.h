@@ -141,6 +141,27 @@ sfr_status sfr_destroy(sfr_ctx* ctx);
  * sfr_solve only, not requests run through sfr_submit. */
 sfr_status sfr_stats(sfr_ctx* ctx, sfr_kernel_stat* out, int32_t count, int32_t reset);
 
+/* sfr_solve without any device allocation, for callers that cannot allocate:
+ * code that runs while a CUDA graph is being captured, processes whose device
+ * memory belongs to a fixed pool or to a framework allocator, and paths that may
+ * not take the allocator's locks.  The paper has no counterpart; this is a
+ * library convenience.  It runs the same FR-ADM kernels as sfr_solve, eagerly
+ * on the context's stream, with all workspace taken from one 32 MiB __device__
+ * array built into the library (every GPU that loads libsfr holds it until the
+ * process exits).
+ *   - FR-ADM only (nys_l == 0) and device buffers only (mem == SFR_MEM_DEVICE).
+ *   - A problem whose workspace exceeds the array is refused with SFR_E_NOMEM.
+ *     The workspace is about 24 bytes (float64 path) or 12 bytes (mixed path)
+ *     per element of M plus the thin and r x r buffers; 500 x 500 at r = 25
+ *     in float64 needs about 10 MiB.
+ *   - The first call on a device looks up the array's device address; make that
+ *     first call before any stream capture begins.
+ *   - All calls share the array and it keeps the previous call's contents (the
+ *     solve clears what must start at zero).  Calls whose GPU work overlaps --
+ *     from two host threads, or two contexts on one device -- race on it.
+ * Same arguments and results as sfr_solve. */
+sfr_status sfr_solve_noalloc(sfr_ctx* ctx, const sfr_problem* prob, sfr_result* res);
+
 /* The last error message of ctx (or of the last failed sfr_create when ctx is NULL). */
 const char* sfr_last_error(const sfr_ctx* ctx);
 

@@ -64,6 +64,7 @@ SIGNATURES = [
                                   ctypes.POINTER(ctypes.c_uint64)]),
     ("sfr_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64]),
     ("sfr_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("sfr_solve_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.POINTER(Result)]),
     ("sfr_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(KernelStat), ctypes.c_int32, ctypes.c_int32]),
     ("sfr_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("sfr_version", ctypes.c_char_p, []),
@@ -112,6 +113,9 @@ class Context:
 
     def solve(self, prob: Problem, res: Result) -> int:
         return self.lib.sfr_solve(self.handle, ctypes.byref(prob), ctypes.byref(res))
+
+    def solve_noalloc(self, prob: Problem, res: Result) -> int:
+        return self.lib.sfr_solve_noalloc(self.handle, ctypes.byref(prob), ctypes.byref(res))
 
     def submit(self, prob: Problem, res: Result) -> int:
         t = ctypes.c_uint64()

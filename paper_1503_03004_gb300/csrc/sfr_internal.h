@@ -5,6 +5,9 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <string>
+#include <vector>
+
 #include "../../include/sfr.h"
 
 namespace sfr {
@@ -101,4 +104,16 @@ constexpr int kGramRows = 64;    // rows per Gram / transform CTA
 
 inline int pad_rank(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 32 ? 32 : 64; }
 
+// ---- host helpers shared by the entry points (solver.cu)
+Shape plan_shape(int64_t m, int64_t n, int64_t ldm, int r, int num_sms);
+size_t carve(const Shape& s, bool fp64, void* base, Buffers* b);  // base == nullptr: size only
+double host_lambda_min(std::vector<double> A, int r);
+int ctx_device(const sfr_ctx* ctx);
+int ctx_num_sms(const sfr_ctx* ctx);
+cudaStream_t ctx_stream(const sfr_ctx* ctx);
+void ctx_set_error(sfr_ctx* ctx, const std::string& msg);
+
 }  // namespace sfr
+
+// Argument checks of sfr_solve / sfr_submit (solver.cu); SFR_OK or SFR_E_INVAL with a reason.
+sfr_status validate(const sfr_problem* p, const sfr_result* r, std::string* why);

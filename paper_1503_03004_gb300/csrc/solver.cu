@@ -86,7 +86,7 @@ struct Carver {
 };
 
 // ---------------------------------------------------------------- planning
-static Shape plan_shape(int64_t m, int64_t n, int64_t ldm, int r, int num_sms) {
+Shape plan_shape(int64_t m, int64_t n, int64_t ldm, int r, int num_sms) {
   Shape s{};
   s.m = m;
   s.n = n;
@@ -113,7 +113,7 @@ static Shape plan_shape(int64_t m, int64_t n, int64_t ldm, int r, int num_sms) {
 }
 
 // Lay out every buffer of one solve inside `base` (or just size it when base == nullptr).
-static size_t carve(const Shape& s, bool fp64, void* base, Buffers* b) {
+size_t carve(const Shape& s, bool fp64, void* base, Buffers* b) {
   const size_t tc = fp64 ? 8 : 4;
   const size_t rp = s.rp, rpsq = rp * rp;
   Carver c(base);
@@ -368,7 +368,7 @@ struct Solver {
 };
 
 // Smallest eigenvalue of a symmetric r x r matrix (cyclic Jacobi on the host, float64).
-static double host_lambda_min(std::vector<double> A, int r) {
+double host_lambda_min(std::vector<double> A, int r) {
   for (int sweep = 0; sweep < 60; ++sweep) {
     double off = 0.0;
     for (int i = 0; i < r; ++i)
@@ -470,7 +470,14 @@ struct sfr_ctx {
 
 static thread_local std::string g_create_error;
 
-static sfr_status validate(const sfr_problem* p, const sfr_result* r, std::string* why) {
+namespace sfr {
+int ctx_device(const sfr_ctx* ctx) { return ctx->device; }
+int ctx_num_sms(const sfr_ctx* ctx) { return ctx->solver->num_sms; }
+cudaStream_t ctx_stream(const sfr_ctx* ctx) { return ctx->stream; }
+void ctx_set_error(sfr_ctx* ctx, const std::string& msg) { ctx->last_error = msg; }
+}  // namespace sfr
+
+sfr_status validate(const sfr_problem* p, const sfr_result* r, std::string* why) {
   if (!p || !r) return *why = "null problem or result", SFR_E_INVAL;
   if (p->m <= 0 || p->n <= 0) return *why = "m and n must be positive", SFR_E_INVAL;
   if (p->ldm < p->n) return *why = "ldm must be >= n", SFR_E_INVAL;
