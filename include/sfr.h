@@ -82,6 +82,8 @@ typedef struct {
   int64_t launches;         /* kernel launches (including launches that found the stop flag set) */
   int64_t timed;            /* launches that did work and were timed (profile != 0)              */
   double total_ms;          /* summed event-to-event duration of the timed launches              */
+  double bytes;             /* algorithmic DRAM bytes of the timed launches: the m x n operands
+                               each must read or write once, given their storage types           */
 } sfr_kernel_stat;
 
 typedef struct {

@@ -38,7 +38,8 @@ STAT_SWEEP, STAT_WPASS, STAT_RXR, STAT_ALL, STAT_COUNT = 0, 1, 2, 3, 4
 
 
 class KernelStat(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64), ("timed", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+    _fields_ = [("launches", ctypes.c_int64), ("timed", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
 
 
 class Problem(ctypes.Structure):
@@ -132,7 +133,7 @@ class Context:
         st = self.lib.sfr_stats(self.handle, arr, STAT_COUNT, int(reset))
         if st != OK:
             raise SfrError(st, self.last_error())
-        return [dict(launches=a.launches, timed=a.timed, total_ms=a.total_ms) for a in arr]
+        return [dict(launches=a.launches, timed=a.timed, total_ms=a.total_ms, bytes=a.bytes) for a in arr]
 
     def close(self):
         if self.handle:

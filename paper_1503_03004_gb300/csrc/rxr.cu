@@ -17,7 +17,19 @@
 //     The residual R is formed in float64; the small correction may be formed
 //     in float32.  Each step contracts the error by roughly the eigenbasis error,
 //     so two or three steps reach float64 round-off.
+//
+// GB300 runs float64 at about 2 FMA per clock per SM, so one r = 64 product (262k FMA)
+// takes ~60 us on one SM.  The kernel therefore runs as a thread-block cluster: every
+// CTA keeps full copies of the r x r matrices in shared memory, computes a slice of rows
+// of each float64 product, and pushes its rows to the other CTAs through distributed
+// shared memory.  Everything else (float32 Jacobi, element-wise steps, scalar decisions)
+// is computed redundantly and identically by every CTA, so control flow stays uniform
+// across the cluster; only rank 0 writes to global memory.
+#include <cooperative_groups.h>
+
 #include "sfr_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace sfr {
 namespace {
@@ -42,6 +54,38 @@ __device__ void mm(const T* A, const T* B, T* C, int r) {
     C[i * LD + j] = acc;
   }
   __syncthreads();
+}
+
+// C = op(A) op(B) for float64, rows split across the cluster and broadcast through DSMEM.
+// C must not alias A or B.  On return every CTA holds the full product.
+template <bool TA, bool TB>
+__device__ void mm_dist(const double* A, const double* B, double* C, int r) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int rpc = (r + cs - 1) / cs, i0 = min(r, rank * rpc), i1 = min(r, i0 + rpc);
+  const int nloc = (i1 - i0) * r;
+  for (int e = threadIdx.x; e < nloc; e += blockDim.x) {
+    const int i = i0 + e / r, j = e % r;
+    double acc = 0.0;
+    for (int k = 0; k < r; ++k) {
+      const double a = TA ? A[k * LD + i] : A[i * LD + k];
+      const double b = TB ? B[j * LD + k] : B[k * LD + j];
+      acc = fma(a, b, acc);
+    }
+    C[i * LD + j] = acc;
+  }
+  __syncthreads();
+  if (cs > 1) {
+    cl.sync();  // every CTA is past its earlier reads of C
+    for (int q = 1; q < cs; ++q) {
+      double* Cq = cl.map_shared_rank(C, (rank + q) % cs);
+      for (int e = threadIdx.x; e < nloc; e += blockDim.x) {
+        const int i = i0 + e / r, j = e % r;
+        Cq[i * LD + j] = C[i * LD + j];
+      }
+    }
+    cl.sync();  // all rows have arrived everywhere
+  }
 }
 
 __device__ double block_reduce(double v, double* red, bool take_max) {
@@ -74,7 +118,9 @@ __device__ void jacobi_f32(float* A, float* Q, int n2, int max_sweeps, double* r
     }
     off = block_reduce(off, red, false);
     dia = block_reduce(dia, red, false);
-    if (!(off > 4e-13 * dia)) break;
+    // off-diagonal mass below (3e-5)^2 of the diagonal: the float64 Newton steps that follow
+    // contract the remaining error by about this factor per step, so stop here
+    if (!(off > 1e-9 * dia)) break;
     for (int step = 0; step < n2 - 1; ++step) {
       if (threadIdx.x < np) {
         const int k = threadIdx.x;
@@ -139,19 +185,35 @@ struct RxrSmem {
   int bad;
 };
 
+// Sum of `count` r x r partials (fixed order); rows split across the cluster, then broadcast.
 __device__ void load_gram(const double* __restrict__ parts, int count, int rp, int r, double* dst) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int rpc = (r + cs - 1) / cs, i0 = min(r, rank * rpc), i1 = min(r, i0 + rpc);
+  const int nloc = (i1 - i0) * r;
   const int rpsq = rp * rp;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    const int i = e / r, j = e % r;
+  for (int e = threadIdx.x; e < nloc; e += blockDim.x) {
+    const int i = i0 + e / r, j = e % r;
     double v = 0.0;
-    for (int c = 0; c < count; ++c) v += parts[(int64_t)c * rpsq + i * rp + j];  // fixed order
+    for (int c = 0; c < count; ++c) v += parts[(int64_t)c * rpsq + i * rp + j];
     dst[i * LD + j] = v;
   }
   __syncthreads();
+  if (cs > 1) {
+    cl.sync();
+    for (int q = 1; q < cs; ++q) {
+      double* Dq = cl.map_shared_rank(dst, (rank + q) % cs);
+      for (int e = threadIdx.x; e < nloc; e += blockDim.x) {
+        const int i = i0 + e / r, j = e % r;
+        Dq[i * LD + j] = dst[i * LD + j];
+      }
+    }
+    cl.sync();
+  }
 }
 
 __device__ void fail(DevState* st, int code) {
-  if (threadIdx.x == 0) { st->status = code; st->done = 1; }
+  if (threadIdx.x == 0 && cg::this_cluster().block_rank() == 0) { st->status = code; st->done = 1; }
 }
 
 // v_side = false: T_U = B (B G_P B)^{-1/2}.
@@ -171,8 +233,8 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
   load_gram(parts, count, rp, r, S.T2);
   for (int e = tid; e < r * r; e += blockDim.x) S.B[(e / r) * LD + e % r] = Bg[(e / r) * rp + e % r];
   __syncthreads();
-  mm<double, false, false>(S.T2, S.B, S.T1, r);
-  mm<double, false, false>(S.B, S.T1, S.Z, r);
+  mm_dist<false, false>(S.T2, S.B, S.T1, r);
+  mm_dist<false, false>(S.B, S.T1, S.Z, r);
   if (tid == 0) {
     double tr = 0.0;
     for (int i = 0; i < r; ++i) tr += S.Z[i * LD + i];
@@ -198,7 +260,7 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
   __syncthreads();
   mm<float, false, false>(F1, S.Qf, F2, n2);
   mm<float, true, false>(S.Qf, F2, S.Af, n2);
-  jacobi_f32(S.Af, S.Qf, n2, 12, S.red, S.cs, S.sn, S.pp, S.qq);
+  jacobi_f32(S.Af, S.Qf, n2, 10, S.red, S.cs, S.sn, S.pp, S.qq);
   // re-orthonormalise the float basis: Q <- Q (3I - Q^T Q) / 2
   mm<float, true, false>(S.Qf, S.Qf, F1, r);
   for (int e = tid; e < r * r; e += blockDim.x) {
@@ -212,7 +274,7 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
   // 3. float64 Rayleigh quotients lambda_p = q_p^T K q_p / q_p^T q_p
   for (int e = tid; e < r * r; e += blockDim.x) S.T1[(e / r) * LD + e % r] = (double)S.Qf[(e / r) * LD + e % r];
   __syncthreads();
-  mm<double, false, false>(S.K, S.T1, S.T2, r);
+  mm_dist<false, false>(S.K, S.T1, S.T2, r);
   for (int p = tid; p < r; p += blockDim.x) {
     double num = 0.0, den = 0.0;
     for (int i = 0; i < r; ++i) {
@@ -227,7 +289,9 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
     for (int p = 1; p < r; ++p) { lo = fmin(lo, S.lam[p]); hi = fmax(hi, S.lam[p]); }
     // Eq. 9 needs rank r; the same relative cut as the oracle's eigenvalue check
     S.bad = !(lo > 1e-14 * hi);
-    if (v_side) st->lam_min_v = lo * S.scale; else st->lam_min_u = lo * S.scale;
+    if (cg::this_cluster().block_rank() == 0) {
+      if (v_side) st->lam_min_v = lo * S.scale; else st->lam_min_u = lo * S.scale;
+    }
     for (int p = 0; p < r; ++p) S.sq[p] = sqrt(fmax(S.lam[p], 1e-300));
   }
   __syncthreads();
@@ -238,11 +302,11 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
     S.T2[i * LD + j] = S.T1[i * LD + j] / S.sq[j];
   }
   __syncthreads();
-  mm<double, false, true>(S.T2, S.T1, S.Z, r);
+  mm_dist<false, true>(S.T2, S.T1, S.Z, r);
   // 5. Newton steps on Z K Z = I (residual in float64, correction in float32)
-  for (int it = 0; it < 5; ++it) {
-    mm<double, false, false>(S.K, S.Z, S.T1, r);
-    mm<double, false, false>(S.Z, S.T1, S.T2, r);
+  for (int it = 0; it < 6; ++it) {
+    mm_dist<false, false>(S.K, S.Z, S.T1, r);
+    mm_dist<false, false>(S.Z, S.T1, S.T2, r);
     double rmax = 0.0;
     for (int e = tid; e < r * r; e += blockDim.x) {
       const int i = e / r, j = e % r;
@@ -272,42 +336,89 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
   const double zs = 1.0 / sqrt(S.scale);
   for (int e = tid; e < r * r; e += blockDim.x) S.Z[(e / r) * LD + e % r] *= zs;
   __syncthreads();
-  mm<double, false, false>(S.B, S.Z, S.T1, r);
-  for (int e = tid; e < rpsq; e += blockDim.x) {
-    const int i = e / rp, j = e % rp;
-    const bool in = i < r && j < r;
-    Tout[e] = in ? S.T1[i * LD + j] : 0.0;
-    Qeig[e] = in ? S.Qf[i * LD + j] : (i == j ? 1.f : 0.f);
-  }
+  mm_dist<false, false>(S.B, S.Z, S.T1, r);
+  const bool writer = cg::this_cluster().block_rank() == 0;
+  if (writer)
+    for (int e = tid; e < rpsq; e += blockDim.x) {
+      const int i = e / rp, j = e % rp;
+      const bool in = i < r && j < r;
+      Tout[e] = in ? S.T1[i * LD + j] : 0.0;
+      Qeig[e] = in ? S.Qf[i * LD + j] : (i == j ? 1.f : 0.f);
+    }
   if (!v_side) return;
   // 7. B_bar = Sym(G_W T_V) (Eq. 10 with W = X^T U_bar), T_C = T_V B_bar
   load_gram(parts, count, rp, r, S.K);
-  mm<double, false, false>(S.K, S.T1, S.T2, r);
+  mm_dist<false, false>(S.K, S.T1, S.T2, r);
   for (int e = tid; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
     S.Z[i * LD + j] = 0.5 * (S.T2[i * LD + j] + S.T2[j * LD + i]);
   }
   __syncthreads();
-  mm<double, false, false>(S.T1, S.Z, S.T2, r);
-  for (int e = tid; e < rpsq; e += blockDim.x) {
-    const int i = e / rp, j = e % rp;
-    const bool in = i < r && j < r;
-    Bg[e] = in ? S.Z[i * LD + j] : 0.0;
-    TCout[e] = in ? S.T2[i * LD + j] : 0.0;
-  }
+  mm_dist<false, false>(S.T1, S.Z, S.T2, r);
+  if (writer)
+    for (int e = tid; e < rpsq; e += blockDim.x) {
+      const int i = e / rp, j = e % rp;
+      const bool in = i < r && j < r;
+      Bg[e] = in ? S.Z[i * LD + j] : 0.0;
+      TCout[e] = in ? S.T2[i * LD + j] : 0.0;
+    }
 }
 
 }  // namespace
+
+// Cluster size for the r x r kernel: 16 CTAs (non-portable size) when the device accepts it
+// with this kernel's shared memory, else 8, else a single CTA.
+static int rxr_cluster_size(size_t smem) {
+  static int cached = 0;
+  if (cached) return cached;
+  int best = 1;
+  if (cudaFuncSetAttribute(rxr_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    cudaGetLastError();
+  for (int cs : {16, 8}) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = cs;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, rxr_kernel, &cfg) == cudaSuccess && nclusters > 0) {
+      best = cs;
+      break;
+    }
+    cudaGetLastError();
+  }
+  cached = best;
+  return best;
+}
 
 cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream_t st) {
   const size_t smem = sizeof(RxrSmem);
   cudaError_t e = cudaFuncSetAttribute(rxr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  const int cs = rxr_cluster_size(smem);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeClusterDimension;
+  at.val.clusterDim.x = cs;
+  at.val.clusterDim.y = 1;
+  at.val.clusterDim.z = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
   if (v_side)
-    rxr_kernel<<<1, kThreads, smem, st>>>(b.GWpart, s.gw_blocks, s.rp, s.r, b.B, b.TV, b.TCm, b.Qeig_v, 1, b.st);
-  else
-    rxr_kernel<<<1, kThreads, smem, st>>>(b.GPpart, s.gp_blocks, s.rp, s.r, b.B, b.TU, nullptr, b.Qeig_u, 0, b.st);
-  return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, rxr_kernel, (const double*)b.GWpart, s.gw_blocks, s.rp, s.r, b.B, b.TV, b.TCm,
+                              b.Qeig_v, 1, b.st);
+  return cudaLaunchKernelEx(&cfg, rxr_kernel, (const double*)b.GPpart, s.gp_blocks, s.rp, s.r, b.B, b.TU,
+                            (double*)nullptr, b.Qeig_u, 0, b.st);
 }
 
 }  // namespace sfr

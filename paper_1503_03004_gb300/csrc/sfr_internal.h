@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/sfr.h"
+#include "tc_sweep.h"
 
 namespace sfr {
 
@@ -75,6 +76,8 @@ struct Buffers {
   float* Qeig_v;        // rp x rp : last V-side eigenvectors
   DevState* st;
   int u_cur;            // which U buffer holds the current U_bar (host-side bookkeeping)
+  bool tc;              // tensor-core path (mixed precision, r <= 64, bfloat16 M)
+  TcBuffers t;          // its extra buffers (Y[] above alias t.Y[] when tc)
 };
 
 // ---- kernel launchers (sweep.cu / rxr.cu) ----
@@ -82,7 +85,8 @@ struct Buffers {
 
 cudaError_t launch_norm_m(const Shape& s, const Buffers& b, cudaStream_t st);
 cudaError_t launch_init_p(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st);
-cudaError_t launch_gram_p(const Shape& s, const Buffers& b, bool fp64, bool sum_parts, cudaStream_t st);
+cudaError_t launch_gram_p(const Shape& s, const Buffers& b, bool fp64, bool sum_parts, cudaStream_t st,
+                          const void* addA = nullptr, const double* H = nullptr);
 cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream_t st);
 cudaError_t launch_apply_u(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st);
 cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first, int u_new, cudaStream_t st);
@@ -91,7 +95,7 @@ cudaError_t launch_apply_v(const Shape& s, const Buffers& b, bool fp64, cudaStre
 cudaError_t launch_sweep(const Shape& s, const Buffers& b, bool fp64, int u_cur, cudaStream_t st);
 cudaError_t launch_iter_end(const Shape& s, const Buffers& b, cudaStream_t st);
 cudaError_t launch_finalize(const Shape& s, const Buffers& b, bool fp64, int u_cur, void* S, sfr_dtype s_dtype,
-                            int64_t lds, void* L, cudaStream_t st);
+                            int64_t lds, void* L, cudaStream_t st);  // Y is bfloat16 (ld t.ldy) when b.tc
 cudaError_t launch_export_factors(const Shape& s, const Buffers& b, bool fp64, int u_cur, double* U, double* V,
                                   cudaStream_t st);
 
@@ -106,7 +110,7 @@ inline int pad_rank(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 32 ? 32 : 6
 
 // ---- host helpers shared by the entry points (solver.cu)
 Shape plan_shape(int64_t m, int64_t n, int64_t ldm, int r, int num_sms);
-size_t carve(const Shape& s, bool fp64, void* base, Buffers* b);  // base == nullptr: size only
+size_t carve(const Shape& s, bool fp64, void* base, Buffers* b, bool tc = false);  // base == nullptr: size only
 double host_lambda_min(std::vector<double> A, int r);
 int ctx_device(const sfr_ctx* ctx);
 int ctx_num_sms(const sfr_ctx* ctx);

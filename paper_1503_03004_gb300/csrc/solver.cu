@@ -103,32 +103,52 @@ Shape plan_shape(int64_t m, int64_t n, int64_t ldm, int r, int num_sms) {
   s.wpass_grid_x = (int)((n + kWBN - 1) / kWBN);
   int64_t rtiles = (m + kWBM - 1) / kWBM;
   int64_t nc = std::max<int64_t>(1, std::min<int64_t>(rtiles, (target + s.wpass_grid_x - 1) / s.wpass_grid_x));
+  // chunks are whole multiples of 64 rows (the tensor-core W pass loads 64-row blocks)
   int64_t rtpc = (rtiles + nc - 1) / nc;
-  s.rows_per_chunk = (int)(rtpc * kWBM);
+  s.rows_per_chunk = (int)(((rtpc * kWBM) + 63) / 64 * 64);
   s.nchunk = (int)((m + s.rows_per_chunk - 1) / s.rows_per_chunk);
   s.gram_rows = kGramRows;
-  s.gp_blocks = (int)((m + kGramRows - 1) / kGramRows);
-  s.gw_blocks = (int)((n + kGramRows - 1) / kGramRows);
+  // thin kernels loop over 64-row tiles with at most one CTA per SM, which bounds the
+  // number of r x r partials the projector kernels reduce
+  s.gp_blocks = (int)std::min<int64_t>((m + kGramRows - 1) / kGramRows, num_sms);
+  s.gw_blocks = (int)std::min<int64_t>((n + kGramRows - 1) / kGramRows, num_sms);
   return s;
 }
 
 // Lay out every buffer of one solve inside `base` (or just size it when base == nullptr).
-size_t carve(const Shape& s, bool fp64, void* base, Buffers* b) {
-  const size_t tc = fp64 ? 8 : 4;
+size_t carve(const Shape& s, bool fp64, void* base, Buffers* b, bool tc) {
+  const size_t tcb = fp64 ? 8 : 4;
   const size_t rp = s.rp, rpsq = rp * rp;
   Carver c(base);
   Buffers x{};
-  x.Y[0] = c.take(tc * s.m * s.n);
-  x.Y[1] = c.take(tc * s.m * s.n);
-  x.D = c.take(tc * s.m * s.n);
-  x.P = c.take(tc * s.m * rp);
-  x.U[0] = c.take(tc * s.m * rp);
-  x.U[1] = c.take(tc * s.m * rp);
-  x.W = c.take(tc * s.n * rp);
-  x.V = c.take(tc * s.n * rp);
-  x.C = c.take(tc * s.n * rp);
-  x.Qpart = c.take(tc * s.nsplit * s.m * rp);
-  x.Wpart = c.take(tc * s.nchunk * s.n * rp);
+  x.tc = tc;
+  if (tc) {
+    // tensor-core path: bfloat16 multiplier and transposed Delta, plus the MMA operand copies
+    x.t.ldy = (s.n + 63) / 64 * 64;
+    x.t.ldd = (s.m + 63) / 64 * 64;
+    x.t.Y[0] = x.Y[0] = c.take(2 * s.m * x.t.ldy);
+    x.t.Y[1] = x.Y[1] = c.take(2 * s.m * x.t.ldy);
+    x.t.Dt = c.take(2 * s.n * x.t.ldd);
+    x.D = nullptr;
+    x.t.Uh = static_cast<float*>(c.take(4 * s.m * 64));
+    x.t.Ul = static_cast<float*>(c.take(4 * s.m * 64));
+    x.t.Ut = c.take(2 * 64 * x.t.ldd);
+    x.t.Ch = static_cast<float*>(c.take(4 * s.n * 64));
+    x.t.Cl = static_cast<float*>(c.take(4 * s.n * 64));
+    x.t.Vt = c.take(2 * 64 * x.t.ldy);
+  } else {
+    x.Y[0] = c.take(tcb * s.m * s.n);
+    x.Y[1] = c.take(tcb * s.m * s.n);
+    x.D = c.take(tcb * s.m * s.n);
+  }
+  x.P = c.take(tcb * s.m * rp);
+  x.U[0] = c.take(tcb * s.m * rp);
+  x.U[1] = c.take(tcb * s.m * rp);
+  x.W = c.take(tcb * s.n * rp);
+  x.V = c.take(tcb * s.n * rp);
+  x.C = c.take(tcb * s.n * rp);
+  x.Qpart = c.take(tcb * s.nsplit * s.m * rp);
+  x.Wpart = c.take(tcb * s.nchunk * s.n * rp);
   x.GPpart = static_cast<double*>(c.take(8 * rpsq * s.gp_blocks));
   x.GWpart = static_cast<double*>(c.take(8 * rpsq * s.gw_blocks));
   x.Hpart = static_cast<double*>(c.take(8 * rpsq * (s.gp_blocks + 1)));
@@ -160,6 +180,8 @@ struct Solver {
   cudaGraphExec_t graph = nullptr;
   std::string graph_key;
   int graph_kernels = 0;
+  TcMaps maps;          // tensor maps of the current tensor-core solve (captured by value in graphs)
+  bool last_tc = false; // whether the last solve took the tensor-core path
   // profiling: kernel counters and events (slot 0: eager iteration, slots 1-2: the graph's two)
   bool profile = false;
   bool count_stats = false;
@@ -167,6 +189,8 @@ struct Solver {
   int64_t launches[SFR_STAT_COUNT] = {};
   int64_t timed[SFR_STAT_COUNT] = {};
   double total_ms[SFR_STAT_COUNT] = {};
+  double bytes[SFR_STAT_COUNT] = {};
+  double sweep_bytes = 0, wpass_bytes = 0, wpass_first_bytes = 0;  // per launch, set per solve
   cudaEvent_t ev[3][4][2] = {};
 
   ~Solver() {
@@ -204,9 +228,11 @@ struct Solver {
       SFR_CUDA(cudaEventElapsedTime(&ms, ev[sl][0][0], ev[sl][0][1]));
       total_ms[SFR_STAT_SWEEP] += ms;
       timed[SFR_STAT_SWEEP] += 1;
+      bytes[SFR_STAT_SWEEP] += sweep_bytes;
       SFR_CUDA(cudaEventElapsedTime(&ms, ev[sl][1][0], ev[sl][1][1]));
       total_ms[SFR_STAT_WPASS] += ms;
       timed[SFR_STAT_WPASS] += 1;
+      bytes[SFR_STAT_WPASS] += sl == 0 ? wpass_first_bytes : wpass_bytes;
       for (int k = 2; k < 4; ++k) {
         SFR_CUDA(cudaEventElapsedTime(&ms, ev[sl][k][0], ev[sl][k][1]));
         total_ms[SFR_STAT_RXR] += ms;
@@ -221,6 +247,7 @@ struct Solver {
 
   // Enqueue one FR-ADM iteration; returns the number of kernels it launches.
   int enqueue_iteration(const Shape& s, Buffers& b, bool fp64, bool first, int slot) {
+    if (b.tc) return enqueue_iteration_tc(s, b, first, slot);
     cudaStream_t st = stream;
     int kernels = 0;
     if (first) {
@@ -244,16 +271,68 @@ struct Solver {
     return kernels;
   }
 
+  // The same iteration on the tensor-core path (mixed precision, bfloat16 storage, r <= 64).
+  int enqueue_iteration_tc(const Shape& s, Buffers& b, bool first, int slot) {
+    cudaStream_t st = stream;
+    int kernels = 0;
+    if (first) {
+      SFR_CUDA(tc_launch_transpose_m(s, b.M, s.ldm, b.t, st));                // Dt <- M^T (X_1 = M)
+      SFR_CUDA(launch_init_p(s, b, false, st));
+      SFR_CUDA(launch_gram_p(s, b, false, false, st));
+      kernels += 3;
+    }
+    timed_launch(slot, 2, [&] { return launch_rxr(s, b, false, st); });      // T_U
+    SFR_CUDA(launch_apply_u(s, b, false, first, st));                         // U_bar = P T_U
+    const int u_new = 1 - b.u_cur;
+    const float* Unew = static_cast<const float*>(b.U[u_new]);
+    SFR_CUDA(tc_launch_prep_u(s, Unew, b.t, b.st, st));                       // TF32 split, U^T
+    timed_launch(slot, 1, [&] { return tc_launch_wpass(s, maps, static_cast<float*>(b.Wpart), b.st, st); });
+    SFR_CUDA(launch_wfinal(s, b, false, first, st));                          // W, G_W partials
+    timed_launch(slot, 3, [&] { return launch_rxr(s, b, true, st); });       // T_V, B_bar, T_C
+    SFR_CUDA(launch_apply_v(s, b, false, st));                                // V_bar, C
+    SFR_CUDA(tc_launch_prep_v(s, static_cast<const float*>(b.C), static_cast<const float*>(b.V), b.t, b.st, st));
+    const int y_in = b.Y[0] == b.t.Y[0] ? 0 : 1;
+    timed_launch(slot, 0, [&] {
+      return tc_launch_sweep(s, maps, y_in, static_cast<float*>(b.Qpart), b.resid_part, b.st, st);
+    });
+    SFR_CUDA(launch_iter_end(s, b, st));
+    // P_{k+1} = U_bar B_bar + Delta V_bar  (L V_bar = U_bar B_bar since V_bar^T V_bar = I)
+    SFR_CUDA(launch_gram_p(s, b, false, true, st, b.U[u_new], b.B));
+    kernels += first ? 11 : 12;
+    b.u_cur = u_new;
+    std::swap(b.Y[0], b.Y[1]);
+    return kernels;
+  }
+
   // Runs Algorithm 1 on a device-resident M.  Returns the final host copy of the state and
   // fills U/V/B/S/L (device pointers) as requested.
   DevState run(const sfr_problem& p, const void* Mdev, double* Udev, double* Bdev, double* Vdev, void* Sdev,
                sfr_dtype s_dtype, int64_t lds, void* Ldev) {
     const bool fp64 = p.precision == SFR_PREC_FP64;
-    const Shape s = plan_shape(p.m, p.n, p.ldm, p.r, num_sms);
+    const Shape s0 = plan_shape(p.m, p.n, p.ldm, p.r, num_sms);
+    const bool tc = !fp64 && tc_supported(s0, p.m_dtype, p.ldm) && ((uintptr_t)Mdev % 16) == 0;
+    last_tc = tc;
+    Shape s = s0;
+    if (tc) {
+      // tensor-core sweep: 128-row CTAs over the whole column range (one P partial per row)
+      s.sweep_grid_x = (int)((p.m + 127) / 128);
+      s.nsplit = 1;
+      s.cols_per_split = (int)((p.n + 63) / 64 * 64);
+    }
     Buffers b{};
-    const size_t bytes = carve(s, fp64, nullptr, nullptr);
+    const size_t bytes = carve(s, fp64, nullptr, nullptr, tc);
     work.ensure(bytes, &held, budget);
-    carve(s, fp64, work.ptr, &b);
+    carve(s, fp64, work.ptr, &b, tc);
+    if (tc) SFR_CUDA(tc_make_maps(s, b.t, Mdev, p.ldm, &maps));
+    {
+      // algorithmic bytes per element: sweep reads M and Y_k, writes Y_{k+1} and Delta; the W pass
+      // reads Delta (iteration 1: M, or M^T on the tensor-core path)
+      const double mn = (double)s.m * s.n, bm = (double)dtype_size(p.m_dtype);
+      const double by = tc ? 2 : (fp64 ? 8 : 4), bd = tc ? 2 : (fp64 ? 8 : 4);
+      sweep_bytes = mn * (bm + 2 * by + bd);
+      wpass_bytes = mn * bd;
+      wpass_first_bytes = mn * (tc ? 2 : bm);
+    }
     b.M = Mdev;
     b.m_dtype = p.m_dtype;
     b.u_cur = 0;
@@ -268,8 +347,8 @@ struct Solver {
     h.max_iter = p.fixed_iters > 0 ? p.fixed_iters : p.max_iter;
     h.status = SFR_OK;
     SFR_CUDA(cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, stream));
-    const size_t tc = fp64 ? 8 : 4;
-    SFR_CUDA(cudaMemsetAsync(b.Y[0], 0, tc * s.m * s.n, stream));  // Y_1 = 0
+    const size_t ybytes = tc ? 2 * (size_t)s.m * b.t.ldy : (fp64 ? 8 : 4) * (size_t)s.m * s.n;
+    SFR_CUDA(cudaMemsetAsync(b.Y[0], 0, ybytes, stream));  // Y_1 = 0
     std::vector<double> eye(s.rp * s.rp, 0.0);
     std::vector<float> eyef(s.rp * s.rp, 0.f);
     for (int i = 0; i < s.rp; ++i) {
@@ -294,7 +373,7 @@ struct Solver {
     // after the stop flag is set, so overshooting the last iteration costs only launches.
     const std::string key0 = fmt("%p/%lld/%lld/%lld/%d/%d/%p", work.ptr, (long long)s.m, (long long)s.n,
                                 (long long)s.ldm, s.r, (int)fp64, Mdev) +
-                            fmt("/%d", (int)p.m_dtype);
+                            fmt("/%d/%d", (int)p.m_dtype, (int)tc);
     const std::string key = key0;
     if (graph_key != key + (profile ? "/p" : "")) {
       if (graph) {
@@ -723,12 +802,14 @@ sfr_status sfr_stats(sfr_ctx* ctx, sfr_kernel_stat* out, int32_t count, int32_t 
     out[k].launches = sv.launches[k];
     out[k].timed = sv.timed[k];
     out[k].total_ms = sv.total_ms[k];
+    out[k].bytes = sv.bytes[k];
   }
   if (reset)
     for (int k = 0; k < SFR_STAT_COUNT; ++k) {
       sv.launches[k] = 0;
       sv.timed[k] = 0;
       sv.total_ms[k] = 0.0;
+      sv.bytes[k] = 0.0;
     }
   return SFR_OK;
 }

@@ -82,8 +82,9 @@ __global__ void init_p_kernel(const TMs* __restrict__ M, int64_t m, int64_t ldm,
 }
 
 // ---------------------------------------------------------------- thin reduce + Gram partials
-// out[i][:] = sum_s parts[s][i][:]  (+ addA[i][:] * H when addA != nullptr), for rows i of
-// this CTA, then gpart[cta] = sum_i out[i]^T out[i]  (r x r, row block of kGramRows rows).
+// For every 64-row tile handled by this CTA (tiles blockIdx.x, blockIdx.x + gridDim.x, ...):
+// out[i][:] = sum_s parts[s][i][:]  (+ addA[i][:] * H when addA != nullptr), then the CTA's
+// Gram partial gpart[cta] = sum over its rows of out[i]^T out[i]  (r x r).
 // nparts == 0 leaves `out` as it is and only forms the Gram partial.
 template <typename TC, int RP>
 __global__ void __launch_bounds__(256) thin_gram_kernel(const TC* __restrict__ parts, int nparts, int64_t part_stride,
@@ -91,56 +92,73 @@ __global__ void __launch_bounds__(256) thin_gram_kernel(const TC* __restrict__ p
                                                         const double* __restrict__ H, double* __restrict__ gpart,
                                                         const DevState* st) {
   if (stopped(st)) return;
+  constexpr int GPT = (RP * RP + 255) / 256;  // Gram entries per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto tile = reinterpret_cast<TC(*)[RP + 1]>(smem_raw);              // [kGramRows][RP + 1]
   auto Hs = reinterpret_cast<TC(*)[RP + 1]>(smem_raw + sizeof(TC) * kGramRows * (RP + 1));  // [RP][RP + 1]
-  const int64_t i0 = (int64_t)blockIdx.x * kGramRows;
   if (addA)
     for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) Hs[e / RP][e % RP] = (TC)H[e];
-  __syncthreads();
-  for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
-    int ii = e / RP, a = e % RP;
-    int64_t i = i0 + ii;
-    TC v = 0;
-    if (i < rows) {
-      if (nparts == 0) {
-        v = out[i * RP + a];
-      } else {
-        for (int s = 0; s < nparts; ++s) v += parts[s * part_stride + i * RP + a];
-        if (addA) {
-          TC acc = 0;
+  TC g[GPT];
+#pragma unroll
+  for (int q = 0; q < GPT; ++q) g[q] = 0;
+  const int64_t ntiles = (rows + kGramRows - 1) / kGramRows;
+  for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+    const int64_t i0 = tl * kGramRows;
+    __syncthreads();  // previous tile consumed; Hs visible
+    for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
+      int ii = e / RP, a = e % RP;
+      int64_t i = i0 + ii;
+      TC v = 0;
+      if (i < rows) {
+        if (nparts == 0) {
+          v = out[i * RP + a];
+        } else {
+          for (int s = 0; s < nparts; ++s) v += parts[s * part_stride + i * RP + a];
+          if (addA) {
+            TC acc = 0;
 #pragma unroll 8
-          for (int b = 0; b < RP; ++b) acc += addA[i * RP + b] * Hs[b][a];
-          v += acc;
+            for (int b = 0; b < RP; ++b) acc += addA[i * RP + b] * Hs[b][a];
+            v += acc;
+          }
+          out[i * RP + a] = v;
         }
-        out[i * RP + a] = v;
+      }
+      tile[ii][a] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < GPT; ++q) {
+      const int e = threadIdx.x + q * 256;
+      if (e < RP * RP) {
+        const int a = e / RP, b = e % RP;
+        TC acc = 0;
+#pragma unroll 8
+        for (int ii = 0; ii < kGramRows; ++ii) acc += tile[ii][a] * tile[ii][b];
+        g[q] += acc;
       }
     }
-    tile[ii][a] = v;
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
-    int a = e / RP, b = e % RP;
-    TC acc = 0;
-#pragma unroll 8
-    for (int ii = 0; ii < kGramRows; ++ii) acc += tile[ii][a] * tile[ii][b];
-    gpart[(int64_t)blockIdx.x * RP * RP + e] = (double)acc;
+#pragma unroll
+  for (int q = 0; q < GPT; ++q) {
+    const int e = threadIdx.x + q * 256;
+    if (e < RP * RP) gpart[(int64_t)blockIdx.x * RP * RP + e] = (double)g[q];
   }
 }
 
-// Sum of `count` rp x rp double partials into out (one CTA, fixed order).
+// Sum of `count` rp x rp double partials into out (one thread per entry, fixed order).
 __global__ void reduce_sq_kernel(const double* __restrict__ parts, int count, int rpsq, double* out, const DevState* st) {
   if (stopped(st)) return;
-  for (int e = threadIdx.x; e < rpsq; e += blockDim.x) {
-    double v = 0.0;
-    for (int c = 0; c < count; ++c) v += parts[(int64_t)c * rpsq + e];
-    out[e] = v;
-  }
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rpsq) return;
+  double v = 0.0;
+  for (int c = 0; c < count; ++c) v += parts[(int64_t)c * rpsq + e];
+  out[e] = v;
 }
 
 // ---------------------------------------------------------------- thin row transform
 // dst[i][:] = src[i][:] T   (T rp x rp, float64 in global), optional second output
-// dst2 = src T2, and optional Gram-like partial hpart[cta] = sum_i old[i]^T dst[i].
+// dst2 = src T2, and optional partial hpart[cta] = sum over the CTA's rows of old[i]^T dst[i].
+// Each CTA handles 64-row tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 template <typename TC, int RP>
 __global__ void __launch_bounds__(256) row_transform_kernel(const TC* __restrict__ src, int64_t rows,
                                                             const double* __restrict__ T, TC* __restrict__ dst,
@@ -148,54 +166,70 @@ __global__ void __launch_bounds__(256) row_transform_kernel(const TC* __restrict
                                                             const TC* __restrict__ old, double* __restrict__ hpart,
                                                             const DevState* st) {
   if (stopped(st)) return;
+  constexpr int GPT = (RP * RP + 255) / 256;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto Ts = reinterpret_cast<TC(*)[RP + 1]>(smem_raw);                                   // [RP][RP + 1]
-  auto srow = reinterpret_cast<TC(*)[RP + 1]>(smem_raw + sizeof(TC) * RP * (RP + 1));    // [kGramRows][RP + 1]
-  auto drow = reinterpret_cast<TC(*)[RP + 1]>(smem_raw + sizeof(TC) * (RP + kGramRows) * (RP + 1));
-  const int64_t i0 = (int64_t)blockIdx.x * kGramRows;
-  for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) Ts[e / RP][e % RP] = (TC)T[e];
-  for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
-    int ii = e / RP, a = e % RP;
-    int64_t i = i0 + ii;
-    srow[ii][a] = i < rows ? src[i * RP + a] : (TC)0;
+  auto T2s = reinterpret_cast<TC(*)[RP + 1]>(smem_raw + sizeof(TC) * RP * (RP + 1));     // [RP][RP + 1]
+  auto srow = reinterpret_cast<TC(*)[RP + 1]>(smem_raw + sizeof(TC) * 2 * RP * (RP + 1));  // [kGramRows][RP + 1]
+  auto drow = reinterpret_cast<TC(*)[RP + 1]>(smem_raw + sizeof(TC) * (2 * RP + kGramRows) * (RP + 1));
+  for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
+    Ts[e / RP][e % RP] = (TC)T[e];
+    if (T2) T2s[e / RP][e % RP] = (TC)T2[e];
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
-    int ii = e / RP, a = e % RP;
-    TC acc = 0;
-#pragma unroll 8
-    for (int b = 0; b < RP; ++b) acc += srow[ii][b] * Ts[b][a];
-    drow[ii][a] = acc;
-    int64_t i = i0 + ii;
-    if (i < rows) dst[i * RP + a] = acc;
-  }
-  if (T2) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) Ts[e / RP][e % RP] = (TC)T2[e];
+  TC h[GPT];
+#pragma unroll
+  for (int q = 0; q < GPT; ++q) h[q] = 0;
+  const int64_t ntiles = (rows + kGramRows - 1) / kGramRows;
+  for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+    const int64_t i0 = tl * kGramRows;
     __syncthreads();
     for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
       int ii = e / RP, a = e % RP;
-      TC acc = 0;
-#pragma unroll 8
-      for (int b = 0; b < RP; ++b) acc += srow[ii][b] * Ts[b][a];
       int64_t i = i0 + ii;
-      if (i < rows) dst2[i * RP + a] = acc;
+      srow[ii][a] = i < rows ? src[i * RP + a] : (TC)0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
+      int ii = e / RP, a = e % RP;
+      TC acc = 0, acc2 = 0;
+#pragma unroll 8
+      for (int b = 0; b < RP; ++b) {
+        acc += srow[ii][b] * Ts[b][a];
+        if (T2) acc2 += srow[ii][b] * T2s[b][a];
+      }
+      drow[ii][a] = acc;
+      int64_t i = i0 + ii;
+      if (i < rows) {
+        dst[i * RP + a] = acc;
+        if (T2) dst2[i * RP + a] = acc2;
+      }
+    }
+    if (hpart) {
+      __syncthreads();  // srow reused for the old rows
+      for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
+        int ii = e / RP, a = e % RP;
+        int64_t i = i0 + ii;
+        srow[ii][a] = i < rows ? old[i * RP + a] : (TC)0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < GPT; ++q) {
+        const int e = threadIdx.x + q * 256;
+        if (e < RP * RP) {
+          const int a = e / RP, b = e % RP;
+          TC acc = 0;
+#pragma unroll 8
+          for (int ii = 0; ii < kGramRows; ++ii) acc += srow[ii][a] * drow[ii][b];
+          h[q] += acc;
+        }
+      }
     }
   }
   if (hpart) {
-    __syncthreads();  // srow reused for the old rows
-    for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
-      int ii = e / RP, a = e % RP;
-      int64_t i = i0 + ii;
-      srow[ii][a] = i < rows ? old[i * RP + a] : (TC)0;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
-      int a = e / RP, b = e % RP;
-      TC acc = 0;
-#pragma unroll 8
-      for (int ii = 0; ii < kGramRows; ++ii) acc += srow[ii][a] * drow[ii][b];
-      hpart[(int64_t)blockIdx.x * RP * RP + e] = (double)acc;
+#pragma unroll
+    for (int q = 0; q < GPT; ++q) {
+      const int e = threadIdx.x + q * 256;
+      if (e < RP * RP) hpart[(int64_t)blockIdx.x * RP * RP + e] = (double)h[q];
     }
   }
 }
@@ -417,9 +451,9 @@ __global__ void norm_finish_kernel(const double* __restrict__ part, int count, D
 // ---------------------------------------------------------------- outputs
 // S = P_ST_{1/mu}(M - L + Y_prev / mu) with the mu, Y_prev and factors of the last iteration
 // (Algorithm 1 returns L_k, S_k); optionally L itself.
-template <typename TC, typename TMs, typename TSo, int RP>
+template <typename TC, typename TMs, typename TSo, typename TY, int RP>
 __global__ void __launch_bounds__(256) finalize_kernel(const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm,
-                                                       const TC* __restrict__ Yprev, const TC* __restrict__ U,
+                                                       const TY* __restrict__ Yprev, int64_t ldy, const TC* __restrict__ U,
                                                        const TC* __restrict__ C, TSo* __restrict__ S, TSo* __restrict__ L,
                                                        int64_t lds, const DevState* st) {
   __shared__ TC us[8][RP];
@@ -442,7 +476,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const TMs* __restrict__ M
   for (int a = 0; a < RP; ++a) l += us[ti][a] * cs[tj][a];
   const double mu = st->mu_last;
   const TC inv_mu = (TC)(1.0 / mu);
-  const TC z = ld_as<TC, TMs>(M + i * ldm + j) - l + Yprev[i * n + j] * inv_mu;
+  const TC z = ld_as<TC, TMs>(M + i * ldm + j) - l + ld_as<TC, TY>(Yprev + i * ldy + j) * inv_mu;
   const TC sv = z > inv_mu ? z - inv_mu : (z < -inv_mu ? z + inv_mu : (TC)0);
   if (S) S[i * lds + j] = (TSo)sv;
   if (L) L[i * lds + j] = (TSo)l;
@@ -490,7 +524,7 @@ inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b);
 template <typename TC, int RP>
 size_t gram_smem() { return sizeof(TC) * (size_t)(kGramRows + RP) * (RP + 1); }
 template <typename TC, int RP>
-size_t transform_smem() { return sizeof(TC) * (size_t)(RP + 2 * kGramRows) * (RP + 1); }
+size_t transform_smem() { return sizeof(TC) * (size_t)(2 * RP + 2 * kGramRows) * (RP + 1); }
 
 template <typename K>
 cudaError_t allow_smem(K kern, size_t bytes) {
@@ -522,7 +556,8 @@ cudaError_t launch_init_p(const Shape& s, const Buffers& b, bool fp64, cudaStrea
   });
 }
 
-cudaError_t launch_gram_p(const Shape& s, const Buffers& b, bool fp64, bool sum_parts, cudaStream_t st) {
+cudaError_t launch_gram_p(const Shape& s, const Buffers& b, bool fp64, bool sum_parts, cudaStream_t st,
+                          const void* addA, const double* H) {
   return by_prec(fp64, [&](auto tc) {
     using TC = decltype(tc);
     return by_rank(s.rp, [&](auto rpc) {
@@ -531,8 +566,8 @@ cudaError_t launch_gram_p(const Shape& s, const Buffers& b, bool fp64, bool sum_
       cudaError_t e = allow_smem(thin_gram_kernel<TC, RP>, sm);
       if (e != cudaSuccess) return e;
       thin_gram_kernel<TC, RP><<<s.gp_blocks, 256, sm, st>>>(
-          static_cast<const TC*>(b.Qpart), sum_parts ? s.nsplit : 0, s.m * RP, static_cast<TC*>(b.P), s.m, nullptr,
-          nullptr, b.GPpart, b.st);
+          static_cast<const TC*>(b.Qpart), sum_parts ? s.nsplit : 0, s.m * RP, static_cast<TC*>(b.P), s.m,
+          static_cast<const TC*>(addA), H, b.GPpart, b.st);
       return cudaGetLastError();
     });
   });
@@ -582,7 +617,7 @@ cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool firs
   // W = sum_c Wpart[c] (+ C_old H, H = U_old^T U_new), then Gram partials of W.
   // H = sum of the U_old^T U_new partials, reduced into the slot after the partials.
   if (!first) {
-    reduce_sq_kernel<<<1, 256, 0, st>>>(b.Hpart, s.gp_blocks, s.rp * s.rp, b.Hpart + (size_t)s.gp_blocks * s.rp * s.rp,
+    reduce_sq_kernel<<<cdiv(s.rp * s.rp, 128), 128, 0, st>>>(b.Hpart, s.gp_blocks, s.rp * s.rp, b.Hpart + (size_t)s.gp_blocks * s.rp * s.rp,
                                         b.st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -659,16 +694,20 @@ cudaError_t launch_finalize(const Shape& s, const Buffers& b, bool fp64, int u_c
       constexpr int RP = decltype(rpc)::value;
       return by_mtype(b.m_dtype, b.M, [&](auto M) {
         using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
-        if (s_dtype == SFR_F64) {
-          finalize_kernel<TC, TMs, double, RP><<<grid, 256, 0, st>>>(
-              M, s.m, s.n, s.ldm, static_cast<const TC*>(b.Y[0]), static_cast<const TC*>(b.U[u_cur]),
-              static_cast<const TC*>(b.C), static_cast<double*>(S), static_cast<double*>(L), lds, b.st);
-        } else {
-          finalize_kernel<TC, TMs, float, RP><<<grid, 256, 0, st>>>(
-              M, s.m, s.n, s.ldm, static_cast<const TC*>(b.Y[0]), static_cast<const TC*>(b.U[u_cur]),
-              static_cast<const TC*>(b.C), static_cast<float*>(S), static_cast<float*>(L), lds, b.st);
-        }
-        return cudaGetLastError();
+        auto go = [&](auto yptr, int64_t ldy) {
+          using TY = std::remove_const_t<std::remove_pointer_t<decltype(yptr)>>;
+          if (s_dtype == SFR_F64)
+            finalize_kernel<TC, TMs, double, TY, RP><<<grid, 256, 0, st>>>(
+                M, s.m, s.n, s.ldm, yptr, ldy, static_cast<const TC*>(b.U[u_cur]), static_cast<const TC*>(b.C),
+                static_cast<double*>(S), static_cast<double*>(L), lds, b.st);
+          else
+            finalize_kernel<TC, TMs, float, TY, RP><<<grid, 256, 0, st>>>(
+                M, s.m, s.n, s.ldm, yptr, ldy, static_cast<const TC*>(b.U[u_cur]), static_cast<const TC*>(b.C),
+                static_cast<float*>(S), static_cast<float*>(L), lds, b.st);
+          return cudaGetLastError();
+        };
+        if (b.tc) return go(static_cast<const __nv_bfloat16*>(b.Y[0]), b.t.ldy);
+        return go(static_cast<const TC*>(b.Y[0]), s.n);
       });
     });
   });

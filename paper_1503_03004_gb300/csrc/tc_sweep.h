@@ -1,0 +1,42 @@
+// Tensor-core (tcgen05 + TMA) passes of the mixed path: buffers, tensor maps, launchers.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sfr {
+
+struct Shape;
+struct DevState;
+
+// Extra device buffers of the tensor-core path (bfloat16 multiplier, transposed Delta, and the
+// split / transposed thin factors the MMAs read).
+struct TcBuffers {
+  void* Y[2];          // multiplier ping-pong, m x ldy bfloat16
+  int64_t ldy;         // n rounded up to 64
+  void* Dt;            // Delta^T, n x ldd bfloat16 (iteration 1: M^T)
+  int64_t ldd;         // m rounded up to 64
+  float* Uh;           // m x 64: U rounded to TF32
+  float* Ul;           // m x 64: U - Uh
+  void* Ut;            // 64 x ldd bfloat16: U^T
+  float* Ch;           // n x 64: C rounded to TF32
+  float* Cl;           // n x 64: C - Ch
+  void* Vt;            // 64 x ldy bfloat16: V^T
+};
+
+struct TcMaps {
+  CUtensorMap M, Y[2], Dt_store, Dt_load, Ut, Uh, Ul, Ch, Cl, Vt;
+};
+
+bool tc_supported(const Shape& s, int m_dtype, int64_t ldm);
+cudaError_t tc_make_maps(const Shape& s, const TcBuffers& t, const void* M, int64_t ldm, TcMaps* maps);
+cudaError_t tc_launch_transpose_m(const Shape& s, const void* M, int64_t ldm, const TcBuffers& t, cudaStream_t st);
+cudaError_t tc_launch_prep_u(const Shape& s, const float* U, const TcBuffers& t, const DevState* dst, cudaStream_t st);
+cudaError_t tc_launch_prep_v(const Shape& s, const float* C, const float* V, const TcBuffers& t, const DevState* dst,
+                             cudaStream_t st);
+cudaError_t tc_launch_wpass(const Shape& s, const TcMaps& mp, float* Wpart, DevState* dst, cudaStream_t st);
+cudaError_t tc_launch_sweep(const Shape& s, const TcMaps& mp, int y_in, float* Qpart, double* resid_part,
+                            DevState* dst, cudaStream_t st);
+
+}  // namespace sfr

@@ -128,6 +128,21 @@ def test_mixed_square_r64_bf16_recipe(ctx):
     assert _rel(sol.S.cpu().numpy().astype(np.float64), ref.S) <= 1e-4
 
 
+@pytest.mark.parametrize("m,n,r", [(1000, 776, 40), (384, 640, 64), (1152, 1088, 33)])
+def test_tensor_core_path_matches_oracle(ctx, m, n, r):
+    # bfloat16 storage with 33 <= r <= 64 takes the tcgen05 path; ragged m and n (not multiples
+    # of the 128-row / 64-column tiles) exercise the TMA bounds handling.  The mixed-path bar
+    # applies to the converged result (early iterates carry bfloat16 rounding of a large Delta).
+    prob = synth.planted(m, n, r, p=0.05, amp=50.0, seed=m + n + r, dtype="bf16")
+    M = prob.values_f64()
+    ref = O.fr_adm(M, r, rho=1.5, mu0=0.05, tol=1e-9, max_iter=300)
+    sol = B.solve_torch(ctx, _dev(prob), r, rho=1.5, mu0=0.05, tol=1e-9, max_iter=300, precision=B.PREC_MIXED,
+                        s_dtype=B.F32)
+    assert abs(sol.iters - ref.iters) <= 3
+    assert _rel(_gpu_L(sol), ref.L) <= MIXED_TOL
+    assert _rel(sol.S.cpu().numpy().astype(np.float64), ref.S) <= 1e-4
+
+
 def test_fp64_path_with_low_precision_storage(ctx):
     prob = synth.planted(256, 192, 6, p=0.1, amp=1.0, seed=5, dtype="bf16")
     M = prob.values_f64()
