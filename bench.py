@@ -101,7 +101,7 @@ class ClockSampler:
 
 def make_workload(seed: int):
     from paper_1503_03004_gb300 import synth
-    return synth.square_large(WORKLOAD["m"], WORKLOAD["r"], dtype="bf16", seed=seed)
+    return synth.square_large(WORKLOAD["m"], WORKLOAD["r"], dtype="bf16", seed=seed)  # m = n
 
 
 def oracle_sample_rate(seed: int = 1001):
@@ -164,7 +164,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--m", type=int, default=WORKLOAD["m"],
+                    help="square size of the same recipe (smaller sizes are for profiler captures)")
     args = ap.parse_args()
+    if args.m != WORKLOAD["m"]:
+        WORKLOAD.update(m=args.m, n=args.m, workload=f"square{args.m}_r64_bf16_mixed")
     if args.impl == "reference":
         return run_reference(args)
 

@@ -88,6 +88,40 @@ __device__ void mm_dist(const double* A, const double* B, double* C, int r) {
   }
 }
 
+// C = op(A) op(B) in float32 on the leading r x r blocks, 4 x 4 outputs per thread (register
+// blocking keeps the shared-memory traffic at 8 loads per 16 FMAs).  Reads may touch rows and
+// columns beyond r (inside the RPMAX x LD arrays); only outputs inside r x r are written.
+template <bool TA, bool TB>
+__device__ void mmf(const float* A, const float* B, float* C, int r) {
+  const int nb = (r + 3) / 4;
+  for (int blk = threadIdx.x; blk < nb * nb; blk += blockDim.x) {
+    const int i0 = 4 * (blk / nb), j0 = 4 * (blk % nb);
+    float acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+    for (int k = 0; k < r; ++k) {
+      float a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = TA ? A[k * LD + i0 + q] : A[(i0 + q) * LD + k];
+        b[q] = TB ? B[(j0 + q) * LD + k] : B[k * LD + j0 + q];
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y)
+        if (i0 + x < r && j0 + y < r) C[(i0 + x) * LD + j0 + y] = acc[x][y];
+  }
+  __syncthreads();
+}
+
 __device__ double block_reduce(double v, double* red, bool take_max) {
   for (int o = 16; o > 0; o >>= 1) {
     const double w = __shfl_xor_sync(0xffffffffu, v, o);
@@ -140,28 +174,29 @@ __device__ void jacobi_f32(float* A, float* Q, int n2, int max_sweeps, double* r
         cs[k] = c; sn[k] = s; pp[k] = p; qq[k] = q;
       }
       __syncthreads();
-      // rows: A <- J^T A
-      for (int e = threadIdx.x; e < np * n2; e += blockDim.x) {
-        const int k = e / n2, j = e % n2;
-        const float c = cs[k], s = sn[k];
-        if (s == 0.f) continue;
-        const int p = pp[k], q = qq[k];
-        const float ap = A[p * LD + j], aq = A[q * LD + j];
-        A[p * LD + j] = c * ap - s * aq;
-        A[q * LD + j] = s * ap + c * aq;
+      // A <- J^T A J in one phase: the pairs partition the indices, so each 2 x 2 block
+      // (rows {p1, q1}, columns {p2, q2}) is touched by exactly one row and one column rotation
+      for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
+        const int k1 = e / np, k2 = e % np;
+        const float c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
+        if (s1 == 0.f && s2 == 0.f) continue;
+        const int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
+        const float a = A[p1 * LD + p2], b = A[p1 * LD + q2], c = A[q1 * LD + p2], d = A[q1 * LD + q2];
+        const float ra = c1 * a - s1 * c, rb = c1 * b - s1 * d, rc = s1 * a + c1 * c, rd = s1 * b + c1 * d;
+        A[p1 * LD + p2] = c2 * ra - s2 * rb;
+        A[p1 * LD + q2] = s2 * ra + c2 * rb;
+        A[q1 * LD + p2] = c2 * rc - s2 * rd;
+        A[q1 * LD + q2] = s2 * rc + c2 * rd;
       }
-      __syncthreads();
-      // columns: A <- A J, Q <- Q J
-      for (int e = threadIdx.x; e < 2 * np * n2; e += blockDim.x) {
-        const int which = e / (np * n2), rem = e % (np * n2);
-        const int k = rem / n2, j = rem % n2;
+      // Q <- Q J
+      for (int e = threadIdx.x; e < np * n2; e += blockDim.x) {
+        const int k = e % np, j = e / np;
         const float c = cs[k], s = sn[k];
         if (s == 0.f) continue;
         const int p = pp[k], q = qq[k];
-        float* X = which ? Q : A;
-        const float xp = X[j * LD + p], xq = X[j * LD + q];
-        X[j * LD + p] = c * xp - s * xq;
-        X[j * LD + q] = s * xp + c * xq;
+        const float xp = Q[j * LD + p], xq = Q[j * LD + q];
+        Q[j * LD + p] = c * xp - s * xq;
+        Q[j * LD + q] = s * xp + c * xq;
       }
       __syncthreads();
     }
@@ -186,7 +221,7 @@ struct RxrSmem {
 };
 
 // Sum of `count` r x r partials (fixed order); rows split across the cluster, then broadcast.
-__device__ void load_gram(const double* __restrict__ parts, int count, int rp, int r, double* dst) {
+__device__ void load_gram(const double* __restrict__ parts, int count, int rp, int r, double* dst, bool fp64sum) {
   cg::cluster_group cl = cg::this_cluster();
   const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int rpc = (r + cs - 1) / cs, i0 = min(r, rank * rpc), i1 = min(r, i0 + rpc);
@@ -194,9 +229,15 @@ __device__ void load_gram(const double* __restrict__ parts, int count, int rp, i
   const int rpsq = rp * rp;
   for (int e = threadIdx.x; e < nloc; e += blockDim.x) {
     const int i = i0 + e / r, j = e % r;
-    double v = 0.0;
-    for (int c = 0; c < count; ++c) v += parts[(int64_t)c * rpsq + i * rp + j];
-    dst[i * LD + j] = v;
+    if (fp64sum) {
+      double v = 0.0;
+      for (int c = 0; c < count; ++c) v += parts[(int64_t)c * rpsq + i * rp + j];
+      dst[i * LD + j] = v;
+    } else {  // partials of a float32 sweep: float32 sums (float64 adds run at 1/64 rate)
+      float v = 0.f;
+      for (int c = 0; c < count; ++c) v += (float)parts[(int64_t)c * rpsq + i * rp + j];
+      dst[i * LD + j] = (double)v;
+    }
   }
   __syncthreads();
   if (cs > 1) {
@@ -218,126 +259,159 @@ __device__ void fail(DevState* st, int code) {
 
 // v_side = false: T_U = B (B G_P B)^{-1/2}.
 // v_side = true:  T_V = B (B G_W B)^{-1/2}, B <- Sym(G_W T_V), T_C = T_V B.
+// float64: the Gram sums (FP64 path), K = B G B, the Newton residual, T, B_bar, T_C.
+// float32: the eigenbasis, eigenvalue estimates, Z0 and the Newton corrections, which only
+// steer the iteration (their error shrinks with each Newton step).
 __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict__ parts, int count, int rp, int r,
                                                        double* __restrict__ Bg, double* __restrict__ Tout,
                                                        double* __restrict__ TCout, float* __restrict__ Qeig,
-                                                       int v_side, DevState* st) {
+                                                       int v_side, int fp64sum, DevState* st) {
   if (stopped(st)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RxrSmem& S = *reinterpret_cast<RxrSmem*>(smem_raw);
   float* F1 = reinterpret_cast<float*>(S.T1);            // float scratch inside T1
   float* F2 = F1 + RPMAX * LD;
+  float* Kf = reinterpret_cast<float*>(S.T2);            // float copy of K inside T2 (until Z0)
+  float* lamf = reinterpret_cast<float*>(S.lam);         // float eigenvalue estimates
+  float* sqf = lamf + RPMAX;                             // sqrt(lambda)
+  float* isqf = reinterpret_cast<float*>(S.sq);          // 1 / sqrt(lambda)
   const int tid = threadIdx.x;
   const int rpsq = rp * rp;
+  const bool writer = cg::this_cluster().block_rank() == 0;
   // 1. Gram of the thin matrix and B; K = B G B (symmetrised) scaled by s = trace / r
-  load_gram(parts, count, rp, r, S.T2);
+  load_gram(parts, count, rp, r, S.T2, fp64sum);
   for (int e = tid; e < r * r; e += blockDim.x) S.B[(e / r) * LD + e % r] = Bg[(e / r) * rp + e % r];
   __syncthreads();
   mm_dist<false, false>(S.T2, S.B, S.T1, r);
   mm_dist<false, false>(S.B, S.T1, S.Z, r);
-  if (tid == 0) {
-    double tr = 0.0;
-    for (int i = 0; i < r; ++i) tr += S.Z[i * LD + i];
-    S.scale = tr / r;
-    S.bad = !(S.scale > 0.0) || !(S.scale < 1e300);
-  }
-  __syncthreads();
-  if (S.bad) { fail(st, SFR_E_NAN); return; }
-  const double inv_s = 1.0 / S.scale;
+  double tr = 0.0;
+  for (int i = tid; i < r; i += blockDim.x) tr += S.Z[i * LD + i];
+  tr = block_reduce(tr, S.red, false);
+  const double scale = tr / r;
+  if (!(scale > 0.0) || !(scale < 1e300)) { fail(st, SFR_E_NAN); return; }
+  const double inv_s = 1.0 / scale;
   for (int e = tid; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
-    S.K[i * LD + j] = 0.5 * (S.Z[i * LD + j] + S.Z[j * LD + i]) * inv_s;
+    const double v = 0.5 * (S.Z[i * LD + j] + S.Z[j * LD + i]) * inv_s;
+    S.K[i * LD + j] = v;
+    Kf[i * LD + j] = (float)v;
   }
-  __syncthreads();
   // 2. float32 Jacobi, warm-started from the previous eigenbasis Qw: A = Qw^T K Qw
   const int n2 = (r + 1) & ~1;
   for (int e = tid; e < n2 * n2; e += blockDim.x) {
     const int i = e / n2, j = e % n2;
     const bool in = i < r && j < r;
-    F1[i * LD + j] = in ? (float)S.K[i * LD + j] : 0.f;
+    if (!in) Kf[i * LD + j] = 0.f;
     S.Qf[i * LD + j] = in ? Qeig[i * rp + j] : (i == j ? 1.f : 0.f);
   }
   __syncthreads();
-  mm<float, false, false>(F1, S.Qf, F2, n2);
-  mm<float, true, false>(S.Qf, F2, S.Af, n2);
+  mmf<false, false>(Kf, S.Qf, F2, n2);
+  mmf<true, false>(S.Qf, F2, S.Af, n2);
   jacobi_f32(S.Af, S.Qf, n2, 10, S.red, S.cs, S.sn, S.pp, S.qq);
   // re-orthonormalise the float basis: Q <- Q (3I - Q^T Q) / 2
-  mm<float, true, false>(S.Qf, S.Qf, F1, r);
+  mmf<true, false>(S.Qf, S.Qf, F1, r);
   for (int e = tid; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
     F1[i * LD + j] = 0.5f * ((i == j ? 3.f : 0.f) - F1[i * LD + j]);
   }
   __syncthreads();
-  mm<float, false, false>(S.Qf, F1, F2, r);
+  mmf<false, false>(S.Qf, F1, F2, r);
   for (int e = tid; e < r * r; e += blockDim.x) S.Qf[(e / r) * LD + e % r] = F2[(e / r) * LD + e % r];
   __syncthreads();
-  // 3. float64 Rayleigh quotients lambda_p = q_p^T K q_p / q_p^T q_p
-  for (int e = tid; e < r * r; e += blockDim.x) S.T1[(e / r) * LD + e % r] = (double)S.Qf[(e / r) * LD + e % r];
-  __syncthreads();
-  mm_dist<false, false>(S.K, S.T1, S.T2, r);
+  // 3. eigenvalue estimates lambda_p = q_p^T K q_p / q_p^T q_p in float32; those far below the
+  //    largest are recomputed in float64 for the rank test (Eq. 9 needs rank r)
+  mmf<false, false>(Kf, S.Qf, F1, r);
   for (int p = tid; p < r; p += blockDim.x) {
-    double num = 0.0, den = 0.0;
+    float num = 0.f, den = 0.f;
     for (int i = 0; i < r; ++i) {
-      num = fma(S.T1[i * LD + p], S.T2[i * LD + p], num);
-      den = fma(S.T1[i * LD + p], S.T1[i * LD + p], den);
+      num = fmaf(S.Qf[i * LD + p], F1[i * LD + p], num);
+      den = fmaf(S.Qf[i * LD + p], S.Qf[i * LD + p], den);
     }
-    S.lam[p] = num / den;
+    lamf[p] = num / den;
   }
   __syncthreads();
-  if (tid == 0) {
-    double lo = S.lam[0], hi = S.lam[0];
-    for (int p = 1; p < r; ++p) { lo = fmin(lo, S.lam[p]); hi = fmax(hi, S.lam[p]); }
-    // Eq. 9 needs rank r; the same relative cut as the oracle's eigenvalue check
-    S.bad = !(lo > 1e-14 * hi);
-    if (cg::this_cluster().block_rank() == 0) {
-      if (v_side) st->lam_min_v = lo * S.scale; else st->lam_min_u = lo * S.scale;
+  float hi = 0.f;
+  for (int p = 0; p < r; ++p) hi = fmaxf(hi, lamf[p]);
+  for (int p = tid; p < r; p += blockDim.x) {
+    if (lamf[p] < 1e-3f * hi) {
+      double num = 0.0, den = 0.0;
+      for (int i = 0; i < r; ++i) {
+        double kq = 0.0;
+        for (int k = 0; k < r; ++k) kq = fma(S.K[i * LD + k], (double)S.Qf[k * LD + p], kq);
+        num = fma((double)S.Qf[i * LD + p], kq, num);
+        den = fma((double)S.Qf[i * LD + p], (double)S.Qf[i * LD + p], den);
+      }
+      lamf[p] = (float)(num / den);
     }
-    for (int p = 0; p < r; ++p) S.sq[p] = sqrt(fmax(S.lam[p], 1e-300));
   }
   __syncthreads();
-  if (S.bad) { fail(st, SFR_E_RANK); return; }
-  // 4. Z0 = Q diag(lambda^{-1/2}) Q^T
+  bool bad = false;
+  float lo = hi;
+  for (int p = 0; p < r; ++p) {
+    lo = fminf(lo, lamf[p]);
+    bad |= !(lamf[p] > 1e-14f * hi);
+  }
+  bad |= !(hi > 0.f);
+  __syncthreads();
+  if (writer && tid == 0) {
+    if (v_side) st->lam_min_v = (double)lo * scale; else st->lam_min_u = (double)lo * scale;
+  }
+  if (bad) { fail(st, SFR_E_RANK); return; }
+  for (int p = tid; p < r; p += blockDim.x) {
+    const float sq = sqrtf(lamf[p]);
+    sqf[p] = sq;
+    isqf[p] = 1.f / sq;
+  }
+  __syncthreads();
+  // 4. Z0 = Q diag(lambda^{-1/2}) Q^T (float32 start; Newton below brings it to float64 accuracy)
   for (int e = tid; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
-    S.T2[i * LD + j] = S.T1[i * LD + j] / S.sq[j];
+    F2[i * LD + j] = S.Qf[i * LD + j] * isqf[j];
   }
   __syncthreads();
-  mm_dist<false, true>(S.T2, S.T1, S.Z, r);
+  mmf<false, true>(F2, S.Qf, F1, r);
+  for (int e = tid; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    S.Z[i * LD + j] = 0.5 * ((double)F1[i * LD + j] + (double)F1[j * LD + i]);
+  }
+  __syncthreads();
   // 5. Newton steps on Z K Z = I (residual in float64, correction in float32)
   for (int it = 0; it < 6; ++it) {
     mm_dist<false, false>(S.K, S.Z, S.T1, r);
     mm_dist<false, false>(S.Z, S.T1, S.T2, r);
-    double rmax = 0.0;
+    float rmax = 0.f;
     for (int e = tid; e < r * r; e += blockDim.x) {
       const int i = e / r, j = e % r;
-      const double v = (i == j ? 1.0 : 0.0) - 0.5 * (S.T2[i * LD + j] + S.T2[j * LD + i]);
-      F1[i * LD + j] = (float)v;
-      rmax = fmax(rmax, fabs(v));
+      const float v = (float)((i == j ? 1.0 : 0.0) - 0.5 * (S.T2[i * LD + j] + S.T2[j * LD + i]));
+      F1[i * LD + j] = v;
+      rmax = fmaxf(rmax, fabsf(v));
     }
-    rmax = block_reduce(rmax, S.red, true);
-    if (!(rmax == rmax)) { fail(st, SFR_E_NAN); return; }
-    if (rmax < 4e-16 * r) break;
-    mm<float, false, false>(F1, S.Qf, F2, r);     // R Q
-    mm<float, true, false>(S.Qf, F2, S.Af, r);    // Q^T R Q
+    const double rm = block_reduce((double)rmax, S.red, true);
+    if (!(rm == rm)) { fail(st, SFR_E_NAN); return; }
+    if (rm < 4e-16 * r) break;
+    mmf<false, false>(F1, S.Qf, F2, r);     // R Q
+    mmf<true, false>(S.Qf, F2, S.Af, r);    // Q^T R Q
     for (int e = tid; e < r * r; e += blockDim.x) {
       const int p = e / r, q = e % r;
-      S.Af[p * LD + q] = S.Af[p * LD + q] / (float)(S.sq[p] + S.sq[q]);
+      S.Af[p * LD + q] = S.Af[p * LD + q] / (sqf[p] + sqf[q]);
     }
     __syncthreads();
-    mm<float, false, true>(S.Af, S.Qf, F2, r);    // Dt Q^T
-    mm<float, false, false>(S.Qf, F2, F1, r);     // Q Dt Q^T
+    mmf<false, true>(S.Af, S.Qf, F2, r);    // Dt Q^T
+    mmf<false, false>(S.Qf, F2, F1, r);     // Q Dt Q^T
     for (int e = tid; e < r * r; e += blockDim.x) {
       const int i = e / r, j = e % r;
       S.Z[i * LD + j] += 0.5 * ((double)F1[i * LD + j] + (double)F1[j * LD + i]);
     }
     __syncthreads();
+    // the step just taken shrinks the residual by about the eigenbasis error (<= 3e-5), so a
+    // residual below 1e-11 is at float64 round-off after it
+    if (rm < 1e-11) break;
   }
   // 6. (B G B)^{-1/2} = Z / sqrt(s); T = B (B G B)^{-1/2}
-  const double zs = 1.0 / sqrt(S.scale);
+  const double zs = 1.0 / sqrt(scale);
   for (int e = tid; e < r * r; e += blockDim.x) S.Z[(e / r) * LD + e % r] *= zs;
   __syncthreads();
   mm_dist<false, false>(S.B, S.Z, S.T1, r);
-  const bool writer = cg::this_cluster().block_rank() == 0;
   if (writer)
     for (int e = tid; e < rpsq; e += blockDim.x) {
       const int i = e / rp, j = e % rp;
@@ -347,7 +421,7 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
     }
   if (!v_side) return;
   // 7. B_bar = Sym(G_W T_V) (Eq. 10 with W = X^T U_bar), T_C = T_V B_bar
-  load_gram(parts, count, rp, r, S.K);
+  load_gram(parts, count, rp, r, S.K, fp64sum);
   mm_dist<false, false>(S.K, S.T1, S.T2, r);
   for (int e = tid; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
@@ -397,7 +471,7 @@ static int rxr_cluster_size(size_t smem) {
   return best;
 }
 
-cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream_t st) {
+cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream_t st, bool fp64sum) {
   const size_t smem = sizeof(RxrSmem);
   cudaError_t e = cudaFuncSetAttribute(rxr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -416,9 +490,9 @@ cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream
   cfg.numAttrs = 1;
   if (v_side)
     return cudaLaunchKernelEx(&cfg, rxr_kernel, (const double*)b.GWpart, s.gw_blocks, s.rp, s.r, b.B, b.TV, b.TCm,
-                              b.Qeig_v, 1, b.st);
+                              b.Qeig_v, 1, (int)fp64sum, b.st);
   return cudaLaunchKernelEx(&cfg, rxr_kernel, (const double*)b.GPpart, s.gp_blocks, s.rp, s.r, b.B, b.TU,
-                            (double*)nullptr, b.Qeig_u, 0, b.st);
+                            (double*)nullptr, b.Qeig_u, 0, (int)fp64sum, b.st);
 }
 
 }  // namespace sfr

@@ -87,7 +87,7 @@ cudaError_t launch_norm_m(const Shape& s, const Buffers& b, cudaStream_t st);
 cudaError_t launch_init_p(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st);
 cudaError_t launch_gram_p(const Shape& s, const Buffers& b, bool fp64, bool sum_parts, cudaStream_t st,
                           const void* addA = nullptr, const double* H = nullptr);
-cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream_t st);
+cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream_t st, bool fp64sum = true);
 cudaError_t launch_apply_u(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st);
 cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first, int u_new, cudaStream_t st);
 cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st);

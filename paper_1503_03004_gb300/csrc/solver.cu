@@ -255,12 +255,12 @@ struct Solver {
       SFR_CUDA(launch_gram_p(s, b, fp64, false, st));
       kernels += 2;
     }
-    timed_launch(slot, 2, [&] { return launch_rxr(s, b, false, st); });      // T_U = B (B G_P B)^{-1/2}
+    timed_launch(slot, 2, [&] { return launch_rxr(s, b, false, st, fp64); });  // T_U = B (B G_P B)^{-1/2}
     SFR_CUDA(launch_apply_u(s, b, fp64, first, st));                          // U_bar = P T_U
     const int u_new = 1 - b.u_cur;
     timed_launch(slot, 1, [&] { return launch_wpass(s, b, fp64, first, u_new, st); });  // X^T U_bar partials
     SFR_CUDA(launch_wfinal(s, b, fp64, first, st));                           // W, G_W partials
-    timed_launch(slot, 3, [&] { return launch_rxr(s, b, true, st); });       // T_V, B_bar, T_C
+    timed_launch(slot, 3, [&] { return launch_rxr(s, b, true, st, fp64); });   // T_V, B_bar, T_C
     SFR_CUDA(launch_apply_v(s, b, fp64, st));                                 // V_bar, C
     timed_launch(slot, 0, [&] { return launch_sweep(s, b, fp64, u_new, st); });  // S/Y steps, Delta, next P
     SFR_CUDA(launch_iter_end(s, b, st));                                      // residual, mu, stop test
@@ -281,14 +281,14 @@ struct Solver {
       SFR_CUDA(launch_gram_p(s, b, false, false, st));
       kernels += 3;
     }
-    timed_launch(slot, 2, [&] { return launch_rxr(s, b, false, st); });      // T_U
+    timed_launch(slot, 2, [&] { return launch_rxr(s, b, false, st, false); });  // T_U
     SFR_CUDA(launch_apply_u(s, b, false, first, st));                         // U_bar = P T_U
     const int u_new = 1 - b.u_cur;
     const float* Unew = static_cast<const float*>(b.U[u_new]);
     SFR_CUDA(tc_launch_prep_u(s, Unew, b.t, b.st, st));                       // TF32 split, U^T
     timed_launch(slot, 1, [&] { return tc_launch_wpass(s, maps, static_cast<float*>(b.Wpart), b.st, st); });
     SFR_CUDA(launch_wfinal(s, b, false, first, st));                          // W, G_W partials
-    timed_launch(slot, 3, [&] { return launch_rxr(s, b, true, st); });       // T_V, B_bar, T_C
+    timed_launch(slot, 3, [&] { return launch_rxr(s, b, true, st, false); });  // T_V, B_bar, T_C
     SFR_CUDA(launch_apply_v(s, b, false, st));                                // V_bar, C
     SFR_CUDA(tc_launch_prep_v(s, static_cast<const float*>(b.C), static_cast<const float*>(b.V), b.t, b.st, st));
     const int y_in = b.Y[0] == b.t.Y[0] ? 0 : 1;

@@ -81,9 +81,42 @@ __global__ void init_p_kernel(const TMs* __restrict__ M, int64_t m, int64_t ldm,
   P[idx] = a < r ? ld_as<TC, TMs>(M + i * ldm + a) : (TC)0;
 }
 
+// ---------------------------------------------------------------- register-blocked small products
+// C[R x N] = op(A)[R x K] B[K x N] on shared-memory operands, 4 x 4 outputs per thread:
+// thread t < (R/4)(N/4) owns rows 4(t / (N/4)) .. +3 and columns 4(t % (N/4)) .. +3.
+// op(A) = A (element (i, k) at A[i * lda + k]) or A^T (element (i, k) at A[k * lda + i]).
+template <typename T, int R, int N, int K, bool TA>
+__device__ __forceinline__ void block_mm(const T* __restrict__ A, int lda, const T* __restrict__ B, int ldb,
+                                         T (&acc)[4][4], int t) {
+  constexpr int NB = N / 4;
+  if (t >= (R / 4) * NB) return;
+  const int i0 = 4 * (t / NB), j0 = 4 * (t % NB);
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    T a[4], bb[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      a[q] = TA ? A[k * lda + i0 + q] : A[(i0 + q) * lda + k];
+      bb[q] = B[k * ldb + j0 + q];
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * bb[y];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void zero44(T (&acc)[4][4]) {
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = 0;
+}
+
 // ---------------------------------------------------------------- thin reduce + Gram partials
 // For every 64-row tile handled by this CTA (tiles blockIdx.x, blockIdx.x + gridDim.x, ...):
-// out[i][:] = sum_s parts[s][i][:]  (+ addA[i][:] * H when addA != nullptr), then the CTA's
+// out[i][:] = sum_s parts[s][i][:]  (+ addA[i][:] H when addA != nullptr), then the CTA's
 // Gram partial gpart[cta] = sum over its rows of out[i]^T out[i]  (r x r).
 // nparts == 0 leaves `out` as it is and only forms the Gram partial.
 template <typename TC, int RP>
@@ -92,56 +125,62 @@ __global__ void __launch_bounds__(256) thin_gram_kernel(const TC* __restrict__ p
                                                         const double* __restrict__ H, double* __restrict__ gpart,
                                                         const DevState* st) {
   if (stopped(st)) return;
-  constexpr int GPT = (RP * RP + 255) / 256;  // Gram entries per thread
+  constexpr int LDT = RP + 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  auto tile = reinterpret_cast<TC(*)[RP + 1]>(smem_raw);              // [kGramRows][RP + 1]
-  auto Hs = reinterpret_cast<TC(*)[RP + 1]>(smem_raw + sizeof(TC) * kGramRows * (RP + 1));  // [RP][RP + 1]
+  TC* tile = reinterpret_cast<TC*>(smem_raw);   // [kGramRows][LDT]
+  TC* arow = tile + kGramRows * LDT;              // [kGramRows][LDT]  addA rows
+  TC* Hs = arow + kGramRows * LDT;                // [RP][LDT]
+  const int t = threadIdx.x;
   if (addA)
-    for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) Hs[e / RP][e % RP] = (TC)H[e];
-  TC g[GPT];
-#pragma unroll
-  for (int q = 0; q < GPT; ++q) g[q] = 0;
+    for (int e = t; e < RP * RP; e += blockDim.x) Hs[(e / RP) * LDT + e % RP] = (TC)H[e];
+  TC g[4][4];
+  zero44(g);
   const int64_t ntiles = (rows + kGramRows - 1) / kGramRows;
   for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
     const int64_t i0 = tl * kGramRows;
     __syncthreads();  // previous tile consumed; Hs visible
-    for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
-      int ii = e / RP, a = e % RP;
-      int64_t i = i0 + ii;
+    for (int e = t; e < kGramRows * RP; e += blockDim.x) {
+      const int ii = e / RP, a = e % RP;
+      const int64_t i = i0 + ii;
       TC v = 0;
       if (i < rows) {
-        if (nparts == 0) {
-          v = out[i * RP + a];
-        } else {
+        if (nparts == 0) v = out[i * RP + a];
+        else
           for (int s = 0; s < nparts; ++s) v += parts[s * part_stride + i * RP + a];
-          if (addA) {
-            TC acc = 0;
-#pragma unroll 8
-            for (int b = 0; b < RP; ++b) acc += addA[i * RP + b] * Hs[b][a];
-            v += acc;
-          }
-          out[i * RP + a] = v;
-        }
       }
-      tile[ii][a] = v;
+      tile[ii * LDT + a] = v;
+      if (addA) arow[ii * LDT + a] = i < rows ? addA[i * RP + a] : (TC)0;
     }
     __syncthreads();
+    if (nparts > 0) {
+      if (addA) {
+        TC acc[4][4];
+        zero44(acc);
+        block_mm<TC, kGramRows, RP, RP, false>(arow, LDT, Hs, LDT, acc, t);
+        if (t < (kGramRows / 4) * (RP / 4)) {
+          const int r0 = 4 * (t / (RP / 4)), c0 = 4 * (t % (RP / 4));
 #pragma unroll
-    for (int q = 0; q < GPT; ++q) {
-      const int e = threadIdx.x + q * 256;
-      if (e < RP * RP) {
-        const int a = e / RP, b = e % RP;
-        TC acc = 0;
-#pragma unroll 8
-        for (int ii = 0; ii < kGramRows; ++ii) acc += tile[ii][a] * tile[ii][b];
-        g[q] += acc;
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) tile[(r0 + x) * LDT + c0 + y] += acc[x][y];
+        }
+        __syncthreads();
+      }
+      for (int e = t; e < kGramRows * RP; e += blockDim.x) {
+        const int ii = e / RP, a = e % RP;
+        const int64_t i = i0 + ii;
+        if (i < rows) out[i * RP + a] = tile[ii * LDT + a];
       }
     }
+    block_mm<TC, RP, RP, kGramRows, true>(tile, LDT, tile, LDT, g, t);
   }
+  if (t < (RP / 4) * (RP / 4)) {
+    const int r0 = 4 * (t / (RP / 4)), c0 = 4 * (t % (RP / 4));
+    double* dst = gpart + (int64_t)blockIdx.x * RP * RP;
 #pragma unroll
-  for (int q = 0; q < GPT; ++q) {
-    const int e = threadIdx.x + q * 256;
-    if (e < RP * RP) gpart[(int64_t)blockIdx.x * RP * RP + e] = (double)g[q];
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) dst[(r0 + x) * RP + c0 + y] = (double)g[x][y];
   }
 }
 
@@ -166,71 +205,72 @@ __global__ void __launch_bounds__(256) row_transform_kernel(const TC* __restrict
                                                             const TC* __restrict__ old, double* __restrict__ hpart,
                                                             const DevState* st) {
   if (stopped(st)) return;
-  constexpr int GPT = (RP * RP + 255) / 256;
+  constexpr int LDT = RP + 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  auto Ts = reinterpret_cast<TC(*)[RP + 1]>(smem_raw);                                   // [RP][RP + 1]
-  auto T2s = reinterpret_cast<TC(*)[RP + 1]>(smem_raw + sizeof(TC) * RP * (RP + 1));     // [RP][RP + 1]
-  auto srow = reinterpret_cast<TC(*)[RP + 1]>(smem_raw + sizeof(TC) * 2 * RP * (RP + 1));  // [kGramRows][RP + 1]
-  auto drow = reinterpret_cast<TC(*)[RP + 1]>(smem_raw + sizeof(TC) * (2 * RP + kGramRows) * (RP + 1));
-  for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
-    Ts[e / RP][e % RP] = (TC)T[e];
-    if (T2) T2s[e / RP][e % RP] = (TC)T2[e];
+  TC* Ts = reinterpret_cast<TC*>(smem_raw);   // [RP][LDT]
+  TC* T2s = Ts + RP * LDT;                     // [RP][LDT]
+  TC* srow = T2s + RP * LDT;                   // [kGramRows][LDT]
+  TC* drow = srow + kGramRows * LDT;           // [kGramRows][LDT]
+  TC* orow = drow + kGramRows * LDT;           // [kGramRows][LDT]
+  const int t = threadIdx.x;
+  for (int e = t; e < RP * RP; e += blockDim.x) {
+    Ts[(e / RP) * LDT + e % RP] = (TC)T[e];
+    if (T2) T2s[(e / RP) * LDT + e % RP] = (TC)T2[e];
   }
-  TC h[GPT];
-#pragma unroll
-  for (int q = 0; q < GPT; ++q) h[q] = 0;
+  TC h[4][4];
+  zero44(h);
+  const int owner = t < (kGramRows / 4) * (RP / 4);
+  const int r0 = 4 * (t / (RP / 4)), c0 = 4 * (t % (RP / 4));
   const int64_t ntiles = (rows + kGramRows - 1) / kGramRows;
   for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
     const int64_t i0 = tl * kGramRows;
     __syncthreads();
-    for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
-      int ii = e / RP, a = e % RP;
-      int64_t i = i0 + ii;
-      srow[ii][a] = i < rows ? src[i * RP + a] : (TC)0;
+    for (int e = t; e < kGramRows * RP; e += blockDim.x) {
+      const int ii = e / RP, a = e % RP;
+      const int64_t i = i0 + ii;
+      srow[ii * LDT + a] = i < rows ? src[i * RP + a] : (TC)0;
+      if (hpart) orow[ii * LDT + a] = i < rows ? old[i * RP + a] : (TC)0;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
-      int ii = e / RP, a = e % RP;
-      TC acc = 0, acc2 = 0;
-#pragma unroll 8
-      for (int b = 0; b < RP; ++b) {
-        acc += srow[ii][b] * Ts[b][a];
-        if (T2) acc2 += srow[ii][b] * T2s[b][a];
-      }
-      drow[ii][a] = acc;
-      int64_t i = i0 + ii;
-      if (i < rows) {
-        dst[i * RP + a] = acc;
-        if (T2) dst2[i * RP + a] = acc2;
-      }
-    }
-    if (hpart) {
-      __syncthreads();  // srow reused for the old rows
-      for (int e = threadIdx.x; e < kGramRows * RP; e += blockDim.x) {
-        int ii = e / RP, a = e % RP;
-        int64_t i = i0 + ii;
-        srow[ii][a] = i < rows ? old[i * RP + a] : (TC)0;
-      }
-      __syncthreads();
+    TC acc[4][4];
+    zero44(acc);
+    block_mm<TC, kGramRows, RP, RP, false>(srow, LDT, Ts, LDT, acc, t);
+    if (owner) {
 #pragma unroll
-      for (int q = 0; q < GPT; ++q) {
-        const int e = threadIdx.x + q * 256;
-        if (e < RP * RP) {
-          const int a = e / RP, b = e % RP;
-          TC acc = 0;
-#pragma unroll 8
-          for (int ii = 0; ii < kGramRows; ++ii) acc += srow[ii][a] * drow[ii][b];
-          h[q] += acc;
+      for (int x = 0; x < 4; ++x) {
+        const int64_t i = i0 + r0 + x;
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          drow[(r0 + x) * LDT + c0 + y] = acc[x][y];
+          if (i < rows) dst[i * RP + c0 + y] = acc[x][y];
         }
       }
     }
-  }
-  if (hpart) {
+    if (T2) {
+      zero44(acc);
+      block_mm<TC, kGramRows, RP, RP, false>(srow, LDT, T2s, LDT, acc, t);
+      if (owner) {
 #pragma unroll
-    for (int q = 0; q < GPT; ++q) {
-      const int e = threadIdx.x + q * 256;
-      if (e < RP * RP) hpart[(int64_t)blockIdx.x * RP * RP + e] = (double)h[q];
+        for (int x = 0; x < 4; ++x) {
+          const int64_t i = i0 + r0 + x;
+          if (i < rows)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) dst2[i * RP + c0 + y] = acc[x][y];
+        }
+      }
     }
+    if (hpart) {
+      __syncthreads();  // drow complete
+      block_mm<TC, RP, RP, kGramRows, true>(orow, LDT, drow, LDT, h, t);
+    }
+  }
+  if (hpart && t < (RP / 4) * (RP / 4)) {
+    const int a0 = 4 * (t / (RP / 4)), b0 = 4 * (t % (RP / 4));
+    double* out = hpart + (int64_t)blockIdx.x * RP * RP;
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) out[(a0 + x) * RP + b0 + y] = (double)h[x][y];
   }
 }
 
@@ -522,9 +562,9 @@ cudaError_t by_prec(bool fp64, F&& f) {
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 template <typename TC, int RP>
-size_t gram_smem() { return sizeof(TC) * (size_t)(kGramRows + RP) * (RP + 1); }
+size_t gram_smem() { return sizeof(TC) * (size_t)(2 * kGramRows + RP) * (RP + 4); }
 template <typename TC, int RP>
-size_t transform_smem() { return sizeof(TC) * (size_t)(2 * RP + 2 * kGramRows) * (RP + 1); }
+size_t transform_smem() { return sizeof(TC) * (size_t)(2 * RP + 3 * kGramRows) * (RP + 4); }
 
 template <typename K>
 cudaError_t allow_smem(K kern, size_t bytes) {
