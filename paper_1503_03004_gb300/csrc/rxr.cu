@@ -403,9 +403,10 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
       S.Z[i * LD + j] += 0.5 * ((double)F1[i * LD + j] + (double)F1[j * LD + i]);
     }
     __syncthreads();
-    // the step just taken shrinks the residual by about the eigenbasis error (<= 3e-5), so a
-    // residual below 1e-11 is at float64 round-off after it
-    if (rm < 1e-11) break;
+    // The step just taken leaves a residual of about (eigenbasis error + float32 rounding of the
+    // correction) x rm <= 1e-7 rm.  From rm < 1e-6 that is below 1e-13, which is float64-level
+    // for what the factors need, so stop without forming the residual again.
+    if (rm < 1e-6) break;
   }
   // 6. (B G B)^{-1/2} = Z / sqrt(s); T = B (B G B)^{-1/2}
   const double zs = 1.0 / sqrt(scale);

@@ -52,6 +52,14 @@ struct DeviceBlock {
   ~DeviceBlock() {
     if (ptr) cudaFree(ptr);
   }
+  void release(size_t* held) {
+    if (ptr) {
+      cudaFree(ptr);
+      *held -= bytes;
+    }
+    ptr = nullptr;
+    bytes = 0;
+  }
   void ensure(size_t want, size_t* held, size_t budget) {
     if (want <= bytes) return;
     if (budget && *held - bytes + want > budget)
@@ -128,7 +136,7 @@ size_t carve(const Shape& s, bool fp64, void* base, Buffers* b, bool tc) {
     x.t.ldd = (s.m + 63) / 64 * 64;
     x.t.Y[0] = x.Y[0] = c.take(2 * s.m * x.t.ldy);
     x.t.Y[1] = x.Y[1] = c.take(2 * s.m * x.t.ldy);
-    x.t.Dt = c.take(2 * s.n * x.t.ldd);
+    x.t.D = c.take(2 * s.m * x.t.ldy);
     x.D = nullptr;
     x.t.Uh = static_cast<float*>(c.take(4 * s.m * 64));
     x.t.Ul = static_cast<float*>(c.take(4 * s.m * 64));
@@ -276,29 +284,28 @@ struct Solver {
     cudaStream_t st = stream;
     int kernels = 0;
     if (first) {
-      SFR_CUDA(tc_launch_transpose_m(s, b.M, s.ldm, b.t, st));                // Dt <- M^T (X_1 = M)
       SFR_CUDA(launch_init_p(s, b, false, st));
       SFR_CUDA(launch_gram_p(s, b, false, false, st));
-      kernels += 3;
+      kernels += 2;
     }
     timed_launch(slot, 2, [&] { return launch_rxr(s, b, false, st, false); });  // T_U
     SFR_CUDA(launch_apply_u(s, b, false, first, st));                         // U_bar = P T_U
     const int u_new = 1 - b.u_cur;
     const float* Unew = static_cast<const float*>(b.U[u_new]);
     SFR_CUDA(tc_launch_prep_u(s, Unew, b.t, b.st, st));                       // TF32 split, U^T
-    timed_launch(slot, 1, [&] { return tc_launch_wpass(s, maps, static_cast<float*>(b.Wpart), b.st, st); });
+    timed_launch(slot, 1, [&] { return tc_launch_wpass(s, maps, first, static_cast<float*>(b.Wpart), b.st, st); });
     SFR_CUDA(launch_wfinal(s, b, false, first, st));                          // W, G_W partials
     timed_launch(slot, 3, [&] { return launch_rxr(s, b, true, st, false); });  // T_V, B_bar, T_C
     SFR_CUDA(launch_apply_v(s, b, false, st));                                // V_bar, C
     SFR_CUDA(tc_launch_prep_v(s, static_cast<const float*>(b.C), static_cast<const float*>(b.V), b.t, b.st, st));
     const int y_in = b.Y[0] == b.t.Y[0] ? 0 : 1;
     timed_launch(slot, 0, [&] {
-      return tc_launch_sweep(s, maps, y_in, static_cast<float*>(b.Qpart), b.resid_part, b.st, st);
+      return tc_launch_sweep(s, maps, b.t, y_in, static_cast<float*>(b.Qpart), b.resid_part, b.st, st);
     });
     SFR_CUDA(launch_iter_end(s, b, st));
     // P_{k+1} = U_bar B_bar + Delta V_bar  (L V_bar = U_bar B_bar since V_bar^T V_bar = I)
     SFR_CUDA(launch_gram_p(s, b, false, true, st, b.U[u_new], b.B));
-    kernels += first ? 11 : 12;
+    kernels += first ? 10 : 12;
     b.u_cur = u_new;
     std::swap(b.Y[0], b.Y[1]);
     return kernels;
@@ -331,7 +338,7 @@ struct Solver {
       const double by = tc ? 2 : (fp64 ? 8 : 4), bd = tc ? 2 : (fp64 ? 8 : 4);
       sweep_bytes = mn * (bm + 2 * by + bd);
       wpass_bytes = mn * bd;
-      wpass_first_bytes = mn * (tc ? 2 : bm);
+      wpass_first_bytes = mn * bm;
     }
     b.M = Mdev;
     b.m_dtype = p.m_dtype;
@@ -534,17 +541,20 @@ struct sfr_ctx {
   bool own_stream = false;
   std::string last_error;
   std::unique_ptr<Solver> solver;
-  // request queue
+  // request queue (sfr_submit / sfr_poll): `max_slots` slots, each a host thread with its own
+  // stream, workspace and graph cache, so admitted requests run concurrently on the device
   int max_slots = 8;
+  size_t budget = 0;      // cap on the summed workspace of running requests (0 = none)
+  size_t in_use = 0;      // workspace bytes of running requests
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<std::shared_ptr<Request>> queue;
   std::map<uint64_t, std::shared_ptr<Request>> live;
   uint64_t next_ticket = 1;
   bool stopping = false;
-  std::thread worker;
-  std::unique_ptr<Solver> worker_solver;
-  cudaStream_t worker_stream = nullptr;
+  std::vector<std::thread> workers;
+  std::vector<std::unique_ptr<Solver>> slot_solvers;
+  std::vector<cudaStream_t> slot_streams;
 };
 
 static thread_local std::string g_create_error;
@@ -651,26 +661,86 @@ static sfr_status solve_with(Solver& sv, const sfr_problem& p, sfr_result* res, 
   }
 }
 
-static void worker_main(sfr_ctx* ctx) {
+// Device bytes one request needs while it runs (workspace, plus staging for host buffers and
+// the FR-Nys block buffers), from the same planner the solve uses.
+static size_t request_bytes(const sfr_problem& p, int num_sms) {
+  const bool fp64 = p.precision == SFR_PREC_FP64;
+  size_t total = 0;
+  auto one = [&](int64_t m, int64_t n) {
+    Shape s = plan_shape(m, n, n, p.r, num_sms);
+    const bool tc = !fp64 && tc_supported(s, p.m_dtype, n);
+    if (tc) {
+      s.sweep_grid_x = (int)((m + 127) / 128);
+      s.nsplit = 1;
+    }
+    return carve(s, fp64, nullptr, nullptr, tc);
+  };
+  if (p.nys_l) {
+    total = std::max(one(p.m, p.nys_l), one(p.nys_l, p.n));
+    total += dtype_size(p.m_dtype) * (size_t)(p.m * p.nys_l + p.nys_l * p.n) + 8 * (size_t)(2 * p.m + 2 * p.nys_l + p.n) * p.r;
+  } else {
+    total = one(p.m, p.n);
+  }
+  if (p.mem == SFR_MEM_HOST) total += dtype_size(p.m_dtype) * (size_t)(p.m * p.ldm) + 16 * (size_t)p.m * p.n;
+  return total;
+}
+
+// One slot: take the oldest request once the HBM budget admits it, solve it on this slot's
+// stream, release its workspace share, take the next (continuous batching of independent solves).
+static void worker_main(sfr_ctx* ctx, int slot) {
   cudaSetDevice(ctx->device);
+  Solver& sv = *ctx->slot_solvers[slot];
   for (;;) {
     std::shared_ptr<Request> rq;
+    size_t need = 0;
     {
       std::unique_lock<std::mutex> lk(ctx->mu);
-      ctx->cv_work.wait(lk, [&] { return ctx->stopping || !ctx->queue.empty(); });
-      if (ctx->queue.empty()) return;
+      for (;;) {
+        if (ctx->queue.empty()) {
+          if (ctx->stopping) return;
+          ctx->cv_work.wait(lk);
+          continue;
+        }
+        need = request_bytes(ctx->queue.front()->prob, sv.num_sms);
+        if (ctx->budget && need > ctx->budget) {  // can never be admitted
+          rq = ctx->queue.front();
+          ctx->queue.pop_front();
+          rq->status = SFR_E_NOMEM;
+          rq->res->status = SFR_E_NOMEM;
+          rq->finished = true;
+          ctx->last_error = fmt("request needs %zu bytes; the HBM budget is %zu", need, ctx->budget);
+          ctx->cv_done.notify_all();
+          rq.reset();
+          continue;
+        }
+        if (!ctx->budget || ctx->in_use + need <= ctx->budget) break;
+        ctx->cv_work.wait(lk);  // wait for a running request to release memory
+      }
       rq = ctx->queue.front();
       ctx->queue.pop_front();
+      ctx->in_use += need;
     }
     std::string err;
-    sfr_status s = solve_with(*ctx->worker_solver, rq->prob, rq->res, &err);
+    sfr_status st = solve_with(sv, rq->prob, rq->res, &err);
+    if (ctx->budget) {  // with a budget the slot keeps no memory between requests
+      sv.graph_key.clear();
+      if (sv.graph) {
+        cudaGraphExecDestroy(sv.graph);
+        sv.graph = nullptr;
+      }
+      sv.work.release(&sv.held);
+      sv.staging.release(&sv.held);
+      sv.nys.release(&sv.held);
+    }
     {
       std::lock_guard<std::mutex> lk(ctx->mu);
-      rq->status = s;
+      ctx->in_use -= need;
+      rq->status = st;
       rq->finished = true;
-      if (s < 0) ctx->last_error = err;
+      if (st < 0) ctx->last_error = err;
     }
     ctx->cv_done.notify_all();
+    ctx->cv_work.notify_all();
   }
 }
 
@@ -698,7 +768,7 @@ sfr_status sfr_create(sfr_ctx** out, const sfr_config* cfg) {
   }
   auto ctx = std::make_unique<sfr_ctx>();
   ctx->device = cfg->device;
-  ctx->max_slots = cfg->max_slots > 0 ? cfg->max_slots : 8;
+  ctx->max_slots = cfg->max_slots > 0 ? std::min(cfg->max_slots, 64) : 8;
   try {
     SFR_CUDA(cudaSetDevice(cfg->device));
     cudaDeviceProp prop;
@@ -709,24 +779,31 @@ sfr_status sfr_create(sfr_ctx** out, const sfr_config* cfg) {
       SFR_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
       ctx->own_stream = true;
     }
-    SFR_CUDA(cudaStreamCreateWithFlags(&ctx->worker_stream, cudaStreamNonBlocking));
-    for (int w = 0; w < 2; ++w) {
+    ctx->budget = cfg->hbm_budget_bytes;
+    auto make_solver = [&](cudaStream_t stream, bool main) {
       auto sv = std::make_unique<Solver>();
       sv->device = cfg->device;
       sv->num_sms = prop.multiProcessorCount;
-      sv->stream = w == 0 ? ctx->stream : ctx->worker_stream;
-      sv->budget = cfg->hbm_budget_bytes;
-      sv->profile = w == 0 && cfg->profile != 0;
-      sv->count_stats = w == 0;
+      sv->stream = stream;
+      sv->budget = main ? cfg->hbm_budget_bytes : 0;  // slots are admitted by the context's budget
+      sv->profile = main && cfg->profile != 0;
+      sv->count_stats = main;
       SFR_CUDA(cudaMallocHost(&sv->host_state, sizeof(DevState)));
-      (w == 0 ? ctx->solver : ctx->worker_solver) = std::move(sv);
+      return sv;
+    };
+    ctx->solver = make_solver(ctx->stream, true);
+    for (int w = 0; w < ctx->max_slots; ++w) {
+      cudaStream_t st;
+      SFR_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      ctx->slot_streams.push_back(st);
+      ctx->slot_solvers.push_back(make_solver(st, false));
     }
   } catch (const Fail& f) {
     g_create_error = f.msg;
     return f.code;
   }
   sfr_ctx* raw = ctx.release();
-  raw->worker = std::thread(worker_main, raw);
+  for (int w = 0; w < raw->max_slots; ++w) raw->workers.emplace_back(worker_main, raw, w);
   *out = raw;
   return SFR_OK;
 }
@@ -821,11 +898,12 @@ sfr_status sfr_destroy(sfr_ctx* ctx) {
     ctx->stopping = true;
   }
   ctx->cv_work.notify_all();
-  if (ctx->worker.joinable()) ctx->worker.join();
+  for (auto& w : ctx->workers)
+    if (w.joinable()) w.join();
   cudaSetDevice(ctx->device);
   ctx->solver.reset();
-  ctx->worker_solver.reset();
-  if (ctx->worker_stream) cudaStreamDestroy(ctx->worker_stream);
+  ctx->slot_solvers.clear();
+  for (cudaStream_t st : ctx->slot_streams) cudaStreamDestroy(st);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return SFR_OK;

@@ -11,8 +11,9 @@
 // which keeps float32-level accuracy; Delta V_bar and Delta^T U_new are bfloat16 products
 // (Delta is O(1/mu), so its rounding is small against L).
 //
-// Sweep CTA: 128 rows x a range of 64-column tiles.  Warps 0-3 are the epilogue (one thread
-// per row, TMEM lane = row), warp 4 issues TMA loads, warp 5 owns TMEM and issues MMAs.
+// Sweep CTA: 128 rows x a range of 64-column tiles.  Warps 0-7 are the epilogue (warp w reads
+// TMEM lanes 32 (w % 4) .. + 31, i.e. rows, and columns 32 (w / 4) .. + 31 of each tile), warp 8
+// issues TMA loads, warp 9 owns TMEM and issues MMAs.
 #include <cuda.h>
 
 #include "sfr_internal.h"
@@ -27,29 +28,29 @@ using namespace tc;
 constexpr int TBM = 128, TBN = 64, TR = 64;
 
 // shared memory map of the sweep kernel (offsets from a 1024-byte aligned base)
-constexpr uint32_t OFF_UH = 0;          // U_hi: 2 K-atoms x 128 rows x 128 B
-constexpr uint32_t OFF_UL = 32768;      // U_lo
-constexpr uint32_t OFF_CH = 65536;      // C_hi tile: 2 K-atoms x 64 rows x 128 B
-constexpr uint32_t OFF_CL = 81920;      // C_lo tile
-constexpr uint32_t OFF_VT = 98304;      // V^T tile (64 a-rows x 64 j bf16), 2 stages x 8 KB
-constexpr uint32_t OFF_MS = 114688;     // M tile (128 x 64 bf16), 2 stages x 16 KB
-constexpr uint32_t OFF_YS = 147456;     // Y tile (128 x 64 bf16), 2 stages x 16 KB; Y_{k+1} written in place
-constexpr uint32_t OFF_DA = 180224;     // Delta tile, A operand of Delta V (128 x 64 bf16)
-constexpr uint32_t OFF_DT = 196608;     // Delta^T staging: 2 boxes x 64 j-rows x 64 i bf16
-constexpr uint32_t OFF_BAR = 212992;    // mbarriers and flags
+constexpr int NSTAGE = 3;
+constexpr uint32_t OFF_C = 0;           // C tiles, 2 buffers x 32 KB: hi (2 K-atoms x 64 rows x 128 B) then lo
+constexpr uint32_t C_BUF = 32768;
+constexpr uint32_t OFF_ST = 65536;      // input stages, 3 x 40 KB: M tile (128 x 64 bf16), Y tile, V^T tile (64 x 64 bf16)
+constexpr uint32_t ST_BYTES = 40960;
+constexpr uint32_t ST_Y = 16384, ST_VT = 32768;
+constexpr uint32_t OFF_YO = OFF_ST + NSTAGE * ST_BYTES;  // Y_{k+1} tile, TMA store source
+constexpr uint32_t OFF_DA = OFF_YO + 16384;              // Delta tile: A operand of Delta V and TMA store source
+constexpr uint32_t OFF_BAR = OFF_DA + 16384;
 constexpr uint32_t SWEEP_SMEM = OFF_BAR + 256 + 1024;
+static_assert(OFF_BAR % 1024 == 0, "alignment");
+// tensor memory columns
+constexpr uint32_t TM_L = 0, TM_Q = 128, TM_UH = 256, TM_UL = 320, TM_COLS = 512;
 
 struct SweepBars {
-  uint64_t u_full;
-  uint64_t stage_full[2];
-  uint64_t stage_empty[2];
-  uint64_t c_full, c_empty;
+  uint64_t stage_full[NSTAGE], stage_empty[NSTAGE];
+  uint64_t c_full[2], c_empty[2];
   uint64_t l_full[2], l_empty[2];
   uint64_t d_full, d_empty;
   uint64_t q_full;
   uint32_t tmem_base;
   int abort;
-  float red[4];
+  float red[8];
 };
 static_assert(sizeof(SweepBars) <= 256, "barrier block");
 
@@ -62,17 +63,43 @@ __device__ __forceinline__ uint32_t pack_bf2(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-__global__ void __launch_bounds__(192, 1) sweep_tc_kernel(const __grid_constant__ CUtensorMap tmM,
-                                                          const __grid_constant__ CUtensorMap tmYin,
-                                                          const __grid_constant__ CUtensorMap tmYout,
-                                                          const __grid_constant__ CUtensorMap tmDt,
-                                                          const __grid_constant__ CUtensorMap tmUh,
-                                                          const __grid_constant__ CUtensorMap tmUl,
-                                                          const __grid_constant__ CUtensorMap tmCh,
-                                                          const __grid_constant__ CUtensorMap tmCl,
-                                                          const __grid_constant__ CUtensorMap tmVt, int64_t m,
-                                                          int64_t n, int cols_per_split, float* __restrict__ Qpart,
-                                                          double* __restrict__ resid_part, DevState* st) {
+__device__ __forceinline__ void mma_tf32_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t id,
+                                                uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(
+          d_tmem),
+      "r"(a_tmem), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])));
+}
+
+constexpr int kEpiThreads = 256;
+constexpr int kSweepThreads = kEpiThreads + 64;
+
+// Sweep CTA: 128 rows x a range of 64-column tiles.  Warps 0-7: epilogue (warp w owns TMEM
+// lanes / rows 32 (w % 4) .. + 31 and columns 32 (w / 4) .. + 31 of each tile); warp 8: TMA
+// producer; warp 9: TMEM owner and MMA issuer.  U_hi / U_lo (the fixed A operand of the L
+// products) live in tensor memory; M, Y and V^T tiles stream through three stages; C tiles
+// are double buffered; Y_{k+1} and Delta leave through TMA stores.
+__global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid_constant__ CUtensorMap tmM,
+                                                                   const __grid_constant__ CUtensorMap tmYin,
+                                                                   const __grid_constant__ CUtensorMap tmYout,
+                                                                   const __grid_constant__ CUtensorMap tmD,
+                                                                   const __grid_constant__ CUtensorMap tmCh,
+                                                                   const __grid_constant__ CUtensorMap tmCl,
+                                                                   const __grid_constant__ CUtensorMap tmVt,
+                                                                   const float* __restrict__ Uh,
+                                                                   const float* __restrict__ Ul, int64_t m, int64_t n,
+                                                                   int cols_per_split, float* __restrict__ Qpart,
+                                                                   double* __restrict__ resid_part, DevState* st) {
   if (stopped(st)) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -85,159 +112,183 @@ __global__ void __launch_bounds__(192, 1) sweep_tc_kernel(const __grid_constant_
   volatile int* abort = &B.abort;
 
   if (tid == 0) {
-    mbar_init(&B.u_full, 1);
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(&B.stage_full[s], 1);
       mbar_init(&B.stage_empty[s], 2);
-      mbar_init(&B.l_full[s], 1);
-      mbar_init(&B.l_empty[s], 128);
     }
-    mbar_init(&B.c_full, 1);
-    mbar_init(&B.c_empty, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&B.c_full[s], 1);
+      mbar_init(&B.c_empty[s], 1);
+      mbar_init(&B.l_full[s], 1);
+      mbar_init(&B.l_empty[s], kEpiThreads);
+    }
     mbar_init(&B.d_full, 1);
     mbar_init(&B.d_empty, 1);
     mbar_init(&B.q_full, 1);
     B.abort = 0;
     mbar_fence_init();
   }
-  if (warp == 5) tmem_alloc(&B.tmem_base, 256);
+  if (warp == 9) tmem_alloc(&B.tmem_base, TM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = B.tmem_base;
+  const int quarter = warp & 3, half = (warp >> 2) & 1;
+  const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+  if (warp < 8) {
+    // U_hi / U_lo rows of this CTA into tensor memory (lane = row, column = k)
+    const int row = quarter * 32 + lane;
+    const int64_t gi = (int64_t)i0 + row;
+    float v[16];
+    for (int part = 0; part < 2; ++part) {
+      const float* src = part ? Ul : Uh;
+      for (int c = 0; c < 32; c += 16) {
+        const int k0 = half * 32 + c;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = gi < m ? src[gi * TR + k0 + q] : 0.f;
+        tmem_st16(tmem + lane_base + (part ? TM_UL : TM_UH) + k0, v);
+      }
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
 
-  if (warp == 4) {
+  if (warp == 8) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       prefetch_map(&tmM);
       prefetch_map(&tmYin);
-      mbar_expect_tx(&B.u_full, 4 * 16384);
-      for (int a = 0; a < 2; ++a) {
-        tma_load_2d(sm + OFF_UH + a * 16384, &tmUh, 32 * a, i0, &B.u_full);
-        tma_load_2d(sm + OFF_UL + a * 16384, &tmUl, 32 * a, i0, &B.u_full);
-      }
-      int armed_stage[2] = {-1, -1}, armed_c = -1;  // last tile whose loads were issued per barrier
+      int armed_stage[NSTAGE] = {-1, -1, -1}, armed_c[2] = {-1, -1};
       for (int t = 0; t < ntiles && !*abort; ++t) {
-        const int s = t & 1, j0 = jbeg + t * TBN;
-        if (t >= 2 && !mbar_wait(&B.stage_empty[s], ((t >> 1) - 1) & 1, abort)) break;
+        const int s = t % NSTAGE, j0 = jbeg + t * TBN;
+        if (t >= NSTAGE && !mbar_wait(&B.stage_empty[s], ((t / NSTAGE) - 1) & 1, abort)) break;
+        unsigned char* stg = sm + OFF_ST + s * ST_BYTES;
         mbar_expect_tx(&B.stage_full[s], 16384 + 16384 + 8192);
-        tma_load_2d(sm + OFF_MS + s * 16384, &tmM, j0, i0, &B.stage_full[s]);
-        tma_load_2d(sm + OFF_YS + s * 16384, &tmYin, j0, i0, &B.stage_full[s]);
-        tma_load_2d(sm + OFF_VT + s * 8192, &tmVt, j0, 0, &B.stage_full[s]);
+        tma_load_2d(stg, &tmM, j0, i0, &B.stage_full[s]);
+        tma_load_2d(stg + ST_Y, &tmYin, j0, i0, &B.stage_full[s]);
+        tma_load_2d(stg + ST_VT, &tmVt, j0, 0, &B.stage_full[s]);
         armed_stage[s] = t;
-        if (t >= 1 && !mbar_wait(&B.c_empty, (t - 1) & 1, abort)) break;
-        mbar_expect_tx(&B.c_full, 4 * 8192);
+        const int cb = t & 1;
+        if (t >= 2 && !mbar_wait(&B.c_empty[cb], ((t >> 1) - 1) & 1, abort)) break;
+        unsigned char* cbuf = sm + OFF_C + cb * C_BUF;
+        mbar_expect_tx(&B.c_full[cb], 4 * 8192);
         for (int a = 0; a < 2; ++a) {
-          tma_load_2d(sm + OFF_CH + a * 8192, &tmCh, 32 * a, j0, &B.c_full);
-          tma_load_2d(sm + OFF_CL + a * 8192, &tmCl, 32 * a, j0, &B.c_full);
+          tma_load_2d(cbuf + a * 8192, &tmCh, 32 * a, j0, &B.c_full[cb]);
+          tma_load_2d(cbuf + 16384 + a * 8192, &tmCl, 32 * a, j0, &B.c_full[cb]);
         }
-        armed_c = t;
+        armed_c[cb] = t;
       }
       if (*abort) {  // let the copies this thread issued land before the CTA exits
-        int dummy = 0;
-        mbar_wait(&B.u_full, 0, &dummy);
+        for (int q = 0; q < NSTAGE; ++q)
+          if (armed_stage[q] >= 0) {
+            int dummy = 0;
+            mbar_wait(&B.stage_full[q], (armed_stage[q] / NSTAGE) & 1, &dummy);
+          }
         for (int q = 0; q < 2; ++q)
-          if (armed_stage[q] >= 0) { dummy = 0; mbar_wait(&B.stage_full[q], (armed_stage[q] >> 1) & 1, &dummy); }
-        if (armed_c >= 0) { dummy = 0; mbar_wait(&B.c_full, armed_c & 1, &dummy); }
+          if (armed_c[q] >= 0) {
+            int dummy = 0;
+            mbar_wait(&B.c_full[q], (armed_c[q] >> 1) & 1, &dummy);
+          }
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == 9) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t id_l = idesc(2, TBM, TBN);   // tf32, 128 x 64
       const uint32_t id_q = idesc(1, TBM, TR);    // bf16, 128 x 64
-      const uint32_t q_tmem = tmem + 128;
       auto delta_v = [&](int tt) -> bool {
-        const int s = tt & 1;
+        const int s = tt % NSTAGE;
         if (!mbar_wait(&B.d_full, tt & 1, abort)) return false;
         tc_fence_after();
+        const uint32_t vt = smem_u32(sm + OFF_ST + s * ST_BYTES + ST_VT);
         for (int kk = 0; kk < TBN / 16; ++kk) {
           const uint64_t a = desc_sw128(smem_u32(sm + OFF_DA) + kk * 32);
-          const uint64_t b = desc_sw128(smem_u32(sm + OFF_VT + s * 8192) + kk * 32);
-          mma_bf16(q_tmem, a, b, id_q, (tt > 0 || kk > 0) ? 1u : 0u);
+          const uint64_t b = desc_sw128(vt + kk * 32);
+          mma_bf16(tmem + TM_Q, a, b, id_q, (tt > 0 || kk > 0) ? 1u : 0u);
         }
         mma_commit(&B.d_empty);
         mma_commit(&B.stage_empty[s]);
         return true;
       };
-      bool ok = mbar_wait(&B.u_full, 0, abort);
+      bool ok = true;
       for (int t = 0; ok && t < ntiles; ++t) {
         const int b = t & 1;
-        if (!mbar_wait(&B.c_full, t & 1, abort)) { ok = false; break; }
+        if (!mbar_wait(&B.c_full[b], (t >> 1) & 1, abort)) { ok = false; break; }
         if (t >= 2 && !mbar_wait(&B.l_empty[b], ((t >> 1) - 1) & 1, abort)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t d = tmem + b * TBN;
-        // L = U_hi C_hi^T + U_hi C_lo^T + U_lo C_hi^T, K = 64 in 8 steps of 8 (32 bytes)
+        const uint32_t d = tmem + TM_L + b * TBN;
+        const uint32_t cbuf = smem_u32(sm + OFF_C + b * C_BUF);
+        // L = U_hi C_hi^T + U_hi C_lo^T + U_lo C_hi^T, K = 64 in 8 steps of 8
         for (int term = 0; term < 3; ++term) {
-          const uint32_t ua = smem_u32(sm + (term == 2 ? OFF_UL : OFF_UH));
-          const uint32_t cb = smem_u32(sm + (term == 1 ? OFF_CL : OFF_CH));
+          const uint32_t ua = tmem + (term == 2 ? TM_UL : TM_UH);
+          const uint32_t cb = cbuf + (term == 1 ? 16384 : 0);
           for (int ks = 0; ks < 8; ++ks) {
-            const uint32_t koff = (ks >> 2) * 0 + (ks & 3) * 32;
-            const uint64_t a = desc_sw128(ua + (ks >> 2) * 16384 + koff);
-            const uint64_t bb = desc_sw128(cb + (ks >> 2) * 8192 + koff);
-            mma_tf32(d, a, bb, id_l, (term > 0 || ks > 0) ? 1u : 0u);
+            const uint64_t bb = desc_sw128(cb + (ks >> 2) * 8192 + (ks & 3) * 32);
+            mma_tf32_tmem_a(d, ua + 8 * ks, bb, id_l, (term > 0 || ks > 0) ? 1u : 0u);
           }
         }
         mma_commit(&B.l_full[b]);
-        mma_commit(&B.c_empty);
+        mma_commit(&B.c_empty[b]);
         if (t >= 1 && !delta_v(t - 1)) { ok = false; break; }
       }
       if (ok && ntiles > 0) ok = delta_v(ntiles - 1);
-      if (ok) mma_commit(&B.q_full);
-      else {  // MMAs already issued must finish before the accumulator memory is released
+      mma_commit(&B.q_full);
+      if (!ok) {  // MMAs already issued must finish before the tensor memory is released
         int dummy = 0;
-        mma_commit(&B.q_full);
         mbar_wait(&B.q_full, 0, &dummy);
       }
     }
   } else {
-    // ------------------------------------------------------------ epilogue: warps 0-3, one row per thread
-    const int row = tid;                      // TMEM lane and tile row
+    // ------------------------------------------------------------ epilogue: warps 0-7
+    const int row = quarter * 32 + lane;          // TMEM lane and tile row
+    const int cbase = half * 32;                  // first of this warp's 32 columns
     const int64_t gi = (int64_t)i0 + row;
     const float mu = (float)st->mu;
     const double mu_next_d = fmin(st->mu_max, st->rho * st->mu);
     const float inv_mu = (float)(1.0 / st->mu), dcoef = (float)(1.0 / st->mu + 1.0 / mu_next_d);
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     float resid = 0.f;
     bool ok = true;
     for (int t = 0; t < ntiles; ++t) {
-      const int s = t & 1, b = t & 1, j0 = jbeg + t * TBN;
-      mbar_wait(&B.l_full[b], (t >> 1) & 1, abort) && mbar_wait(&B.stage_full[s], (t >> 1) & 1, abort) &&
+      const int s = t % NSTAGE, b = t & 1, j0 = jbeg + t * TBN;
+      mbar_wait(&B.l_full[b], (t >> 1) & 1, abort) && mbar_wait(&B.stage_full[s], (t / NSTAGE) & 1, abort) &&
           (t == 0 || mbar_wait(&B.d_empty, (t - 1) & 1, abort));
-      named_bar(1, 128);  // the abort decision below is the same for all epilogue threads
+      if (tid == 0 && t >= 1) tma_store_wait_read0();  // YO / DA of the previous tile have been read
+      named_bar(1, kEpiThreads);  // the abort decision below is the same for all epilogue threads
       if (*abort) {
         ok = false;
         break;
       }
       tc_fence_after();
-      float L[TBN];
-#pragma unroll
-      for (int c = 0; c < TBN; c += 16) tmem_ld16(tmem + lane_base + b * TBN + c, L + c);
+      float L[32];
+      tmem_ld16(tmem + lane_base + TM_L + b * TBN + cbase, L);
+      tmem_ld16(tmem + lane_base + TM_L + b * TBN + cbase + 16, L + 16);
       tmem_ld_wait();
       tc_fence_before();
       mbar_arrive(&B.l_empty[b]);
-      unsigned char* ms = sm + OFF_MS + s * 16384;
-      unsigned char* ys = sm + OFF_YS + s * 16384;
+      const unsigned char* ms = sm + OFF_ST + s * ST_BYTES;
+      const unsigned char* ys = ms + ST_Y;
+      unsigned char* yo = sm + OFF_YO;
       unsigned char* da = sm + OFF_DA;
-      unsigned char* dt = sm + OFF_DT + (row >> 6) * 8192;
-      const int ir = row & 63;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {  // 16-byte chunk c = columns 8c .. 8c+7
+      for (int cc = 0; cc < 4; ++cc) {  // 16-byte chunk c = columns 8c .. 8c+7
+        const int c = half * 4 + cc;
         const uint32_t off = sw128(row, c);
         const uint4 mw = *reinterpret_cast<const uint4*>(ms + off);
         const uint4 yw = *reinterpret_cast<const uint4*>(ys + off);
         const uint32_t mv[4] = {mw.x, mw.y, mw.z, mw.w}, yv[4] = {yw.x, yw.y, yw.z, yw.w};
-        uint32_t yo[4], dd[4];
+        uint32_t yn2[4], dd[4];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
           float ynew[2], dnew[2];
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
-            const int col = 8 * c + 2 * h + e;
+            const int lc = 8 * cc + 2 * h + e;     // column within this warp's 32
             const float mval = e ? bf_hi(mv[h]) : bf_lo(mv[h]);
             const float y = e ? bf_hi(yv[h]) : bf_lo(yv[h]);
-            const bool in = j0 + col < jend;
-            const float z = mval - L[col] + y * inv_mu;
+            const bool in = j0 + cbase + lc < jend;
+            const float z = mval - L[lc] + y * inv_mu;
             float yn = fminf(1.f, fmaxf(-1.f, mu * z));
             yn = in ? __bfloat162float(__float2bfloat16_rn(yn)) : 0.f;  // value as stored
             const float dv = yn * dcoef - y * inv_mu;
@@ -246,60 +297,52 @@ __global__ void __launch_bounds__(192, 1) sweep_tc_kernel(const __grid_constant_
             ynew[e] = yn;
             dnew[e] = in ? dv : 0.f;
           }
-          yo[h] = pack_bf2(ynew[0], ynew[1]);
+          yn2[h] = pack_bf2(ynew[0], ynew[1]);
           dd[h] = pack_bf2(dnew[0], dnew[1]);
         }
-        *reinterpret_cast<uint4*>(ys + off) = make_uint4(yo[0], yo[1], yo[2], yo[3]);
+        *reinterpret_cast<uint4*>(yo + off) = make_uint4(yn2[0], yn2[1], yn2[2], yn2[3]);
         *reinterpret_cast<uint4*>(da + off) = make_uint4(dd[0], dd[1], dd[2], dd[3]);
-        // transposed copy: element (j = 8c + q, i = row) -> box (row / 64), row j, i-chunk (ir / 8)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const uint32_t w = dd[q >> 1];
-          const unsigned short hv = (unsigned short)((q & 1) ? (w >> 16) : (w & 0xFFFF));
-          *reinterpret_cast<unsigned short*>(dt + sw128(8 * c + q, ir >> 3) + (ir & 7) * 2) = hv;
-        }
       }
       fence_async_smem();
-      named_bar(1, 128);
+      named_bar(1, kEpiThreads);
       if (tid == 0) {
+        mbar_arrive(&B.stage_empty[s]);  // M and Y of this stage have been read
         mbar_arrive(&B.d_full);
-        tma_store_2d(&tmYout, ys, j0, i0);
-        tma_store_2d(&tmDt, sm + OFF_DT, i0, j0);
-        tma_store_2d(&tmDt, sm + OFF_DT + 8192, i0 + 64, j0);
+        tma_store_2d(&tmYout, yo, j0, i0);
+        tma_store_2d(&tmD, da, j0, i0);
         tma_store_commit();
-        tma_store_wait_read0();
-        mbar_arrive(&B.stage_empty[s]);
       }
-      named_bar(1, 128);
     }
     if (ok && ntiles > 0) mbar_wait(&B.q_full, 0, abort);
-    named_bar(1, 128);  // uniform decision before the warp-collective TMEM loads
+    named_bar(1, kEpiThreads);  // uniform decision before the warp-collective TMEM loads
     if (ok && ntiles > 0 && !*abort) {
       tc_fence_after();
-      float q[TR];
-#pragma unroll
-      for (int c = 0; c < TR; c += 16) tmem_ld16(tmem + lane_base + 128 + c, q + c);
+      float q[32];
+      tmem_ld16(tmem + lane_base + TM_Q + cbase, q);
+      tmem_ld16(tmem + lane_base + TM_Q + cbase + 16, q + 16);
       tmem_ld_wait();
       if (gi < m) {
-        float4* dst = reinterpret_cast<float4*>(Qpart + ((int64_t)blockIdx.y * m + gi) * TR);
+        float4* dst = reinterpret_cast<float4*>(Qpart + ((int64_t)blockIdx.y * m + gi) * TR + cbase);
 #pragma unroll
-        for (int c = 0; c < TR / 4; ++c) dst[c] = make_float4(q[4 * c], q[4 * c + 1], q[4 * c + 2], q[4 * c + 3]);
+        for (int c = 0; c < 8; ++c) dst[c] = make_float4(q[4 * c], q[4 * c + 1], q[4 * c + 2], q[4 * c + 3]);
       }
     }
     if (tid == 0) tma_store_wait0();
-    // residual: warp sums, then thread 0 combines the four warps in a fixed order
+    // residual: warp sums, then thread 0 combines the eight warps in a fixed order
     for (int o = 16; o > 0; o >>= 1) resid += __shfl_xor_sync(0xffffffffu, resid, o);
     if (lane == 0) B.red[warp] = resid;
-    named_bar(1, 128);
-    if (tid == 0)
-      resid_part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] =
-          (double)B.red[0] + (double)B.red[1] + (double)B.red[2] + (double)B.red[3];
+    named_bar(1, kEpiThreads);
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < 8; ++w) tot += (double)B.red[w];
+      resid_part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+    }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 5) {
+  if (warp == 9) {
     tc_fence_after();
-    tmem_dealloc(tmem, 256);
+    tmem_dealloc(tmem, TM_COLS);
   }
   if (tid == 0 && B.abort) {
     st->status = SFR_E_TIMEOUT;
@@ -307,12 +350,25 @@ __global__ void __launch_bounds__(192, 1) sweep_tc_kernel(const __grid_constant_
   }
 }
 
-// ---------------------------------------------------------------- W pass: W = Delta^T U on tensor cores
-// CTA: 128 columns j of Delta (rows of Delta^T) x a chunk of rows i; D (128 x 64) in TMEM.
+// ---------------------------------------------------------------- W pass: W = X^T U on tensor cores
+// CTA: 128 columns j x a chunk of rows i; D (128 x 64) in TMEM.  A = the m x n source (Delta, or
+// M on iteration 1) read row-major as an MN-major operand (M index = column j), B = U^T (K-major).
 constexpr int WSTAGES = 4;
 constexpr uint32_t W_A_BYTES = 16384, W_B_BYTES = 8192, W_STAGE = W_A_BYTES + W_B_BYTES;
 constexpr uint32_t W_OFF_BAR = WSTAGES * W_STAGE;
 constexpr uint32_t WPASS_SMEM = W_OFF_BAR + 128 + 1024;
+
+// MN-major operand in the 128-byte swizzle layout: 64-element atoms along M 8 KB apart (LBO),
+// 8-row groups along K 1024 bytes apart (SBO)
+__device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)(8192 >> 4) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
 
 struct WBars {
   uint64_t full[WSTAGES], empty[WSTAGES];
@@ -321,7 +377,7 @@ struct WBars {
   int abort;
 };
 
-__global__ void __launch_bounds__(192, 1) wpass_tc_kernel(const __grid_constant__ CUtensorMap tmDt,
+__global__ void __launch_bounds__(192, 1) wpass_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                           const __grid_constant__ CUtensorMap tmUt, int64_t m,
                                                           int64_t n, int rows_per_chunk, float* __restrict__ Wpart,
                                                           DevState* st) {
@@ -357,7 +413,8 @@ __global__ void __launch_bounds__(192, 1) wpass_tc_kernel(const __grid_constant_
         const int s = k % WSTAGES;
         if (k >= WSTAGES && !mbar_wait(&B.empty[s], ((k / WSTAGES) - 1) & 1, abort)) break;
         mbar_expect_tx(&B.full[s], W_STAGE);
-        tma_load_2d(sm + s * W_STAGE, &tmDt, r0 + 64 * k, j0, &B.full[s]);
+        tma_load_2d(sm + s * W_STAGE, &tmA, j0, r0 + 64 * k, &B.full[s]);
+        tma_load_2d(sm + s * W_STAGE + 8192, &tmA, j0 + 64, r0 + 64 * k, &B.full[s]);
         tma_load_2d(sm + s * W_STAGE + W_A_BYTES, &tmUt, r0 + 64 * k, 0, &B.full[s]);
         armed[s] = k;
       }
@@ -370,14 +427,14 @@ __global__ void __launch_bounds__(192, 1) wpass_tc_kernel(const __grid_constant_
     }
   } else if (warp == 5) {
     if (lane == 0) {
-      const uint32_t id = idesc(1, 128, TR);
+      const uint32_t id = idesc(1, 128, TR) | (1u << 15);  // A MN-major
       bool ok = true;
       for (int k = 0; k < nk; ++k) {
         const int s = k % WSTAGES;
         if (!mbar_wait(&B.full[s], (k / WSTAGES) & 1, abort)) { ok = false; break; }
         tc_fence_after();
         for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t a = desc_sw128(smem_u32(sm + s * W_STAGE) + kk * 32);
+          const uint64_t a = desc_sw128_mn(smem_u32(sm + s * W_STAGE) + kk * 2048);
           const uint64_t b = desc_sw128(smem_u32(sm + s * W_STAGE + W_A_BYTES) + kk * 32);
           mma_bf16(tmem, a, b, id, (k > 0 || kk > 0) ? 1u : 0u);
         }
@@ -462,22 +519,6 @@ __global__ void split_transpose_kernel(const float* __restrict__ X, const float*
   }
 }
 
-// Mt = M^T (bf16), so iteration 1's W = M^T U uses the same K-major pass as later iterations.
-__global__ void transpose_bf16_kernel(const __nv_bfloat16* __restrict__ M, int64_t m, int64_t n, int64_t ldm,
-                                      __nv_bfloat16* __restrict__ Mt, int64_t ldt) {
-  __shared__ __nv_bfloat16 tile[64][66];
-  const int64_t i0 = (int64_t)blockIdx.y * 64, j0 = (int64_t)blockIdx.x * 64;
-  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-    const int ii = e / 64, jj = e % 64;
-    tile[ii][jj] = (i0 + ii < m && j0 + jj < n) ? M[(i0 + ii) * ldm + j0 + jj] : __float2bfloat16_rn(0.f);
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-    const int jj = e / 64, ii = e % 64;
-    if (i0 + ii < m && j0 + jj < n) Mt[(j0 + jj) * ldt + i0 + ii] = tile[ii][jj];
-  }
-}
-
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 // ---------------------------------------------------------------- tensor maps
@@ -521,23 +562,15 @@ cudaError_t tc_make_maps(const Shape& s, const TcBuffers& t, const void* M, int6
   const auto BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   bool ok = true;
   ok &= make_map(&maps->M, M, BF, s.n, s.m, 2 * ldm, 64, 128);
+  ok &= make_map(&maps->M_w, M, BF, s.n, s.m, 2 * ldm, 64, 64);
   for (int q = 0; q < 2; ++q) ok &= make_map(&maps->Y[q], t.Y[q], BF, s.n, s.m, 2 * t.ldy, 64, 128);
-  ok &= make_map(&maps->Dt_store, t.Dt, BF, s.m, s.n, 2 * t.ldd, 64, 64);
-  ok &= make_map(&maps->Dt_load, t.Dt, BF, s.m, s.n, 2 * t.ldd, 64, 128);
+  ok &= make_map(&maps->D, t.D, BF, s.n, s.m, 2 * t.ldy, 64, 128);
+  ok &= make_map(&maps->D_w, t.D, BF, s.n, s.m, 2 * t.ldy, 64, 64);
   ok &= make_map(&maps->Ut, t.Ut, BF, s.m, 64, 2 * t.ldd, 64, 64);
-  ok &= make_map(&maps->Uh, t.Uh, F32, 64, s.m, 256, 32, 128);
-  ok &= make_map(&maps->Ul, t.Ul, F32, 64, s.m, 256, 32, 128);
   ok &= make_map(&maps->Ch, t.Ch, F32, 64, s.n, 256, 32, 64);
   ok &= make_map(&maps->Cl, t.Cl, F32, 64, s.n, 256, 32, 64);
   ok &= make_map(&maps->Vt, t.Vt, BF, s.n, 64, 2 * t.ldy, 64, 64);
   return ok ? cudaSuccess : cudaErrorInvalidValue;
-}
-
-cudaError_t tc_launch_transpose_m(const Shape& s, const void* M, int64_t ldm, const TcBuffers& t, cudaStream_t st) {
-  dim3 grid(cdiv(s.n, 64), cdiv(s.m, 64));
-  transpose_bf16_kernel<<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(M), s.m, s.n, ldm,
-                                              static_cast<__nv_bfloat16*>(t.Dt), t.ldd);
-  return cudaGetLastError();
 }
 
 cudaError_t tc_launch_prep_u(const Shape& s, const float* U, const TcBuffers& t, const DevState* dst, cudaStream_t st) {
@@ -553,21 +586,24 @@ cudaError_t tc_launch_prep_v(const Shape& s, const float* C, const float* V, con
   return cudaGetLastError();
 }
 
-cudaError_t tc_launch_wpass(const Shape& s, const TcMaps& mp, float* Wpart, DevState* dst, cudaStream_t st) {
+cudaError_t tc_launch_wpass(const Shape& s, const TcMaps& mp, bool first, float* Wpart, DevState* dst,
+                            cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(wpass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WPASS_SMEM);
   if (e != cudaSuccess) return e;
   dim3 grid(cdiv(s.n, 128), s.nchunk);
-  wpass_tc_kernel<<<grid, 192, WPASS_SMEM, st>>>(mp.Dt_load, mp.Ut, s.m, s.n, s.rows_per_chunk, Wpart, dst);
+  wpass_tc_kernel<<<grid, 192, WPASS_SMEM, st>>>(first ? mp.M_w : mp.D_w, mp.Ut, s.m, s.n, s.rows_per_chunk, Wpart,
+                                                  dst);
   return cudaGetLastError();
 }
 
-cudaError_t tc_launch_sweep(const Shape& s, const TcMaps& mp, int y_in, float* Qpart, double* resid_part,
-                            DevState* dst, cudaStream_t st) {
+cudaError_t tc_launch_sweep(const Shape& s, const TcMaps& mp, const TcBuffers& t, int y_in, float* Qpart,
+                            double* resid_part, DevState* dst, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(sweep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
   if (e != cudaSuccess) return e;
   dim3 grid(cdiv(s.m, TBM), s.nsplit);
-  sweep_tc_kernel<<<grid, 192, SWEEP_SMEM, st>>>(mp.M, mp.Y[y_in], mp.Y[1 - y_in], mp.Dt_store, mp.Uh, mp.Ul, mp.Ch,
-                                                  mp.Cl, mp.Vt, s.m, s.n, s.cols_per_split, Qpart, resid_part, dst);
+  sweep_tc_kernel<<<grid, kSweepThreads, SWEEP_SMEM, st>>>(mp.M, mp.Y[y_in], mp.Y[1 - y_in], mp.D, mp.Ch, mp.Cl,
+                                                            mp.Vt, t.Uh, t.Ul, s.m, s.n, s.cols_per_split, Qpart,
+                                                            resid_part, dst);
   return cudaGetLastError();
 }
 

@@ -15,8 +15,8 @@ struct DevState;
 struct TcBuffers {
   void* Y[2];          // multiplier ping-pong, m x ldy bfloat16
   int64_t ldy;         // n rounded up to 64
-  void* Dt;            // Delta^T, n x ldd bfloat16 (iteration 1: M^T)
-  int64_t ldd;         // m rounded up to 64
+  void* D;             // Delta, m x ldy bfloat16
+  int64_t ldd;         // m rounded up to 64 (leading dimension of U^T)
   float* Uh;           // m x 64: U rounded to TF32
   float* Ul;           // m x 64: U - Uh
   void* Ut;            // 64 x ldd bfloat16: U^T
@@ -26,17 +26,17 @@ struct TcBuffers {
 };
 
 struct TcMaps {
-  CUtensorMap M, Y[2], Dt_store, Dt_load, Ut, Uh, Ul, Ch, Cl, Vt;
+  CUtensorMap M, M_w, Y[2], D, D_w, Ut, Ch, Cl, Vt;  // *_w: 64 x 64 boxes for the W pass
 };
 
 bool tc_supported(const Shape& s, int m_dtype, int64_t ldm);
 cudaError_t tc_make_maps(const Shape& s, const TcBuffers& t, const void* M, int64_t ldm, TcMaps* maps);
-cudaError_t tc_launch_transpose_m(const Shape& s, const void* M, int64_t ldm, const TcBuffers& t, cudaStream_t st);
 cudaError_t tc_launch_prep_u(const Shape& s, const float* U, const TcBuffers& t, const DevState* dst, cudaStream_t st);
 cudaError_t tc_launch_prep_v(const Shape& s, const float* C, const float* V, const TcBuffers& t, const DevState* dst,
                              cudaStream_t st);
-cudaError_t tc_launch_wpass(const Shape& s, const TcMaps& mp, float* Wpart, DevState* dst, cudaStream_t st);
-cudaError_t tc_launch_sweep(const Shape& s, const TcMaps& mp, int y_in, float* Qpart, double* resid_part,
-                            DevState* dst, cudaStream_t st);
+cudaError_t tc_launch_wpass(const Shape& s, const TcMaps& mp, bool first, float* Wpart, DevState* dst,
+                            cudaStream_t st);
+cudaError_t tc_launch_sweep(const Shape& s, const TcMaps& mp, const TcBuffers& t, int y_in, float* Qpart,
+                            double* resid_part, DevState* dst, cudaStream_t st);
 
 }  // namespace sfr

@@ -1,0 +1,94 @@
+"""Serving: sfr_submit / sfr_poll with several slots (continuous batching of independent solves).
+
+Requests of uneven shape and precision run concurrently on the device, each slot on its own
+stream; every result must equal the same problem solved alone with sfr_solve (the kernels are
+deterministic, so equality is exact), and the HBM budget must gate admission.
+"""
+import numpy as np
+import pytest
+
+from paper_1503_03004_gb300 import binding as B
+from paper_1503_03004_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _dev(prob):
+    if prob.dtype == "bf16":
+        return torch.from_numpy(prob.M.view(np.int16)).view(torch.bfloat16).cuda()
+    return torch.from_numpy(prob.M).cuda()
+
+
+def _request(prob, precision, **kw):
+    m, n = prob.shape
+    r = prob.r
+    Md = _dev(prob)
+    f64 = dict(dtype=torch.float64, device="cuda")
+    U, Bm, V = torch.empty((m, r), **f64), torch.empty((r, r), **f64), torch.empty((n, r), **f64)
+    S = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    code = {"f64": B.F64, "f32": B.F32, "bf16": B.BF16}[prob.dtype]
+    p = B.make_problem(m=m, n=n, r=r, M_ptr=Md.data_ptr(), m_dtype=code, precision=precision, **kw)
+    res = B.make_result(U_ptr=U.data_ptr(), B_ptr=Bm.data_ptr(), V_ptr=V.data_ptr(), S_ptr=S.data_ptr(),
+                        s_dtype=B.F32, lds=n)
+    return dict(M=Md, U=U, B=Bm, V=V, S=S, p=p, res=res)
+
+
+def _workload():
+    out = []
+    for i, (m, n, r, dt, prec) in enumerate([(300, 200, 5, "f64", B.PREC_FP64), (700, 96, 3, "f32", B.PREC_MIXED),
+                                             (512, 512, 40, "bf16", B.PREC_MIXED), (256, 384, 10, "f64", B.PREC_FP64),
+                                             (1024, 64, 8, "bf16", B.PREC_MIXED), (640, 640, 64, "bf16", B.PREC_MIXED),
+                                             (128, 1000, 4, "f32", B.PREC_FP64), (900, 300, 25, "bf16", B.PREC_MIXED)]):
+        prob = synth.planted(m, n, r, p=0.06, amp=50.0, seed=500 + i, dtype=dt)
+        out.append((prob, prec))
+    return out
+
+
+def test_concurrent_requests_equal_solo_solves():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    kw = dict(rho=1.5, mu0=0.05, tol=1e-9, max_iter=300)
+    work = _workload()
+    with B.Context(0, max_slots=4) as ctx:
+        solo = []
+        for prob, prec in work:
+            q = _request(prob, prec, **kw)
+            assert ctx.solve(q["p"], q["res"]) == B.OK, ctx.last_error()
+            solo.append(q)
+        mixed = [_request(prob, prec, **kw) for prob, prec in work]
+        tickets = [ctx.submit(q["p"], q["res"]) for q in mixed]
+        for t in tickets:
+            assert ctx.poll(t, -1) == B.OK, ctx.last_error()
+    for a, b in zip(solo, mixed):
+        assert a["res"].iters == b["res"].iters
+        for key in ("U", "B", "V", "S"):
+            assert torch.equal(a[key], b[key]), key
+
+
+def test_poll_reports_pending_then_done():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    prob = synth.planted(2048, 2048, 64, p=0.05, amp=50.0, seed=77, dtype="bf16")
+    with B.Context(0, max_slots=2) as ctx:
+        q = _request(prob, B.PREC_MIXED, rho=1.5, mu0=0.05, tol=1e-9, max_iter=300)
+        t = ctx.submit(q["p"], q["res"])
+        first = ctx.poll(t, 0)
+        assert first in (B.PENDING, B.OK)
+        assert ctx.poll(t, -1) == B.OK
+        assert q["res"].status == B.OK
+
+
+def test_hbm_budget_gates_admission():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    small = synth.planted(200, 150, 4, p=0.05, amp=1.0, seed=3, dtype="f64")
+    big = synth.planted(3000, 3000, 16, p=0.05, amp=1.0, seed=4, dtype="f64")
+    with B.Context(0, max_slots=3, hbm_budget_bytes=64 << 20) as ctx:
+        qs = [_request(small, B.PREC_FP64, fixed_iters=5), _request(big, B.PREC_FP64, fixed_iters=5),
+              _request(small, B.PREC_FP64, fixed_iters=5)]
+        ts = [ctx.submit(q["p"], q["res"]) for q in qs]
+        st = [ctx.poll(t, -1) for t in ts]
+    assert st == [B.OK, B.E_NOMEM, B.OK]
+    assert torch.equal(qs[0]["U"], qs[2]["U"])
