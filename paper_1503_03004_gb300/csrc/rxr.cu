@@ -143,6 +143,8 @@ __device__ double block_reduce(double v, double* red, bool take_max) {
 __device__ void jacobi_f32(float* A, float* Q, int n2, int max_sweeps, double* red, float* cs, float* sn, int* pp,
                            int* qq) {
   const int np = n2 / 2;
+  const bool pow2 = (np & (np - 1)) == 0;
+  const int lg = 31 - __clz(np);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     double off = 0.0, dia = 0.0;
     for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
@@ -177,7 +179,7 @@ __device__ void jacobi_f32(float* A, float* Q, int n2, int max_sweeps, double* r
       // A <- J^T A J in one phase: the pairs partition the indices, so each 2 x 2 block
       // (rows {p1, q1}, columns {p2, q2}) is touched by exactly one row and one column rotation
       for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
-        const int k1 = e / np, k2 = e % np;
+        const int k1 = pow2 ? (e >> lg) : e / np, k2 = pow2 ? (e & (np - 1)) : e % np;
         const float c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
         if (s1 == 0.f && s2 == 0.f) continue;
         const int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
@@ -190,7 +192,7 @@ __device__ void jacobi_f32(float* A, float* Q, int n2, int max_sweeps, double* r
       }
       // Q <- Q J
       for (int e = threadIdx.x; e < np * n2; e += blockDim.x) {
-        const int k = e % np, j = e / np;
+        const int k = pow2 ? (e & (np - 1)) : e % np, j = pow2 ? (e >> lg) : e / np;
         const float c = cs[k], s = sn[k];
         if (s == 0.f) continue;
         const int p = pp[k], q = qq[k];
@@ -201,6 +203,59 @@ __device__ void jacobi_f32(float* A, float* Q, int n2, int max_sweeps, double* r
       __syncthreads();
     }
   }
+}
+
+// One first-order eigenbasis refinement round for a nearly diagonal A = Q^T K Q (float32):
+// Q <- Q (I + E), E_pq = A_pq / (A_qq - A_pp) for p != q (the small-angle Jacobi rotation of
+// every pair at once), then one Newton-Schulz re-orthonormalisation and A <- Q^T K Q.
+// Returns false (leaving Q, A unchanged) when some |E_pq| > 0.25, i.e. A is not close enough
+// to diagonal for the first-order step; pairs with (relative) gaps below 1e-5 are left alone,
+// since any basis of a cluster serves the Newton preconditioner.
+__device__ bool refine_basis(const float* Kf, float* Q, float* A, float* F1, float* F2, int r, double* red) {
+  float big = 0.f;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int p = e / r, q = e % r;
+    float v = 0.f;
+    if (p != q) {
+      const float gap = A[q * LD + q] - A[p * LD + p];
+      const float scl = fmaxf(fabsf(A[p * LD + p]), fabsf(A[q * LD + q]));
+      if (fabsf(gap) > 1e-5f * scl) v = A[p * LD + q] / gap;
+    }
+    F1[p * LD + q] = v;
+    big = fmaxf(big, fabsf(v));
+  }
+  big = (float)block_reduce((double)big, red, true);
+  if (!(big <= 0.25f)) return false;
+  mmf<false, false>(Q, F1, F2, r);                  // Q E
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    Q[i * LD + j] += F2[i * LD + j];
+  }
+  __syncthreads();
+  mmf<true, false>(Q, Q, F1, r);                    // Q^T Q
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    F1[i * LD + j] = 0.5f * ((i == j ? 3.f : 0.f) - F1[i * LD + j]);
+  }
+  __syncthreads();
+  mmf<false, false>(Q, F1, F2, r);                  // Q (3I - Q^T Q) / 2
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) Q[(e / r) * LD + e % r] = F2[(e / r) * LD + e % r];
+  __syncthreads();
+  mmf<false, false>(Kf, Q, F1, r);                  // A = Q^T K Q
+  mmf<true, false>(Q, F1, A, r);
+  return true;
+}
+
+__device__ bool near_diagonal(const float* A, int r, double* red) {
+  double off = 0.0, dia = 0.0;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    const double v = (double)A[i * LD + j];
+    if (i == j) dia += v * v; else off += v * v;
+  }
+  off = block_reduce(off, red, false);
+  dia = block_reduce(dia, red, false);
+  return !(off > 1e-9 * dia);
 }
 
 struct RxrSmem {
@@ -229,14 +284,25 @@ __device__ void load_gram(const double* __restrict__ parts, int count, int rp, i
   const int rpsq = rp * rp;
   for (int e = threadIdx.x; e < nloc; e += blockDim.x) {
     const int i = i0 + e / r, j = e % r;
+    // eight interleaved accumulators keep eight loads in flight (the partials sit in L2);
+    // they are combined in a fixed order, so the sum is deterministic
+    const double* src = parts + i * rp + j;
     if (fp64sum) {
-      double v = 0.0;
-      for (int c = 0; c < count; ++c) v += parts[(int64_t)c * rpsq + i * rp + j];
-      dst[i * LD + j] = v;
+      double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      int c = 0;
+      for (; c + 8 <= count; c += 8)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] += src[(int64_t)(c + q) * rpsq];
+      for (; c < count; ++c) a[0] += src[(int64_t)c * rpsq];
+      dst[i * LD + j] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     } else {  // partials of a float32 sweep: float32 sums (float64 adds run at 1/64 rate)
-      float v = 0.f;
-      for (int c = 0; c < count; ++c) v += (float)parts[(int64_t)c * rpsq + i * rp + j];
-      dst[i * LD + j] = (double)v;
+      float a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      int c = 0;
+      for (; c + 8 <= count; c += 8)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] += (float)src[(int64_t)(c + q) * rpsq];
+      for (; c < count; ++c) a[0] += (float)src[(int64_t)c * rpsq];
+      dst[i * LD + j] = (double)(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
     }
   }
   __syncthreads();
@@ -307,7 +373,14 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
   __syncthreads();
   mmf<false, false>(Kf, S.Qf, F2, n2);
   mmf<true, false>(S.Qf, F2, S.Af, n2);
-  jacobi_f32(S.Af, S.Qf, n2, 10, S.red, S.cs, S.sn, S.pp, S.qq);
+  // the basis of the previous call is usually close: refine it to first order (cheap), and fall
+  // back to Jacobi sweeps only when that does not converge
+  bool diag = near_diagonal(S.Af, n2, S.red);
+  for (int round = 0; round < 3 && !diag; ++round) {
+    if (!refine_basis(Kf, S.Qf, S.Af, F1, F2, n2, S.red)) break;
+    diag = near_diagonal(S.Af, n2, S.red);
+  }
+  if (!diag) jacobi_f32(S.Af, S.Qf, n2, 10, S.red, S.cs, S.sn, S.pp, S.qq);
   // re-orthonormalise the float basis: Q <- Q (3I - Q^T Q) / 2
   mmf<true, false>(S.Qf, S.Qf, F1, r);
   for (int e = tid; e < r * r; e += blockDim.x) {

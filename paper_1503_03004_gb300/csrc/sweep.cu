@@ -189,9 +189,13 @@ __global__ void reduce_sq_kernel(const double* __restrict__ parts, int count, in
   if (stopped(st)) return;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= rpsq) return;
-  double v = 0.0;
-  for (int c = 0; c < count; ++c) v += parts[(int64_t)c * rpsq + e];
-  out[e] = v;
+  double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // eight loads in flight, combined in a fixed order
+  int c = 0;
+  for (; c + 8 <= count; c += 8)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] += parts[(int64_t)(c + q) * rpsq + e];
+  for (; c < count; ++c) a[0] += parts[(int64_t)c * rpsq + e];
+  out[e] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
 // ---------------------------------------------------------------- thin row transform
