@@ -128,6 +128,24 @@ def oracle_sample_rate(seed: int = 1001):
             "sample_iters": res.iters, "sample_seconds": dt, "converged": bool(res.converged)}, np
 
 
+def reduce_max(x: float, device=None) -> float:
+    """Max of a float over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(steps: int, elapsed_ms: float) -> float:
+    """Whole-job solves/s: every rank solves `steps` problems; time is the slowest rank's."""
+    import torch.distributed as dist
+    world = dist.get_world_size() if (dist.is_available() and dist.is_initialized()) else 1
+    return world * steps / (reduce_max(elapsed_ms) / 1000.0)
+
+
 def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -164,6 +182,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-profile", action="store_true",
+                    help="do not time kernels with events (no roofline; for measuring the profiling cost)")
     ap.add_argument("--m", type=int, default=WORKLOAD["m"],
                     help="square size of the same recipe (smaller sizes are for profiler captures)")
     args = ap.parse_args()
@@ -180,7 +200,8 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        # gloo carries the two scalar reductions (barrier, max time); the data path has no collective
+        dist.init_process_group("gloo")
 
     def barrier():
         if world > 1:
@@ -198,7 +219,7 @@ def main():
     V = torch.empty((n, r), dtype=torch.float64, device="cuda")
     S = torch.empty((m, n), dtype=torch.float32, device="cuda")
     stream = torch.cuda.Stream()           # the library and the timing events share this stream
-    ctx = B.Context(local, stream=stream.cuda_stream, profile=True)
+    ctx = B.Context(local, stream=stream.cuda_stream, profile=not args.no_profile)
     kw = dict(m=m, n=n, r=r, m_dtype=B.BF16, mu0=WORKLOAD["mu0"], rho=WORKLOAD["rho"], tol=WORKLOAD["tol"],
               max_iter=WORKLOAD["max_iter"], precision=B.PREC_MIXED)
     p = B.make_problem(M_ptr=M_dev.data_ptr(), **kw)
@@ -234,26 +255,25 @@ def main():
     barrier()
     elapsed_ms = t_start.elapsed_time(t_end)
     stats = ctx.stats(reset=True)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = world * args.steps / (elapsed_ms / 1000.0)
+    value = aggregate(args.steps, elapsed_ms)
+    elapsed_ms = reduce_max(elapsed_ms)
     clocks = clk.summary()
 
     # roofline of the fused sweep kernel: algorithmic bytes per launch / event-timed duration
     sw = stats[B.STAT_SWEEP]
-    # algorithmic bytes per launch as the library accounts them: M, Y_k read, Y_{k+1}, Delta written
-    alg_bytes = sw["bytes"] / max(1, sw["timed"])
-    avg_ms = sw["total_ms"] / max(1, sw["timed"])
-    achieved = alg_bytes / (avg_ms / 1000.0) / 1e9
     peak, peak_kind = peaks()
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "fused sweep", "bytes_per_launch": alg_bytes,
-                "bytes_per_element": alg_bytes / (m * n),
-                "avg_launch_ms": avg_ms, "timed_launches": sw["timed"], "peak_source": peak_kind + " hbm_gbs",
-                "wpass_avg_ms": stats[B.STAT_WPASS]["total_ms"] / max(1, stats[B.STAT_WPASS]["timed"]),
-                "rxr_avg_ms": stats[B.STAT_RXR]["total_ms"] / max(1, stats[B.STAT_RXR]["timed"])}
+    roofline = None
+    if sw["timed"] > 0:
+        # algorithmic bytes per launch as the library accounts them: M, Y_k read, Y_{k+1}, Delta written
+        alg_bytes = sw["bytes"] / sw["timed"]
+        avg_ms = sw["total_ms"] / sw["timed"]
+        achieved = alg_bytes / (avg_ms / 1000.0) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": None, "kernel": "fused sweep", "bytes_per_launch": alg_bytes,
+                    "bytes_per_element": alg_bytes / (m * n), "avg_launch_ms": avg_ms, "timed_launches": sw["timed"],
+                    "peak_source": peak_kind + " hbm_gbs",
+                    "wpass_avg_ms": stats[B.STAT_WPASS]["total_ms"] / max(1, stats[B.STAT_WPASS]["timed"]),
+                    "rxr_avg_ms": stats[B.STAT_RXR]["total_ms"] / max(1, stats[B.STAT_RXR]["timed"])}
 
     # ---- e2e: the same solve through the C ABI with pinned host buffers (copies inside the region)
     M_host = torch.from_numpy(prob.M.view(np.int16)).pin_memory()
@@ -269,11 +289,7 @@ def main():
     for _ in range(args.e2e_steps):
         if ctx.solve(ph, rh) != B.OK:
             raise RuntimeError(ctx.last_error())
-    e2e_s = time.perf_counter() - a
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max(time.perf_counter() - a)
     e2e = {"value": world * args.e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 2 * m * n,
            "d2h_bytes_per_step": 4 * m * n + 8 * (m * r + r * r + n * r)}
 

@@ -477,9 +477,9 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
     }
     __syncthreads();
     // The step just taken leaves a residual of about (eigenbasis error + float32 rounding of the
-    // correction) x rm <= 1e-7 rm.  From rm < 1e-6 that is below 1e-13, which is float64-level
-    // for what the factors need, so stop without forming the residual again.
-    if (rm < 1e-6) break;
+    // correction) x rm + O(rm^2): from rm < 3e-6 about 1e-11 (mixed path), from rm < 1e-7 about
+    // 1e-14 (float64 path), so stop without forming it again.
+    if (rm < (fp64sum ? 1e-7 : 3e-6)) break;
   }
   // 6. (B G B)^{-1/2} = Z / sqrt(s); T = B (B G B)^{-1/2}
   const double zs = 1.0 / sqrt(scale);

@@ -185,7 +185,8 @@ struct Solver {
   DeviceBlock nys;      // FR-Nys: gathered blocks and block factors
   DevState* host_state = nullptr;  // pinned
   // graph cache, keyed by the buffer layout it was captured with
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;    // two iterations, event slots 1-2
+  cudaGraphExec_t graph_b = nullptr;  // the same two iterations, event slots 3-4
   std::string graph_key;
   int graph_kernels = 0;
   TcMaps maps;          // tensor maps of the current tensor-core solve (captured by value in graphs)
@@ -199,15 +200,27 @@ struct Solver {
   double total_ms[SFR_STAT_COUNT] = {};
   double bytes[SFR_STAT_COUNT] = {};
   double sweep_bytes = 0, wpass_bytes = 0, wpass_first_bytes = 0;  // per launch, set per solve
-  cudaEvent_t ev[3][4][2] = {};
+  cudaEvent_t ev[5][4][2] = {};       // slot 0: eager iteration; 1-2: graph A; 3-4: graph B
+  cudaEvent_t done_ev[2] = {};        // completion of the last launch of graph A / B
+  DevState* host_state2 = nullptr;    // pinned state copies taken after graph A / B
 
   ~Solver() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (graph_b) cudaGraphExecDestroy(graph_b);
     if (host_state) cudaFreeHost(host_state);
+    if (host_state2) cudaFreeHost(host_state2);
+    for (auto& e : done_ev)
+      if (e) cudaEventDestroy(e);
     for (auto& a : ev)
       for (auto& b : a)
         for (auto& e : b)
           if (e) cudaEventDestroy(e);
+  }
+
+  void make_done_events() {
+    for (auto& e : done_ev)
+      if (!e) SFR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (!host_state2) SFR_CUDA(cudaMallocHost(&host_state2, 2 * sizeof(DevState)));
   }
 
   void make_events() {
@@ -383,50 +396,72 @@ struct Solver {
                             fmt("/%d/%d", (int)p.m_dtype, (int)tc);
     const std::string key = key0;
     if (graph_key != key + (profile ? "/p" : "")) {
-      if (graph) {
-        cudaGraphExecDestroy(graph);
-        graph = nullptr;
-      }
-      cudaGraph_t g;
-      SFR_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed));
-      capturing = true;
-      try {
-        graph_kernels = enqueue_iteration(s, b, fp64, false, 1);
-        graph_kernels += enqueue_iteration(s, b, fp64, false, 2);
-      } catch (...) {
+      for (cudaGraphExec_t* gp : {&graph, &graph_b})
+        if (*gp) {
+          cudaGraphExecDestroy(*gp);
+          *gp = nullptr;
+        }
+      for (int which = 0; which < 2; ++which) {
+        b = after_first;
+        cudaGraph_t g;
+        SFR_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed));
+        capturing = true;
+        try {
+          graph_kernels = enqueue_iteration(s, b, fp64, false, 1 + 2 * which);
+          graph_kernels += enqueue_iteration(s, b, fp64, false, 2 + 2 * which);
+        } catch (...) {
+          capturing = false;
+          cudaStreamEndCapture(stream, &g);
+          throw;
+        }
         capturing = false;
-        cudaStreamEndCapture(stream, &g);
-        throw;
+        SFR_CUDA(cudaStreamEndCapture(stream, &g));
+        cudaError_t e = cudaGraphInstantiate(which ? &graph_b : &graph, g, 0);
+        cudaGraphDestroy(g);
+        SFR_CUDA(e);
       }
-      capturing = false;
-      SFR_CUDA(cudaStreamEndCapture(stream, &g));
-      cudaError_t e = cudaGraphInstantiate(&graph, g, 0);
-      cudaGraphDestroy(g);
-      SFR_CUDA(e);
       graph_key = key + (profile ? "/p" : "");
       b = after_first;
     }
     const int cap = h.max_iter;
-    int launched = 1;
-    int per_check = 1;
+    make_done_events();
     SFR_CUDA(cudaMemcpyAsync(host_state, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
     SFR_CUDA(cudaStreamSynchronize(stream));
     harvest(0, host_state->iter >= 1 ? 1 : 0);
-    while (!host_state->done && launched < cap) {
-      const int before = host_state->iter;
-      for (int k = 0; k < per_check && launched < cap; ++k) {
-        SFR_CUDA(cudaGraphLaunch(graph, stream));
+    // Graphs A and B (two iterations each) alternate; the host reads the state copied after the
+    // previous launch while the next one already runs, so the GPU does not wait for the host.
+    // A launch issued after convergence finds the stop flag set and costs only its launches.
+    int launched = 1, last_iter = host_state->iter, which = 0;
+    int queue[2], queued = 0;  // launched graphs whose state has not been read yet (oldest first)
+    bool stop = host_state->done != 0;
+    while (!stop) {
+      if (launched < cap) {
+        SFR_CUDA(cudaGraphLaunch(which ? graph_b : graph, stream));
+        SFR_CUDA(cudaMemcpyAsync(host_state2 + which, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
+        SFR_CUDA(cudaEventRecord(done_ev[which], stream));
         launched += 2;
         count(SFR_STAT_ALL, graph_kernels);
         count(SFR_STAT_SWEEP, 2);
         count(SFR_STAT_WPASS, 2);
         count(SFR_STAT_RXR, 4);
+        queue[queued++] = which;
+        which ^= 1;
       }
-      SFR_CUDA(cudaMemcpyAsync(host_state, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
-      SFR_CUDA(cudaStreamSynchronize(stream));
-      harvest(1, host_state->iter - before);  // profiling keeps per_check at 1
-      if (!profile) per_check = std::min(per_check * 2, 8);
+      if (queued == 2 || (launched >= cap && queued > 0)) {
+        const int y = queue[0];
+        queue[0] = queue[1];
+        --queued;
+        SFR_CUDA(cudaEventSynchronize(done_ev[y]));
+        const DevState& hs = host_state2[y];
+        harvest(1 + 2 * y, hs.iter - last_iter);
+        last_iter = hs.iter;
+        *host_state = hs;
+        stop = hs.done != 0;
+      }
+      if (launched >= cap && queued == 0) stop = true;
     }
+    SFR_CUDA(cudaMemcpyAsync(host_state, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
+    SFR_CUDA(cudaStreamSynchronize(stream));
     DevState out = *host_state;
     const int K = out.iter;
     // buffers of the last completed iteration (see the graph's two-iteration period)
