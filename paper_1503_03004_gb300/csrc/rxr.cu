@@ -66,13 +66,22 @@ __device__ void mm_dist(const double* A, const double* B, double* C, int r) {
   const int nloc = (i1 - i0) * r;
   for (int e = threadIdx.x; e < nloc; e += blockDim.x) {
     const int i = i0 + e / r, j = e % r;
-    double acc = 0.0;
-    for (int k = 0; k < r; ++k) {
+    // four independent chains (k mod 4) keep the float64 pipe busy with 8 warps per SM
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int k = 0;
+    for (; k + 4 <= r; k += 4)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double a = TA ? A[(k + q) * LD + i] : A[i * LD + k + q];
+        const double b = TB ? B[j * LD + k + q] : B[(k + q) * LD + j];
+        acc[q] = fma(a, b, acc[q]);
+      }
+    for (; k < r; ++k) {
       const double a = TA ? A[k * LD + i] : A[i * LD + k];
       const double b = TB ? B[j * LD + k] : B[k * LD + j];
-      acc = fma(a, b, acc);
+      acc[0] = fma(a, b, acc[0]);
     }
-    C[i * LD + j] = acc;
+    C[i * LD + j] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
   }
   __syncthreads();
   if (cs > 1) {
@@ -101,6 +110,7 @@ __device__ void mmf(const float* A, const float* B, float* C, int r) {
     for (int x = 0; x < 4; ++x)
 #pragma unroll
       for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+#pragma unroll 4
     for (int k = 0; k < r; ++k) {
       float a[4], b[4];
 #pragma unroll
@@ -275,48 +285,13 @@ struct RxrSmem {
   int bad;
 };
 
-// Sum of `count` r x r partials (fixed order); rows split across the cluster, then broadcast.
-__device__ void load_gram(const double* __restrict__ parts, int count, int rp, int r, double* dst, bool fp64sum) {
-  cg::cluster_group cl = cg::this_cluster();
-  const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
-  const int rpc = (r + cs - 1) / cs, i0 = min(r, rank * rpc), i1 = min(r, i0 + rpc);
-  const int nloc = (i1 - i0) * r;
-  const int rpsq = rp * rp;
-  for (int e = threadIdx.x; e < nloc; e += blockDim.x) {
-    const int i = i0 + e / r, j = e % r;
-    // eight interleaved accumulators keep eight loads in flight (the partials sit in L2);
-    // they are combined in a fixed order, so the sum is deterministic
-    const double* src = parts + i * rp + j;
-    if (fp64sum) {
-      double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      int c = 0;
-      for (; c + 8 <= count; c += 8)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) a[q] += src[(int64_t)(c + q) * rpsq];
-      for (; c < count; ++c) a[0] += src[(int64_t)c * rpsq];
-      dst[i * LD + j] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-    } else {  // partials of a float32 sweep: float32 sums (float64 adds run at 1/64 rate)
-      float a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      int c = 0;
-      for (; c + 8 <= count; c += 8)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) a[q] += (float)src[(int64_t)(c + q) * rpsq];
-      for (; c < count; ++c) a[0] += (float)src[(int64_t)c * rpsq];
-      dst[i * LD + j] = (double)(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
-    }
+// dst = the summed r x r Gram G (rp x rp float64 in global memory; every CTA reads all of it).
+__device__ void load_gram(const double* __restrict__ G, int rp, int r, double* dst) {
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    dst[i * LD + j] = G[i * rp + j];
   }
   __syncthreads();
-  if (cs > 1) {
-    cl.sync();
-    for (int q = 1; q < cs; ++q) {
-      double* Dq = cl.map_shared_rank(dst, (rank + q) % cs);
-      for (int e = threadIdx.x; e < nloc; e += blockDim.x) {
-        const int i = i0 + e / r, j = e % r;
-        Dq[i * LD + j] = dst[i * LD + j];
-      }
-    }
-    cl.sync();
-  }
 }
 
 __device__ void fail(DevState* st, int code) {
@@ -325,13 +300,13 @@ __device__ void fail(DevState* st, int code) {
 
 // v_side = false: T_U = B (B G_P B)^{-1/2}.
 // v_side = true:  T_V = B (B G_W B)^{-1/2}, B <- Sym(G_W T_V), T_C = T_V B.
-// float64: the Gram sums (FP64 path), K = B G B, the Newton residual, T, B_bar, T_C.
+// float64: K = B G B, the Newton residual, T, B_bar, T_C (G: the float64 sum of the partials).
 // float32: the eigenbasis, eigenvalue estimates, Z0 and the Newton corrections, which only
 // steer the iteration (their error shrinks with each Newton step).
-__global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict__ parts, int count, int rp, int r,
+__global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict__ G, int rp, int r,
                                                        double* __restrict__ Bg, double* __restrict__ Tout,
                                                        double* __restrict__ TCout, float* __restrict__ Qeig,
-                                                       int v_side, int fp64sum, DevState* st) {
+                                                       int v_side, int mixed, DevState* st) {
   if (stopped(st)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RxrSmem& S = *reinterpret_cast<RxrSmem*>(smem_raw);
@@ -345,7 +320,7 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
   const int rpsq = rp * rp;
   const bool writer = cg::this_cluster().block_rank() == 0;
   // 1. Gram of the thin matrix and B; K = B G B (symmetrised) scaled by s = trace / r
-  load_gram(parts, count, rp, r, S.T2, fp64sum);
+  load_gram(G, rp, r, S.T2);
   for (int e = tid; e < r * r; e += blockDim.x) S.B[(e / r) * LD + e % r] = Bg[(e / r) * rp + e % r];
   __syncthreads();
   mm_dist<false, false>(S.T2, S.B, S.T1, r);
@@ -477,9 +452,9 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
     }
     __syncthreads();
     // The step just taken leaves a residual of about (eigenbasis error + float32 rounding of the
-    // correction) x rm + O(rm^2): from rm < 3e-6 about 1e-11 (mixed path), from rm < 1e-7 about
-    // 1e-14 (float64 path), so stop without forming it again.
-    if (rm < (fp64sum ? 1e-7 : 3e-6)) break;
+    // correction) x rm + O(rm^2): from rm < 3e-6 about 1e-11 (mixed path, whose Gram carries
+    // float32 rounding), from rm < 1e-7 about 1e-14 (float64 path), so stop without forming it again.
+    if (rm < (mixed ? 3e-6 : 1e-7)) break;
   }
   // 6. (B G B)^{-1/2} = Z / sqrt(s); T = B (B G B)^{-1/2}
   const double zs = 1.0 / sqrt(scale);
@@ -495,7 +470,7 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
     }
   if (!v_side) return;
   // 7. B_bar = Sym(G_W T_V) (Eq. 10 with W = X^T U_bar), T_C = T_V B_bar
-  load_gram(parts, count, rp, r, S.K, fp64sum);
+  load_gram(G, rp, r, S.K);
   mm_dist<false, false>(S.K, S.T1, S.T2, r);
   for (int e = tid; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
@@ -511,6 +486,7 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
       TCout[e] = in ? S.T2[i * LD + j] : 0.0;
     }
 }
+
 
 }  // namespace
 
@@ -545,9 +521,13 @@ static int rxr_cluster_size(size_t smem) {
   return best;
 }
 
-cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream_t st, bool fp64sum) {
+cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream_t st, bool fp64) {
+  const double* parts = v_side ? b.GWpart : b.GPpart;
+  const int count = v_side ? s.gw_blocks : s.gp_blocks;
+  cudaError_t e = launch_reduce_parts(parts, count, s.rp * s.rp, b.Gsum, b.st, st);
+  if (e != cudaSuccess) return e;
   const size_t smem = sizeof(RxrSmem);
-  cudaError_t e = cudaFuncSetAttribute(rxr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(rxr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int cs = rxr_cluster_size(smem);
   cudaLaunchConfig_t cfg = {};
@@ -562,11 +542,9 @@ cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream
   at.val.clusterDim.z = 1;
   cfg.attrs = &at;
   cfg.numAttrs = 1;
-  if (v_side)
-    return cudaLaunchKernelEx(&cfg, rxr_kernel, (const double*)b.GWpart, s.gw_blocks, s.rp, s.r, b.B, b.TV, b.TCm,
-                              b.Qeig_v, 1, (int)fp64sum, b.st);
-  return cudaLaunchKernelEx(&cfg, rxr_kernel, (const double*)b.GPpart, s.gp_blocks, s.rp, s.r, b.B, b.TU,
-                            (double*)nullptr, b.Qeig_u, 0, (int)fp64sum, b.st);
+  return cudaLaunchKernelEx(&cfg, rxr_kernel, (const double*)b.Gsum, s.rp, s.r, b.B, v_side ? b.TV : b.TU,
+                            v_side ? b.TCm : (double*)nullptr, v_side ? b.Qeig_v : b.Qeig_u, v_side ? 1 : 0,
+                            fp64 ? 0 : 1, b.st);
 }
 
 }  // namespace sfr

@@ -66,6 +66,7 @@ struct Buffers {
   double* GPpart;       // gp_blocks x rp x rp
   double* GWpart;       // gw_blocks x rp x rp
   double* Hpart;        // gp_blocks x rp x rp : U_old^T U_new partials
+  double* Gsum;         // rp x rp : summed Gram (input of the r x r projector)
   double* resid_part;   // sweep CTAs
   double* normm_part;   // ||M||^2 partials
   double* B;            // rp x rp
@@ -87,7 +88,12 @@ cudaError_t launch_norm_m(const Shape& s, const Buffers& b, cudaStream_t st);
 cudaError_t launch_init_p(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st);
 cudaError_t launch_gram_p(const Shape& s, const Buffers& b, bool fp64, bool sum_parts, cudaStream_t st,
                           const void* addA = nullptr, const double* H = nullptr);
-cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream_t st, bool fp64sum = true);
+// Sums the Gram partials into b.Gsum, then runs the r x r projector; fp64 = false (mixed path)
+// stops Newton at the float32 resolution of its Gram.
+cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream_t st, bool fp64 = true);
+// out[e] = sum over c < count of parts[c * rpsq + e], in a fixed order (float64)
+cudaError_t launch_reduce_parts(const double* parts, int count, int rpsq, double* out, const DevState* dst,
+                                cudaStream_t st);
 cudaError_t launch_apply_u(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st);
 cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first, int u_new, cudaStream_t st);
 cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st);

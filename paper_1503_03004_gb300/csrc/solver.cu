@@ -160,6 +160,7 @@ size_t carve(const Shape& s, bool fp64, void* base, Buffers* b, bool tc) {
   x.GPpart = static_cast<double*>(c.take(8 * rpsq * s.gp_blocks));
   x.GWpart = static_cast<double*>(c.take(8 * rpsq * s.gw_blocks));
   x.Hpart = static_cast<double*>(c.take(8 * rpsq * (s.gp_blocks + 1)));
+  x.Gsum = static_cast<double*>(c.take(8 * rpsq));
   x.resid_part = static_cast<double*>(c.take(8 * (size_t)s.sweep_grid_x * s.nsplit));
   x.normm_part = static_cast<double*>(c.take(8 * 1024));
   x.B = static_cast<double*>(c.take(8 * rpsq));
@@ -481,7 +482,11 @@ struct Solver {
           SFR_CUDA(cudaMemcpyAsync(Bdev + (size_t)i * p.r, fin.B + (size_t)i * s.rp, 8 * p.r,
                                    cudaMemcpyDeviceToDevice, stream));
       }
-      if (Sdev || Ldev) SFR_CUDA(launch_finalize(s, fin, fp64, fin.u_cur, Sdev, s_dtype, lds, Ldev, stream));
+      if ((Sdev || Ldev) && fin.tc)
+        SFR_CUDA(tc_launch_finalize(s, maps, fin.t, fin.Y[0] == fin.t.Y[0] ? 0 : 1, Sdev, (int)s_dtype, lds, Ldev,
+                                    fin.st, stream));
+      else if (Sdev || Ldev)
+        SFR_CUDA(launch_finalize(s, fin, fp64, fin.u_cur, Sdev, s_dtype, lds, Ldev, stream));
     }
     SFR_CUDA(cudaStreamSynchronize(stream));
     return out;

@@ -114,6 +114,52 @@ __device__ __forceinline__ void zero44(T (&acc)[4][4]) {
     for (int y = 0; y < 4; ++y) acc[x][y] = 0;
 }
 
+// The thin kernels run 256 threads; their global loads are unrolled with compile-time trip
+// counts so that every load of a thread is in flight before the first shared-memory store.
+constexpr int kThinThreads = 256;
+
+// s[RP x RP] (row stride LDT, type TC) = g[RP x RP] (float64, dense).
+template <typename TC, int RP, int LDT>
+__device__ __forceinline__ void load_rr(const double* __restrict__ g, TC* s, int t) {
+  constexpr int PER = (RP * RP + kThinThreads - 1) / kThinThreads;
+  double v[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = t + q * kThinThreads;
+    v[q] = e < RP * RP ? g[e] : 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = t + q * kThinThreads;
+    if (e < RP * RP) s[(e / RP) * LDT + e % RP] = (TC)v[q];
+  }
+}
+
+// Elements of a kGramRows x RP row tile owned by thread t: e = t + q * 256, q < RP / 4.
+template <int RP>
+struct TileIdx {
+  static constexpr int PER = kGramRows * RP / kThinThreads;
+  static __device__ __forceinline__ int row(int t, int q) { return (t + q * kThinThreads) / RP; }
+  static __device__ __forceinline__ int col(int t, int q) { return (t + q * kThinThreads) % RP; }
+};
+
+// v[q] = src[(i0 + row) * RP + col] for the thread's elements (0 past `rows`).
+template <typename TC, int RP>
+__device__ __forceinline__ void load_tile(const TC* __restrict__ src, int64_t i0, int64_t rows, int t,
+                                          TC (&v)[TileIdx<RP>::PER]) {
+#pragma unroll
+  for (int q = 0; q < TileIdx<RP>::PER; ++q) {
+    const int64_t i = i0 + TileIdx<RP>::row(t, q);
+    v[q] = i < rows ? src[i * RP + TileIdx<RP>::col(t, q)] : (TC)0;
+  }
+}
+
+template <typename TC, int RP, int LDT>
+__device__ __forceinline__ void store_tile(TC* s, int t, const TC (&v)[TileIdx<RP>::PER]) {
+#pragma unroll
+  for (int q = 0; q < TileIdx<RP>::PER; ++q) s[TileIdx<RP>::row(t, q) * LDT + TileIdx<RP>::col(t, q)] = v[q];
+}
+
 // ---------------------------------------------------------------- thin reduce + Gram partials
 // For every 64-row tile handled by this CTA (tiles blockIdx.x, blockIdx.x + gridDim.x, ...):
 // out[i][:] = sum_s parts[s][i][:]  (+ addA[i][:] H when addA != nullptr), then the CTA's
@@ -131,26 +177,29 @@ __global__ void __launch_bounds__(256) thin_gram_kernel(const TC* __restrict__ p
   TC* arow = tile + kGramRows * LDT;              // [kGramRows][LDT]  addA rows
   TC* Hs = arow + kGramRows * LDT;                // [RP][LDT]
   const int t = threadIdx.x;
-  if (addA)
-    for (int e = t; e < RP * RP; e += blockDim.x) Hs[(e / RP) * LDT + e % RP] = (TC)H[e];
+  if (addA) load_rr<TC, RP, LDT>(H, Hs, t);
   TC g[4][4];
   zero44(g);
   const int64_t ntiles = (rows + kGramRows - 1) / kGramRows;
   for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
     const int64_t i0 = tl * kGramRows;
-    __syncthreads();  // previous tile consumed; Hs visible
-    for (int e = t; e < kGramRows * RP; e += blockDim.x) {
-      const int ii = e / RP, a = e % RP;
-      const int64_t i = i0 + ii;
-      TC v = 0;
-      if (i < rows) {
-        if (nparts == 0) v = out[i * RP + a];
-        else
-          for (int s = 0; s < nparts; ++s) v += parts[s * part_stride + i * RP + a];
+    TC v[TileIdx<RP>::PER];
+    if (nparts == 0) {
+      load_tile<TC, RP>(out, i0, rows, t, v);
+    } else {
+      load_tile<TC, RP>(parts, i0, rows, t, v);
+      for (int s = 1; s < nparts; ++s) {
+        TC w[TileIdx<RP>::PER];
+        load_tile<TC, RP>(parts + s * part_stride, i0, rows, t, w);
+#pragma unroll
+        for (int q = 0; q < TileIdx<RP>::PER; ++q) v[q] += w[q];
       }
-      tile[ii * LDT + a] = v;
-      if (addA) arow[ii * LDT + a] = i < rows ? addA[i * RP + a] : (TC)0;
     }
+    TC av[TileIdx<RP>::PER];
+    if (addA) load_tile<TC, RP>(addA, i0, rows, t, av);
+    __syncthreads();  // previous tile consumed; Hs visible
+    store_tile<TC, RP, LDT>(tile, t, v);
+    if (addA) store_tile<TC, RP, LDT>(arow, t, av);
     __syncthreads();
     if (nparts > 0) {
       if (addA) {
@@ -184,18 +233,36 @@ __global__ void __launch_bounds__(256) thin_gram_kernel(const TC* __restrict__ p
   }
 }
 
-// Sum of `count` rp x rp double partials into out (one thread per entry, fixed order).
-__global__ void reduce_sq_kernel(const double* __restrict__ parts, int count, int rpsq, double* out, const DevState* st) {
+// Sum of `count` partials of rpsq doubles into out, in a fixed order: warp w of a CTA adds the
+// partials w, w + 8, w + 16, ... of 32 consecutive entries (four loads in flight), then the
+// eight warp sums are added in warp order.
+__global__ void __launch_bounds__(256) reduce_sq_kernel(const double* __restrict__ parts, int count, int rpsq,
+                                                        double* out, const DevState* st) {
   if (stopped(st)) return;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= rpsq) return;
-  double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // eight loads in flight, combined in a fixed order
-  int c = 0;
-  for (; c + 8 <= count; c += 8)
+  __shared__ double red[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * 32 + lane;
+  double a = 0.0;
+  if (e < rpsq) {
+    int c = warp;
+    for (; c + 24 < count; c += 32) {
+      const double v0 = parts[(int64_t)c * rpsq + e], v1 = parts[(int64_t)(c + 8) * rpsq + e];
+      const double v2 = parts[(int64_t)(c + 16) * rpsq + e], v3 = parts[(int64_t)(c + 24) * rpsq + e];
+      a += v0;
+      a += v1;
+      a += v2;
+      a += v3;
+    }
+    for (; c < count; c += 8) a += parts[(int64_t)c * rpsq + e];
+  }
+  red[warp][lane] = a;
+  __syncthreads();
+  if (warp == 0 && e < rpsq) {
+    double s = red[0][lane];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) a[q] += parts[(int64_t)(c + q) * rpsq + e];
-  for (; c < count; ++c) a[0] += parts[(int64_t)c * rpsq + e];
-  out[e] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    for (int w = 1; w < 8; ++w) s += red[w][lane];
+    out[e] = s;
+  }
 }
 
 // ---------------------------------------------------------------- thin row transform
@@ -217,10 +284,8 @@ __global__ void __launch_bounds__(256) row_transform_kernel(const TC* __restrict
   TC* drow = srow + kGramRows * LDT;           // [kGramRows][LDT]
   TC* orow = drow + kGramRows * LDT;           // [kGramRows][LDT]
   const int t = threadIdx.x;
-  for (int e = t; e < RP * RP; e += blockDim.x) {
-    Ts[(e / RP) * LDT + e % RP] = (TC)T[e];
-    if (T2) T2s[(e / RP) * LDT + e % RP] = (TC)T2[e];
-  }
+  load_rr<TC, RP, LDT>(T, Ts, t);
+  if (T2) load_rr<TC, RP, LDT>(T2, T2s, t);
   TC h[4][4];
   zero44(h);
   const int owner = t < (kGramRows / 4) * (RP / 4);
@@ -228,13 +293,12 @@ __global__ void __launch_bounds__(256) row_transform_kernel(const TC* __restrict
   const int64_t ntiles = (rows + kGramRows - 1) / kGramRows;
   for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
     const int64_t i0 = tl * kGramRows;
+    TC v[TileIdx<RP>::PER], ov[TileIdx<RP>::PER];
+    load_tile<TC, RP>(src, i0, rows, t, v);
+    if (hpart) load_tile<TC, RP>(old, i0, rows, t, ov);
     __syncthreads();
-    for (int e = t; e < kGramRows * RP; e += blockDim.x) {
-      const int ii = e / RP, a = e % RP;
-      const int64_t i = i0 + ii;
-      srow[ii * LDT + a] = i < rows ? src[i * RP + a] : (TC)0;
-      if (hpart) orow[ii * LDT + a] = i < rows ? old[i * RP + a] : (TC)0;
-    }
+    store_tile<TC, RP, LDT>(srow, t, v);
+    if (hpart) store_tile<TC, RP, LDT>(orow, t, ov);
     __syncthreads();
     TC acc[4][4];
     zero44(acc);
@@ -577,6 +641,12 @@ cudaError_t allow_smem(K kern, size_t bytes) {
 
 }  // namespace
 
+cudaError_t launch_reduce_parts(const double* parts, int count, int rpsq, double* out, const DevState* dst,
+                                cudaStream_t st) {
+  reduce_sq_kernel<<<cdiv(rpsq, 32), 256, 0, st>>>(parts, count, rpsq, out, dst);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_norm_m(const Shape& s, const Buffers& b, cudaStream_t st) {
   const int blocks = (int)std::min<int64_t>(s.m, 1024);
   cudaError_t e = by_mtype(b.m_dtype, b.M, [&](auto M) {
@@ -661,7 +731,7 @@ cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool firs
   // W = sum_c Wpart[c] (+ C_old H, H = U_old^T U_new), then Gram partials of W.
   // H = sum of the U_old^T U_new partials, reduced into the slot after the partials.
   if (!first) {
-    reduce_sq_kernel<<<cdiv(s.rp * s.rp, 128), 128, 0, st>>>(b.Hpart, s.gp_blocks, s.rp * s.rp, b.Hpart + (size_t)s.gp_blocks * s.rp * s.rp,
+    reduce_sq_kernel<<<cdiv(s.rp * s.rp, 32), 256, 0, st>>>(b.Hpart, s.gp_blocks, s.rp * s.rp, b.Hpart + (size_t)s.gp_blocks * s.rp * s.rp,
                                         b.st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -34,9 +34,10 @@ constexpr uint32_t C_BUF = 32768;
 constexpr uint32_t OFF_ST = 65536;      // input stages, 3 x 40 KB: M tile (128 x 64 bf16), Y tile, V^T tile (64 x 64 bf16)
 constexpr uint32_t ST_BYTES = 40960;
 constexpr uint32_t ST_Y = 16384, ST_VT = 32768;
-constexpr uint32_t OFF_YO = OFF_ST + NSTAGE * ST_BYTES;  // Y_{k+1} tile, TMA store source
-constexpr uint32_t OFF_DA = OFF_YO + 16384;              // Delta tile: A operand of Delta V and TMA store source
-constexpr uint32_t OFF_BAR = OFF_DA + 16384;
+constexpr uint32_t OFF_DA = OFF_ST + NSTAGE * ST_BYTES;  // Delta tiles, 2 x 16 KB: A operand of Delta V and
+                                                         // TMA store source (tile t uses buffer t % 2)
+constexpr uint32_t DA_BYTES = 16384;
+constexpr uint32_t OFF_BAR = OFF_DA + 2 * DA_BYTES;
 constexpr uint32_t SWEEP_SMEM = OFF_BAR + 256 + 1024;
 static_assert(OFF_BAR % 1024 == 0, "alignment");
 // tensor memory columns
@@ -46,7 +47,7 @@ struct SweepBars {
   uint64_t stage_full[NSTAGE], stage_empty[NSTAGE];
   uint64_t c_full[2], c_empty[2];
   uint64_t l_full[2], l_empty[2];
-  uint64_t d_full, d_empty;
+  uint64_t d_full[2], d_empty[2];
   uint64_t q_full;
   uint32_t tmem_base;
   int abort;
@@ -81,6 +82,63 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
       "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])));
 }
 
+// One 16-byte chunk (8 columns) of a row of the sweep epilogue: from M, Y_k (bfloat16 pairs) and L,
+//   Y_{k+1} = clip(mu (M - L + Y_k / mu), -1, 1) rounded to bfloat16 (the stored value is the one used),
+//   Delta = Y_{k+1} (1/mu + 1/mu_next) - Y_k / mu, resid += (Y_{k+1} - Y_k)^2.
+// FULL: all 8 columns valid; else the first `nvalid` are (the rest give Y_{k+1} = Delta = 0).
+template <bool FULL>
+__device__ __forceinline__ void epi_chunk(const uint4& mw, const uint4& yw, const float* L, int nvalid, float mu,
+                                          float inv_mu, float dcoef, uint4& yn_out, uint4& d_out, float& resid) {
+  const uint32_t mv[4] = {mw.x, mw.y, mw.z, mw.w}, yv[4] = {yw.x, yw.y, yw.z, yw.w};
+  uint32_t yn2[4], dd[4];
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    float y[2], ynr[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const float mval = e ? bf_hi(mv[h]) : bf_lo(mv[h]);
+      y[e] = e ? bf_hi(yv[h]) : bf_lo(yv[h]);
+      const float z = mval - L[2 * h + e] + y[e] * inv_mu;
+      ynr[e] = fminf(1.f, fmaxf(-1.f, mu * z));
+      if (!FULL && 2 * h + e >= nvalid) ynr[e] = 0.f;
+    }
+    const uint32_t p = pack_bf2(ynr[0], ynr[1]);
+    yn2[h] = p;
+    float dv[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const float yn = e ? bf_hi(p) : bf_lo(p);
+      const float dy = yn - y[e];
+      resid = fmaf(dy, dy, resid);
+      dv[e] = yn * dcoef - y[e] * inv_mu;
+      if (!FULL && 2 * h + e >= nvalid) dv[e] = 0.f;
+    }
+    dd[h] = pack_bf2(dv[0], dv[1]);
+  }
+  yn_out = make_uint4(yn2[0], yn2[1], yn2[2], yn2[3]);
+  d_out = make_uint4(dd[0], dd[1], dd[2], dd[3]);
+}
+
+// Writes this thread's 32 columns of a row (the first ncol of them valid): 16-byte vector stores
+// when the destination allows them, else element by element.
+template <typename TSo>
+__device__ __forceinline__ void store_cols(TSo* dst, const float* v, int ncol, bool vec) {
+  if (vec && ncol >= 32) {
+    if constexpr (sizeof(TSo) == 4) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) reinterpret_cast<double2*>(dst)[q] = make_double2(v[2 * q], v[2 * q + 1]);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+      if (q < ncol) dst[q] = (TSo)v[q];
+  }
+}
+
 constexpr int kEpiThreads = 256;
 constexpr int kSweepThreads = kEpiThreads + 64;
 
@@ -88,19 +146,28 @@ constexpr int kSweepThreads = kEpiThreads + 64;
 // lanes / rows 32 (w % 4) .. + 31 and columns 32 (w / 4) .. + 31 of each tile); warp 8: TMA
 // producer; warp 9: TMEM owner and MMA issuer.  U_hi / U_lo (the fixed A operand of the L
 // products) live in tensor memory; M, Y and V^T tiles stream through three stages; C tiles
-// are double buffered; Y_{k+1} and Delta leave through TMA stores.
+// are double buffered; Y_{k+1} goes to global memory straight from registers (each thread
+// writes 64 contiguous bytes of its row); Delta tiles are double buffered in shared memory,
+// where they serve as the A operand of Delta V_bar and as the source of a TMA store.
+// FINAL: the output pass after the last iteration instead (Algorithm 1 returns L_k, S_k):
+// S = P_ST_{1/mu}(M - L + Y_k / mu) with the last iteration's mu, Y_k and factors, written
+// (with L when requested) from registers; no V^T tiles, no Delta, no Y_{k+1}.
+template <bool FINAL, typename TSo>
 __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid_constant__ CUtensorMap tmM,
                                                                    const __grid_constant__ CUtensorMap tmYin,
-                                                                   const __grid_constant__ CUtensorMap tmYout,
                                                                    const __grid_constant__ CUtensorMap tmD,
                                                                    const __grid_constant__ CUtensorMap tmCh,
                                                                    const __grid_constant__ CUtensorMap tmCl,
                                                                    const __grid_constant__ CUtensorMap tmVt,
                                                                    const float* __restrict__ Uh,
-                                                                   const float* __restrict__ Ul, int64_t m, int64_t n,
+                                                                   const float* __restrict__ Ul,
+                                                                   __nv_bfloat16* __restrict__ Yout, int64_t ldy,
+                                                                   int64_t m, int64_t n,
                                                                    int cols_per_split, float* __restrict__ Qpart,
-                                                                   double* __restrict__ resid_part, DevState* st) {
-  if (stopped(st)) return;
+                                                                   double* __restrict__ resid_part, DevState* st,
+                                                                   TSo* __restrict__ Sout, TSo* __restrict__ Lout,
+                                                                   int64_t lds, int vec_out) {
+  if (!FINAL && stopped(st)) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   SweepBars& B = *reinterpret_cast<SweepBars*>(sm + OFF_BAR);
@@ -114,7 +181,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(&B.stage_full[s], 1);
-      mbar_init(&B.stage_empty[s], 2);
+      mbar_init(&B.stage_empty[s], FINAL ? 1 : 2);  // epilogue (+ the Delta V MMA reading V^T)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&B.c_full[s], 1);
@@ -122,8 +189,10 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
       mbar_init(&B.l_full[s], 1);
       mbar_init(&B.l_empty[s], kEpiThreads);
     }
-    mbar_init(&B.d_full, 1);
-    mbar_init(&B.d_empty, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&B.d_full[s], 1);
+      mbar_init(&B.d_empty[s], 1);
+    }
     mbar_init(&B.q_full, 1);
     B.abort = 0;
     mbar_fence_init();
@@ -165,10 +234,10 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
         const int s = t % NSTAGE, j0 = jbeg + t * TBN;
         if (t >= NSTAGE && !mbar_wait(&B.stage_empty[s], ((t / NSTAGE) - 1) & 1, abort)) break;
         unsigned char* stg = sm + OFF_ST + s * ST_BYTES;
-        mbar_expect_tx(&B.stage_full[s], 16384 + 16384 + 8192);
+        mbar_expect_tx(&B.stage_full[s], FINAL ? 16384 + 16384 : 16384 + 16384 + 8192);
         tma_load_2d(stg, &tmM, j0, i0, &B.stage_full[s]);
         tma_load_2d(stg + ST_Y, &tmYin, j0, i0, &B.stage_full[s]);
-        tma_load_2d(stg + ST_VT, &tmVt, j0, 0, &B.stage_full[s]);
+        if (!FINAL) tma_load_2d(stg + ST_VT, &tmVt, j0, 0, &B.stage_full[s]);
         armed_stage[s] = t;
         const int cb = t & 1;
         if (t >= 2 && !mbar_wait(&B.c_empty[cb], ((t >> 1) - 1) & 1, abort)) break;
@@ -200,15 +269,16 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
       const uint32_t id_q = idesc(1, TBM, TR);    // bf16, 128 x 64
       auto delta_v = [&](int tt) -> bool {
         const int s = tt % NSTAGE;
-        if (!mbar_wait(&B.d_full, tt & 1, abort)) return false;
+        const int db = tt & 1;
+        if (!mbar_wait(&B.d_full[db], (tt >> 1) & 1, abort)) return false;
         tc_fence_after();
         const uint32_t vt = smem_u32(sm + OFF_ST + s * ST_BYTES + ST_VT);
         for (int kk = 0; kk < TBN / 16; ++kk) {
-          const uint64_t a = desc_sw128(smem_u32(sm + OFF_DA) + kk * 32);
+          const uint64_t a = desc_sw128(smem_u32(sm + OFF_DA + db * DA_BYTES) + kk * 32);
           const uint64_t b = desc_sw128(vt + kk * 32);
           mma_bf16(tmem + TM_Q, a, b, id_q, (tt > 0 || kk > 0) ? 1u : 0u);
         }
-        mma_commit(&B.d_empty);
+        mma_commit(&B.d_empty[db]);
         mma_commit(&B.stage_empty[s]);
         return true;
       };
@@ -231,9 +301,9 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
         }
         mma_commit(&B.l_full[b]);
         mma_commit(&B.c_empty[b]);
-        if (t >= 1 && !delta_v(t - 1)) { ok = false; break; }
+        if (!FINAL && t >= 1 && !delta_v(t - 1)) { ok = false; break; }
       }
-      if (ok && ntiles > 0) ok = delta_v(ntiles - 1);
+      if (!FINAL && ok && ntiles > 0) ok = delta_v(ntiles - 1);
       mma_commit(&B.q_full);
       if (!ok) {  // MMAs already issued must finish before the tensor memory is released
         int dummy = 0;
@@ -246,15 +316,56 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
     const int cbase = half * 32;                  // first of this warp's 32 columns
     const int64_t gi = (int64_t)i0 + row;
     const float mu = (float)st->mu;
+    const float inv_mu_last = (float)(1.0 / st->mu_last);
     const double mu_next_d = fmin(st->mu_max, st->rho * st->mu);
     const float inv_mu = (float)(1.0 / st->mu), dcoef = (float)(1.0 / st->mu + 1.0 / mu_next_d);
     float resid = 0.f;
     bool ok = true;
+    __nv_bfloat16* yrow = Yout + gi * ldy + cbase;  // this thread's 32 columns of Y_{k+1} (j0 added per tile)
     for (int t = 0; t < ntiles; ++t) {
       const int s = t % NSTAGE, b = t & 1, j0 = jbeg + t * TBN;
+      if constexpr (FINAL) {
+        mbar_wait(&B.l_full[b], (t >> 1) & 1, abort) && mbar_wait(&B.stage_full[s], (t / NSTAGE) & 1, abort);
+        named_bar(1, kEpiThreads);
+        if (*abort) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        float L[32], sv[32];
+        tmem_ld16(tmem + lane_base + TM_L + b * TBN + cbase, L);
+        tmem_ld16(tmem + lane_base + TM_L + b * TBN + cbase + 16, L + 16);
+        tmem_ld_wait();
+        tc_fence_before();
+        mbar_arrive(&B.l_empty[b]);
+        const unsigned char* ms = sm + OFF_ST + s * ST_BYTES;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const uint32_t off = sw128(row, half * 4 + cc);
+          const uint4 mw = *reinterpret_cast<const uint4*>(ms + off);
+          const uint4 yw = *reinterpret_cast<const uint4*>(ms + ST_Y + off);
+          const uint32_t mv[4] = {mw.x, mw.y, mw.z, mw.w}, yv[4] = {yw.x, yw.y, yw.z, yw.w};
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float mval = (q & 1) ? bf_hi(mv[q >> 1]) : bf_lo(mv[q >> 1]);
+            const float y = (q & 1) ? bf_hi(yv[q >> 1]) : bf_lo(yv[q >> 1]);
+            const float z = mval - L[8 * cc + q] + y * inv_mu_last;
+            sv[8 * cc + q] = z > inv_mu_last ? z - inv_mu_last : (z < -inv_mu_last ? z + inv_mu_last : 0.f);
+          }
+        }
+        named_bar(1, kEpiThreads);  // the stage has been read by every thread
+        if (tid == 0) mbar_arrive(&B.stage_empty[s]);
+        if (gi < m) {
+          const int ncol = jend - j0 - cbase;
+          const int64_t o = gi * lds + j0 + cbase;
+          if (Sout) store_cols(Sout + o, sv, ncol, vec_out != 0);
+          if (Lout) store_cols(Lout + o, L, ncol, vec_out != 0);
+        }
+        continue;
+      }
       mbar_wait(&B.l_full[b], (t >> 1) & 1, abort) && mbar_wait(&B.stage_full[s], (t / NSTAGE) & 1, abort) &&
-          (t == 0 || mbar_wait(&B.d_empty, (t - 1) & 1, abort));
-      if (tid == 0 && t >= 1) tma_store_wait_read0();  // YO / DA of the previous tile have been read
+          (t < 2 || mbar_wait(&B.d_empty[b], ((t >> 1) - 1) & 1, abort));  // Delta V of tile t - 2 done
+      if (tid == 0 && t >= 2) tma_store_wait_read1();  // the Delta store of tile t - 2 has read its buffer
       named_bar(1, kEpiThreads);  // the abort decision below is the same for all epilogue threads
       if (*abort) {
         ok = false;
@@ -269,53 +380,32 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
       mbar_arrive(&B.l_empty[b]);
       const unsigned char* ms = sm + OFF_ST + s * ST_BYTES;
       const unsigned char* ys = ms + ST_Y;
-      unsigned char* yo = sm + OFF_YO;
-      unsigned char* da = sm + OFF_DA;
+      unsigned char* da = sm + OFF_DA + b * DA_BYTES;
+      const int ncol = jend - j0 - cbase;  // valid columns among this thread's 32 (may be <= 0)
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {  // 16-byte chunk c = columns 8c .. 8c+7
         const int c = half * 4 + cc;
         const uint32_t off = sw128(row, c);
         const uint4 mw = *reinterpret_cast<const uint4*>(ms + off);
         const uint4 yw = *reinterpret_cast<const uint4*>(ys + off);
-        const uint32_t mv[4] = {mw.x, mw.y, mw.z, mw.w}, yv[4] = {yw.x, yw.y, yw.z, yw.w};
-        uint32_t yn2[4], dd[4];
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          float ynew[2], dnew[2];
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int lc = 8 * cc + 2 * h + e;     // column within this warp's 32
-            const float mval = e ? bf_hi(mv[h]) : bf_lo(mv[h]);
-            const float y = e ? bf_hi(yv[h]) : bf_lo(yv[h]);
-            const bool in = j0 + cbase + lc < jend;
-            const float z = mval - L[lc] + y * inv_mu;
-            float yn = fminf(1.f, fmaxf(-1.f, mu * z));
-            yn = in ? __bfloat162float(__float2bfloat16_rn(yn)) : 0.f;  // value as stored
-            const float dv = yn * dcoef - y * inv_mu;
-            const float dy = yn - y;
-            resid = fmaf(dy, dy, resid);
-            ynew[e] = yn;
-            dnew[e] = in ? dv : 0.f;
-          }
-          yn2[h] = pack_bf2(ynew[0], ynew[1]);
-          dd[h] = pack_bf2(dnew[0], dnew[1]);
-        }
-        *reinterpret_cast<uint4*>(yo + off) = make_uint4(yn2[0], yn2[1], yn2[2], yn2[3]);
-        *reinterpret_cast<uint4*>(da + off) = make_uint4(dd[0], dd[1], dd[2], dd[3]);
+        uint4 yn, dd;
+        if (ncol >= 32) epi_chunk<true>(mw, yw, L + 8 * cc, 0, mu, inv_mu, dcoef, yn, dd, resid);
+        else epi_chunk<false>(mw, yw, L + 8 * cc, ncol - 8 * cc, mu, inv_mu, dcoef, yn, dd, resid);
+        if (gi < m) *reinterpret_cast<uint4*>(yrow + j0 + 8 * cc) = yn;  // j0 + 63 < ldy: in the row
+        *reinterpret_cast<uint4*>(da + off) = dd;
       }
       fence_async_smem();
       named_bar(1, kEpiThreads);
       if (tid == 0) {
         mbar_arrive(&B.stage_empty[s]);  // M and Y of this stage have been read
-        mbar_arrive(&B.d_full);
-        tma_store_2d(&tmYout, yo, j0, i0);
+        mbar_arrive(&B.d_full[b]);
         tma_store_2d(&tmD, da, j0, i0);
         tma_store_commit();
       }
     }
     if (ok && ntiles > 0) mbar_wait(&B.q_full, 0, abort);
     named_bar(1, kEpiThreads);  // uniform decision before the warp-collective TMEM loads
-    if (ok && ntiles > 0 && !*abort) {
+    if (!FINAL && ok && ntiles > 0 && !*abort) {
       tc_fence_after();
       float q[32];
       tmem_ld16(tmem + lane_base + TM_Q + cbase, q);
@@ -332,7 +422,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
     for (int o = 16; o > 0; o >>= 1) resid += __shfl_xor_sync(0xffffffffu, resid, o);
     if (lane == 0) B.red[warp] = resid;
     named_bar(1, kEpiThreads);
-    if (tid == 0) {
+    if (!FINAL && tid == 0) {
       double tot = 0.0;
       for (int w = 0; w < 8; ++w) tot += (double)B.red[w];
       resid_part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
@@ -492,28 +582,38 @@ __device__ __forceinline__ float tf32_round(float x) {
 
 // From U (rows x 64 f32): hi = tf32(U), lo = U - hi (rows x 64 f32), and U^T in bf16 (64 x ldt).
 // Same routine for C (hi/lo) with V^T taken from a second input.
-__global__ void split_transpose_kernel(const float* __restrict__ X, const float* __restrict__ Xt_src, int64_t rows,
-                                       float* __restrict__ hi, float* __restrict__ lo, __nv_bfloat16* __restrict__ t,
-                                       int64_t ldt, const DevState* st) {
+__global__ void __launch_bounds__(256) split_transpose_kernel(const float* __restrict__ X,
+                                                              const float* __restrict__ Xt_src, int64_t rows,
+                                                              float* __restrict__ hi, float* __restrict__ lo,
+                                                              __nv_bfloat16* __restrict__ t, int64_t ldt,
+                                                              const DevState* st) {
   if (stopped(st)) return;
   __shared__ float tile[64][65];
   const int64_t r0 = (int64_t)blockIdx.x * 64;
-  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-    const int rr = e / 64, a = e % 64;
+  const int tid = threadIdx.x;
+  float xv[16], tv[16];  // element e = tid + 256 q of the 64 x 64 tile: all loads in flight first
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int e = tid + 256 * q;
+    const int64_t i = r0 + e / 64;
+    xv[q] = i < rows ? X[i * 64 + e % 64] : 0.f;
+    tv[q] = i < rows ? Xt_src[i * 64 + e % 64] : 0.f;
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int e = tid + 256 * q, rr = e / 64, a = e % 64;
     const int64_t i = r0 + rr;
     if (i < rows) {
-      const float x = X[i * 64 + a];
-      const float h = tf32_round(x);
+      const float h = tf32_round(xv[q]);
       hi[i * 64 + a] = h;
-      lo[i * 64 + a] = x - h;
-      tile[rr][a] = Xt_src[i * 64 + a];
-    } else {
-      tile[rr][a] = 0.f;
+      lo[i * 64 + a] = xv[q] - h;
     }
+    tile[rr][a] = tv[q];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-    const int a = e / 64, rr = e % 64;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int e = tid + 256 * q, a = e / 64, rr = e % 64;
     const int64_t i = r0 + rr;
     if (i < rows) t[(int64_t)a * ldt + i] = __float2bfloat16_rn(tile[rr][a]);
   }
@@ -598,13 +698,32 @@ cudaError_t tc_launch_wpass(const Shape& s, const TcMaps& mp, bool first, float*
 
 cudaError_t tc_launch_sweep(const Shape& s, const TcMaps& mp, const TcBuffers& t, int y_in, float* Qpart,
                             double* resid_part, DevState* dst, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(sweep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
+  auto kern = sweep_tc_kernel<false, float>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
   if (e != cudaSuccess) return e;
   dim3 grid(cdiv(s.m, TBM), s.nsplit);
-  sweep_tc_kernel<<<grid, kSweepThreads, SWEEP_SMEM, st>>>(mp.M, mp.Y[y_in], mp.Y[1 - y_in], mp.D, mp.Ch, mp.Cl,
-                                                            mp.Vt, t.Uh, t.Ul, s.m, s.n, s.cols_per_split, Qpart,
-                                                            resid_part, dst);
+  kern<<<grid, kSweepThreads, SWEEP_SMEM, st>>>(mp.M, mp.Y[y_in], mp.D, mp.Ch, mp.Cl, mp.Vt, t.Uh, t.Ul,
+                                                static_cast<__nv_bfloat16*>(t.Y[1 - y_in]), t.ldy, s.m, s.n,
+                                                s.cols_per_split, Qpart, resid_part, dst, nullptr, nullptr, 0, 0);
   return cudaGetLastError();
+}
+
+cudaError_t tc_launch_finalize(const Shape& s, const TcMaps& mp, const TcBuffers& t, int y_in, void* S,
+                               int s_dtype, int64_t lds, void* L, DevState* dst, cudaStream_t st) {
+  const size_t es = s_dtype == SFR_F64 ? 8 : 4;
+  const bool vec = ((uintptr_t)S % 16 == 0) && ((uintptr_t)L % 16 == 0) && ((size_t)lds * es) % 16 == 0;
+  dim3 grid(cdiv(s.m, TBM), 1);
+  auto go = [&](auto zero) -> cudaError_t {
+    using TSo = decltype(zero);
+    auto kern = sweep_tc_kernel<true, TSo>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kSweepThreads, SWEEP_SMEM, st>>>(mp.M, mp.Y[y_in], mp.D, mp.Ch, mp.Cl, mp.Vt, t.Uh, t.Ul, nullptr,
+                                                  t.ldy, s.m, s.n, (int)((s.n + 63) / 64 * 64), nullptr, nullptr,
+                                                  dst, static_cast<TSo*>(S), static_cast<TSo*>(L), lds, vec ? 1 : 0);
+    return cudaGetLastError();
+  };
+  return s_dtype == SFR_F64 ? go(0.0) : go(0.f);
 }
 
 }  // namespace sfr

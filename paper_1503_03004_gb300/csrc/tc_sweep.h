@@ -38,5 +38,10 @@ cudaError_t tc_launch_wpass(const Shape& s, const TcMaps& mp, bool first, float*
                             cudaStream_t st);
 cudaError_t tc_launch_sweep(const Shape& s, const TcMaps& mp, const TcBuffers& t, int y_in, float* Qpart,
                             double* resid_part, DevState* dst, cudaStream_t st);
+// S = P_ST_{1/mu}(M - L + Y / mu) (and L when non-null) from the last iteration's factors, mu
+// and multiplier Y = t.Y[y_in]; S / L are m x n with leading dimension lds, float64 when
+// s_dtype == SFR_F64 else float32.
+cudaError_t tc_launch_finalize(const Shape& s, const TcMaps& mp, const TcBuffers& t, int y_in, void* S,
+                               int s_dtype, int64_t lds, void* L, DevState* dst, cudaStream_t st);
 
 }  // namespace sfr
