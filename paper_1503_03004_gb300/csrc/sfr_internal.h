@@ -47,7 +47,18 @@ struct Shape {
   int gram_rows;        // rows per CTA in the Gram / row-transform kernels
   int gp_blocks;        // ceil(m / gram_rows)
   int gw_blocks;        // ceil(n / gram_rows)
+  int resid_parts;      // residual partials written by one sweep
+  int q_ctas;           // > 0: persistent tensor-core sweep over this many CTAs, whose Q partials per
+                        // 128-row block are the CTAs owning its tiles (tc_q_slots); nsplit = max slots
 };
+
+// Persistent tensor-core sweep: the N = R T (128-row block, 64-column tile) pairs, row-major,
+// are split into G contiguous ranges; CTA c owns tiles [c N / G, (c + 1) N / G).
+__host__ __device__ inline int64_t tc_tile_owner(int64_t x, int64_t N, int64_t G) { return ((x + 1) * G - 1) / N; }
+// Number of CTAs (Q partial slots) that own tiles of row block rb; slot k is CTA owner(rb T) + k.
+__host__ __device__ inline int tc_q_slots(int64_t rb, int64_t T, int64_t N, int64_t G) {
+  return (int)(tc_tile_owner(rb * T + T - 1, N, G) - tc_tile_owner(rb * T, N, G) + 1);
+}
 
 // Device buffers of one solve.  TC is double (FP64 path) or float (mixed path);
 // the pointers below are typed void* and cast by the launchers.

@@ -120,6 +120,8 @@ Shape plan_shape(int64_t m, int64_t n, int64_t ldm, int r, int num_sms) {
   // number of r x r partials the projector kernels reduce
   s.gp_blocks = (int)std::min<int64_t>((m + kGramRows - 1) / kGramRows, num_sms);
   s.gw_blocks = (int)std::min<int64_t>((n + kGramRows - 1) / kGramRows, num_sms);
+  s.resid_parts = s.sweep_grid_x * s.nsplit;
+  s.q_ctas = 0;
   return s;
 }
 
@@ -161,7 +163,7 @@ size_t carve(const Shape& s, bool fp64, void* base, Buffers* b, bool tc) {
   x.GWpart = static_cast<double*>(c.take(8 * rpsq * s.gw_blocks));
   x.Hpart = static_cast<double*>(c.take(8 * rpsq * (s.gp_blocks + 1)));
   x.Gsum = static_cast<double*>(c.take(8 * rpsq));
-  x.resid_part = static_cast<double*>(c.take(8 * (size_t)s.sweep_grid_x * s.nsplit));
+  x.resid_part = static_cast<double*>(c.take(8 * (size_t)s.resid_parts));
   x.normm_part = static_cast<double*>(c.take(8 * 1024));
   x.B = static_cast<double*>(c.take(8 * rpsq));
   x.TU = static_cast<double*>(c.take(8 * rpsq));
@@ -334,12 +336,7 @@ struct Solver {
     const bool tc = !fp64 && tc_supported(s0, p.m_dtype, p.ldm) && ((uintptr_t)Mdev % 16) == 0;
     last_tc = tc;
     Shape s = s0;
-    if (tc) {
-      // tensor-core sweep: 128-row CTAs over the whole column range (one P partial per row)
-      s.sweep_grid_x = (int)((p.m + 127) / 128);
-      s.nsplit = 1;
-      s.cols_per_split = (int)((p.n + 63) / 64 * 64);
-    }
+    if (tc) tc_plan(&s, num_sms);  // persistent sweep over the SMs
     Buffers b{};
     const size_t bytes = carve(s, fp64, nullptr, nullptr, tc);
     work.ensure(bytes, &held, budget);
@@ -493,36 +490,66 @@ struct Solver {
   }
 };
 
-// Smallest eigenvalue of a symmetric r x r matrix (cyclic Jacobi on the host, float64).
+// Smallest eigenvalue of a symmetric r x r matrix (host, float64): Householder reduction to
+// tridiagonal form, then bisection on the Sturm count (the number of negative pivots of
+// T - x I, which equals the number of eigenvalues below x).  O(r^3) once, O(r) per probe.
 double host_lambda_min(std::vector<double> A, int r) {
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0;
-    for (int i = 0; i < r; ++i)
-      for (int j = 0; j < r; ++j)
-        if (i != j) off += A[i * r + j] * A[i * r + j];
-    if (off < 1e-30) break;
-    for (int p = 0; p < r; ++p)
-      for (int q = p + 1; q < r; ++q) {
-        const double apq = A[p * r + q];
-        if (std::fabs(apq) < 1e-300) continue;
-        const double th = (A[q * r + q] - A[p * r + p]) / (2 * apq);
-        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(1 + th * th));
-        const double c = 1 / std::sqrt(1 + t * t), s = t * c;
-        for (int k = 0; k < r; ++k) {
-          const double ap = A[p * r + k], aq = A[q * r + k];
-          A[p * r + k] = c * ap - s * aq;
-          A[q * r + k] = s * ap + c * aq;
-        }
-        for (int k = 0; k < r; ++k) {
-          const double ap = A[k * r + p], aq = A[k * r + q];
-          A[k * r + p] = c * ap - s * aq;
-          A[k * r + q] = s * ap + c * aq;
-        }
-      }
+  if (r <= 0) return NAN;
+  std::vector<double> v(r), pv(r), d(r), e(r, 0.0);
+  for (int k = 0; k + 2 < r; ++k) {
+    double alpha = 0.0;
+    for (int i = k + 1; i < r; ++i) alpha += A[i * r + k] * A[i * r + k];
+    alpha = std::sqrt(alpha);
+    if (alpha == 0.0) continue;
+    if (A[(k + 1) * r + k] > 0) alpha = -alpha;
+    double vv = 0.0;
+    for (int i = k + 1; i < r; ++i) {
+      v[i] = A[i * r + k] - (i == k + 1 ? alpha : 0.0);
+      vv += v[i] * v[i];
+    }
+    if (vv == 0.0) continue;
+    const double beta = 2.0 / vv;
+    // trailing block: A <- H A H, H = I - beta v v^T, as A - v w^T - w v^T
+    double pv_dot = 0.0;
+    for (int i = k + 1; i < r; ++i) {
+      double s = 0.0;
+      for (int j = k + 1; j < r; ++j) s += A[i * r + j] * v[j];
+      pv[i] = beta * s;
+      pv_dot += pv[i] * v[i];
+    }
+    const double c = 0.5 * beta * pv_dot;
+    for (int i = k + 1; i < r; ++i) pv[i] -= c * v[i];  // w
+    for (int i = k + 1; i < r; ++i)
+      for (int j = k + 1; j < r; ++j) A[i * r + j] -= v[i] * pv[j] + pv[i] * v[j];
+    A[(k + 1) * r + k] = A[k * r + k + 1] = alpha;
+    for (int i = k + 2; i < r; ++i) A[i * r + k] = A[k * r + i] = 0.0;
   }
-  double lo = A[0];
-  for (int i = 1; i < r; ++i) lo = std::min(lo, A[i * r + i]);
-  return lo;
+  for (int i = 0; i < r; ++i) d[i] = A[i * r + i];
+  for (int i = 0; i + 1 < r; ++i) e[i] = A[(i + 1) * r + i];
+  auto below = [&](double x) {  // eigenvalues of the tridiagonal matrix below x
+    int count = 0;
+    double q = d[0] - x;
+    for (int i = 0;; ++i) {
+      if (q < 0) ++count;
+      if (i + 1 == r) break;
+      if (q == 0.0) q = 1e-300;
+      q = d[i + 1] - x - e[i] * e[i] / q;
+    }
+    return count;
+  };
+  double lo = d[0], hi = d[0];
+  for (int i = 0; i < r; ++i) {  // Gershgorin interval
+    const double rad = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < r ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - rad);
+    hi = std::max(hi, d[i] + rad);
+  }
+  if (!(lo == lo) || !(hi == hi)) return NAN;
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid == lo || mid == hi) break;
+    if (below(mid) >= 1) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
 }
 
 DevState solver_run(Solver& sv, const sfr_problem& p, const void* Mdev, double* U, double* B, double* V, void* S,
@@ -709,10 +736,7 @@ static size_t request_bytes(const sfr_problem& p, int num_sms) {
   auto one = [&](int64_t m, int64_t n) {
     Shape s = plan_shape(m, n, n, p.r, num_sms);
     const bool tc = !fp64 && tc_supported(s, p.m_dtype, n);
-    if (tc) {
-      s.sweep_grid_x = (int)((m + 127) / 128);
-      s.nsplit = 1;
-    }
+    if (tc) tc_plan(&s, num_sms);
     return carve(s, fp64, nullptr, nullptr, tc);
   };
   if (p.nys_l) {

@@ -164,12 +164,14 @@ __device__ __forceinline__ void store_tile(TC* s, int t, const TC (&v)[TileIdx<R
 // For every 64-row tile handled by this CTA (tiles blockIdx.x, blockIdx.x + gridDim.x, ...):
 // out[i][:] = sum_s parts[s][i][:]  (+ addA[i][:] H when addA != nullptr), then the CTA's
 // Gram partial gpart[cta] = sum over its rows of out[i]^T out[i]  (r x r).
-// nparts == 0 leaves `out` as it is and only forms the Gram partial.
+// nparts == 0 leaves `out` as it is and only forms the Gram partial.  q_ctas > 0: the partials
+// come from the persistent tensor-core sweep (q_tiles column tiles per 128-row block), and rows of
+// block rb have tc_q_slots(rb) of them.
 template <typename TC, int RP>
 __global__ void __launch_bounds__(256) thin_gram_kernel(const TC* __restrict__ parts, int nparts, int64_t part_stride,
                                                         TC* __restrict__ out, int64_t rows, const TC* __restrict__ addA,
                                                         const double* __restrict__ H, double* __restrict__ gpart,
-                                                        const DevState* st) {
+                                                        const DevState* st, int q_ctas = 0, int64_t q_tiles = 0) {
   if (stopped(st)) return;
   constexpr int LDT = RP + 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -187,8 +189,13 @@ __global__ void __launch_bounds__(256) thin_gram_kernel(const TC* __restrict__ p
     if (nparts == 0) {
       load_tile<TC, RP>(out, i0, rows, t, v);
     } else {
+      int np = nparts;
+      if (q_ctas > 0) {  // a 64-row tile lies in one 128-row block
+        const int64_t nblk = (rows + 127) / 128;
+        np = min(nparts, tc_q_slots(i0 / 128, q_tiles, nblk * q_tiles, q_ctas));
+      }
       load_tile<TC, RP>(parts, i0, rows, t, v);
-      for (int s = 1; s < nparts; ++s) {
+      for (int s = 1; s < np; ++s) {
         TC w[TileIdx<RP>::PER];
         load_tile<TC, RP>(parts + s * part_stride, i0, rows, t, w);
 #pragma unroll
@@ -681,7 +688,7 @@ cudaError_t launch_gram_p(const Shape& s, const Buffers& b, bool fp64, bool sum_
       if (e != cudaSuccess) return e;
       thin_gram_kernel<TC, RP><<<s.gp_blocks, 256, sm, st>>>(
           static_cast<const TC*>(b.Qpart), sum_parts ? s.nsplit : 0, s.m * RP, static_cast<TC*>(b.P), s.m,
-          static_cast<const TC*>(addA), H, b.GPpart, b.st);
+          static_cast<const TC*>(addA), H, b.GPpart, b.st, s.q_ctas, (s.n + 63) / 64);
       return cudaGetLastError();
     });
   });
@@ -794,7 +801,7 @@ cudaError_t launch_sweep(const Shape& s, const Buffers& b, bool fp64, int u_cur,
 }
 
 cudaError_t launch_iter_end(const Shape& s, const Buffers& b, cudaStream_t st) {
-  iter_end_kernel<<<1, 256, 0, st>>>(b.resid_part, s.sweep_grid_x * s.nsplit, b.st);
+  iter_end_kernel<<<1, 256, 0, st>>>(b.resid_part, s.resid_parts, b.st);
   return cudaGetLastError();
 }
 

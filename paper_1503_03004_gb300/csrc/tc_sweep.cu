@@ -16,6 +16,8 @@
 // issues TMA loads, warp 9 owns TMEM and issues MMAs.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "sfr_internal.h"
 #include "tc_common.cuh"
 #include "tc_sweep.h"
@@ -31,29 +33,35 @@ constexpr int TBM = 128, TBN = 64, TR = 64;
 constexpr int NSTAGE = 3;
 constexpr uint32_t OFF_C = 0;           // C tiles, 2 buffers x 32 KB: hi (2 K-atoms x 64 rows x 128 B) then lo
 constexpr uint32_t C_BUF = 32768;
-constexpr uint32_t OFF_ST = 65536;      // input stages, 3 x 40 KB: M tile (128 x 64 bf16), Y tile, V^T tile (64 x 64 bf16)
-constexpr uint32_t ST_BYTES = 40960;
-constexpr uint32_t ST_Y = 16384, ST_VT = 32768;
-constexpr uint32_t OFF_DA = OFF_ST + NSTAGE * ST_BYTES;  // Delta tiles, 2 x 16 KB: A operand of Delta V and
-                                                         // TMA store source (tile t uses buffer t % 2)
+constexpr uint32_t OFF_ST = 65536;      // input stages, 3 x 32 KB: M tile (128 x 64 bf16), Y tile; each epilogue
+constexpr uint32_t ST_BYTES = 32768;    // warp releases a stage as soon as it has its M and Y values in registers
+constexpr uint32_t ST_Y = 16384;
+constexpr int NVT = 4;                  // V^T tiles (64 x 64 bf16), a ring of 4: held until Delta V_bar is done
+constexpr uint32_t OFF_VT = OFF_ST + NSTAGE * ST_BYTES;
+constexpr uint32_t VT_BYTES = 8192;
+constexpr uint32_t OFF_DA = OFF_VT + NVT * VT_BYTES;  // Delta tiles, 2 x 16 KB: A operand of Delta V and
+                                                      // TMA store source (tile t uses buffer t % 2)
 constexpr uint32_t DA_BYTES = 16384;
 constexpr uint32_t OFF_BAR = OFF_DA + 2 * DA_BYTES;
-constexpr uint32_t SWEEP_SMEM = OFF_BAR + 256 + 1024;
+constexpr uint32_t SWEEP_SMEM = OFF_BAR + 512 + 1024;
 static_assert(OFF_BAR % 1024 == 0, "alignment");
-// tensor memory columns
-constexpr uint32_t TM_L = 0, TM_Q = 128, TM_UH = 256, TM_UL = 320, TM_COLS = 512;
+static_assert(SWEEP_SMEM <= 232448, "shared memory per CTA");
+// tensor memory columns: L double buffer; per segment s (a CTA's tiles span at most two 128-row
+// blocks): Q at TM_Q + 64 s, U_hi at TM_U + 128 s, U_lo at TM_U + 128 s + 64
+constexpr uint32_t TM_L = 0, TM_Q = 128, TM_U = 256, TM_COLS = 512;
 
 struct SweepBars {
   uint64_t stage_full[NSTAGE], stage_empty[NSTAGE];
+  uint64_t vt_full[NVT], vt_empty[NVT];
   uint64_t c_full[2], c_empty[2];
   uint64_t l_full[2], l_empty[2];
   uint64_t d_full[2], d_empty[2];
   uint64_t q_full;
   uint32_t tmem_base;
   int abort;
-  float red[8];
+  float red[16];
 };
-static_assert(sizeof(SweepBars) <= 256, "barrier block");
+static_assert(sizeof(SweepBars) <= 512, "barrier block");
 
 __device__ __forceinline__ bool stopped(const DevState* st) { return *(volatile const int32_t*)&st->done != 0; }
 
@@ -119,32 +127,41 @@ __device__ __forceinline__ void epi_chunk(const uint4& mw, const uint4& yw, cons
   d_out = make_uint4(dd[0], dd[1], dd[2], dd[3]);
 }
 
-// Writes this thread's 32 columns of a row (the first ncol of them valid): 16-byte vector stores
+// Writes this thread's NC columns of a row (the first ncol of them valid): 16-byte vector stores
 // when the destination allows them, else element by element.
-template <typename TSo>
+template <typename TSo, int NC>
 __device__ __forceinline__ void store_cols(TSo* dst, const float* v, int ncol, bool vec) {
-  if (vec && ncol >= 32) {
+  if (vec && ncol >= NC) {
     if constexpr (sizeof(TSo) == 4) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
+      for (int q = 0; q < NC / 4; ++q)
         reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     } else {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) reinterpret_cast<double2*>(dst)[q] = make_double2(v[2 * q], v[2 * q + 1]);
+      for (int q = 0; q < NC / 2; ++q) reinterpret_cast<double2*>(dst)[q] = make_double2(v[2 * q], v[2 * q + 1]);
     }
   } else {
 #pragma unroll
-    for (int q = 0; q < 32; ++q)
+    for (int q = 0; q < NC; ++q)
       if (q < ncol) dst[q] = (TSo)v[q];
   }
 }
 
-constexpr int kEpiThreads = 256;
-constexpr int kSweepThreads = kEpiThreads + 64;
+// Epilogue: kEpiWarps warps; warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and the
+// kEpiCols columns kEpiCols (w / 4) .. of each 64-column tile.  Then the M / Y / V^T producer
+// warp, the MMA warp and the C producer warp.
+constexpr int kEpiWarps = 16;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kEpiCols = TBN / (kEpiWarps / 4);   // 16
+constexpr int kEpiChunks = kEpiCols / 8;          // 16-byte chunks of a row per thread
+constexpr int kProdWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1, kCProdWarp = kEpiWarps + 2;
+constexpr int kSweepThreads = kEpiThreads + 96;
+static_assert(kEpiCols % 16 == 0, "TMEM loads of 16 columns");
 
-// Sweep CTA: 128 rows x a range of 64-column tiles.  Warps 0-7: epilogue (warp w owns TMEM
-// lanes / rows 32 (w % 4) .. + 31 and columns 32 (w / 4) .. + 31 of each tile); warp 8: TMA
-// producer; warp 9: TMEM owner and MMA issuer.  U_hi / U_lo (the fixed A operand of the L
+// Sweep CTA: a contiguous range of (128-row block, 64-column tile) pairs.  Warps 0-15: epilogue
+// (warp w owns TMEM lanes / rows 32 (w % 4) .. + 31 and columns 16 (w / 4) .. + 15 of each tile);
+// warp 16: TMA producer of M, Y and V^T; warp 17: TMEM owner and MMA issuer; warp 18: TMA
+// producer of the C tiles.  U_hi / U_lo (the fixed A operand of the L
 // products) live in tensor memory; M, Y and V^T tiles stream through three stages; C tiles
 // are double buffered; Y_{k+1} goes to global memory straight from registers (each thread
 // writes 64 contiguous bytes of its row); Delta tiles are double buffered in shared memory,
@@ -162,8 +179,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
                                                                    const float* __restrict__ Uh,
                                                                    const float* __restrict__ Ul,
                                                                    __nv_bfloat16* __restrict__ Yout, int64_t ldy,
-                                                                   int64_t m, int64_t n,
-                                                                   int cols_per_split, float* __restrict__ Qpart,
+                                                                   int64_t m, int64_t n, float* __restrict__ Qpart,
                                                                    double* __restrict__ resid_part, DevState* st,
                                                                    TSo* __restrict__ Sout, TSo* __restrict__ Lout,
                                                                    int64_t lds, int vec_out) {
@@ -172,16 +188,27 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
   unsigned char* sm = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   SweepBars& B = *reinterpret_cast<SweepBars*>(sm + OFF_BAR);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int i0 = blockIdx.x * TBM;
-  const int jbeg = blockIdx.y * cols_per_split;
-  const int jend = (int)(((int64_t)jbeg + cols_per_split < n) ? (int64_t)jbeg + cols_per_split : n);
-  const int ntiles = (jend - jbeg + TBN - 1) / TBN;
+  // this CTA's tiles: [x0, x1) of the N (row block, column tile) pairs (tc_tile_owner); the host
+  // keeps x1 - x0 <= T, so they span at most two row blocks: local tiles [0, kb) are segment 0
+  // (row block rb0), [kb, ntiles) segment 1 (row block rb0 + 1)
+  const int64_t T = (n + TBN - 1) / TBN, N = ((m + TBM - 1) / TBM) * T, G = gridDim.x;
+  const int64_t x0 = (int64_t)blockIdx.x * N / G, x1 = ((int64_t)blockIdx.x + 1) * N / G;
+  const int ntiles = (int)(x1 - x0);
+  const int64_t rb0 = x0 / T;
+  const int kb = (int)(((rb0 + 1) * T < x1 ? (rb0 + 1) * T : x1) - x0);
+  const int nseg = kb < ntiles ? 2 : 1;
+  auto tile_i0 = [&](int k) -> int { return (int)((rb0 + (k >= kb)) * TBM); };
+  auto tile_j0 = [&](int k) -> int { return (int)((x0 + k - (rb0 + (k >= kb)) * T) * TBN); };
   volatile int* abort = &B.abort;
 
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(&B.stage_full[s], 1);
-      mbar_init(&B.stage_empty[s], FINAL ? 1 : 2);  // epilogue (+ the Delta V MMA reading V^T)
+      mbar_init(&B.stage_empty[s], kEpiWarps);  // one arrival per epilogue warp
+    }
+    for (int v = 0; v < NVT; ++v) {
+      mbar_init(&B.vt_full[v], 1);
+      mbar_init(&B.vt_empty[v], 1);  // the Delta V MMAs of the tile have completed
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&B.c_full[s], 1);
@@ -197,17 +224,18 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
     B.abort = 0;
     mbar_fence_init();
   }
-  if (warp == 9) tmem_alloc(&B.tmem_base, TM_COLS);
+  if (warp == kMmaWarp) tmem_alloc(&B.tmem_base, TM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = B.tmem_base;
-  const int quarter = warp & 3, half = (warp >> 2) & 1;
+  const int quarter = warp & 3, grp = warp >> 2;
   const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-  if (warp < 8) {
-    // U_hi / U_lo rows of this CTA into tensor memory (lane = row, column = k)
+  if (warp < 8 * nseg) {
+    // U_hi / U_lo rows of segment `seg` into tensor memory (lane = row, column = k)
+    const int half = grp & 1, seg = warp >> 3;
     const int row = quarter * 32 + lane;
-    const int64_t gi = (int64_t)i0 + row;
+    const int64_t gi = (rb0 + seg) * TBM + row;
     float v[16];
     for (int part = 0; part < 2; ++part) {
       const float* src = part ? Ul : Uh;
@@ -215,7 +243,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
         const int k0 = half * 32 + c;
 #pragma unroll
         for (int q = 0; q < 16; ++q) v[q] = gi < m ? src[gi * TR + k0 + q] : 0.f;
-        tmem_st16(tmem + lane_base + (part ? TM_UL : TM_UH) + k0, v);
+        tmem_st16(tmem + lane_base + TM_U + 128 * seg + (part ? 64 : 0) + k0, v);
       }
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -224,22 +252,48 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
   __syncthreads();
   tc_fence_after();
 
-  if (warp == 8) {
+  if (warp == kProdWarp) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       prefetch_map(&tmM);
       prefetch_map(&tmYin);
-      int armed_stage[NSTAGE] = {-1, -1, -1}, armed_c[2] = {-1, -1};
+      int armed_stage[NSTAGE] = {-1, -1, -1}, armed_vt[NVT] = {-1, -1, -1, -1};
       for (int t = 0; t < ntiles && !*abort; ++t) {
-        const int s = t % NSTAGE, j0 = jbeg + t * TBN;
+        const int s = t % NSTAGE, i0 = tile_i0(t), j0 = tile_j0(t);
         if (t >= NSTAGE && !mbar_wait(&B.stage_empty[s], ((t / NSTAGE) - 1) & 1, abort)) break;
         unsigned char* stg = sm + OFF_ST + s * ST_BYTES;
-        mbar_expect_tx(&B.stage_full[s], FINAL ? 16384 + 16384 : 16384 + 16384 + 8192);
+        mbar_expect_tx(&B.stage_full[s], 16384 + 16384);
         tma_load_2d(stg, &tmM, j0, i0, &B.stage_full[s]);
         tma_load_2d(stg + ST_Y, &tmYin, j0, i0, &B.stage_full[s]);
-        if (!FINAL) tma_load_2d(stg + ST_VT, &tmVt, j0, 0, &B.stage_full[s]);
         armed_stage[s] = t;
-        const int cb = t & 1;
+        if (!FINAL) {
+          const int v = t % NVT;
+          if (t >= NVT && !mbar_wait(&B.vt_empty[v], ((t / NVT) - 1) & 1, abort)) break;
+          mbar_expect_tx(&B.vt_full[v], VT_BYTES);
+          tma_load_2d(sm + OFF_VT + v * VT_BYTES, &tmVt, j0, 0, &B.vt_full[v]);
+          armed_vt[v] = t;
+        }
+      }
+      if (*abort) {  // let the copies this thread issued land before the CTA exits
+        for (int q = 0; q < NSTAGE; ++q)
+          if (armed_stage[q] >= 0) {
+            int dummy = 0;
+            mbar_wait(&B.stage_full[q], (armed_stage[q] / NSTAGE) & 1, &dummy);
+          }
+        for (int q = 0; q < NVT; ++q)
+          if (armed_vt[q] >= 0) {
+            int dummy = 0;
+            mbar_wait(&B.vt_full[q], (armed_vt[q] / NVT) & 1, &dummy);
+          }
+      }
+    }
+  } else if (warp == kCProdWarp) {
+    // ------------------------------------------------------------ TMA producer of the C tiles
+    // (its own thread, so that waiting for a C buffer never holds back the M / Y stream)
+    if (lane == 0) {
+      int armed_c[2] = {-1, -1};
+      for (int t = 0; t < ntiles && !*abort; ++t) {
+        const int cb = t & 1, j0 = tile_j0(t);
         if (t >= 2 && !mbar_wait(&B.c_empty[cb], ((t >> 1) - 1) & 1, abort)) break;
         unsigned char* cbuf = sm + OFF_C + cb * C_BUF;
         mbar_expect_tx(&B.c_full[cb], 4 * 8192);
@@ -249,37 +303,33 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
         }
         armed_c[cb] = t;
       }
-      if (*abort) {  // let the copies this thread issued land before the CTA exits
-        for (int q = 0; q < NSTAGE; ++q)
-          if (armed_stage[q] >= 0) {
-            int dummy = 0;
-            mbar_wait(&B.stage_full[q], (armed_stage[q] / NSTAGE) & 1, &dummy);
-          }
+      if (*abort)
         for (int q = 0; q < 2; ++q)
           if (armed_c[q] >= 0) {
             int dummy = 0;
             mbar_wait(&B.c_full[q], (armed_c[q] >> 1) & 1, &dummy);
           }
-      }
     }
-  } else if (warp == 9) {
+  } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t id_l = idesc(2, TBM, TBN);   // tf32, 128 x 64
       const uint32_t id_q = idesc(1, TBM, TR);    // bf16, 128 x 64
       auto delta_v = [&](int tt) -> bool {
-        const int s = tt % NSTAGE;
+        const int v = tt % NVT;
         const int db = tt & 1;
         if (!mbar_wait(&B.d_full[db], (tt >> 1) & 1, abort)) return false;
+        if (!mbar_wait(&B.vt_full[v], (tt / NVT) & 1, abort)) return false;
         tc_fence_after();
-        const uint32_t vt = smem_u32(sm + OFF_ST + s * ST_BYTES + ST_VT);
+        const uint32_t vt = smem_u32(sm + OFF_VT + v * VT_BYTES);
         for (int kk = 0; kk < TBN / 16; ++kk) {
           const uint64_t a = desc_sw128(smem_u32(sm + OFF_DA + db * DA_BYTES) + kk * 32);
           const uint64_t b = desc_sw128(vt + kk * 32);
-          mma_bf16(tmem + TM_Q, a, b, id_q, (tt > 0 || kk > 0) ? 1u : 0u);
+          const int seg = tt >= kb, first = seg ? kb : 0;  // Q of each segment starts from zero
+          mma_bf16(tmem + TM_Q + 64 * seg, a, b, id_q, (tt > first || kk > 0) ? 1u : 0u);
         }
         mma_commit(&B.d_empty[db]);
-        mma_commit(&B.stage_empty[s]);
+        mma_commit(&B.vt_empty[v]);
         return true;
       };
       bool ok = true;
@@ -292,7 +342,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
         const uint32_t cbuf = smem_u32(sm + OFF_C + b * C_BUF);
         // L = U_hi C_hi^T + U_hi C_lo^T + U_lo C_hi^T, K = 64 in 8 steps of 8
         for (int term = 0; term < 3; ++term) {
-          const uint32_t ua = tmem + (term == 2 ? TM_UL : TM_UH);
+          const uint32_t ua = tmem + TM_U + 128 * (t >= kb) + (term == 2 ? 64 : 0);
           const uint32_t cb = cbuf + (term == 1 ? 16384 : 0);
           for (int ks = 0; ks < 8; ++ks) {
             const uint64_t bb = desc_sw128(cb + (ks >> 2) * 8192 + (ks & 3) * 32);
@@ -311,19 +361,18 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
       }
     }
   } else {
-    // ------------------------------------------------------------ epilogue: warps 0-7
+    // ------------------------------------------------------------ epilogue warps
     const int row = quarter * 32 + lane;          // TMEM lane and tile row
-    const int cbase = half * 32;                  // first of this warp's 32 columns
-    const int64_t gi = (int64_t)i0 + row;
+    const int cbase = grp * kEpiCols;             // first of this warp's columns
     const float mu = (float)st->mu;
     const float inv_mu_last = (float)(1.0 / st->mu_last);
     const double mu_next_d = fmin(st->mu_max, st->rho * st->mu);
     const float inv_mu = (float)(1.0 / st->mu), dcoef = (float)(1.0 / st->mu + 1.0 / mu_next_d);
     float resid = 0.f;
     bool ok = true;
-    __nv_bfloat16* yrow = Yout + gi * ldy + cbase;  // this thread's 32 columns of Y_{k+1} (j0 added per tile)
     for (int t = 0; t < ntiles; ++t) {
-      const int s = t % NSTAGE, b = t & 1, j0 = jbeg + t * TBN;
+      const int s = t % NSTAGE, b = t & 1, i0 = tile_i0(t), j0 = tile_j0(t);
+      const int64_t gi = (int64_t)i0 + row;
       if constexpr (FINAL) {
         mbar_wait(&B.l_full[b], (t >> 1) & 1, abort) && mbar_wait(&B.stage_full[s], (t / NSTAGE) & 1, abort);
         named_bar(1, kEpiThreads);
@@ -331,19 +380,26 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
           ok = false;
           break;
         }
+        const unsigned char* ms = sm + OFF_ST + s * ST_BYTES;
+        uint4 mwr[kEpiChunks], ywr[kEpiChunks];
+#pragma unroll
+        for (int cc = 0; cc < kEpiChunks; ++cc) {
+          const uint32_t off = sw128(row, grp * kEpiChunks + cc);
+          mwr[cc] = *reinterpret_cast<const uint4*>(ms + off);
+          ywr[cc] = *reinterpret_cast<const uint4*>(ms + ST_Y + off);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&B.stage_empty[s]);  // this warp is done with the stage
         tc_fence_after();
-        float L[32], sv[32];
-        tmem_ld16(tmem + lane_base + TM_L + b * TBN + cbase, L);
-        tmem_ld16(tmem + lane_base + TM_L + b * TBN + cbase + 16, L + 16);
+        float L[kEpiCols], sv[kEpiCols];
+#pragma unroll
+        for (int q = 0; q < kEpiCols / 16; ++q) tmem_ld16(tmem + lane_base + TM_L + b * TBN + cbase + 16 * q, L + 16 * q);
         tmem_ld_wait();
         tc_fence_before();
         mbar_arrive(&B.l_empty[b]);
-        const unsigned char* ms = sm + OFF_ST + s * ST_BYTES;
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          const uint32_t off = sw128(row, half * 4 + cc);
-          const uint4 mw = *reinterpret_cast<const uint4*>(ms + off);
-          const uint4 yw = *reinterpret_cast<const uint4*>(ms + ST_Y + off);
+        for (int cc = 0; cc < kEpiChunks; ++cc) {
+          const uint4 mw = mwr[cc], yw = ywr[cc];
           const uint32_t mv[4] = {mw.x, mw.y, mw.z, mw.w}, yv[4] = {yw.x, yw.y, yw.z, yw.w};
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
@@ -353,13 +409,11 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
             sv[8 * cc + q] = z > inv_mu_last ? z - inv_mu_last : (z < -inv_mu_last ? z + inv_mu_last : 0.f);
           }
         }
-        named_bar(1, kEpiThreads);  // the stage has been read by every thread
-        if (tid == 0) mbar_arrive(&B.stage_empty[s]);
         if (gi < m) {
-          const int ncol = jend - j0 - cbase;
+          const int ncol = (int)(n - j0 - cbase);
           const int64_t o = gi * lds + j0 + cbase;
-          if (Sout) store_cols(Sout + o, sv, ncol, vec_out != 0);
-          if (Lout) store_cols(Lout + o, L, ncol, vec_out != 0);
+          if (Sout) store_cols<TSo, kEpiCols>(Sout + o, sv, ncol, vec_out != 0);
+          if (Lout) store_cols<TSo, kEpiCols>(Lout + o, L, ncol, vec_out != 0);
         }
         continue;
       }
@@ -371,33 +425,38 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
         ok = false;
         break;
       }
+      const unsigned char* ms = sm + OFF_ST + s * ST_BYTES;
+      uint4 mwr[kEpiChunks], ywr[kEpiChunks];
+#pragma unroll
+      for (int cc = 0; cc < kEpiChunks; ++cc) {
+        const uint32_t off = sw128(row, grp * kEpiChunks + cc);
+        mwr[cc] = *reinterpret_cast<const uint4*>(ms + off);
+        ywr[cc] = *reinterpret_cast<const uint4*>(ms + ST_Y + off);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&B.stage_empty[s]);  // this warp is done with the stage
       tc_fence_after();
-      float L[32];
-      tmem_ld16(tmem + lane_base + TM_L + b * TBN + cbase, L);
-      tmem_ld16(tmem + lane_base + TM_L + b * TBN + cbase + 16, L + 16);
+      float L[kEpiCols];
+#pragma unroll
+      for (int q = 0; q < kEpiCols / 16; ++q) tmem_ld16(tmem + lane_base + TM_L + b * TBN + cbase + 16 * q, L + 16 * q);
       tmem_ld_wait();
       tc_fence_before();
       mbar_arrive(&B.l_empty[b]);
-      const unsigned char* ms = sm + OFF_ST + s * ST_BYTES;
-      const unsigned char* ys = ms + ST_Y;
       unsigned char* da = sm + OFF_DA + b * DA_BYTES;
-      const int ncol = jend - j0 - cbase;  // valid columns among this thread's 32 (may be <= 0)
+      const int ncol = (int)(n - j0 - cbase);  // valid columns among this thread's (may be <= 0)
+      __nv_bfloat16* yrow = Yout + gi * ldy + j0 + cbase;  // this thread's columns of Y_{k+1}
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {  // 16-byte chunk c = columns 8c .. 8c+7
-        const int c = half * 4 + cc;
-        const uint32_t off = sw128(row, c);
-        const uint4 mw = *reinterpret_cast<const uint4*>(ms + off);
-        const uint4 yw = *reinterpret_cast<const uint4*>(ys + off);
+      for (int cc = 0; cc < kEpiChunks; ++cc) {  // 16-byte chunk c = columns 8c .. 8c+7
+        const uint32_t off = sw128(row, grp * kEpiChunks + cc);
         uint4 yn, dd;
-        if (ncol >= 32) epi_chunk<true>(mw, yw, L + 8 * cc, 0, mu, inv_mu, dcoef, yn, dd, resid);
-        else epi_chunk<false>(mw, yw, L + 8 * cc, ncol - 8 * cc, mu, inv_mu, dcoef, yn, dd, resid);
-        if (gi < m) *reinterpret_cast<uint4*>(yrow + j0 + 8 * cc) = yn;  // j0 + 63 < ldy: in the row
+        if (ncol >= kEpiCols) epi_chunk<true>(mwr[cc], ywr[cc], L + 8 * cc, 0, mu, inv_mu, dcoef, yn, dd, resid);
+        else epi_chunk<false>(mwr[cc], ywr[cc], L + 8 * cc, ncol - 8 * cc, mu, inv_mu, dcoef, yn, dd, resid);
+        if (gi < m) *reinterpret_cast<uint4*>(yrow + 8 * cc) = yn;  // j0 + 63 < ldy: in the row
         *reinterpret_cast<uint4*>(da + off) = dd;
       }
       fence_async_smem();
       named_bar(1, kEpiThreads);
       if (tid == 0) {
-        mbar_arrive(&B.stage_empty[s]);  // M and Y of this stage have been read
         mbar_arrive(&B.d_full[b]);
         tma_store_2d(&tmD, da, j0, i0);
         tma_store_commit();
@@ -407,30 +466,37 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
     named_bar(1, kEpiThreads);  // uniform decision before the warp-collective TMEM loads
     if (!FINAL && ok && ntiles > 0 && !*abort) {
       tc_fence_after();
-      float q[32];
-      tmem_ld16(tmem + lane_base + TM_Q + cbase, q);
-      tmem_ld16(tmem + lane_base + TM_Q + cbase + 16, q + 16);
-      tmem_ld_wait();
-      if (gi < m) {
-        float4* dst = reinterpret_cast<float4*>(Qpart + ((int64_t)blockIdx.y * m + gi) * TR + cbase);
+      for (int seg = 0; seg < nseg; ++seg) {
+        // Q partial of row block rb into slot (this CTA - the block's first owner)
+        const int64_t rb = rb0 + seg, gi = rb * TBM + row;
+        const int64_t slot = blockIdx.x - tc_tile_owner(rb * T, N, G);
+        float q[kEpiCols];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) dst[c] = make_float4(q[4 * c], q[4 * c + 1], q[4 * c + 2], q[4 * c + 3]);
+        for (int c = 0; c < kEpiCols / 16; ++c)
+          tmem_ld16(tmem + lane_base + TM_Q + 64 * seg + cbase + 16 * c, q + 16 * c);
+        tmem_ld_wait();
+        if (gi < m) {
+          float4* dst = reinterpret_cast<float4*>(Qpart + (slot * m + gi) * TR + cbase);
+#pragma unroll
+          for (int c = 0; c < kEpiCols / 4; ++c)
+            dst[c] = make_float4(q[4 * c], q[4 * c + 1], q[4 * c + 2], q[4 * c + 3]);
+        }
       }
     }
     if (tid == 0) tma_store_wait0();
-    // residual: warp sums, then thread 0 combines the eight warps in a fixed order
+    // residual: warp sums, then thread 0 combines the epilogue warps in a fixed order
     for (int o = 16; o > 0; o >>= 1) resid += __shfl_xor_sync(0xffffffffu, resid, o);
     if (lane == 0) B.red[warp] = resid;
     named_bar(1, kEpiThreads);
     if (!FINAL && tid == 0) {
       double tot = 0.0;
-      for (int w = 0; w < 8; ++w) tot += (double)B.red[w];
-      resid_part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+      for (int w = 0; w < kEpiWarps; ++w) tot += (double)B.red[w];
+      resid_part[blockIdx.x] = tot;
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 9) {
+  if (warp == kMmaWarp) {
     tc_fence_after();
     tmem_dealloc(tmem, TM_COLS);
   }
@@ -654,6 +720,19 @@ bool make_map(CUtensorMap* map, const void* base, CUtensorMapDataType dt, uint64
 
 }  // namespace
 
+void tc_plan(Shape* s, int num_sms) {
+  const int64_t R = (s->m + TBM - 1) / TBM, T = (s->n + TBN - 1) / TBN, N = R * T;
+  int64_t G = std::min<int64_t>(num_sms, N);
+  if (G < R) G = R;  // then every CTA owns at most T tiles, i.e. at most two row blocks
+  int slots = 1;
+  for (int64_t rb = 0; rb < R; ++rb) slots = std::max(slots, tc_q_slots(rb, T, N, G));
+  s->sweep_grid_x = (int)G;
+  s->nsplit = slots;
+  s->cols_per_split = (int)(T * TBN);
+  s->resid_parts = (int)G;
+  s->q_ctas = (int)G;
+}
+
 bool tc_supported(const Shape& s, int m_dtype, int64_t ldm) {
   return s.rp == 64 && m_dtype == SFR_BF16 && ldm % 8 == 0 && s.n % 8 == 0 && s.m % 8 == 0 && encode_fn() != nullptr;
 }
@@ -701,10 +780,9 @@ cudaError_t tc_launch_sweep(const Shape& s, const TcMaps& mp, const TcBuffers& t
   auto kern = sweep_tc_kernel<false, float>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
   if (e != cudaSuccess) return e;
-  dim3 grid(cdiv(s.m, TBM), s.nsplit);
-  kern<<<grid, kSweepThreads, SWEEP_SMEM, st>>>(mp.M, mp.Y[y_in], mp.D, mp.Ch, mp.Cl, mp.Vt, t.Uh, t.Ul,
-                                                static_cast<__nv_bfloat16*>(t.Y[1 - y_in]), t.ldy, s.m, s.n,
-                                                s.cols_per_split, Qpart, resid_part, dst, nullptr, nullptr, 0, 0);
+  kern<<<s.sweep_grid_x, kSweepThreads, SWEEP_SMEM, st>>>(mp.M, mp.Y[y_in], mp.D, mp.Ch, mp.Cl, mp.Vt, t.Uh, t.Ul,
+                                                         static_cast<__nv_bfloat16*>(t.Y[1 - y_in]), t.ldy, s.m, s.n,
+                                                         Qpart, resid_part, dst, nullptr, nullptr, 0, 0);
   return cudaGetLastError();
 }
 
@@ -712,15 +790,15 @@ cudaError_t tc_launch_finalize(const Shape& s, const TcMaps& mp, const TcBuffers
                                int s_dtype, int64_t lds, void* L, DevState* dst, cudaStream_t st) {
   const size_t es = s_dtype == SFR_F64 ? 8 : 4;
   const bool vec = ((uintptr_t)S % 16 == 0) && ((uintptr_t)L % 16 == 0) && ((size_t)lds * es) % 16 == 0;
-  dim3 grid(cdiv(s.m, TBM), 1);
   auto go = [&](auto zero) -> cudaError_t {
     using TSo = decltype(zero);
     auto kern = sweep_tc_kernel<true, TSo>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kSweepThreads, SWEEP_SMEM, st>>>(mp.M, mp.Y[y_in], mp.D, mp.Ch, mp.Cl, mp.Vt, t.Uh, t.Ul, nullptr,
-                                                  t.ldy, s.m, s.n, (int)((s.n + 63) / 64 * 64), nullptr, nullptr,
-                                                  dst, static_cast<TSo*>(S), static_cast<TSo*>(L), lds, vec ? 1 : 0);
+    kern<<<s.sweep_grid_x, kSweepThreads, SWEEP_SMEM, st>>>(mp.M, mp.Y[y_in], mp.D, mp.Ch, mp.Cl, mp.Vt, t.Uh, t.Ul,
+                                                           nullptr, t.ldy, s.m, s.n, nullptr, nullptr, dst,
+                                                           static_cast<TSo*>(S), static_cast<TSo*>(L), lds,
+                                                           vec ? 1 : 0);
     return cudaGetLastError();
   };
   return s_dtype == SFR_F64 ? go(0.0) : go(0.f);
