@@ -35,7 +35,7 @@ namespace sfr {
 namespace {
 
 constexpr int RPMAX = kMaxRank;
-constexpr int LD = RPMAX + 1;
+constexpr int LD = RPMAX + 4;  // row stride of the r x r arrays: 16-byte aligned float rows
 constexpr int kThreads = 256;
 
 __device__ __forceinline__ bool stopped(const DevState* st) { return *(volatile const int32_t*)&st->done != 0; }
@@ -59,7 +59,7 @@ __device__ void mm(const T* A, const T* B, T* C, int r) {
 // C = op(A) op(B) for float64, rows split across the cluster and broadcast through DSMEM.
 // C must not alias A or B.  On return every CTA holds the full product.
 template <bool TA, bool TB>
-__device__ void mm_dist(const double* A, const double* B, double* C, int r) {
+__device__ void mm_dist(const double* A, const double* B, double* C, int r, double scale = 1.0) {
   cg::cluster_group cl = cg::this_cluster();
   const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int rpc = (r + cs - 1) / cs, i0 = min(r, rank * rpc), i1 = min(r, i0 + rpc);
@@ -81,7 +81,7 @@ __device__ void mm_dist(const double* A, const double* B, double* C, int r) {
       const double b = TB ? B[j * LD + k] : B[k * LD + j];
       acc[0] = fma(a, b, acc[0]);
     }
-    C[i * LD + j] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    C[i * LD + j] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) * scale;
   }
   __syncthreads();
   if (cs > 1) {
@@ -97,12 +97,13 @@ __device__ void mm_dist(const double* A, const double* B, double* C, int r) {
   }
 }
 
-// C = op(A) op(B) in float32 on the leading r x r blocks, 4 x 4 outputs per thread (register
-// blocking keeps the shared-memory traffic at 8 loads per 16 FMAs).  Reads may touch rows and
-// columns beyond r (inside the RPMAX x LD arrays); only outputs inside r x r are written.
+// C = op(A) op(B) in float32 on the leading r x r blocks, 4 x 4 outputs per thread.  Operands
+// move in 16-byte loads, 4 x 4 blocks of A and B per 4 steps of k (8 loads per 64 FMAs); the
+// sum over k runs in order.  Reads may touch rows and columns beyond r (inside the RPMAX x LD
+// arrays); only outputs inside r x r are written.
 template <bool TA, bool TB>
 __device__ void mmf(const float* A, const float* B, float* C, int r) {
-  const int nb = (r + 3) / 4;
+  const int nb = (r + 3) / 4, r4 = r & ~3;
   for (int blk = threadIdx.x; blk < nb * nb; blk += blockDim.x) {
     const int i0 = 4 * (blk / nb), j0 = 4 * (blk % nb);
     float acc[4][4];
@@ -110,18 +111,37 @@ __device__ void mmf(const float* A, const float* B, float* C, int r) {
     for (int x = 0; x < 4; ++x)
 #pragma unroll
       for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
-#pragma unroll 4
-    for (int k = 0; k < r; ++k) {
-      float a[4], b[4];
+    for (int k = 0; k < r4; k += 4) {
+      float a[4][4], b[4][4];  // a[x][q] = op(A)(i0 + x, k + q), b[q][y] = op(B)(k + q, j0 + y)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        a[q] = TA ? A[k * LD + i0 + q] : A[(i0 + q) * LD + k];
-        b[q] = TB ? B[(j0 + q) * LD + k] : B[k * LD + j0 + q];
+        const float4 va = TA ? *reinterpret_cast<const float4*>(A + (k + q) * LD + i0)
+                             : *reinterpret_cast<const float4*>(A + (i0 + q) * LD + k);
+        const float4 vb = TB ? *reinterpret_cast<const float4*>(B + (j0 + q) * LD + k)
+                             : *reinterpret_cast<const float4*>(B + (k + q) * LD + j0);
+        const float fa[4] = {va.x, va.y, va.z, va.w}, fb[4] = {vb.x, vb.y, vb.z, vb.w};
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          if (TA) a[w][q] = fa[w]; else a[q][w] = fa[w];
+          if (TB) b[w][q] = fb[w]; else b[q][w] = fb[w];
+        }
       }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x][q], b[q][y], acc[x][y]);
+    }
+    for (int k = r4; k < r; ++k) {
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+        for (int y = 0; y < 4; ++y) {
+          const float av = TA ? A[k * LD + i0 + x] : A[(i0 + x) * LD + k];
+          const float bv = TB ? B[(j0 + y) * LD + k] : B[k * LD + j0 + y];
+          acc[x][y] = fmaf(av, bv, acc[x][y]);
+        }
     }
 #pragma unroll
     for (int x = 0; x < 4; ++x)
@@ -130,6 +150,24 @@ __device__ void mmf(const float* A, const float* B, float* C, int r) {
         if (i0 + x < r && j0 + y < r) C[(i0 + x) * LD + j0 + y] = acc[x][y];
   }
   __syncthreads();
+}
+
+// dst[i * LD + j] = src[i * rp + j] for i, j < r; for r <= i, j < n the identity's entries
+// (pad_diag on the diagonal, 0 elsewhere).  Every load of a thread is issued before any store.
+template <typename TS, typename TD>
+__device__ __forceinline__ void load_sq(const TS* __restrict__ src, int rp, int r, int n, TD* dst, TD pad_diag) {
+  constexpr int PER = RPMAX * RPMAX / kThreads;
+  TS v[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = threadIdx.x + q * kThreads, i = e / RPMAX, j = e % RPMAX;
+    v[q] = (i < r && j < r) ? src[i * rp + j] : (TS)0;
+  }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = threadIdx.x + q * kThreads, i = e / RPMAX, j = e % RPMAX;
+    if (i < n && j < n) dst[i * LD + j] = (i < r && j < r) ? (TD)v[q] : (i == j ? pad_diag : (TD)0);
+  }
 }
 
 __device__ double block_reduce(double v, double* red, bool take_max) {
@@ -141,8 +179,24 @@ __device__ double block_reduce(double v, double* red, bool take_max) {
   __syncthreads();
   if (l == 0) red[w] = v;
   __syncthreads();
-  double t = take_max ? 0.0 : 0.0;
-  for (int i = 0; i < nw; ++i) t = take_max ? fmax(t, red[i]) : t + red[i];
+  double t = red[0];
+  for (int i = 1; i < nw; ++i) t = take_max ? fmax(t, red[i]) : t + red[i];
+  __syncthreads();
+  return t;
+}
+
+// float version (the sums and maxima it serves steer decisions only)
+__device__ float block_reduce_f(float v, float* red, bool take_max) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = take_max ? fmaxf(v, w) : v + w;
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float t = red[0];
+  for (int i = 1; i < nw; ++i) t = take_max ? fmaxf(t, red[i]) : t + red[i];
   __syncthreads();
   return t;
 }
@@ -156,17 +210,17 @@ __device__ void jacobi_f32(float* A, float* Q, int n2, int max_sweeps, double* r
   const bool pow2 = (np & (np - 1)) == 0;
   const int lg = 31 - __clz(np);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    double off = 0.0, dia = 0.0;
+    float off = 0.f, dia = 0.f;
     for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
       const int i = e / n2, j = e % n2;
-      const double v = (double)A[i * LD + j];
-      if (i == j) dia += v * v; else off += v * v;
+      const float v = A[i * LD + j];
+      if (i == j) dia = fmaf(v, v, dia); else off = fmaf(v, v, off);
     }
-    off = block_reduce(off, red, false);
-    dia = block_reduce(dia, red, false);
-    // off-diagonal mass below (3e-5)^2 of the diagonal: the float64 Newton steps that follow
-    // contract the remaining error by about this factor per step, so stop here
-    if (!(off > 1e-9 * dia)) break;
+    off = block_reduce_f(off, reinterpret_cast<float*>(red), false);
+    dia = block_reduce_f(dia, reinterpret_cast<float*>(red), false);
+    // off-diagonal mass below (1e-3)^2 of the diagonal: each float64 Newton step that follows
+    // contracts the residual by about this factor (the next call refines the basis further)
+    if (!(off > 1e-6 * dia)) break;
     for (int step = 0; step < n2 - 1; ++step) {
       if (threadIdx.x < np) {
         const int k = threadIdx.x;
@@ -187,28 +241,76 @@ __device__ void jacobi_f32(float* A, float* Q, int n2, int max_sweeps, double* r
       }
       __syncthreads();
       // A <- J^T A J in one phase: the pairs partition the indices, so each 2 x 2 block
-      // (rows {p1, q1}, columns {p2, q2}) is touched by exactly one row and one column rotation
-      for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
-        const int k1 = pow2 ? (e >> lg) : e / np, k2 = pow2 ? (e & (np - 1)) : e % np;
-        const float c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
-        if (s1 == 0.f && s2 == 0.f) continue;
-        const int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
-        const float a = A[p1 * LD + p2], b = A[p1 * LD + q2], c = A[q1 * LD + p2], d = A[q1 * LD + q2];
-        const float ra = c1 * a - s1 * c, rb = c1 * b - s1 * d, rc = s1 * a + c1 * c, rd = s1 * b + c1 * d;
-        A[p1 * LD + p2] = c2 * ra - s2 * rb;
-        A[p1 * LD + q2] = s2 * ra + c2 * rb;
-        A[q1 * LD + p2] = c2 * rc - s2 * rd;
-        A[q1 * LD + q2] = s2 * rc + c2 * rd;
+      // (rows {p1, q1}, columns {p2, q2}) is touched by exactly one row and one column rotation.
+      // Each thread takes up to four blocks, loads all of them, then rotates and stores.
+      {
+        constexpr int MB = (RPMAX / 2) * (RPMAX / 2) / kThreads;
+        float v[MB][4];
+        int pos[MB][4];
+        float rc[MB][4];
+        bool act[MB];
+        // with 32 pairs a thread's column pair k2 is its lane for every u: load it once
+        const bool lanepair = np == 32;
+        const int kl = threadIdx.x & 31;
+        const float cl = cs[kl], sl = sn[kl];
+        const int pl = pp[kl], ql = qq[kl];
+#pragma unroll
+        for (int u = 0; u < MB; ++u) {
+          const int e = threadIdx.x + u * kThreads;
+          act[u] = e < np * np;
+          if (!act[u]) continue;
+          const int k1 = pow2 ? (e >> lg) : e / np, k2 = pow2 ? (e & (np - 1)) : e % np;
+          rc[u][0] = cs[k1]; rc[u][1] = sn[k1];
+          rc[u][2] = lanepair ? cl : cs[k2];
+          rc[u][3] = lanepair ? sl : sn[k2];
+          act[u] = !(rc[u][1] == 0.f && rc[u][3] == 0.f);
+          const int p1 = pp[k1], q1 = qq[k1], p2 = lanepair ? pl : pp[k2], q2 = lanepair ? ql : qq[k2];
+          pos[u][0] = p1 * LD + p2; pos[u][1] = p1 * LD + q2; pos[u][2] = q1 * LD + p2; pos[u][3] = q1 * LD + q2;
+#pragma unroll
+          for (int w = 0; w < 4; ++w) v[u][w] = A[pos[u][w]];
+        }
+#pragma unroll
+        for (int u = 0; u < MB; ++u) {
+          if (!act[u]) continue;
+          const float c1 = rc[u][0], s1 = rc[u][1], c2 = rc[u][2], s2 = rc[u][3];
+          const float ra = c1 * v[u][0] - s1 * v[u][2], rb = c1 * v[u][1] - s1 * v[u][3];
+          const float rcc = s1 * v[u][0] + c1 * v[u][2], rd = s1 * v[u][1] + c1 * v[u][3];
+          A[pos[u][0]] = c2 * ra - s2 * rb;
+          A[pos[u][1]] = s2 * ra + c2 * rb;
+          A[pos[u][2]] = c2 * rcc - s2 * rd;
+          A[pos[u][3]] = s2 * rcc + c2 * rd;
+        }
       }
-      // Q <- Q J
-      for (int e = threadIdx.x; e < np * n2; e += blockDim.x) {
-        const int k = pow2 ? (e & (np - 1)) : e % np, j = pow2 ? (e >> lg) : e / np;
-        const float c = cs[k], s = sn[k];
-        if (s == 0.f) continue;
-        const int p = pp[k], q = qq[k];
-        const float xp = Q[j * LD + p], xq = Q[j * LD + q];
-        Q[j * LD + p] = c * xp - s * xq;
-        Q[j * LD + q] = s * xp + c * xq;
+      // Q <- Q J, up to eight (row, pair) items per thread, loads first
+      {
+        constexpr int MQ = (RPMAX / 2) * RPMAX / kThreads;
+        float x2[MQ][2], cq[MQ][2];
+        int qp[MQ][2];
+        bool act[MQ];
+        const bool lanepair = np == 32;
+        const int kl = threadIdx.x & 31;
+        const float cl = cs[kl], sl = sn[kl];
+        const int pl = pp[kl], ql = qq[kl];
+#pragma unroll
+        for (int u = 0; u < MQ; ++u) {
+          const int e = threadIdx.x + u * kThreads;
+          act[u] = e < np * n2;
+          if (!act[u]) continue;
+          const int k = pow2 ? (e & (np - 1)) : e % np, j = pow2 ? (e >> lg) : e / np;
+          cq[u][0] = lanepair ? cl : cs[k];
+          cq[u][1] = lanepair ? sl : sn[k];
+          act[u] = cq[u][1] != 0.f;
+          qp[u][0] = j * LD + (lanepair ? pl : pp[k]);
+          qp[u][1] = j * LD + (lanepair ? ql : qq[k]);
+          x2[u][0] = Q[qp[u][0]]; x2[u][1] = Q[qp[u][1]];
+        }
+#pragma unroll
+        for (int u = 0; u < MQ; ++u) {
+          if (!act[u]) continue;
+          const float c = cq[u][0], sv = cq[u][1];
+          Q[qp[u][0]] = c * x2[u][0] - sv * x2[u][1];
+          Q[qp[u][1]] = sv * x2[u][0] + c * x2[u][1];
+        }
       }
       __syncthreads();
     }
@@ -234,7 +336,7 @@ __device__ bool refine_basis(const float* Kf, float* Q, float* A, float* F1, flo
     F1[p * LD + q] = v;
     big = fmaxf(big, fabsf(v));
   }
-  big = (float)block_reduce((double)big, red, true);
+  big = block_reduce_f(big, reinterpret_cast<float*>(red), true);
   if (!(big <= 0.25f)) return false;
   mmf<false, false>(Q, F1, F2, r);                  // Q E
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
@@ -256,16 +358,17 @@ __device__ bool refine_basis(const float* Kf, float* Q, float* A, float* F1, flo
   return true;
 }
 
-__device__ bool near_diagonal(const float* A, int r, double* red) {
-  double off = 0.0, dia = 0.0;
+// Off-diagonal mass of A below tol^2 of its diagonal mass (Frobenius), float32 sums.
+__device__ bool near_diagonal(const float* A, int r, double* red, double tol2 = 1e-9) {
+  float off = 0.f, dia = 0.f;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
-    const double v = (double)A[i * LD + j];
-    if (i == j) dia += v * v; else off += v * v;
+    const float v = A[i * LD + j];
+    if (i == j) dia = fmaf(v, v, dia); else off = fmaf(v, v, off);
   }
-  off = block_reduce(off, red, false);
-  dia = block_reduce(dia, red, false);
-  return !(off > 1e-9 * dia);
+  const float o = block_reduce_f(off, reinterpret_cast<float*>(red), false);
+  const float d = block_reduce_f(dia, reinterpret_cast<float*>(red), false);
+  return !((double)o > tol2 * (double)d);
 }
 
 struct RxrSmem {
@@ -276,6 +379,7 @@ struct RxrSmem {
   double T2[RPMAX * LD];   // scratch
   float Af[RPMAX * LD];    // Jacobi matrix / float scratch
   float Qf[RPMAX * LD];    // approximate eigenbasis
+  float QT[RPMAX * LD];    // its transpose (keeps every float32 product in the conflict-free forms)
   double lam[RPMAX];
   double sq[RPMAX];
   double red[32];
@@ -284,15 +388,6 @@ struct RxrSmem {
   double scale;
   int bad;
 };
-
-// dst = the summed r x r Gram G (rp x rp float64 in global memory; every CTA reads all of it).
-__device__ void load_gram(const double* __restrict__ G, int rp, int r, double* dst) {
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    const int i = e / r, j = e % r;
-    dst[i * LD + j] = G[i * rp + j];
-  }
-  __syncthreads();
-}
 
 __device__ void fail(DevState* st, int code) {
   if (threadIdx.x == 0 && cg::this_cluster().block_rank() == 0) { st->status = code; st->done = 1; }
@@ -320,8 +415,8 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
   const int rpsq = rp * rp;
   const bool writer = cg::this_cluster().block_rank() == 0;
   // 1. Gram of the thin matrix and B; K = B G B (symmetrised) scaled by s = trace / r
-  load_gram(G, rp, r, S.T2);
-  for (int e = tid; e < r * r; e += blockDim.x) S.B[(e / r) * LD + e % r] = Bg[(e / r) * rp + e % r];
+  load_sq(G, rp, r, r, S.T2, 0.0);
+  load_sq(Bg, rp, r, r, S.B, 0.0);
   __syncthreads();
   mm_dist<false, false>(S.T2, S.B, S.T1, r);
   mm_dist<false, false>(S.B, S.T1, S.Z, r);
@@ -331,9 +426,9 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
   const double scale = tr / r;
   if (!(scale > 0.0) || !(scale < 1e300)) { fail(st, SFR_E_NAN); return; }
   const double inv_s = 1.0 / scale;
-  for (int e = tid; e < r * r; e += blockDim.x) {
+  for (int e = tid; e < r * r; e += blockDim.x) {  // B (G B) is symmetric to float64 rounding
     const int i = e / r, j = e % r;
-    const double v = 0.5 * (S.Z[i * LD + j] + S.Z[j * LD + i]) * inv_s;
+    const double v = S.Z[i * LD + j] * inv_s;
     S.K[i * LD + j] = v;
     Kf[i * LD + j] = (float)v;
   }
@@ -341,66 +436,67 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
   const int n2 = (r + 1) & ~1;
   for (int e = tid; e < n2 * n2; e += blockDim.x) {
     const int i = e / n2, j = e % n2;
-    const bool in = i < r && j < r;
-    if (!in) Kf[i * LD + j] = 0.f;
-    S.Qf[i * LD + j] = in ? Qeig[i * rp + j] : (i == j ? 1.f : 0.f);
+    if (i >= r || j >= r) Kf[i * LD + j] = 0.f;
   }
+  load_sq(Qeig, rp, r, n2, S.Qf, 1.f);
   __syncthreads();
   mmf<false, false>(Kf, S.Qf, F2, n2);
   mmf<true, false>(S.Qf, F2, S.Af, n2);
   // the basis of the previous call is usually close: refine it to first order (cheap), and fall
   // back to Jacobi sweeps only when that does not converge
   bool diag = near_diagonal(S.Af, n2, S.red);
+  const bool kept = diag;  // the stored basis (orthonormal to float32 rounding) is used as it is
   for (int round = 0; round < 3 && !diag; ++round) {
     if (!refine_basis(Kf, S.Qf, S.Af, F1, F2, n2, S.red)) break;
     diag = near_diagonal(S.Af, n2, S.red);
   }
   if (!diag) jacobi_f32(S.Af, S.Qf, n2, 10, S.red, S.cs, S.sn, S.pp, S.qq);
-  // re-orthonormalise the float basis: Q <- Q (3I - Q^T Q) / 2
-  mmf<true, false>(S.Qf, S.Qf, F1, r);
-  for (int e = tid; e < r * r; e += blockDim.x) {
-    const int i = e / r, j = e % r;
-    F1[i * LD + j] = 0.5f * ((i == j ? 3.f : 0.f) - F1[i * LD + j]);
-  }
-  __syncthreads();
-  mmf<false, false>(S.Qf, F1, F2, r);
-  for (int e = tid; e < r * r; e += blockDim.x) S.Qf[(e / r) * LD + e % r] = F2[(e / r) * LD + e % r];
-  __syncthreads();
-  // 3. eigenvalue estimates lambda_p = q_p^T K q_p / q_p^T q_p in float32; those far below the
-  //    largest are recomputed in float64 for the rank test (Eq. 9 needs rank r)
-  mmf<false, false>(Kf, S.Qf, F1, r);
-  for (int p = tid; p < r; p += blockDim.x) {
-    float num = 0.f, den = 0.f;
-    for (int i = 0; i < r; ++i) {
-      num = fmaf(S.Qf[i * LD + p], F1[i * LD + p], num);
-      den = fmaf(S.Qf[i * LD + p], S.Qf[i * LD + p], den);
+  if (!kept) {
+    // re-orthonormalise the float basis: Q <- Q (3I - Q^T Q) / 2
+    mmf<true, false>(S.Qf, S.Qf, F1, r);
+    for (int e = tid; e < r * r; e += blockDim.x) {
+      const int i = e / r, j = e % r;
+      F1[i * LD + j] = 0.5f * ((i == j ? 3.f : 0.f) - F1[i * LD + j]);
     }
-    lamf[p] = num / den;
+    __syncthreads();
+    mmf<false, false>(S.Qf, F1, F2, r);
+    for (int e = tid; e < r * r; e += blockDim.x) S.Qf[(e / r) * LD + e % r] = F2[(e / r) * LD + e % r];
+    __syncthreads();
   }
+  for (int e = tid; e < r * r; e += blockDim.x) S.QT[(e % r) * LD + e / r] = S.Qf[(e / r) * LD + e % r];
+  // 3. eigenvalue estimates: the diagonal of A = Q^T K Q (Rayleigh quotients of the basis, to
+  //    float32 rounding); those far below the largest are recomputed in float64 for the rank
+  //    test (Eq. 9 needs rank r)
+  for (int p = tid; p < r; p += blockDim.x) lamf[p] = S.Af[p * LD + p];
   __syncthreads();
+  float* redf = reinterpret_cast<float*>(S.red);
   float hi = 0.f;
-  for (int p = 0; p < r; ++p) hi = fmaxf(hi, lamf[p]);
-  for (int p = tid; p < r; p += blockDim.x) {
-    if (lamf[p] < 1e-3f * hi) {
-      double num = 0.0, den = 0.0;
-      for (int i = 0; i < r; ++i) {
-        double kq = 0.0;
-        for (int k = 0; k < r; ++k) kq = fma(S.K[i * LD + k], (double)S.Qf[k * LD + p], kq);
-        num = fma((double)S.Qf[i * LD + p], kq, num);
-        den = fma((double)S.Qf[i * LD + p], (double)S.Qf[i * LD + p], den);
-      }
-      lamf[p] = (float)(num / den);
-    }
-  }
-  __syncthreads();
-  bool bad = false;
-  float lo = hi;
+  for (int p = tid; p < r; p += blockDim.x) hi = fmaxf(hi, lamf[p]);
+  hi = block_reduce_f(hi, redf, true);
+  // the float32 estimates carry errors near 1e-7 hi: below 1e-6 hi, recompute q_p^T K q_p in
+  // float64 (every thread takes one row of K q_p, then a block sum)
   for (int p = 0; p < r; ++p) {
-    lo = fminf(lo, lamf[p]);
-    bad |= !(lamf[p] > 1e-14f * hi);
+    if (!(lamf[p] < 1e-6f * hi)) continue;  // uniform: lamf is in shared memory
+    double num = 0.0, den = 0.0;
+    if (tid < r) {
+      double kq = 0.0;
+      for (int k = 0; k < r; ++k) kq = fma(S.K[tid * LD + k], (double)S.Qf[k * LD + p], kq);
+      const double qi = (double)S.Qf[tid * LD + p];
+      num = qi * kq;
+      den = qi * qi;
+    }
+    num = block_reduce(num, S.red, false);
+    den = block_reduce(den, S.red, false);
+    if (tid == 0) lamf[p] = (float)(num / den);
+    __syncthreads();
   }
-  bad |= !(hi > 0.f);
-  __syncthreads();
+  float nlo = -hi, badf = 0.f;  // max of -lambda and of the rank-failure flag
+  for (int p = tid; p < r; p += blockDim.x) {
+    nlo = fmaxf(nlo, -lamf[p]);
+    if (!(lamf[p] > 1e-14f * hi)) badf = 1.f;
+  }
+  const float lo = -block_reduce_f(nlo, redf, true);
+  const bool bad = block_reduce_f(badf, redf, true) > 0.f || !(hi > 0.f);
   if (writer && tid == 0) {
     if (v_side) st->lam_min_v = (double)lo * scale; else st->lam_min_u = (double)lo * scale;
   }
@@ -417,10 +513,10 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
     F2[i * LD + j] = S.Qf[i * LD + j] * isqf[j];
   }
   __syncthreads();
-  mmf<false, true>(F2, S.Qf, F1, r);
+  mmf<false, false>(F2, S.QT, F1, r);
   for (int e = tid; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
-    S.Z[i * LD + j] = 0.5 * ((double)F1[i * LD + j] + (double)F1[j * LD + i]);
+    S.Z[i * LD + j] = (double)(0.5f * (F1[i * LD + j] + F1[j * LD + i]));
   }
   __syncthreads();
   // 5. Newton steps on Z K Z = I (residual in float64, correction in float32)
@@ -428,27 +524,32 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
     mm_dist<false, false>(S.K, S.Z, S.T1, r);
     mm_dist<false, false>(S.Z, S.T1, S.T2, r);
     float rmax = 0.f;
-    for (int e = tid; e < r * r; e += blockDim.x) {
+    for (int e = tid; e < r * r; e += blockDim.x) {  // I - Z K Z, rounded to float32
       const int i = e / r, j = e % r;
-      const float v = (float)((i == j ? 1.0 : 0.0) - 0.5 * (S.T2[i * LD + j] + S.T2[j * LD + i]));
+      const float v = (float)((i == j ? 1.0 : 0.0) - S.T2[i * LD + j]);
       F1[i * LD + j] = v;
       rmax = fmaxf(rmax, fabsf(v));
     }
-    const double rm = block_reduce((double)rmax, S.red, true);
+    const float rm = block_reduce_f(rmax, redf, true);
     if (!(rm == rm)) { fail(st, SFR_E_NAN); return; }
-    if (rm < 4e-16 * r) break;
-    mmf<false, false>(F1, S.Qf, F2, r);     // R Q
-    mmf<true, false>(S.Qf, F2, S.Af, r);    // Q^T R Q
+    if (rm < 4e-16f * r) break;
+    for (int e = tid; e < r * r; e += blockDim.x) {  // R = Sym(I - Z K Z)
+      const int i = e / r, j = e % r;
+      F2[i * LD + j] = 0.5f * (F1[i * LD + j] + F1[j * LD + i]);
+    }
+    __syncthreads();
+    mmf<false, false>(F2, S.Qf, F1, r);     // R Q
+    mmf<true, false>(S.Qf, F1, S.Af, r);    // Q^T R Q
     for (int e = tid; e < r * r; e += blockDim.x) {
       const int p = e / r, q = e % r;
       S.Af[p * LD + q] = S.Af[p * LD + q] / (sqf[p] + sqf[q]);
     }
     __syncthreads();
-    mmf<false, true>(S.Af, S.Qf, F2, r);    // Dt Q^T
+    mmf<false, false>(S.Af, S.QT, F2, r);   // Dt Q^T
     mmf<false, false>(S.Qf, F2, F1, r);     // Q Dt Q^T
     for (int e = tid; e < r * r; e += blockDim.x) {
       const int i = e / r, j = e % r;
-      S.Z[i * LD + j] += 0.5 * ((double)F1[i * LD + j] + (double)F1[j * LD + i]);
+      S.Z[i * LD + j] += (double)(0.5f * (F1[i * LD + j] + F1[j * LD + i]));
     }
     __syncthreads();
     // The step just taken leaves a residual of about (eigenbasis error + float32 rounding of the
@@ -457,10 +558,7 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
     if (rm < (mixed ? 3e-6 : 1e-7)) break;
   }
   // 6. (B G B)^{-1/2} = Z / sqrt(s); T = B (B G B)^{-1/2}
-  const double zs = 1.0 / sqrt(scale);
-  for (int e = tid; e < r * r; e += blockDim.x) S.Z[(e / r) * LD + e % r] *= zs;
-  __syncthreads();
-  mm_dist<false, false>(S.B, S.Z, S.T1, r);
+  mm_dist<false, false>(S.B, S.Z, S.T1, r, 1.0 / sqrt(scale));
   if (writer)
     for (int e = tid; e < rpsq; e += blockDim.x) {
       const int i = e / rp, j = e % rp;
@@ -470,7 +568,8 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
     }
   if (!v_side) return;
   // 7. B_bar = Sym(G_W T_V) (Eq. 10 with W = X^T U_bar), T_C = T_V B_bar
-  load_gram(G, rp, r, S.K);
+  load_sq(G, rp, r, r, S.K, 0.0);
+  __syncthreads();
   mm_dist<false, false>(S.K, S.T1, S.T2, r);
   for (int e = tid; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
