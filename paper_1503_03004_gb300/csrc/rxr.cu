@@ -36,7 +36,7 @@ namespace {
 
 constexpr int RPMAX = kMaxRank;
 constexpr int LD = RPMAX + 4;  // row stride of the r x r arrays: 16-byte aligned float rows
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 
 __device__ __forceinline__ bool stopped(const DevState* st) { return *(volatile const int32_t*)&st->done != 0; }
 
@@ -86,12 +86,14 @@ __device__ void mm_dist(const double* A, const double* B, double* C, int r, doub
   __syncthreads();
   if (cs > 1) {
     cl.sync();  // every CTA is past its earlier reads of C
-    for (int q = 1; q < cs; ++q) {
+    // push this CTA's rows to the other CTAs in 16-byte pieces (column pairs; with r odd the
+    // last pair carries column r, which no product reads)
+    const int np2 = (r + 1) / 2, per = (i1 - i0) * np2;
+    for (int e = threadIdx.x; e < (cs - 1) * per; e += blockDim.x) {
+      const int q = 1 + e / per, w = e % per;
+      const int i = i0 + w / np2, j = 2 * (w % np2);
       double* Cq = cl.map_shared_rank(C, (rank + q) % cs);
-      for (int e = threadIdx.x; e < nloc; e += blockDim.x) {
-        const int i = i0 + e / r, j = e % r;
-        Cq[i * LD + j] = C[i * LD + j];
-      }
+      *reinterpret_cast<double2*>(Cq + i * LD + j) = *reinterpret_cast<const double2*>(C + i * LD + j);
     }
     cl.sync();  // all rows have arrived everywhere
   }
@@ -230,10 +232,10 @@ __device__ void jacobi_f32(float* A, float* Q, int n2, int max_sweeps, double* r
         const float apq = A[p * LD + q], app = A[p * LD + p], aqq = A[q * LD + q];
         float c = 1.f, s = 0.f;
         if (fabsf(apq) > 1e-9f * sqrtf(fabsf(app * aqq)) && apq != 0.f) {
-          const float th = (aqq - app) / (2.f * apq);
+          const float th = __fdividef(aqq - app, 2.f * apq);
           float t;
-          if (fabsf(th) > 1e15f) t = 0.5f / th;
-          else t = copysignf(1.f, th) / (fabsf(th) + sqrtf(1.f + th * th));
+          if (fabsf(th) > 1e15f) t = __fdividef(0.5f, th);
+          else t = copysignf(1.f, th) * __frcp_rn(fabsf(th) + sqrtf(1.f + th * th));
           c = rsqrtf(1.f + t * t);
           s = t * c;
         }
@@ -331,7 +333,7 @@ __device__ bool refine_basis(const float* Kf, float* Q, float* A, float* F1, flo
     if (p != q) {
       const float gap = A[q * LD + q] - A[p * LD + p];
       const float scl = fmaxf(fabsf(A[p * LD + p]), fabsf(A[q * LD + q]));
-      if (fabsf(gap) > 1e-5f * scl) v = A[p * LD + q] / gap;
+      if (fabsf(gap) > 1e-5f * scl) v = __fdividef(A[p * LD + q], gap);  // first-order term: 2 ulp is ample
     }
     F1[p * LD + q] = v;
     big = fmaxf(big, fabsf(v));
@@ -420,9 +422,15 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
   __syncthreads();
   mm_dist<false, false>(S.T2, S.B, S.T1, r);
   mm_dist<false, false>(S.B, S.T1, S.Z, r);
-  double tr = 0.0;
-  for (int i = tid; i < r; i += blockDim.x) tr += S.Z[i * LD + i];
-  tr = block_reduce(tr, S.red, false);
+  double tr = 0.0;  // trace of B G B: float64 sums within the first two warps (r <= 64)
+  if (tid < 64) {
+    tr = tid < r ? S.Z[tid * LD + tid] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if ((tid & 31) == 0) S.red[tid >> 5] = tr;
+  }
+  __syncthreads();
+  tr = S.red[0] + S.red[1];
+  __syncthreads();
   const double scale = tr / r;
   if (!(scale > 0.0) || !(scale < 1e300)) { fail(st, SFR_E_NAN); return; }
   const double inv_s = 1.0 / scale;
@@ -444,14 +452,17 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
   mmf<true, false>(S.Qf, F2, S.Af, n2);
   // the basis of the previous call is usually close: refine it to first order (cheap), and fall
   // back to Jacobi sweeps only when that does not converge
-  bool diag = near_diagonal(S.Af, n2, S.red);
-  const bool kept = diag;  // the stored basis (orthonormal to float32 rounding) is used as it is
-  for (int round = 0; round < 3 && !diag; ++round) {
+  // at least one refinement round: a basis accurate to float32 rounding lets one Newton step
+  // (two float64 products) replace two
+  bool diag = false;
+  for (int round = 0; round < 3; ++round) {
     if (!refine_basis(Kf, S.Qf, S.Af, F1, F2, n2, S.red)) break;
     diag = near_diagonal(S.Af, n2, S.red);
+    if (diag) break;
   }
-  if (!diag) jacobi_f32(S.Af, S.Qf, n2, 10, S.red, S.cs, S.sn, S.pp, S.qq);
-  if (!kept) {
+  const bool rotated = !diag;
+  if (rotated) jacobi_f32(S.Af, S.Qf, n2, 10, S.red, S.cs, S.sn, S.pp, S.qq);
+  if (rotated) {
     // re-orthonormalise the float basis: Q <- Q (3I - Q^T Q) / 2
     mmf<true, false>(S.Qf, S.Qf, F1, r);
     for (int e = tid; e < r * r; e += blockDim.x) {
@@ -475,7 +486,11 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
   hi = block_reduce_f(hi, redf, true);
   // the float32 estimates carry errors near 1e-7 hi: below 1e-6 hi, recompute q_p^T K q_p in
   // float64 (every thread takes one row of K q_p, then a block sum)
-  for (int p = 0; p < r; ++p) {
+  float anysmall = 0.f;
+  for (int p = tid; p < r; p += blockDim.x)
+    if (lamf[p] < 1e-6f * hi) anysmall = 1.f;
+  anysmall = block_reduce_f(anysmall, redf, true);
+  for (int p = 0; anysmall > 0.f && p < r; ++p) {
     if (!(lamf[p] < 1e-6f * hi)) continue;  // uniform: lamf is in shared memory
     double num = 0.0, den = 0.0;
     if (tid < r) {
@@ -542,7 +557,7 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
     mmf<true, false>(S.Qf, F1, S.Af, r);    // Q^T R Q
     for (int e = tid; e < r * r; e += blockDim.x) {
       const int p = e / r, q = e % r;
-      S.Af[p * LD + q] = S.Af[p * LD + q] / (sqf[p] + sqf[q]);
+      S.Af[p * LD + q] = __fdividef(S.Af[p * LD + q], sqf[p] + sqf[q]);
     }
     __syncthreads();
     mmf<false, false>(S.Af, S.QT, F2, r);   // Dt Q^T
