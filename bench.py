@@ -33,9 +33,28 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(workload="square16384_r64_bf16_mixed", m=16384, n=16384, r=64, storage="bf16", precision="mixed",
                 outlier_fraction=0.05, outlier_range=[-50, 50], mu0=0.05, rho=1.5, tol=1e-9, max_iter=300,
-                l2="inputs larger than L2 (M 512 MB, multipliers 2 x 1 GB); no flush")
+                l2="inputs larger than L2 (M 512 MB, multipliers 2 x 512 MB, Delta 512 MB); no flush")
 SAMPLE = dict(m=2048, n=2048)          # CPU oracle sample of the same recipe (about 10 s of CPU work)
 FALLBACK_HBM_GBS = 6800.0
+
+
+def sweep_traffic(m: int, n: int):
+    """DRAM bytes of one sweep launch from the committed ncu summary, scaled by m n.
+
+    The summary records bytes per element and the hash of the kernel source it was measured
+    on; if the source has changed since, the figure no longer applies and None is returned.
+    """
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "sweep_tc_square8192_r64_bf16.md")) as f:
+            kv = dict(line.strip().split(": ", 1) for line in f if line.startswith("    ") and ": " in line
+                      and line.strip().split(": ", 1)[0] in ("traffic_bytes_per_element", "source", "source_sha256"))
+        with open(os.path.join(ROOT, kv["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != kv["source_sha256"]:
+                return None
+        return float(kv["traffic_bytes_per_element"]) * m * n
+    except Exception:
+        return None
 
 
 def peaks():
@@ -188,7 +207,9 @@ def main():
                     help="square size of the same recipe (smaller sizes are for profiler captures)")
     args = ap.parse_args()
     if args.m != WORKLOAD["m"]:
-        WORKLOAD.update(m=args.m, n=args.m, workload=f"square{args.m}_r64_bf16_mixed")
+        mb = args.m * args.m * 2 // (1 << 20)
+        WORKLOAD.update(m=args.m, n=args.m, workload=f"square{args.m}_r64_bf16_mixed",
+                        l2=f"M {mb} MB, multipliers 2 x {mb} MB, Delta {mb} MB; no flush")
     if args.impl == "reference":
         return run_reference(args)
 
@@ -269,7 +290,7 @@ def main():
         avg_ms = sw["total_ms"] / sw["timed"]
         achieved = alg_bytes / (avg_ms / 1000.0) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": "fused sweep", "bytes_per_launch": alg_bytes,
+                    "traffic": sweep_traffic(m, n), "kernel": "fused sweep", "bytes_per_launch": alg_bytes,
                     "bytes_per_element": alg_bytes / (m * n), "avg_launch_ms": avg_ms, "timed_launches": sw["timed"],
                     "peak_source": peak_kind + " hbm_gbs",
                     "wpass_avg_ms": stats[B.STAT_WPASS]["total_ms"] / max(1, stats[B.STAT_WPASS]["timed"]),
