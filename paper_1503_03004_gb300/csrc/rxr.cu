@@ -223,6 +223,70 @@ __device__ void jacobi_f32(float* A, float* Q, int n2, int max_sweeps, double* r
     // off-diagonal mass below (1e-3)^2 of the diagonal: each float64 Newton step that follows
     // contracts the residual by about this factor (the next call refines the basis further)
     if (!(off > 1e-6 * dia)) break;
+    if (n2 == 64 && blockDim.x == kThreads) {
+      // 32 pairs: every warp computes all 32 rotations itself (lane k: pair k) and takes the
+      // ones it needs by shuffles, so a step needs a single barrier; a thread rotates the two
+      // 2 x 2 blocks (pair w + 16u, pair lane) of A and the four (row w + 16u v, pair lane)
+      // entries pairs of Q, all loads first
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      constexpr int NW = kThreads / 32;
+      for (int step = 0; step < 63; ++step) {
+        const int p = lane == 0 ? 63 : (step + lane) % 63, q = lane == 0 ? step : (step - lane + 63) % 63;
+        const float apq = A[p * LD + q], app = A[p * LD + p], aqq = A[q * LD + q];
+        float c = 1.f, sn_ = 0.f;
+        if (fabsf(apq) > 1e-9f * sqrtf(fabsf(app * aqq)) && apq != 0.f) {
+          const float th = __fdividef(aqq - app, 2.f * apq);
+          const float t = fabsf(th) > 1e15f ? __fdividef(0.5f, th)
+                                           : copysignf(1.f, th) * __frcp_rn(fabsf(th) + sqrtf(1.f + th * th));
+          c = rsqrtf(1.f + t * t);
+          sn_ = t * c;
+        }
+        float v[2][4], x[4][2];
+        int k1p[2], k1q[2];
+        float c1[2], s1[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int k1 = warp + NW * u;
+          c1[u] = __shfl_sync(0xffffffffu, c, k1);
+          s1[u] = __shfl_sync(0xffffffffu, sn_, k1);
+          k1p[u] = __shfl_sync(0xffffffffu, p, k1);
+          k1q[u] = __shfl_sync(0xffffffffu, q, k1);
+        }
+        __syncthreads();  // every warp has read the pivots of this step
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          v[u][0] = A[k1p[u] * LD + p]; v[u][1] = A[k1p[u] * LD + q];
+          v[u][2] = A[k1q[u] * LD + p]; v[u][3] = A[k1q[u] * LD + q];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = warp + NW * u;
+          x[u][0] = Q[j * LD + p];
+          x[u][1] = Q[j * LD + q];
+        }
+        if (sn_ != 0.f || s1[0] != 0.f || s1[1] != 0.f) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const float ra = c1[u] * v[u][0] - s1[u] * v[u][2], rb = c1[u] * v[u][1] - s1[u] * v[u][3];
+            const float rc = s1[u] * v[u][0] + c1[u] * v[u][2], rd = s1[u] * v[u][1] + c1[u] * v[u][3];
+            A[k1p[u] * LD + p] = c * ra - sn_ * rb;
+            A[k1p[u] * LD + q] = sn_ * ra + c * rb;
+            A[k1q[u] * LD + p] = c * rc - sn_ * rd;
+            A[k1q[u] * LD + q] = sn_ * rc + c * rd;
+          }
+        }
+        if (sn_ != 0.f) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = warp + NW * u;
+            Q[j * LD + p] = c * x[u][0] - sn_ * x[u][1];
+            Q[j * LD + q] = sn_ * x[u][0] + c * x[u][1];
+          }
+        }
+        __syncthreads();
+      }
+      continue;
+    }
     for (int step = 0; step < n2 - 1; ++step) {
       if (threadIdx.x < np) {
         const int k = threadIdx.x;
