@@ -30,10 +30,11 @@ using namespace tc;
 constexpr int TBM = 128, TBN = 64, TR = 64;
 
 // shared memory map of the sweep kernel (offsets from a 1024-byte aligned base)
-constexpr int NSTAGE = 3;
-constexpr uint32_t OFF_C = 0;           // C tiles, 2 buffers x 32 KB: hi (2 K-atoms x 64 rows x 128 B) then lo
+constexpr int NSTAGE = 2;
+constexpr int NCB = 2;  // C tile buffers
+constexpr uint32_t OFF_C = 0;           // C tiles, NCB buffers x 32 KB: hi (2 K-atoms x 64 rows x 128 B) then lo
 constexpr uint32_t C_BUF = 32768;
-constexpr uint32_t OFF_ST = 65536;      // input stages, 3 x 32 KB: M tile (128 x 64 bf16), Y tile; each epilogue
+constexpr uint32_t OFF_ST = NCB * 32768;      // input stages, 3 x 32 KB: M tile (128 x 64 bf16), Y tile; each epilogue
 constexpr uint32_t ST_BYTES = 32768;    // warp releases a stage as soon as it has its M and Y values in registers
 constexpr uint32_t ST_Y = 16384;
 constexpr int NVT = 4;                  // V^T tiles (64 x 64 bf16), a ring of 4: held until Delta V_bar is done
@@ -42,7 +43,8 @@ constexpr uint32_t VT_BYTES = 8192;
 constexpr uint32_t OFF_DA = OFF_VT + NVT * VT_BYTES;  // Delta tiles, 2 x 16 KB: A operand of Delta V and
                                                       // TMA store source (tile t uses buffer t % 2)
 constexpr uint32_t DA_BYTES = 16384;
-constexpr uint32_t OFF_BAR = OFF_DA + 2 * DA_BYTES;
+constexpr uint32_t OFF_YO = OFF_DA + 2 * DA_BYTES;    // Y_{k+1} tiles, 2 x 16 KB: TMA store sources
+constexpr uint32_t OFF_BAR = OFF_YO + 2 * DA_BYTES;
 constexpr uint32_t SWEEP_SMEM = OFF_BAR + 512 + 1024;
 static_assert(OFF_BAR % 1024 == 0, "alignment");
 static_assert(SWEEP_SMEM <= 232448, "shared memory per CTA");
@@ -53,7 +55,7 @@ constexpr uint32_t TM_L = 0, TM_Q = 128, TM_U = 256, TM_COLS = 512;
 struct SweepBars {
   uint64_t stage_full[NSTAGE], stage_empty[NSTAGE];
   uint64_t vt_full[NVT], vt_empty[NVT];
-  uint64_t c_full[2], c_empty[2];
+  uint64_t c_full[NCB], c_empty[NCB];
   uint64_t l_full[2], l_empty[2];
   uint64_t d_full[2], d_empty[2];
   uint64_t q_full;
@@ -163,22 +165,21 @@ static_assert(kEpiCols % 16 == 0, "TMEM loads of 16 columns");
 // warp 16: TMA producer of M, Y and V^T; warp 17: TMEM owner and MMA issuer; warp 18: TMA
 // producer of the C tiles.  U_hi / U_lo (the fixed A operand of the L
 // products) live in tensor memory; M, Y and V^T tiles stream through three stages; C tiles
-// are double buffered; Y_{k+1} goes to global memory straight from registers (each thread
-// writes 64 contiguous bytes of its row); Delta tiles are double buffered in shared memory,
-// where they serve as the A operand of Delta V_bar and as the source of a TMA store.
+// are double buffered; Y_{k+1} and Delta tiles are double buffered in shared memory and leave
+// through TMA stores (the Delta tile is also the A operand of Delta V_bar).
 // FINAL: the output pass after the last iteration instead (Algorithm 1 returns L_k, S_k):
 // S = P_ST_{1/mu}(M - L + Y_k / mu) with the last iteration's mu, Y_k and factors, written
 // (with L when requested) from registers; no V^T tiles, no Delta, no Y_{k+1}.
 template <bool FINAL, typename TSo>
 __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid_constant__ CUtensorMap tmM,
                                                                    const __grid_constant__ CUtensorMap tmYin,
+                                                                   const __grid_constant__ CUtensorMap tmYout,
                                                                    const __grid_constant__ CUtensorMap tmD,
                                                                    const __grid_constant__ CUtensorMap tmCh,
                                                                    const __grid_constant__ CUtensorMap tmCl,
                                                                    const __grid_constant__ CUtensorMap tmVt,
                                                                    const float* __restrict__ Uh,
                                                                    const float* __restrict__ Ul,
-                                                                   __nv_bfloat16* __restrict__ Yout, int64_t ldy,
                                                                    int64_t m, int64_t n, float* __restrict__ Qpart,
                                                                    double* __restrict__ resid_part, DevState* st,
                                                                    TSo* __restrict__ Sout, TSo* __restrict__ Lout,
@@ -210,9 +211,11 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
       mbar_init(&B.vt_full[v], 1);
       mbar_init(&B.vt_empty[v], 1);  // the Delta V MMAs of the tile have completed
     }
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NCB; ++s) {
       mbar_init(&B.c_full[s], 1);
       mbar_init(&B.c_empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
       mbar_init(&B.l_full[s], 1);
       mbar_init(&B.l_empty[s], kEpiThreads);
     }
@@ -257,7 +260,9 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
     if (lane == 0) {
       prefetch_map(&tmM);
       prefetch_map(&tmYin);
-      int armed_stage[NSTAGE] = {-1, -1, -1}, armed_vt[NVT] = {-1, -1, -1, -1};
+      int armed_stage[NSTAGE], armed_vt[NVT];
+      for (int q = 0; q < NSTAGE; ++q) armed_stage[q] = -1;
+      for (int q = 0; q < NVT; ++q) armed_vt[q] = -1;
       for (int t = 0; t < ntiles && !*abort; ++t) {
         const int s = t % NSTAGE, i0 = tile_i0(t), j0 = tile_j0(t);
         if (t >= NSTAGE && !mbar_wait(&B.stage_empty[s], ((t / NSTAGE) - 1) & 1, abort)) break;
@@ -291,10 +296,11 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
     // ------------------------------------------------------------ TMA producer of the C tiles
     // (its own thread, so that waiting for a C buffer never holds back the M / Y stream)
     if (lane == 0) {
-      int armed_c[2] = {-1, -1};
+      int armed_c[NCB];
+      for (int q = 0; q < NCB; ++q) armed_c[q] = -1;
       for (int t = 0; t < ntiles && !*abort; ++t) {
-        const int cb = t & 1, j0 = tile_j0(t);
-        if (t >= 2 && !mbar_wait(&B.c_empty[cb], ((t >> 1) - 1) & 1, abort)) break;
+        const int cb = t % NCB, j0 = tile_j0(t);
+        if (t >= NCB && !mbar_wait(&B.c_empty[cb], ((t / NCB) - 1) & 1, abort)) break;
         unsigned char* cbuf = sm + OFF_C + cb * C_BUF;
         mbar_expect_tx(&B.c_full[cb], 4 * 8192);
         for (int a = 0; a < 2; ++a) {
@@ -304,10 +310,10 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
         armed_c[cb] = t;
       }
       if (*abort)
-        for (int q = 0; q < 2; ++q)
+        for (int q = 0; q < NCB; ++q)
           if (armed_c[q] >= 0) {
             int dummy = 0;
-            mbar_wait(&B.c_full[q], (armed_c[q] >> 1) & 1, &dummy);
+            mbar_wait(&B.c_full[q], (armed_c[q] / NCB) & 1, &dummy);
           }
     }
   } else if (warp == kMmaWarp) {
@@ -334,12 +340,12 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
       };
       bool ok = true;
       for (int t = 0; ok && t < ntiles; ++t) {
-        const int b = t & 1;
-        if (!mbar_wait(&B.c_full[b], (t >> 1) & 1, abort)) { ok = false; break; }
+        const int b = t & 1, cbi = t % NCB;
+        if (!mbar_wait(&B.c_full[cbi], (t / NCB) & 1, abort)) { ok = false; break; }
         if (t >= 2 && !mbar_wait(&B.l_empty[b], ((t >> 1) - 1) & 1, abort)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d = tmem + TM_L + b * TBN;
-        const uint32_t cbuf = smem_u32(sm + OFF_C + b * C_BUF);
+        const uint32_t cbuf = smem_u32(sm + OFF_C + cbi * C_BUF);
         // L = U_hi C_hi^T + U_hi C_lo^T + U_lo C_hi^T, K = 64 in 8 steps of 8
         for (int term = 0; term < 3; ++term) {
           const uint32_t ua = tmem + TM_U + 128 * (t >= kb) + (term == 2 ? 64 : 0);
@@ -350,7 +356,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
           }
         }
         mma_commit(&B.l_full[b]);
-        mma_commit(&B.c_empty[b]);
+        mma_commit(&B.c_empty[cbi]);
         if (!FINAL && t >= 1 && !delta_v(t - 1)) { ok = false; break; }
       }
       if (!FINAL && ok && ntiles > 0) ok = delta_v(ntiles - 1);
@@ -444,20 +450,21 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
       mbar_arrive(&B.l_empty[b]);
       unsigned char* da = sm + OFF_DA + b * DA_BYTES;
       const int ncol = (int)(n - j0 - cbase);  // valid columns among this thread's (may be <= 0)
-      __nv_bfloat16* yrow = Yout + gi * ldy + j0 + cbase;  // this thread's columns of Y_{k+1}
+      unsigned char* yo = sm + OFF_YO + b * DA_BYTES;
 #pragma unroll
       for (int cc = 0; cc < kEpiChunks; ++cc) {  // 16-byte chunk c = columns 8c .. 8c+7
         const uint32_t off = sw128(row, grp * kEpiChunks + cc);
         uint4 yn, dd;
         if (ncol >= kEpiCols) epi_chunk<true>(mwr[cc], ywr[cc], L + 8 * cc, 0, mu, inv_mu, dcoef, yn, dd, resid);
         else epi_chunk<false>(mwr[cc], ywr[cc], L + 8 * cc, ncol - 8 * cc, mu, inv_mu, dcoef, yn, dd, resid);
-        if (gi < m) *reinterpret_cast<uint4*>(yrow + 8 * cc) = yn;  // j0 + 63 < ldy: in the row
+        *reinterpret_cast<uint4*>(yo + off) = yn;
         *reinterpret_cast<uint4*>(da + off) = dd;
       }
       fence_async_smem();
       named_bar(1, kEpiThreads);
       if (tid == 0) {
         mbar_arrive(&B.d_full[b]);
+        tma_store_2d(&tmYout, yo, j0, i0);
         tma_store_2d(&tmD, da, j0, i0);
         tma_store_commit();
       }
@@ -780,9 +787,9 @@ cudaError_t tc_launch_sweep(const Shape& s, const TcMaps& mp, const TcBuffers& t
   auto kern = sweep_tc_kernel<false, float>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
   if (e != cudaSuccess) return e;
-  kern<<<s.sweep_grid_x, kSweepThreads, SWEEP_SMEM, st>>>(mp.M, mp.Y[y_in], mp.D, mp.Ch, mp.Cl, mp.Vt, t.Uh, t.Ul,
-                                                         static_cast<__nv_bfloat16*>(t.Y[1 - y_in]), t.ldy, s.m, s.n,
-                                                         Qpart, resid_part, dst, nullptr, nullptr, 0, 0);
+  kern<<<s.sweep_grid_x, kSweepThreads, SWEEP_SMEM, st>>>(mp.M, mp.Y[y_in], mp.Y[1 - y_in], mp.D, mp.Ch, mp.Cl, mp.Vt,
+                                                         t.Uh, t.Ul, s.m, s.n, Qpart, resid_part, dst, nullptr,
+                                                         nullptr, 0, 0);
   return cudaGetLastError();
 }
 
@@ -795,8 +802,8 @@ cudaError_t tc_launch_finalize(const Shape& s, const TcMaps& mp, const TcBuffers
     auto kern = sweep_tc_kernel<true, TSo>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
     if (e != cudaSuccess) return e;
-    kern<<<s.sweep_grid_x, kSweepThreads, SWEEP_SMEM, st>>>(mp.M, mp.Y[y_in], mp.D, mp.Ch, mp.Cl, mp.Vt, t.Uh, t.Ul,
-                                                           nullptr, t.ldy, s.m, s.n, nullptr, nullptr, dst,
+    kern<<<s.sweep_grid_x, kSweepThreads, SWEEP_SMEM, st>>>(mp.M, mp.Y[y_in], mp.Y[1 - y_in], mp.D, mp.Ch, mp.Cl,
+                                                           mp.Vt, t.Uh, t.Ul, s.m, s.n, nullptr, nullptr, dst,
                                                            static_cast<TSo*>(S), static_cast<TSo*>(L), lds,
                                                            vec ? 1 : 0);
     return cudaGetLastError();
