@@ -31,7 +31,7 @@ constexpr int TBM = 128, TBN = 64, TR = 64;
 
 // shared memory map of the sweep kernel (offsets from a 1024-byte aligned base)
 constexpr int NSTAGE = 2;
-constexpr int NCB = 2;  // C tile buffers
+constexpr int NCB = 3;  // C tile buffers (they come from L2 about 3 us after issue)
 constexpr uint32_t OFF_C = 0;           // C tiles, NCB buffers x 32 KB: hi (2 K-atoms x 64 rows x 128 B) then lo
 constexpr uint32_t C_BUF = 32768;
 constexpr uint32_t OFF_ST = NCB * 32768;      // input stages, 3 x 32 KB: M tile (128 x 64 bf16), Y tile; each epilogue
@@ -40,11 +40,10 @@ constexpr uint32_t ST_Y = 16384;
 constexpr int NVT = 4;                  // V^T tiles (64 x 64 bf16), a ring of 4: held until Delta V_bar is done
 constexpr uint32_t OFF_VT = OFF_ST + NSTAGE * ST_BYTES;
 constexpr uint32_t VT_BYTES = 8192;
-constexpr uint32_t OFF_DA = OFF_VT + NVT * VT_BYTES;  // Delta tiles, 2 x 16 KB: A operand of Delta V and
-                                                      // TMA store source (tile t uses buffer t % 2)
-constexpr uint32_t DA_BYTES = 16384;
-constexpr uint32_t OFF_YO = OFF_DA + 2 * DA_BYTES;    // Y_{k+1} tiles, 2 x 16 KB: TMA store sources
-constexpr uint32_t OFF_BAR = OFF_YO + 2 * DA_BYTES;
+constexpr uint32_t OFF_DA = OFF_VT + NVT * VT_BYTES;  // Delta tile, 16 KB: A operand of Delta V and TMA store
+constexpr uint32_t DA_BYTES = 16384;                  // source; rewritten only once both are done with it
+constexpr uint32_t OFF_YO = OFF_DA + DA_BYTES;        // Y_{k+1} tile, 16 KB: TMA store source
+constexpr uint32_t OFF_BAR = OFF_YO + DA_BYTES;
 constexpr uint32_t SWEEP_SMEM = OFF_BAR + 512 + 1024;
 static_assert(OFF_BAR % 1024 == 0, "alignment");
 static_assert(SWEEP_SMEM <= 232448, "shared memory per CTA");
@@ -57,7 +56,7 @@ struct SweepBars {
   uint64_t vt_full[NVT], vt_empty[NVT];
   uint64_t c_full[NCB], c_empty[NCB];
   uint64_t l_full[2], l_empty[2];
-  uint64_t d_full[2], d_empty[2];
+  uint64_t d_full, d_empty;
   uint64_t q_full;
   uint32_t tmem_base;
   int abort;
@@ -165,8 +164,8 @@ static_assert(kEpiCols % 16 == 0, "TMEM loads of 16 columns");
 // warp 16: TMA producer of M, Y and V^T; warp 17: TMEM owner and MMA issuer; warp 18: TMA
 // producer of the C tiles.  U_hi / U_lo (the fixed A operand of the L
 // products) live in tensor memory; M, Y and V^T tiles stream through three stages; C tiles
-// are double buffered; Y_{k+1} and Delta tiles are double buffered in shared memory and leave
-// through TMA stores (the Delta tile is also the A operand of Delta V_bar).
+// are triple buffered; Y_{k+1} and Delta tiles are staged in shared memory and leave through TMA
+// stores (the Delta tile is also the A operand of Delta V_bar).
 // FINAL: the output pass after the last iteration instead (Algorithm 1 returns L_k, S_k):
 // S = P_ST_{1/mu}(M - L + Y_k / mu) with the last iteration's mu, Y_k and factors, written
 // (with L when requested) from registers; no V^T tiles, no Delta, no Y_{k+1}.
@@ -220,8 +219,10 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
       mbar_init(&B.l_empty[s], kEpiThreads);
     }
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&B.d_full[s], 1);
-      mbar_init(&B.d_empty[s], 1);
+      if (s == 0) {
+        mbar_init(&B.d_full, 1);
+        mbar_init(&B.d_empty, 1);
+      }
     }
     mbar_init(&B.q_full, 1);
     B.abort = 0;
@@ -323,18 +324,17 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
       const uint32_t id_q = idesc(1, TBM, TR);    // bf16, 128 x 64
       auto delta_v = [&](int tt) -> bool {
         const int v = tt % NVT;
-        const int db = tt & 1;
-        if (!mbar_wait(&B.d_full[db], (tt >> 1) & 1, abort)) return false;
+        if (!mbar_wait(&B.d_full, tt & 1, abort)) return false;
         if (!mbar_wait(&B.vt_full[v], (tt / NVT) & 1, abort)) return false;
         tc_fence_after();
         const uint32_t vt = smem_u32(sm + OFF_VT + v * VT_BYTES);
         for (int kk = 0; kk < TBN / 16; ++kk) {
-          const uint64_t a = desc_sw128(smem_u32(sm + OFF_DA + db * DA_BYTES) + kk * 32);
+          const uint64_t a = desc_sw128(smem_u32(sm + OFF_DA) + kk * 32);
           const uint64_t b = desc_sw128(vt + kk * 32);
           const int seg = tt >= kb, first = seg ? kb : 0;  // Q of each segment starts from zero
           mma_bf16(tmem + TM_Q + 64 * seg, a, b, id_q, (tt > first || kk > 0) ? 1u : 0u);
         }
-        mma_commit(&B.d_empty[db]);
+        mma_commit(&B.d_empty);
         mma_commit(&B.vt_empty[v]);
         return true;
       };
@@ -423,9 +423,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
         }
         continue;
       }
-      mbar_wait(&B.l_full[b], (t >> 1) & 1, abort) && mbar_wait(&B.stage_full[s], (t / NSTAGE) & 1, abort) &&
-          (t < 2 || mbar_wait(&B.d_empty[b], ((t >> 1) - 1) & 1, abort));  // Delta V of tile t - 2 done
-      if (tid == 0 && t >= 2) tma_store_wait_read1();  // the Delta store of tile t - 2 has read its buffer
+      mbar_wait(&B.l_full[b], (t >> 1) & 1, abort) && mbar_wait(&B.stage_full[s], (t / NSTAGE) & 1, abort);
       named_bar(1, kEpiThreads);  // the abort decision below is the same for all epilogue threads
       if (*abort) {
         ok = false;
@@ -448,22 +446,30 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
       tmem_ld_wait();
       tc_fence_before();
       mbar_arrive(&B.l_empty[b]);
-      unsigned char* da = sm + OFF_DA + b * DA_BYTES;
+      unsigned char* da = sm + OFF_DA;
+      unsigned char* yo = sm + OFF_YO;
       const int ncol = (int)(n - j0 - cbase);  // valid columns among this thread's (may be <= 0)
-      unsigned char* yo = sm + OFF_YO + b * DA_BYTES;
+      uint4 yn[kEpiChunks], dd[kEpiChunks];
 #pragma unroll
       for (int cc = 0; cc < kEpiChunks; ++cc) {  // 16-byte chunk c = columns 8c .. 8c+7
+        if (ncol >= kEpiCols) epi_chunk<true>(mwr[cc], ywr[cc], L + 8 * cc, 0, mu, inv_mu, dcoef, yn[cc], dd[cc], resid);
+        else epi_chunk<false>(mwr[cc], ywr[cc], L + 8 * cc, ncol - 8 * cc, mu, inv_mu, dcoef, yn[cc], dd[cc], resid);
+      }
+      // the single Delta / Y_{k+1} tiles are free once Delta V of tile t - 1 is done and the TMA
+      // stores of tile t - 1 have read them (long done by now: the waits come after the compute)
+      if (t >= 1) mbar_wait(&B.d_empty, (t - 1) & 1, abort);
+      if (tid == 0 && t >= 1) tma_store_wait_read0();
+      named_bar(1, kEpiThreads);
+#pragma unroll
+      for (int cc = 0; cc < kEpiChunks; ++cc) {
         const uint32_t off = sw128(row, grp * kEpiChunks + cc);
-        uint4 yn, dd;
-        if (ncol >= kEpiCols) epi_chunk<true>(mwr[cc], ywr[cc], L + 8 * cc, 0, mu, inv_mu, dcoef, yn, dd, resid);
-        else epi_chunk<false>(mwr[cc], ywr[cc], L + 8 * cc, ncol - 8 * cc, mu, inv_mu, dcoef, yn, dd, resid);
-        *reinterpret_cast<uint4*>(yo + off) = yn;
-        *reinterpret_cast<uint4*>(da + off) = dd;
+        *reinterpret_cast<uint4*>(yo + off) = yn[cc];
+        *reinterpret_cast<uint4*>(da + off) = dd[cc];
       }
       fence_async_smem();
       named_bar(1, kEpiThreads);
       if (tid == 0) {
-        mbar_arrive(&B.d_full[b]);
+        mbar_arrive(&B.d_full);
         tma_store_2d(&tmYout, yo, j0, i0);
         tma_store_2d(&tmD, da, j0, i0);
         tma_store_commit();
