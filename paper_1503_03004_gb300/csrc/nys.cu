@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(256) nys_residual_kernel(const TMs* __restrict
                                                            TSo* __restrict__ L, int64_t lds) {
   __shared__ TC us[8][CR];
   __shared__ TC vs[32][CR + 1];
-  const int64_t i0 = (int64_t)blockIdx.y * 8, j0 = (int64_t)blockIdx.x * 32;
+  const int64_t nbx = (n + 31) / 32;  // 1-D grid over (8-row, 32-column) blocks, columns fastest
+  const int64_t i0 = ((int64_t)blockIdx.x / nbx) * 8, j0 = ((int64_t)blockIdx.x % nbx) * 32;
   const int tj = threadIdx.x & 31, ti = threadIdx.x >> 5;
   for (int e = threadIdx.x; e < 8 * r; e += blockDim.x) {
     int ii = e / r, a = e % r;
@@ -286,7 +287,9 @@ sfr_status nys_solve_device(Solver& sv, const sfr_problem& p, const void* Mdev, 
   if (e != cudaSuccess) { *err = cudaGetErrorString(e); return SFR_E_CUDA; }
   if (hflag) { *err = "FR-Nys: singular l x l block"; return SFR_E_RANK; }
   if (Sdev || Ldev) {
-    dim3 grid(cdiv(n, 32), cdiv(m, 8));
+    const int64_t nblk = (int64_t)cdiv(n, 32) * cdiv(m, 8);
+    if (nblk > 0x7fffffffLL) { *err = "FR-Nys output: m x n too large for one launch"; return SFR_E_INVAL; }
+    const unsigned grid = (unsigned)nblk;
     const bool fp64 = p.precision == SFR_PREC_FP64;
     e = by_mtype(p.m_dtype, Mdev, [&](auto M) {
       using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;

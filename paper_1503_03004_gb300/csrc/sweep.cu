@@ -573,7 +573,9 @@ __global__ void __launch_bounds__(256) finalize_kernel(const TMs* __restrict__ M
                                                        int64_t lds, const DevState* st) {
   __shared__ TC us[8][RP];
   __shared__ TC cs[32][RP + 1];
-  const int64_t i0 = (int64_t)blockIdx.y * 8, j0 = (int64_t)blockIdx.x * 32;
+  // 1-D grid over (8-row, 32-column) blocks, columns fastest (a 2-D grid would cap m at 65535 x 8)
+  const int64_t nbx = (n + 31) / 32;
+  const int64_t i0 = ((int64_t)blockIdx.x / nbx) * 8, j0 = ((int64_t)blockIdx.x % nbx) * 32;
   const int tj = threadIdx.x & 31, ti = threadIdx.x >> 5;
   for (int e = threadIdx.x; e < 8 * RP; e += blockDim.x) {
     int ii = e / RP, a = e % RP;
@@ -808,7 +810,9 @@ cudaError_t launch_iter_end(const Shape& s, const Buffers& b, cudaStream_t st) {
 cudaError_t launch_finalize(const Shape& s, const Buffers& b, bool fp64, int u_cur, void* S, sfr_dtype s_dtype,
                             int64_t lds, void* L, cudaStream_t st) {
   // Y_prev is the multiplier the last sweep read: Buffers::Y[0] by the host's swap convention.
-  dim3 grid(cdiv(s.n, 32), cdiv(s.m, 8));
+  const int64_t nblk = (int64_t)cdiv(s.n, 32) * cdiv(s.m, 8);
+  if (nblk > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)nblk;
   return by_prec(fp64, [&](auto tc) {
     using TC = decltype(tc);
     return by_rank(s.rp, [&](auto rpc) {
