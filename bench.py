@@ -172,6 +172,89 @@ def dist_setup():
     return rank, world, local
 
 
+def run_serving(args):
+    """Serving-stream workload: uneven planted requests (m in [256, 8192], n in [16, 512],
+    r in {3, 5, 10, 25}, outliers 2-15 % in [-50, 50], bf16 storage), three ways:
+      * serving: the mixed path through sfr_submit / sfr_poll with --slots slots, all requests
+        queued at once (throughput), then again with Poisson arrivals at 70 % of that rate
+        (latency p50 / p99 from arrival to completion);
+      * per-problem float64: sfr_solve one request at a time on the float64 path;
+      * per-problem mixed: sfr_solve one request at a time on the mixed path.
+    Inputs are on the device before timing.  Prints one JSON line (supplementary; the main
+    benchmark line is the default mode)."""
+    import numpy as np
+    import torch
+    from paper_1503_03004_gb300 import binding as B, synth
+    torch.cuda.set_device(0)
+    reqs = synth.request_stream(args.requests, rate_per_s=1000.0)
+    items = []
+    for q in reqs:
+        prob = synth.planted(q.m, q.n, q.r, p=q.p, amp=50.0, seed=q.seed, dtype="bf16")
+        Md = torch.from_numpy(prob.M.view(np.int16)).view(torch.bfloat16).cuda()
+        f64 = dict(dtype=torch.float64, device="cuda")
+        out = dict(U=torch.empty((q.m, q.r), **f64), B=torch.empty((q.r, q.r), **f64),
+                   V=torch.empty((q.n, q.r), **f64), S=torch.empty((q.m, q.n), dtype=torch.float32, device="cuda"))
+        items.append((q, Md, out))
+    torch.cuda.synchronize()
+    kw = dict(rho=1.5, mu0=0.05, tol=1e-9, max_iter=300)
+
+    def mk(q, Md, out, prec):
+        p = B.make_problem(m=q.m, n=q.n, r=q.r, M_ptr=Md.data_ptr(), m_dtype=B.BF16, precision=prec, **kw)
+        res = B.make_result(U_ptr=out["U"].data_ptr(), B_ptr=out["B"].data_ptr(), V_ptr=out["V"].data_ptr(),
+                            S_ptr=out["S"].data_ptr(), s_dtype=B.F32, lds=q.n)
+        return p, res
+
+    def sequential(prec):
+        with B.Context(0) as ctx:
+            for q, Md, out in items[:8]:  # warm-up: graphs, workspaces
+                p, res = mk(q, Md, out, prec)
+                ctx.solve(p, res)
+            t0 = time.perf_counter()
+            for q, Md, out in items:
+                p, res = mk(q, Md, out, prec)
+                if ctx.solve(p, res) not in (B.OK, B.E_NOCONV):
+                    raise RuntimeError(ctx.last_error())
+            return len(items) / (time.perf_counter() - t0)
+
+    def serving(rate):
+        with B.Context(0, max_slots=args.slots, hbm_budget_bytes=args.budget_gb << 30) as ctx:
+            for q, Md, out in items[:args.slots]:
+                p, res = mk(q, Md, out, B.PREC_MIXED)
+                ctx.poll(ctx.submit(p, res), -1)
+            keep, pending, done = [], {}, {}
+            t0 = time.perf_counter()
+            for k, (q, Md, out) in enumerate(items):
+                if rate:
+                    wait = t0 + q.arrival_s * (1000.0 / rate) - time.perf_counter()
+                    if wait > 0:
+                        time.sleep(wait)
+                p, res = mk(q, Md, out, B.PREC_MIXED)
+                keep.append((p, res))
+                pending[ctx.submit(p, res)] = (k, time.perf_counter())
+                for t in [t for t in pending if ctx.poll(t, 0) != B.PENDING]:
+                    done[pending[t][0]] = time.perf_counter() - pending.pop(t)[1]
+            while pending:
+                for t in [t for t in pending if ctx.poll(t, 0) != B.PENDING]:
+                    done[pending[t][0]] = time.perf_counter() - pending.pop(t)[1]
+                time.sleep(1e-4)
+            wall = time.perf_counter() - t0
+            lat = sorted(v * 1000.0 for v in done.values())
+            return len(items) / wall, lat[len(lat) // 2], lat[min(len(lat) - 1, int(0.99 * len(lat)))]
+
+    thr, _, _ = serving(None)
+    rate = 0.7 * thr
+    _, p50, p99 = serving(rate)
+    f64 = sequential(B.PREC_FP64)
+    mix = sequential(B.PREC_MIXED)
+    line = {"metric": "serving solves/s", "requests": len(items), "slots": args.slots,
+            "value": thr, "unit": "solves/s", "per_problem_fp64": f64, "per_problem_mixed": mix,
+            "latency_ms_at_rate": {"rate_per_s": rate, "p50": p50, "p99": p99},
+            "config": {"workload": "serving_stream", "m": [256, 8192], "n": [16, 512], "r": [3, 5, 10, 25],
+                       "outlier_fraction": [0.02, 0.15], "storage": "bf16", "tol": 1e-9}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_setup()
     if rank != 0:
@@ -203,6 +286,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true",
                     help="do not time kernels with events (no roofline; for measuring the profiling cost)")
+    ap.add_argument("--serving", action="store_true",
+                    help="supplementary: the serving-stream workload (submit/poll slots vs per-problem solves)")
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--budget-gb", type=int, default=64)
     ap.add_argument("--m", type=int, default=WORKLOAD["m"],
                     help="square size of the same recipe (smaller sizes are for profiler captures)")
     args = ap.parse_args()
@@ -212,6 +300,8 @@ def main():
                         l2=f"M {mb} MB, multipliers 2 x {mb} MB, Delta {mb} MB; no flush")
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving:
+        return run_serving(args)
 
     import numpy as np
     import torch
