@@ -222,6 +222,12 @@ def run_serving(args):
                 p, res = mk(q, Md, out, B.PREC_MIXED)
                 ctx.poll(ctx.submit(p, res), -1)
             keep, pending, done = [], {}, {}
+
+            def reap():
+                for t in [t for t in pending if ctx.poll(t, 0) != B.PENDING]:
+                    k, ts = pending.pop(t)
+                    done[k] = time.perf_counter() - ts
+
             t0 = time.perf_counter()
             for k, (q, Md, out) in enumerate(items):
                 if rate:
@@ -231,11 +237,9 @@ def run_serving(args):
                 p, res = mk(q, Md, out, B.PREC_MIXED)
                 keep.append((p, res))
                 pending[ctx.submit(p, res)] = (k, time.perf_counter())
-                for t in [t for t in pending if ctx.poll(t, 0) != B.PENDING]:
-                    done[pending[t][0]] = time.perf_counter() - pending.pop(t)[1]
+                reap()
             while pending:
-                for t in [t for t in pending if ctx.poll(t, 0) != B.PENDING]:
-                    done[pending[t][0]] = time.perf_counter() - pending.pop(t)[1]
+                reap()
                 time.sleep(1e-4)
             wall = time.perf_counter() - t0
             lat = sorted(v * 1000.0 for v in done.values())
