@@ -289,7 +289,7 @@ struct Solver {
     timed_launch(slot, 0, [&] { return launch_sweep(s, b, fp64, u_new, st); });  // S/Y steps, Delta, next P
     SFR_CUDA(launch_iter_end(s, b, st));                                      // residual, mu, stop test
     SFR_CUDA(launch_gram_p(s, b, fp64, true, st));                            // P = sum of partials, G_P
-    kernels += first ? 9 : 10;
+    kernels += first ? 11 : 12;  // as on the tensor-core path below
     b.u_cur = u_new;
     std::swap(b.Y[0], b.Y[1]);
     return kernels;
@@ -305,15 +305,12 @@ struct Solver {
       kernels += 2;
     }
     timed_launch(slot, 2, [&] { return launch_rxr(s, b, false, st, false); });  // T_U
-    SFR_CUDA(launch_apply_u(s, b, false, first, st));                         // U_bar = P T_U
+    SFR_CUDA(launch_apply_u(s, b, false, first, st));  // U_bar = P T_U, with its TF32 split and U^T
     const int u_new = 1 - b.u_cur;
-    const float* Unew = static_cast<const float*>(b.U[u_new]);
-    SFR_CUDA(tc_launch_prep_u(s, Unew, b.t, b.st, st));                       // TF32 split, U^T
     timed_launch(slot, 1, [&] { return tc_launch_wpass(s, maps, first, static_cast<float*>(b.Wpart), b.st, st); });
     SFR_CUDA(launch_wfinal(s, b, false, first, st));                          // W, G_W partials
     timed_launch(slot, 3, [&] { return launch_rxr(s, b, true, st, false); });  // T_V, B_bar, T_C
-    SFR_CUDA(launch_apply_v(s, b, false, st));                                // V_bar, C
-    SFR_CUDA(tc_launch_prep_v(s, static_cast<const float*>(b.C), static_cast<const float*>(b.V), b.t, b.st, st));
+    SFR_CUDA(launch_apply_v(s, b, false, st));  // V_bar, C, with the TF32 split of C and V^T
     const int y_in = b.Y[0] == b.t.Y[0] ? 0 : 1;
     timed_launch(slot, 0, [&] {
       return tc_launch_sweep(s, maps, b.t, y_in, static_cast<float*>(b.Qpart), b.resid_part, b.st, st);
@@ -321,7 +318,9 @@ struct Solver {
     SFR_CUDA(launch_iter_end(s, b, st));
     // P_{k+1} = U_bar B_bar + Delta V_bar  (L V_bar = U_bar B_bar since V_bar^T V_bar = I)
     SFR_CUDA(launch_gram_p(s, b, false, true, st, b.U[u_new], b.B));
-    kernels += first ? 10 : 12;
+    // launches: projector 2 + 2 (partial sums, cluster kernel), transforms 2, W pass 1, W final
+    // 1 (+1 H sum after the first), sweep 1, iteration end 1, P / Gram 1
+    kernels += first ? 11 : 12;
     b.u_cur = u_new;
     std::swap(b.Y[0], b.Y[1]);
     return kernels;

@@ -15,6 +15,8 @@
 //     Delta_{k+1} = Y_{k+1} (1/mu_k + 1/mu_{k+1}) - Y_k / mu_k,
 // so the sweep writes Delta and accumulates P_{k+1} = X_{k+1} V_{k+1} row by row,
 // and the second pass forms X_{k+1}^T U = C (U_old^T U) + Delta^T U with L = U_old C^T.
+#include <type_traits>
+
 #include "sfr_internal.h"
 
 namespace sfr {
@@ -272,6 +274,12 @@ __global__ void __launch_bounds__(256) reduce_sq_kernel(const double* __restrict
   }
 }
 
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 // ---------------------------------------------------------------- thin row transform
 // dst[i][:] = src[i][:] T   (T rp x rp, float64 in global), optional second output
 // dst2 = src T2, and optional partial hpart[cta] = sum over the CTA's rows of old[i]^T dst[i].
@@ -281,9 +289,15 @@ __global__ void __launch_bounds__(256) row_transform_kernel(const TC* __restrict
                                                             const double* __restrict__ T, TC* __restrict__ dst,
                                                             const double* __restrict__ T2, TC* __restrict__ dst2,
                                                             const TC* __restrict__ old, double* __restrict__ hpart,
-                                                            const DevState* st) {
+                                                            const DevState* st, float* __restrict__ sp_hi = nullptr,
+                                                            float* __restrict__ sp_lo = nullptr,
+                                                            __nv_bfloat16* __restrict__ trans = nullptr,
+                                                            int64_t ldt = 0) {
+  // Tensor-core path extras (float, RP = 64): sp_hi / sp_lo = TF32 split (hi = x rounded to TF32,
+  // lo = x - hi) of dst2 (or of dst without T2), trans = dst transposed in bfloat16 (ld ldt).
   if (stopped(st)) return;
   constexpr int LDT = RP + 4;
+  constexpr bool kF32 = std::is_same<TC, float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TC* Ts = reinterpret_cast<TC*>(smem_raw);   // [RP][LDT]
   TC* T2s = Ts + RP * LDT;                     // [RP][LDT]
@@ -318,6 +332,13 @@ __global__ void __launch_bounds__(256) row_transform_kernel(const TC* __restrict
         for (int y = 0; y < 4; ++y) {
           drow[(r0 + x) * LDT + c0 + y] = acc[x][y];
           if (i < rows) dst[i * RP + c0 + y] = acc[x][y];
+          if constexpr (kF32) {
+            if (!T2 && sp_hi && i < rows) {
+              const float hv = to_tf32(acc[x][y]);
+              sp_hi[i * RP + c0 + y] = hv;
+              sp_lo[i * RP + c0 + y] = acc[x][y] - hv;
+            }
+          }
         }
       }
     }
@@ -330,13 +351,30 @@ __global__ void __launch_bounds__(256) row_transform_kernel(const TC* __restrict
           const int64_t i = i0 + r0 + x;
           if (i < rows)
 #pragma unroll
-            for (int y = 0; y < 4; ++y) dst2[i * RP + c0 + y] = acc[x][y];
+            for (int y = 0; y < 4; ++y) {
+              dst2[i * RP + c0 + y] = acc[x][y];
+              if constexpr (kF32) {
+                if (sp_hi) {
+                  const float hv = to_tf32(acc[x][y]);
+                  sp_hi[i * RP + c0 + y] = hv;
+                  sp_lo[i * RP + c0 + y] = acc[x][y] - hv;
+                }
+              }
+            }
         }
       }
     }
-    if (hpart) {
-      __syncthreads();  // drow complete
-      block_mm<TC, RP, RP, kGramRows, true>(orow, LDT, drow, LDT, h, t);
+    if (hpart || trans) __syncthreads();  // drow complete
+    if (hpart) block_mm<TC, RP, RP, kGramRows, true>(orow, LDT, drow, LDT, h, t);
+    if constexpr (kF32) {
+      if (trans) {  // column a of the tile -> row a of the transpose, 64 consecutive rows i
+#pragma unroll
+        for (int q = 0; q < TileIdx<RP>::PER; ++q) {
+          const int e = t + q * kThinThreads, a = e / kGramRows, ii = e % kGramRows;
+          const int64_t i = i0 + ii;
+          if (i < rows) trans[(int64_t)a * ldt + i] = __float2bfloat16_rn(drow[ii * LDT + a]);
+        }
+      }
     }
   }
   if (hpart && t < (RP / 4) * (RP / 4)) {
@@ -706,9 +744,13 @@ cudaError_t launch_apply_u(const Shape& s, const Buffers& b, bool fp64, bool fir
       const size_t sm = transform_smem<TC, RP>();
       cudaError_t e = allow_smem(row_transform_kernel<TC, RP>, sm);
       if (e != cudaSuccess) return e;
+      // tensor-core path: also the TF32 split of U_new and its bfloat16 transpose (MMA operands)
+      const bool tcx = b.tc && RP == 64 && !fp64;
       row_transform_kernel<TC, RP><<<s.gp_blocks, 256, sm, st>>>(
           static_cast<const TC*>(b.P), s.m, b.TU, static_cast<TC*>(b.U[u_new]), nullptr, nullptr,
-          first ? nullptr : static_cast<const TC*>(b.U[u_old]), first ? nullptr : b.Hpart, b.st);
+          first ? nullptr : static_cast<const TC*>(b.U[u_old]), first ? nullptr : b.Hpart, b.st,
+          tcx ? b.t.Uh : nullptr, tcx ? b.t.Ul : nullptr, tcx ? static_cast<__nv_bfloat16*>(b.t.Ut) : nullptr,
+          b.t.ldd);
       return cudaGetLastError();
     });
   });
@@ -769,9 +811,12 @@ cudaError_t launch_apply_v(const Shape& s, const Buffers& b, bool fp64, cudaStre
       const size_t sm = transform_smem<TC, RP>();
       cudaError_t e = allow_smem(row_transform_kernel<TC, RP>, sm);
       if (e != cudaSuccess) return e;
-      row_transform_kernel<TC, RP><<<s.gw_blocks, 256, sm, st>>>(static_cast<const TC*>(b.W), s.n, b.TV,
-                                                                static_cast<TC*>(b.V), b.TCm, static_cast<TC*>(b.C),
-                                                                nullptr, nullptr, b.st);
+      // tensor-core path: also the TF32 split of C and the bfloat16 transpose of V
+      const bool tcx = b.tc && RP == 64 && !fp64;
+      row_transform_kernel<TC, RP><<<s.gw_blocks, 256, sm, st>>>(
+          static_cast<const TC*>(b.W), s.n, b.TV, static_cast<TC*>(b.V), b.TCm, static_cast<TC*>(b.C), nullptr, nullptr,
+          b.st, tcx ? b.t.Ch : nullptr, tcx ? b.t.Cl : nullptr, tcx ? static_cast<__nv_bfloat16*>(b.t.Vt) : nullptr,
+          b.t.ldy);
       return cudaGetLastError();
     });
   });

@@ -652,52 +652,6 @@ __global__ void __launch_bounds__(192, 1) wpass_tc_kernel(const __grid_constant_
   }
 }
 
-// ---------------------------------------------------------------- thin preparation kernels
-__device__ __forceinline__ float tf32_round(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-// From U (rows x 64 f32): hi = tf32(U), lo = U - hi (rows x 64 f32), and U^T in bf16 (64 x ldt).
-// Same routine for C (hi/lo) with V^T taken from a second input.
-__global__ void __launch_bounds__(256) split_transpose_kernel(const float* __restrict__ X,
-                                                              const float* __restrict__ Xt_src, int64_t rows,
-                                                              float* __restrict__ hi, float* __restrict__ lo,
-                                                              __nv_bfloat16* __restrict__ t, int64_t ldt,
-                                                              const DevState* st) {
-  if (stopped(st)) return;
-  __shared__ float tile[64][65];
-  const int64_t r0 = (int64_t)blockIdx.x * 64;
-  const int tid = threadIdx.x;
-  float xv[16], tv[16];  // element e = tid + 256 q of the 64 x 64 tile: all loads in flight first
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int e = tid + 256 * q;
-    const int64_t i = r0 + e / 64;
-    xv[q] = i < rows ? X[i * 64 + e % 64] : 0.f;
-    tv[q] = i < rows ? Xt_src[i * 64 + e % 64] : 0.f;
-  }
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int e = tid + 256 * q, rr = e / 64, a = e % 64;
-    const int64_t i = r0 + rr;
-    if (i < rows) {
-      const float h = tf32_round(xv[q]);
-      hi[i * 64 + a] = h;
-      lo[i * 64 + a] = xv[q] - h;
-    }
-    tile[rr][a] = tv[q];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int e = tid + 256 * q, a = e / 64, rr = e % 64;
-    const int64_t i = r0 + rr;
-    if (i < rows) t[(int64_t)a * ldt + i] = __float2bfloat16_rn(tile[rr][a]);
-  }
-}
-
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 // ---------------------------------------------------------------- tensor maps
@@ -763,19 +717,6 @@ cudaError_t tc_make_maps(const Shape& s, const TcBuffers& t, const void* M, int6
   ok &= make_map(&maps->Cl, t.Cl, F32, 64, s.n, 256, 32, 64);
   ok &= make_map(&maps->Vt, t.Vt, BF, s.n, 64, 2 * t.ldy, 64, 64);
   return ok ? cudaSuccess : cudaErrorInvalidValue;
-}
-
-cudaError_t tc_launch_prep_u(const Shape& s, const float* U, const TcBuffers& t, const DevState* dst, cudaStream_t st) {
-  split_transpose_kernel<<<cdiv(s.m, 64), 256, 0, st>>>(U, U, s.m, t.Uh, t.Ul, static_cast<__nv_bfloat16*>(t.Ut),
-                                                        t.ldd, dst);
-  return cudaGetLastError();
-}
-
-cudaError_t tc_launch_prep_v(const Shape& s, const float* C, const float* V, const TcBuffers& t, const DevState* dst,
-                             cudaStream_t st) {
-  split_transpose_kernel<<<cdiv(s.n, 64), 256, 0, st>>>(C, V, s.n, t.Ch, t.Cl, static_cast<__nv_bfloat16*>(t.Vt),
-                                                        t.ldy, dst);
-  return cudaGetLastError();
 }
 
 cudaError_t tc_launch_wpass(const Shape& s, const TcMaps& mp, bool first, float* Wpart, DevState* dst,

@@ -34,9 +34,6 @@ bool tc_supported(const Shape& s, int m_dtype, int64_t ldm);
 // the residual partial count and q_ctas.
 void tc_plan(Shape* s, int num_sms);
 cudaError_t tc_make_maps(const Shape& s, const TcBuffers& t, const void* M, int64_t ldm, TcMaps* maps);
-cudaError_t tc_launch_prep_u(const Shape& s, const float* U, const TcBuffers& t, const DevState* dst, cudaStream_t st);
-cudaError_t tc_launch_prep_v(const Shape& s, const float* C, const float* V, const TcBuffers& t, const DevState* dst,
-                             cudaStream_t st);
 cudaError_t tc_launch_wpass(const Shape& s, const TcMaps& mp, bool first, float* Wpart, DevState* dst,
                             cudaStream_t st);
 cudaError_t tc_launch_sweep(const Shape& s, const TcMaps& mp, const TcBuffers& t, int y_in, float* Qpart,
