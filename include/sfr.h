@@ -65,8 +65,9 @@ typedef struct {
   size_t hbm_budget_bytes;  /* cap on workspace bytes the context may hold; 0 = no cap     */
   int max_slots;            /* concurrent requests for sfr_submit; 0 = default (8)         */
   void* cuda_stream;        /* cudaStream_t for sfr_solve; NULL = a stream the ctx creates */
-  int profile;              /* nonzero: time the sweep, W-pass and r x r kernels of sfr_solve
-                               with CUDA events on the solve stream (see sfr_stats)        */
+  int profile;              /* nonzero: time the sweep (or P pass), W-pass and r x r kernels of
+                               sfr_solve / sfr_fixed_rank_opt_full with CUDA events on the
+                               solve stream (see sfr_stats)                                */
 } sfr_config;
 
 /* Kernel classes counted by sfr_stats. */
@@ -75,7 +76,8 @@ typedef enum {
   SFR_STAT_WPASS = 1,       /* X^T U_bar pass (V-step product of Algorithm 3)                      */
   SFR_STAT_RXR = 2,         /* r x r projector kernels (Eq. 9, Eq. 10)                           */
   SFR_STAT_ALL = 3,         /* every kernel launch of the library (total_ms unused)              */
-  SFR_STAT_COUNT = 4
+  SFR_STAT_PPASS = 4,       /* M V pass of sfr_fixed_rank_opt_full (U-step product, Algorithm 4)  */
+  SFR_STAT_COUNT = 5
 } sfr_stat_kind;
 
 typedef struct {
@@ -118,6 +120,41 @@ typedef struct {
   sfr_status status;        /* outcome of this problem                                     */
 } sfr_result;
 
+/* FixedRankOptFull (Algorithm 4, Appendix): FixedRankOptStep (Algorithm 3)
+ * iterated on a fixed M, i.e. alternating minimisation of ||M - U B V^T||_F over
+ * U in St(m, r), B symmetric, V in St(n, r).  Each iteration computes
+ *     U = P_O[M V B],  V = P_O[M^T U B],  B = Sym(U^T M V)      (Eq. 9, Eq. 10),
+ * and by Theorem 2 the iterates converge Q-linearly (subspace error shrinking by
+ * (sigma_{r+1} / sigma_r)^2 per iteration) to factors of the rank-r truncated SVD
+ * of M, whenever rank(M V_0) = r: a TSVD replacement on the same kernels as FR-ADM. */
+typedef struct {
+  int64_t m, n, ldm;        /* M is m x n, row-major, leading dimension ldm >= n           */
+  int32_t r;                /* target rank, 1 <= r <= min(m, n) and r <= 64                */
+  sfr_dtype m_dtype;        /* storage type of M                                           */
+  const void* M;            /* the data matrix (read only)                                 */
+  const double* V0;         /* n x r initial V (orthonormal columns); NULL = I_{n x r}     */
+  const double* B0;         /* r x r initial B, symmetric and invertible (Algorithm 4 asks
+                               for SPD; Lemma 1 needs only rank r); NULL = I_r.  A
+                               nonsymmetric B0 is refused with SFR_E_INVAL               */
+  double tol;               /* stop when ||B_i - B_{i-1}||_F <= tol ||B_i||_F (the paper's
+                               "until converged" is unspecified); 0 = run exactly max_iter  */
+  int32_t max_iter;         /* > 0; with tol > 0, SFR_E_NOCONV after this many iterations  */
+  sfr_precision precision;  /* SFR_PREC_MIXED: float32 thin products (bfloat16 M on the
+                               tensor cores when r > 32), float64 r x r steps             */
+  sfr_memspace mem;         /* where M, V0, B0 and the result buffers live                 */
+} sfr_opt_full_problem;
+
+typedef struct {
+  double* U;                /* m x r; NULL = do not return                                 */
+  double* B;                /* r x r; NULL = do not return                                 */
+  double* V;                /* n x r; NULL = do not return                                 */
+  int32_t iters;            /* iterations run                                              */
+  double rel_change;        /* ||B_K - B_{K-1}||_F / ||B_K||_F of the last iteration       */
+  double lambda_min_B;      /* smallest eigenvalue of B_K (B is SPD near the optimum, Lemma 2);
+                               NaN when B is not returned                                  */
+  sfr_status status;        /* outcome (SFR_E_RANK if rank(M V_i B_i) < r, Eq. 9)          */
+} sfr_opt_full_result;
+
 /* Create a context on cfg->device.  *out receives the handle. */
 sfr_status sfr_create(sfr_ctx** out, const sfr_config* cfg);
 
@@ -138,9 +175,14 @@ sfr_status sfr_poll(sfr_ctx* ctx, uint64_t ticket, int64_t timeout_us);
 /* Finish or cancel outstanding requests, free the workspace and the context. */
 sfr_status sfr_destroy(sfr_ctx* ctx);
 
-/* Copy the per-kernel-class counters of sfr_solve calls on ctx into out[0 .. count)
- * (indexed by sfr_stat_kind); reset != 0 zeroes them afterwards.  Counts cover
- * sfr_solve only, not requests run through sfr_submit. */
+/* Run FixedRankOptFull (Algorithm 4) on one matrix and wait for it, on the
+ * context's stream (the same stream and workspace as sfr_solve).  Returns the same
+ * status as res->status; SFR_E_INVAL for bad sizes, dtypes or a null M. */
+sfr_status sfr_fixed_rank_opt_full(sfr_ctx* ctx, const sfr_opt_full_problem* prob, sfr_opt_full_result* res);
+
+/* Copy the per-kernel-class counters of sfr_solve and sfr_fixed_rank_opt_full calls
+ * on ctx into out[0 .. count) (indexed by sfr_stat_kind); reset != 0 zeroes them
+ * afterwards.  Counts do not cover requests run through sfr_submit. */
 sfr_status sfr_stats(sfr_ctx* ctx, sfr_kernel_stat* out, int32_t count, int32_t reset);
 
 /* sfr_solve without any device allocation, for callers that cannot allocate:

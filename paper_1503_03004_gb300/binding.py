@@ -34,7 +34,7 @@ class Config(ctypes.Structure):
 
 
 # sfr_stat_kind
-STAT_SWEEP, STAT_WPASS, STAT_RXR, STAT_ALL, STAT_COUNT = 0, 1, 2, 3, 4
+STAT_SWEEP, STAT_WPASS, STAT_RXR, STAT_ALL, STAT_PPASS, STAT_COUNT = 0, 1, 2, 3, 4, 5
 
 
 class KernelStat(ctypes.Structure):
@@ -57,6 +57,18 @@ class Result(ctypes.Structure):
                 ("status", ctypes.c_int)]
 
 
+class OptFullProblem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("ldm", ctypes.c_int64), ("r", ctypes.c_int32),
+                ("m_dtype", ctypes.c_int), ("M", ctypes.c_void_p), ("V0", ctypes.c_void_p), ("B0", ctypes.c_void_p),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int),
+                ("mem", ctypes.c_int)]
+
+
+class OptFullResult(ctypes.Structure):
+    _fields_ = [("U", ctypes.c_void_p), ("B", ctypes.c_void_p), ("V", ctypes.c_void_p), ("iters", ctypes.c_int32),
+                ("rel_change", ctypes.c_double), ("lambda_min_B", ctypes.c_double), ("status", ctypes.c_int)]
+
+
 # (name, restype, argtypes) of every entry point declared in include/sfr.h
 SIGNATURES = [
     ("sfr_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Config)]),
@@ -66,6 +78,8 @@ SIGNATURES = [
     ("sfr_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64]),
     ("sfr_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("sfr_solve_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.POINTER(Result)]),
+    ("sfr_fixed_rank_opt_full", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(OptFullProblem),
+                                               ctypes.POINTER(OptFullResult)]),
     ("sfr_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(KernelStat), ctypes.c_int32, ctypes.c_int32]),
     ("sfr_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("sfr_version", ctypes.c_char_p, []),
@@ -117,6 +131,9 @@ class Context:
 
     def solve_noalloc(self, prob: Problem, res: Result) -> int:
         return self.lib.sfr_solve_noalloc(self.handle, ctypes.byref(prob), ctypes.byref(res))
+
+    def opt_full(self, prob: OptFullProblem, res: OptFullResult) -> int:
+        return self.lib.sfr_fixed_rank_opt_full(self.handle, ctypes.byref(prob), ctypes.byref(res))
 
     def submit(self, prob: Problem, res: Result) -> int:
         t = ctypes.c_uint64()
@@ -214,3 +231,41 @@ def solve_torch(ctx: Context, M, r: int, *, precision: int = PREC_FP64, want_L: 
         raise SfrError(st, ctx.last_error())
     return Solution(U=U, B=B, V=V, S=S, L=L, iters=res.iters, rel_residual=res.rel_residual,
                     lambda_min_B=res.lambda_min_B, status=st)
+
+
+@dataclass
+class OptFullSolution:
+    U: object
+    B: object
+    V: object
+    iters: int
+    rel_change: float
+    lambda_min_B: float
+    status: int
+
+
+def opt_full_torch(ctx: Context, M, r: int, *, V0=None, B0=None, tol: float = 0.0, max_iter: int = 50,
+                   precision: int = PREC_FP64, check: bool = True) -> OptFullSolution:
+    """FixedRankOptFull (Algorithm 4) on a device tensor M (2-D CUDA tensor with unit column stride;
+    float64/float32/bfloat16).  V0 (n x r) and B0 (r x r) are optional float64 CUDA tensors."""
+    import torch
+    assert M.is_cuda and M.dim() == 2 and M.stride(1) == 1
+    code = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}[M.dtype]
+    m, n = M.shape
+    dev = M.device
+    U = torch.empty((m, r), dtype=torch.float64, device=dev)
+    B = torch.empty((r, r), dtype=torch.float64, device=dev)
+    V = torch.empty((n, r), dtype=torch.float64, device=dev)
+    for t, shape in ((V0, (n, r)), (B0, (r, r))):
+        assert t is None or (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and tuple(t.shape) == shape)
+    prob = OptFullProblem(m=m, n=n, ldm=M.stride(0), r=r, m_dtype=code, M=M.data_ptr(),
+                          V0=V0.data_ptr() if V0 is not None else None, B0=B0.data_ptr() if B0 is not None else None,
+                          tol=tol, max_iter=max_iter, precision=precision, mem=MEM_DEVICE)
+    res = OptFullResult(U=U.data_ptr(), B=B.data_ptr(), V=V.data_ptr(), iters=0, rel_change=0.0, lambda_min_B=0.0,
+                        status=PENDING)
+    torch.cuda.synchronize(dev)
+    st = ctx.opt_full(prob, res)
+    if check and st != OK:
+        raise SfrError(st, ctx.last_error())
+    return OptFullSolution(U=U, B=B, V=V, iters=res.iters, rel_change=res.rel_change, lambda_min_B=res.lambda_min_B,
+                           status=st)

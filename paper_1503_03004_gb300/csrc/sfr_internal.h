@@ -81,6 +81,7 @@ struct Buffers {
   double* resid_part;   // sweep CTAs
   double* normm_part;   // ||M||^2 partials
   double* B;            // rp x rp
+  double* Bprev;        // rp x rp : B of the previous iteration (Algorithm 4 stopping rule)
   double* TU;           // rp x rp : U_bar = P T_U
   double* TV;           // rp x rp : V_bar = W T_V
   double* TCm;          // rp x rp : C = W T_C
@@ -89,6 +90,8 @@ struct Buffers {
   DevState* st;
   int u_cur;            // which U buffer holds the current U_bar (host-side bookkeeping)
   bool tc;              // tensor-core path (mixed precision, r <= 64, bfloat16 M)
+  bool full;            // Algorithm 4 on a fixed M: no multiplier or Delta buffers; the
+                        // tensor-core path keeps two-term bfloat16 splits of U^T and V^T
   TcBuffers t;          // its extra buffers (Y[] above alias t.Y[] when tc)
 };
 
@@ -113,6 +116,11 @@ cudaError_t launch_sweep(const Shape& s, const Buffers& b, bool fp64, int u_cur,
 cudaError_t launch_iter_end(const Shape& s, const Buffers& b, cudaStream_t st);
 cudaError_t launch_finalize(const Shape& s, const Buffers& b, bool fp64, int u_cur, void* S, sfr_dtype s_dtype,
                             int64_t lds, void* L, cudaStream_t st);  // Y is bfloat16 (ld t.ldy) when b.tc
+// Algorithm 4 (FixedRankOptFull): Qpart = split partials of M V (SIMT), the end-of-iteration
+// stopping rule on the change of B, and the float64 -> working-precision copy of V_0.
+cudaError_t launch_ppass(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st);
+cudaError_t launch_full_end(const Shape& s, const Buffers& b, cudaStream_t st);
+cudaError_t launch_import(const Shape& s, const double* src, int64_t rows, void* dst, bool fp64, cudaStream_t st);
 cudaError_t launch_export_factors(const Shape& s, const Buffers& b, bool fp64, int u_cur, double* U, double* V,
                                   cudaStream_t st);
 
@@ -127,7 +135,8 @@ inline int pad_rank(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 32 ? 32 : 6
 
 // ---- host helpers shared by the entry points (solver.cu)
 Shape plan_shape(int64_t m, int64_t n, int64_t ldm, int r, int num_sms);
-size_t carve(const Shape& s, bool fp64, void* base, Buffers* b, bool tc = false);  // base == nullptr: size only
+// base == nullptr: size only.  full: the buffers of Algorithm 4 (no m x n workspace).
+size_t carve(const Shape& s, bool fp64, void* base, Buffers* b, bool tc = false, bool full = false);
 double host_lambda_min(std::vector<double> A, int r);
 int ctx_device(const sfr_ctx* ctx);
 int ctx_num_sms(const sfr_ctx* ctx);

@@ -126,27 +126,31 @@ Shape plan_shape(int64_t m, int64_t n, int64_t ldm, int r, int num_sms) {
 }
 
 // Lay out every buffer of one solve inside `base` (or just size it when base == nullptr).
-size_t carve(const Shape& s, bool fp64, void* base, Buffers* b, bool tc) {
+size_t carve(const Shape& s, bool fp64, void* base, Buffers* b, bool tc, bool full) {
   const size_t tcb = fp64 ? 8 : 4;
   const size_t rp = s.rp, rpsq = rp * rp;
   Carver c(base);
   Buffers x{};
   x.tc = tc;
+  x.full = full;
   if (tc) {
     // tensor-core path: bfloat16 multiplier and transposed Delta, plus the MMA operand copies
+    // (Algorithm 4 on a fixed M needs only the transposed, split thin factors)
     x.t.ldy = (s.n + 63) / 64 * 64;
     x.t.ldd = (s.m + 63) / 64 * 64;
-    x.t.Y[0] = x.Y[0] = c.take(2 * s.m * x.t.ldy);
-    x.t.Y[1] = x.Y[1] = c.take(2 * s.m * x.t.ldy);
-    x.t.D = c.take(2 * s.m * x.t.ldy);
+    if (!full) {
+      x.t.Y[0] = x.Y[0] = c.take(2 * s.m * x.t.ldy);
+      x.t.Y[1] = x.Y[1] = c.take(2 * s.m * x.t.ldy);
+      x.t.D = c.take(2 * s.m * x.t.ldy);
+      x.t.Uh = static_cast<float*>(c.take(4 * s.m * 64));
+      x.t.Ul = static_cast<float*>(c.take(4 * s.m * 64));
+      x.t.Ch = static_cast<float*>(c.take(4 * s.n * 64));
+      x.t.Cl = static_cast<float*>(c.take(4 * s.n * 64));
+    }
     x.D = nullptr;
-    x.t.Uh = static_cast<float*>(c.take(4 * s.m * 64));
-    x.t.Ul = static_cast<float*>(c.take(4 * s.m * 64));
-    x.t.Ut = c.take(2 * 64 * x.t.ldd);
-    x.t.Ch = static_cast<float*>(c.take(4 * s.n * 64));
-    x.t.Cl = static_cast<float*>(c.take(4 * s.n * 64));
-    x.t.Vt = c.take(2 * 64 * x.t.ldy);
-  } else {
+    x.t.Ut = c.take(2 * 128 * x.t.ldd);
+    x.t.Vt = c.take(2 * 128 * x.t.ldy);
+  } else if (!full) {
     x.Y[0] = c.take(tcb * s.m * s.n);
     x.Y[1] = c.take(tcb * s.m * s.n);
     x.D = c.take(tcb * s.m * s.n);
@@ -166,6 +170,7 @@ size_t carve(const Shape& s, bool fp64, void* base, Buffers* b, bool tc) {
   x.resid_part = static_cast<double*>(c.take(8 * (size_t)s.resid_parts));
   x.normm_part = static_cast<double*>(c.take(8 * 1024));
   x.B = static_cast<double*>(c.take(8 * rpsq));
+  x.Bprev = static_cast<double*>(c.take(8 * rpsq));
   x.TU = static_cast<double*>(c.take(8 * rpsq));
   x.TV = static_cast<double*>(c.take(8 * rpsq));
   x.TCm = static_cast<double*>(c.take(8 * rpsq));
@@ -203,6 +208,7 @@ struct Solver {
   double total_ms[SFR_STAT_COUNT] = {};
   double bytes[SFR_STAT_COUNT] = {};
   double sweep_bytes = 0, wpass_bytes = 0, wpass_first_bytes = 0;  // per launch, set per solve
+  int pass_kind = SFR_STAT_SWEEP;  // class of the m x n pass timed in event slot 0 (sweep or P pass)
   cudaEvent_t ev[5][4][2] = {};       // slot 0: eager iteration; 1-2: graph A; 3-4: graph B
   cudaEvent_t done_ev[2] = {};        // completion of the last launch of graph A / B
   DevState* host_state2 = nullptr;    // pinned state copies taken after graph A / B
@@ -250,9 +256,9 @@ struct Solver {
     for (int sl = first; sl < first + count; ++sl) {
       float ms;
       SFR_CUDA(cudaEventElapsedTime(&ms, ev[sl][0][0], ev[sl][0][1]));
-      total_ms[SFR_STAT_SWEEP] += ms;
-      timed[SFR_STAT_SWEEP] += 1;
-      bytes[SFR_STAT_SWEEP] += sweep_bytes;
+      total_ms[pass_kind] += ms;
+      timed[pass_kind] += 1;
+      bytes[pass_kind] += sweep_bytes;
       SFR_CUDA(cudaEventElapsedTime(&ms, ev[sl][1][0], ev[sl][1][1]));
       total_ms[SFR_STAT_WPASS] += ms;
       timed[SFR_STAT_WPASS] += 1;
@@ -326,6 +332,81 @@ struct Solver {
     return kernels;
   }
 
+  // Iterations 2, 3, ... after an eager first one: two graphs (A, B) of two iterations each,
+  // captured from `after_first` once per buffer layout (`key`) and replayed alternately until the
+  // device state says done.  The host reads the state copied after the previous launch while the
+  // next one already runs, so the GPU does not wait for the host; a launch issued after
+  // convergence finds the stop flag set and costs only its launches.  `iter(b, slot)` enqueues
+  // one iteration (event slot `slot`) and returns its kernel count.  On return host_state holds
+  // the final device state.
+  template <typename F>
+  void drive(const Buffers& after_first, const std::string& key, int cap, bool timed_first, F&& iter) {
+    Buffers b = after_first;
+    if (graph_key != key + (profile ? "/p" : "")) {
+      for (cudaGraphExec_t* gp : {&graph, &graph_b})
+        if (*gp) {
+          cudaGraphExecDestroy(*gp);
+          *gp = nullptr;
+        }
+      for (int which = 0; which < 2; ++which) {
+        b = after_first;
+        cudaGraph_t g;
+        SFR_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed));
+        capturing = true;
+        try {
+          graph_kernels = iter(b, 1 + 2 * which);
+          graph_kernels += iter(b, 2 + 2 * which);
+        } catch (...) {
+          capturing = false;
+          cudaStreamEndCapture(stream, &g);
+          throw;
+        }
+        capturing = false;
+        SFR_CUDA(cudaStreamEndCapture(stream, &g));
+        cudaError_t e = cudaGraphInstantiate(which ? &graph_b : &graph, g, 0);
+        cudaGraphDestroy(g);
+        SFR_CUDA(e);
+      }
+      graph_key = key + (profile ? "/p" : "");
+    }
+    make_done_events();
+    SFR_CUDA(cudaMemcpyAsync(host_state, after_first.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
+    SFR_CUDA(cudaStreamSynchronize(stream));
+    if (timed_first) harvest(0, host_state->iter >= 1 ? 1 : 0);
+    int launched = 1, last_iter = host_state->iter, which = 0;
+    int queue[2], queued = 0;  // launched graphs whose state has not been read yet (oldest first)
+    bool stop = host_state->done != 0;
+    while (!stop) {
+      if (launched < cap) {
+        SFR_CUDA(cudaGraphLaunch(which ? graph_b : graph, stream));
+        SFR_CUDA(cudaMemcpyAsync(host_state2 + which, after_first.st, sizeof(DevState), cudaMemcpyDeviceToHost,
+                                 stream));
+        SFR_CUDA(cudaEventRecord(done_ev[which], stream));
+        launched += 2;
+        count(SFR_STAT_ALL, graph_kernels);
+        count(pass_kind, 2);
+        count(SFR_STAT_WPASS, 2);
+        count(SFR_STAT_RXR, 4);
+        queue[queued++] = which;
+        which ^= 1;
+      }
+      if (queued == 2 || (launched >= cap && queued > 0)) {
+        const int y = queue[0];
+        queue[0] = queue[1];
+        --queued;
+        SFR_CUDA(cudaEventSynchronize(done_ev[y]));
+        const DevState& hs = host_state2[y];
+        harvest(1 + 2 * y, hs.iter - last_iter);
+        last_iter = hs.iter;
+        *host_state = hs;
+        stop = hs.done != 0;
+      }
+      if (launched >= cap && queued == 0) stop = true;
+    }
+    SFR_CUDA(cudaMemcpyAsync(host_state, after_first.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
+    SFR_CUDA(cudaStreamSynchronize(stream));
+  }
+
   // Runs Algorithm 1 on a device-resident M.  Returns the final host copy of the state and
   // fills U/V/B/S/L (device pointers) as requested.
   DevState run(const sfr_problem& p, const void* Mdev, double* Udev, double* Bdev, double* Vdev, void* Sdev,
@@ -341,6 +422,7 @@ struct Solver {
     work.ensure(bytes, &held, budget);
     carve(s, fp64, work.ptr, &b, tc);
     if (tc) SFR_CUDA(tc_make_maps(s, b.t, Mdev, p.ldm, &maps));
+    pass_kind = SFR_STAT_SWEEP;
     {
       // algorithmic bytes per element: sweep reads M and Y_k, writes Y_{k+1} and Delta; the W pass
       // reads Delta (iteration 1: M, or M^T on the tensor-core path)
@@ -385,80 +467,11 @@ struct Solver {
     count(SFR_STAT_WPASS, 1);
     count(SFR_STAT_RXR, 2);
     const Buffers after_first = b;
-
-    // iterations 2, 3, ...: a graph of two iterations, replayed; every kernel exits at once
-    // after the stop flag is set, so overshooting the last iteration costs only launches.
-    const std::string key0 = fmt("%p/%lld/%lld/%lld/%d/%d/%p", work.ptr, (long long)s.m, (long long)s.n,
+    const std::string key = fmt("%p/%lld/%lld/%lld/%d/%d/%p", work.ptr, (long long)s.m, (long long)s.n,
                                 (long long)s.ldm, s.r, (int)fp64, Mdev) +
                             fmt("/%d/%d", (int)p.m_dtype, (int)tc);
-    const std::string key = key0;
-    if (graph_key != key + (profile ? "/p" : "")) {
-      for (cudaGraphExec_t* gp : {&graph, &graph_b})
-        if (*gp) {
-          cudaGraphExecDestroy(*gp);
-          *gp = nullptr;
-        }
-      for (int which = 0; which < 2; ++which) {
-        b = after_first;
-        cudaGraph_t g;
-        SFR_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed));
-        capturing = true;
-        try {
-          graph_kernels = enqueue_iteration(s, b, fp64, false, 1 + 2 * which);
-          graph_kernels += enqueue_iteration(s, b, fp64, false, 2 + 2 * which);
-        } catch (...) {
-          capturing = false;
-          cudaStreamEndCapture(stream, &g);
-          throw;
-        }
-        capturing = false;
-        SFR_CUDA(cudaStreamEndCapture(stream, &g));
-        cudaError_t e = cudaGraphInstantiate(which ? &graph_b : &graph, g, 0);
-        cudaGraphDestroy(g);
-        SFR_CUDA(e);
-      }
-      graph_key = key + (profile ? "/p" : "");
-      b = after_first;
-    }
-    const int cap = h.max_iter;
-    make_done_events();
-    SFR_CUDA(cudaMemcpyAsync(host_state, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
-    SFR_CUDA(cudaStreamSynchronize(stream));
-    harvest(0, host_state->iter >= 1 ? 1 : 0);
-    // Graphs A and B (two iterations each) alternate; the host reads the state copied after the
-    // previous launch while the next one already runs, so the GPU does not wait for the host.
-    // A launch issued after convergence finds the stop flag set and costs only its launches.
-    int launched = 1, last_iter = host_state->iter, which = 0;
-    int queue[2], queued = 0;  // launched graphs whose state has not been read yet (oldest first)
-    bool stop = host_state->done != 0;
-    while (!stop) {
-      if (launched < cap) {
-        SFR_CUDA(cudaGraphLaunch(which ? graph_b : graph, stream));
-        SFR_CUDA(cudaMemcpyAsync(host_state2 + which, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
-        SFR_CUDA(cudaEventRecord(done_ev[which], stream));
-        launched += 2;
-        count(SFR_STAT_ALL, graph_kernels);
-        count(SFR_STAT_SWEEP, 2);
-        count(SFR_STAT_WPASS, 2);
-        count(SFR_STAT_RXR, 4);
-        queue[queued++] = which;
-        which ^= 1;
-      }
-      if (queued == 2 || (launched >= cap && queued > 0)) {
-        const int y = queue[0];
-        queue[0] = queue[1];
-        --queued;
-        SFR_CUDA(cudaEventSynchronize(done_ev[y]));
-        const DevState& hs = host_state2[y];
-        harvest(1 + 2 * y, hs.iter - last_iter);
-        last_iter = hs.iter;
-        *host_state = hs;
-        stop = hs.done != 0;
-      }
-      if (launched >= cap && queued == 0) stop = true;
-    }
-    SFR_CUDA(cudaMemcpyAsync(host_state, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
-    SFR_CUDA(cudaStreamSynchronize(stream));
+    drive(after_first, key, h.max_iter, true,
+          [&](Buffers& bb, int slot) { return enqueue_iteration(s, bb, fp64, false, slot); });
     DevState out = *host_state;
     const int K = out.iter;
     // buffers of the last completed iteration (see the graph's two-iteration period)
@@ -487,7 +500,114 @@ struct Solver {
     SFR_CUDA(cudaStreamSynchronize(stream));
     return out;
   }
+  // One iteration of Algorithm 4: FixedRankOptStep (Algorithm 3) with X = M fixed, so both thin
+  // products read M itself: P = M V_i (init_p: the first r columns of M, for V_0 = I_{n x r}),
+  // U = P T_U, W = M^T U, V = W T_V, B = Sym(G_W T_V); then the stopping rule on the change of B.
+  int enqueue_full(const Shape& s, Buffers& b, bool fp64, bool init_p, int slot) {
+    cudaStream_t st = stream;
+    if (init_p) {
+      SFR_CUDA(launch_init_p(s, b, fp64, st));
+    } else {
+      timed_launch(slot, 0, [&] {
+        return b.tc ? tc_launch_full_ppass(s, maps, static_cast<float*>(b.Qpart), b.st, st) : launch_ppass(s, b, fp64, st);
+      });
+    }
+    SFR_CUDA(launch_gram_p(s, b, fp64, !init_p, st));                          // P, G_P partials
+    timed_launch(slot, 2, [&] { return launch_rxr(s, b, false, st, fp64); });  // T_U = B (B G_P B)^{-1/2}
+    SFR_CUDA(launch_apply_u(s, b, fp64, true, st));                            // U = P T_U
+    const int u_new = 1 - b.u_cur;
+    timed_launch(slot, 1, [&] {
+      return b.tc ? tc_launch_full_wpass(s, maps, static_cast<float*>(b.Wpart), b.st, st)
+                  : launch_wpass(s, b, fp64, true, u_new, st);
+    });
+    SFR_CUDA(launch_wfinal(s, b, fp64, true, st));                             // W = M^T U, G_W partials
+    timed_launch(slot, 3, [&] { return launch_rxr(s, b, true, st, fp64); });   // T_V, B = Sym(G_W T_V)
+    SFR_CUDA(launch_apply_v(s, b, fp64, st));                                  // V = W T_V
+    SFR_CUDA(launch_full_end(s, b, st));
+    b.u_cur = u_new;
+    // P pass (or init_p) 1, P sum / Gram 1, projectors 2 + 2, transforms 2, W pass 1, W sum 1, end 1
+    return 11;
+  }
+
+  // Runs Algorithm 4 (FixedRankOptFull) on a device-resident M from V_0 (NULL: I_{n x r}) and
+  // B_0 (NULL: I_r), both device float64; writes U, B, V (device, float64) where non-null.
+  DevState run_full(const sfr_opt_full_problem& p, const void* Mdev, const double* V0, const double* B0, double* Udev,
+                    double* Bdev, double* Vdev) {
+    const bool fp64 = p.precision == SFR_PREC_FP64;
+    const Shape s0 = plan_shape(p.m, p.n, p.ldm, p.r, num_sms);
+    const bool tc = !fp64 && tc_supported(s0, p.m_dtype, p.ldm) && ((uintptr_t)Mdev % 16) == 0;
+    last_tc = tc;
+    Shape s = s0;
+    if (tc) tc_plan(&s, num_sms);  // the P pass uses the sweep's persistent partition
+    Buffers b{};
+    work.ensure(carve(s, fp64, nullptr, nullptr, tc, true), &held, budget);
+    carve(s, fp64, work.ptr, &b, tc, true);
+    if (tc) SFR_CUDA(tc_make_full_maps(s, b.t, Mdev, p.ldm, &maps));
+    pass_kind = SFR_STAT_PPASS;
+    {
+      // algorithmic bytes per element: each of the two passes reads M once
+      const double mn = (double)s.m * s.n, bm = (double)dtype_size(p.m_dtype);
+      sweep_bytes = wpass_bytes = wpass_first_bytes = mn * bm;
+    }
+    b.M = Mdev;
+    b.m_dtype = p.m_dtype;
+    b.u_cur = 0;
+
+    DevState h{};
+    h.tol = p.tol;
+    h.fixed = p.tol == 0.0;
+    h.max_iter = p.max_iter;
+    h.status = SFR_OK;
+    SFR_CUDA(cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, stream));
+    std::vector<double> eye(s.rp * s.rp, 0.0);
+    std::vector<float> eyef(s.rp * s.rp, 0.f);
+    for (int i = 0; i < s.rp; ++i) {
+      eye[i * s.rp + i] = 1.0;
+      eyef[i * s.rp + i] = 1.f;
+    }
+    SFR_CUDA(cudaMemcpyAsync(b.B, eye.data(), 8 * eye.size(), cudaMemcpyHostToDevice, stream));
+    if (B0)  // B_0 in the leading r x r block, identity in the padding
+      SFR_CUDA(cudaMemcpy2DAsync(b.B, 8 * s.rp, B0, 8 * p.r, 8 * p.r, p.r, cudaMemcpyDeviceToDevice, stream));
+    SFR_CUDA(cudaMemcpyAsync(b.Bprev, b.B, 8 * eye.size(), cudaMemcpyDeviceToDevice, stream));
+    SFR_CUDA(cudaMemcpyAsync(b.Qeig_u, eyef.data(), 4 * eyef.size(), cudaMemcpyHostToDevice, stream));
+    SFR_CUDA(cudaMemcpyAsync(b.Qeig_v, eyef.data(), 4 * eyef.size(), cudaMemcpyHostToDevice, stream));
+    if (profile) make_events();
+
+    // iteration 1, eager
+    if (V0) {
+      // V = V_0 in working precision (with its split transpose on the tensor-core path): the
+      // V-side row transform of W = V_0 with T_V = I (and C = V_0 B_0)
+      SFR_CUDA(launch_import(s, V0, s.n, b.W, fp64, stream));
+      SFR_CUDA(cudaMemcpyAsync(b.TV, eye.data(), 8 * eye.size(), cudaMemcpyHostToDevice, stream));
+      SFR_CUDA(cudaMemcpyAsync(b.TCm, b.B, 8 * eye.size(), cudaMemcpyDeviceToDevice, stream));
+      SFR_CUDA(launch_apply_v(s, b, fp64, stream));
+      count(SFR_STAT_ALL, 2);
+    }
+    count(SFR_STAT_ALL, enqueue_full(s, b, fp64, V0 == nullptr, 0));
+    count(SFR_STAT_PPASS, V0 ? 1 : 0);
+    count(SFR_STAT_WPASS, 1);
+    count(SFR_STAT_RXR, 2);
+    const Buffers after_first = b;
+    const std::string key = fmt("full/%p/%lld/%lld/%lld/%d/%d/%p", work.ptr, (long long)s.m, (long long)s.n,
+                                (long long)s.ldm, s.r, (int)fp64, Mdev) +
+                            fmt("/%d/%d", (int)p.m_dtype, (int)tc);
+    drive(after_first, key, h.max_iter, V0 != nullptr,
+          [&](Buffers& bb, int slot) { return enqueue_full(s, bb, fp64, false, slot); });
+    DevState out = *host_state;
+    const int K = out.iter;
+    Buffers fin = after_first;
+    if (K >= 2 && K % 2 == 0) fin.u_cur = 1 - after_first.u_cur;  // U of the first iteration of a pair
+    if (out.status == SFR_OK || out.status == SFR_E_NOCONV) {
+      SFR_CUDA(launch_export_factors(s, fin, fp64, fin.u_cur, Udev, Vdev, stream));
+      count(SFR_STAT_ALL, (Udev ? 1 : 0) + (Vdev ? 1 : 0));
+      if (Bdev)
+        SFR_CUDA(cudaMemcpy2DAsync(Bdev, 8 * p.r, fin.B, 8 * s.rp, 8 * p.r, p.r, cudaMemcpyDeviceToDevice, stream));
+    }
+    SFR_CUDA(cudaStreamSynchronize(stream));
+    return out;
+  }
 };
+
 
 // Smallest eigenvalue of a symmetric r x r matrix (host, float64): Householder reduction to
 // tridiagonal form, then bisection on the Sturm count (the number of negative pivots of
@@ -727,6 +847,101 @@ static sfr_status solve_with(Solver& sv, const sfr_problem& p, sfr_result* res, 
   }
 }
 
+static sfr_status validate_full(const sfr_opt_full_problem* p, const sfr_opt_full_result* r, std::string* why) {
+  if (!p || !r) return *why = "null problem or result", SFR_E_INVAL;
+  if (p->m <= 0 || p->n <= 0) return *why = "m and n must be positive", SFR_E_INVAL;
+  if (p->ldm < p->n) return *why = "ldm must be >= n", SFR_E_INVAL;
+  if (p->r < 1 || p->r > kMaxRank || p->r > p->m || p->r > p->n)
+    return *why = fmt("need 1 <= r <= min(m, n, %d)", kMaxRank), SFR_E_INVAL;
+  if (!p->M) return *why = "M is null", SFR_E_INVAL;
+  if (p->m_dtype != SFR_F64 && p->m_dtype != SFR_F32 && p->m_dtype != SFR_BF16) return *why = "bad m_dtype", SFR_E_INVAL;
+  if (p->max_iter <= 0 || !(p->tol >= 0.0)) return *why = "need max_iter > 0 and tol >= 0", SFR_E_INVAL;
+  if (p->precision != SFR_PREC_FP64 && p->precision != SFR_PREC_MIXED) return *why = "bad precision", SFR_E_INVAL;
+  if (p->mem != SFR_MEM_DEVICE && p->mem != SFR_MEM_HOST) return *why = "bad mem", SFR_E_INVAL;
+  if ((int64_t)p->m * p->n > (int64_t)1 << 40) return *why = "matrix too large", SFR_E_INVAL;
+  return SFR_OK;
+}
+
+// Algorithm 4 on `sv`, staging host buffers when p.mem == SFR_MEM_HOST.
+static sfr_status full_with(Solver& sv, const sfr_opt_full_problem& p, sfr_opt_full_result* res, std::string* err) {
+  try {
+    SFR_CUDA(cudaSetDevice(sv.device));
+    const void* Mdev = p.M;
+    const double *V0 = p.V0, *B0 = p.B0;
+    double *U = res->U, *B = res->B, *V = res->V;
+    const size_t mbytes = dtype_size(p.m_dtype) * (size_t)((p.m - 1) * p.ldm + p.n);
+    const size_t ub = 8 * (size_t)p.m * p.r, vb = 8 * (size_t)p.n * p.r, bb = 8 * (size_t)p.r * p.r;
+    if (p.mem == SFR_MEM_HOST) {
+      size_t need = 0;
+      auto add = [&](size_t bytes) { need = (need + 255) & ~size_t(255); size_t o = need; need += bytes; return o; };
+      const size_t offM = add(mbytes), offV0 = V0 ? add(vb) : 0, offB0 = B0 ? add(bb) : 0;
+      const size_t offU = U ? add(ub) : 0, offV = V ? add(vb) : 0, offB = B ? add(bb) : 0;
+      sv.staging.ensure(need + 256, &sv.held, sv.budget);
+      char* st = static_cast<char*>(sv.staging.ptr);
+      SFR_CUDA(cudaMemcpyAsync(st + offM, p.M, mbytes, cudaMemcpyHostToDevice, sv.stream));
+      Mdev = st + offM;
+      if (V0) {
+        SFR_CUDA(cudaMemcpyAsync(st + offV0, p.V0, vb, cudaMemcpyHostToDevice, sv.stream));
+        V0 = reinterpret_cast<const double*>(st + offV0);
+      }
+      if (B0) {
+        SFR_CUDA(cudaMemcpyAsync(st + offB0, p.B0, bb, cudaMemcpyHostToDevice, sv.stream));
+        B0 = reinterpret_cast<const double*>(st + offB0);
+      }
+      if (U) U = reinterpret_cast<double*>(st + offU);
+      if (V) V = reinterpret_cast<double*>(st + offV);
+      if (B) B = reinterpret_cast<double*>(st + offB);
+    }
+    if (p.B0) {
+      // the projector forms (B G B)^{-1/2}, i.e. it needs B = B^T (Algorithm 4 takes B_0 in SPD_r;
+      // Lemma 1 needs only rank(B_0) = r, so an indefinite symmetric B_0 is accepted)
+      std::vector<double> hb((size_t)p.r * p.r);
+      if (p.mem == SFR_MEM_HOST) memcpy(hb.data(), p.B0, bb);
+      else SFR_CUDA(cudaMemcpy(hb.data(), p.B0, bb, cudaMemcpyDeviceToHost));
+      double amax = 0.0, asym = 0.0;
+      for (int i = 0; i < p.r; ++i)
+        for (int j = 0; j < p.r; ++j) {
+          amax = std::max(amax, std::fabs(hb[i * p.r + j]));
+          asym = std::max(asym, std::fabs(hb[i * p.r + j] - hb[j * p.r + i]));
+        }
+      if (!(amax > 0.0 && amax < 1e300) || asym > 1e-12 * amax) {
+        *err = "B0 must be a finite, nonzero symmetric matrix";
+        res->status = SFR_E_INVAL;
+        return SFR_E_INVAL;
+      }
+    }
+    DevState out = sv.run_full(p, Mdev, V0, B0, U, B, V);
+    res->iters = out.iter;
+    res->rel_change = out.res;
+    res->status = (sfr_status)out.status;
+    res->lambda_min_B = NAN;
+    const bool ok = res->status == SFR_OK || res->status == SFR_E_NOCONV;
+    if (p.mem == SFR_MEM_HOST && ok) {
+      if (res->U) SFR_CUDA(cudaMemcpyAsync(res->U, U, ub, cudaMemcpyDeviceToHost, sv.stream));
+      if (res->V) SFR_CUDA(cudaMemcpyAsync(res->V, V, vb, cudaMemcpyDeviceToHost, sv.stream));
+      if (res->B) SFR_CUDA(cudaMemcpyAsync(res->B, B, bb, cudaMemcpyDeviceToHost, sv.stream));
+      SFR_CUDA(cudaStreamSynchronize(sv.stream));
+    }
+    if (ok && res->B) {
+      std::vector<double> hb((size_t)p.r * p.r);
+      if (p.mem == SFR_MEM_HOST) memcpy(hb.data(), res->B, bb);
+      else SFR_CUDA(cudaMemcpy(hb.data(), res->B, bb, cudaMemcpyDeviceToHost));
+      res->lambda_min_B = host_lambda_min(hb, p.r);
+    }
+    if (res->status != SFR_OK) {
+      *err = res->status == SFR_E_NOCONV  ? fmt("B still changing by %.3e after %d iterations", out.res, out.iter)
+             : res->status == SFR_E_RANK ? fmt("rank-deficient thin product at iteration %d", out.iter + 1)
+             : res->status == SFR_E_NAN  ? fmt("non-finite value at iteration %d", out.iter + 1)
+                                         : fmt("FixedRankOptFull failed with status %d", (int)res->status);
+    }
+    return res->status;
+  } catch (const Fail& f) {
+    *err = f.msg;
+    res->status = f.code;
+    return f.code;
+  }
+}
+
 // Device bytes one request needs while it runs (workspace, plus staging for host buffers and
 // the FR-Nys block buffers), from the same planner the solve uses.
 static size_t request_bytes(const sfr_problem& p, int num_sms) {
@@ -882,6 +1097,21 @@ sfr_status sfr_solve(sfr_ctx* ctx, const sfr_problem* prob, sfr_result* res) {
   }
   std::string err;
   sfr_status s = solve_with(*ctx->solver, *prob, res, &err);
+  if (s < 0) ctx->last_error = err;
+  return s;
+}
+
+sfr_status sfr_fixed_rank_opt_full(sfr_ctx* ctx, const sfr_opt_full_problem* prob, sfr_opt_full_result* res) {
+  if (!ctx) return SFR_E_INVAL;
+  std::string why;
+  sfr_status v = validate_full(prob, res, &why);
+  if (v != SFR_OK) {
+    ctx->last_error = why;
+    if (res) res->status = v;
+    return v;
+  }
+  std::string err;
+  sfr_status s = full_with(*ctx->solver, *prob, res, &err);
   if (s < 0) ctx->last_error = err;
   return s;
 }

@@ -292,9 +292,10 @@ __global__ void __launch_bounds__(256) row_transform_kernel(const TC* __restrict
                                                             const DevState* st, float* __restrict__ sp_hi = nullptr,
                                                             float* __restrict__ sp_lo = nullptr,
                                                             __nv_bfloat16* __restrict__ trans = nullptr,
-                                                            int64_t ldt = 0) {
+                                                            int64_t ldt = 0, int trans_lo = 0) {
   // Tensor-core path extras (float, RP = 64): sp_hi / sp_lo = TF32 split (hi = x rounded to TF32,
-  // lo = x - hi) of dst2 (or of dst without T2), trans = dst transposed in bfloat16 (ld ldt).
+  // lo = x - hi) of dst2 (or of dst without T2), trans = dst transposed in bfloat16 (ld ldt);
+  // trans_lo != 0: also the bfloat16 rounding of x - hi into row RP + a (a two-term split).
   if (stopped(st)) return;
   constexpr int LDT = RP + 4;
   constexpr bool kF32 = std::is_same<TC, float>::value;
@@ -372,7 +373,12 @@ __global__ void __launch_bounds__(256) row_transform_kernel(const TC* __restrict
         for (int q = 0; q < TileIdx<RP>::PER; ++q) {
           const int e = t + q * kThinThreads, a = e / kGramRows, ii = e % kGramRows;
           const int64_t i = i0 + ii;
-          if (i < rows) trans[(int64_t)a * ldt + i] = __float2bfloat16_rn(drow[ii * LDT + a]);
+          if (i < rows) {
+            const float x = drow[ii * LDT + a];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            trans[(int64_t)a * ldt + i] = hi;
+            if (trans_lo) trans[(int64_t)(RP + a) * ldt + i] = __float2bfloat16_rn(x - __bfloat162float(hi));
+          }
         }
       }
     }
@@ -435,6 +441,59 @@ __global__ void __launch_bounds__(256) wpass_kernel(const TS* __restrict__ src, 
     TC* dst = Wpart + (int64_t)blockIdx.y * n * RP + j * RP + ta * APT;
 #pragma unroll
     for (int c = 0; c < APT; ++c) dst[c] = acc[c];
+  }
+}
+
+// ---------------------------------------------------------------- P pass (Algorithm 4)
+// Qpart[s][i][:] = sum_{j in split s} M[i][j] V[j][:]: the U-step product M V_i of Algorithm 3
+// when it is iterated on a fixed M (Algorithm 4), in the layout of the sweep's Q partials
+// (32-row blocks x column splits; thin_gram_kernel sums the splits).
+constexpr int kPBN = 32;  // columns per P-pass tile
+template <typename TC, typename TMs, int RP>
+__global__ void __launch_bounds__(256) ppass_kernel(const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm,
+                                                    const TC* __restrict__ V, TC* __restrict__ Qpart,
+                                                    int cols_per_split, const DevState* st) {
+  if (stopped(st)) return;
+  constexpr int BM = kSweepBM, QPT = RP / 8;  // 8 warps split the rank
+  __shared__ TC Xs[BM][kPBN + 1];
+  __shared__ TC Vs[kPBN][RP];
+  const int64_t i0 = (int64_t)blockIdx.x * BM;
+  const int64_t jbeg = (int64_t)blockIdx.y * cols_per_split;
+  const int64_t jend = min(n, jbeg + cols_per_split);
+  const int t = threadIdx.x, qi = t & 31, qg = t >> 5;
+  TC q[QPT];
+#pragma unroll
+  for (int c = 0; c < QPT; ++c) q[c] = 0;
+  for (int64_t j0 = jbeg; j0 < jend; j0 += kPBN) {
+    __syncthreads();  // previous tile consumed
+    for (int e = t; e < BM * kPBN; e += blockDim.x) {
+      const int ii = e / kPBN, jj = e % kPBN;
+      const int64_t i = i0 + ii, j = j0 + jj;
+      Xs[ii][jj] = (i < m && j < jend) ? ld_as<TC, TMs>(M + i * ldm + j) : (TC)0;
+    }
+    for (int e = t; e < kPBN * RP; e += blockDim.x) {
+      const int jj = e / RP, a = e % RP;
+      const int64_t j = j0 + jj;
+      Vs[jj][a] = j < jend ? V[j * RP + a] : (TC)0;
+    }
+    __syncthreads();
+    TC part[QPT];
+#pragma unroll
+    for (int c = 0; c < QPT; ++c) part[c] = 0;
+#pragma unroll 4
+    for (int jj = 0; jj < kPBN; ++jj) {
+      const TC xv = Xs[qi][jj];
+#pragma unroll
+      for (int c = 0; c < QPT; ++c) part[c] += xv * Vs[jj][qg * QPT + c];
+    }
+#pragma unroll
+    for (int c = 0; c < QPT; ++c) q[c] += part[c];
+  }
+  const int64_t i = i0 + qi;
+  if (i < m) {
+    TC* dst = Qpart + (int64_t)blockIdx.y * m * RP + i * RP + qg * QPT;
+#pragma unroll
+    for (int c = 0; c < QPT; ++c) dst[c] = q[c];
   }
 }
 
@@ -601,6 +660,41 @@ __global__ void norm_finish_kernel(const double* __restrict__ part, int count, D
   }
 }
 
+// ---------------------------------------------------------------- end of an Algorithm 4 iteration
+// Stopping rule of FixedRankOptFull ("while not converged", Algorithm 4): the relative change
+// of B, ||B_i - B_{i-1}||_F / ||B_i||_F, over the leading r x r block; then B_prev = B_i.
+__global__ void full_end_kernel(const double* __restrict__ B, double* __restrict__ Bprev, int rp, int r,
+                                DevState* st) {
+  __shared__ double red[32];
+  if (stopped(st)) return;
+  double d2 = 0.0, b2 = 0.0;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int a = e / r, c = e % r;
+    const double bv = B[a * rp + c], dv = bv - Bprev[a * rp + c];
+    d2 += dv * dv;
+    b2 += bv * bv;
+  }
+  d2 = block_sum(d2, red);
+  b2 = block_sum(b2, red);
+  for (int e = threadIdx.x; e < rp * rp; e += blockDim.x) Bprev[e] = B[e];
+  if (threadIdx.x == 0) {
+    const double res = sqrt(d2 / b2);
+    st->res = res;
+    st->iter += 1;
+    if (!(res == res) || !(b2 < 1e300)) {
+      st->status = SFR_E_NAN;
+      st->done = 1;
+    } else if (st->fixed) {
+      if (st->iter >= st->max_iter) st->done = 1;
+    } else if (res <= st->tol) {
+      st->done = 1;
+    } else if (st->iter >= st->max_iter) {
+      st->status = SFR_E_NOCONV;
+      st->done = 1;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- outputs
 // S = P_ST_{1/mu}(M - L + Y_prev / mu) with the mu, Y_prev and factors of the last iteration
 // (Algorithm 1 returns L_k, S_k); optionally L itself.
@@ -644,6 +738,16 @@ __global__ void export_kernel(const TC* __restrict__ src, int64_t rows, int r, d
   int64_t i = idx / r;
   int a = (int)(idx % r);
   dst[idx] = (double)src[i * RP + a];
+}
+
+// dst (rows x RP, TC) = src (rows x r, float64), padding columns r .. RP-1 with zeros.
+template <typename TC, int RP>
+__global__ void import_kernel(const double* __restrict__ src, int64_t rows, int r, TC* __restrict__ dst) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * RP) return;
+  const int64_t i = idx / RP;
+  const int a = (int)(idx % RP);
+  dst[idx] = a < r ? (TC)src[i * r + a] : (TC)0;
 }
 
 // ---------------------------------------------------------------- dispatch helpers
@@ -745,12 +849,13 @@ cudaError_t launch_apply_u(const Shape& s, const Buffers& b, bool fp64, bool fir
       cudaError_t e = allow_smem(row_transform_kernel<TC, RP>, sm);
       if (e != cudaSuccess) return e;
       // tensor-core path: also the TF32 split of U_new and its bfloat16 transpose (MMA operands)
-      const bool tcx = b.tc && RP == 64 && !fp64;
+      // (Algorithm 4: the two-term bfloat16 split of U^T instead, the B operand of M^T U)
+      const bool tcx = b.tc && RP == 64 && !fp64, tf = tcx && !b.full;
       row_transform_kernel<TC, RP><<<s.gp_blocks, 256, sm, st>>>(
           static_cast<const TC*>(b.P), s.m, b.TU, static_cast<TC*>(b.U[u_new]), nullptr, nullptr,
           first ? nullptr : static_cast<const TC*>(b.U[u_old]), first ? nullptr : b.Hpart, b.st,
-          tcx ? b.t.Uh : nullptr, tcx ? b.t.Ul : nullptr, tcx ? static_cast<__nv_bfloat16*>(b.t.Ut) : nullptr,
-          b.t.ldd);
+          tf ? b.t.Uh : nullptr, tf ? b.t.Ul : nullptr, tcx ? static_cast<__nv_bfloat16*>(b.t.Ut) : nullptr,
+          b.t.ldd, b.full ? 1 : 0);
       return cudaGetLastError();
     });
   });
@@ -812,11 +917,12 @@ cudaError_t launch_apply_v(const Shape& s, const Buffers& b, bool fp64, cudaStre
       cudaError_t e = allow_smem(row_transform_kernel<TC, RP>, sm);
       if (e != cudaSuccess) return e;
       // tensor-core path: also the TF32 split of C and the bfloat16 transpose of V
-      const bool tcx = b.tc && RP == 64 && !fp64;
+      // (Algorithm 4: the two-term bfloat16 split of V^T instead, the B operand of M V)
+      const bool tcx = b.tc && RP == 64 && !fp64, tf = tcx && !b.full;
       row_transform_kernel<TC, RP><<<s.gw_blocks, 256, sm, st>>>(
           static_cast<const TC*>(b.W), s.n, b.TV, static_cast<TC*>(b.V), b.TCm, static_cast<TC*>(b.C), nullptr, nullptr,
-          b.st, tcx ? b.t.Ch : nullptr, tcx ? b.t.Cl : nullptr, tcx ? static_cast<__nv_bfloat16*>(b.t.Vt) : nullptr,
-          b.t.ldy);
+          b.st, tf ? b.t.Ch : nullptr, tf ? b.t.Cl : nullptr, tcx ? static_cast<__nv_bfloat16*>(b.t.Vt) : nullptr,
+          b.t.ldy, b.full ? 1 : 0);
       return cudaGetLastError();
     });
   });
@@ -891,6 +997,38 @@ cudaError_t launch_export_factors(const Shape& s, const Buffers& b, bool fp64, i
       constexpr int RP = decltype(rpc)::value;
       if (U) export_kernel<TC, RP><<<cdiv(s.m * s.r, 256), 256, 0, st>>>(static_cast<const TC*>(b.U[u_cur]), s.m, s.r, U);
       if (V) export_kernel<TC, RP><<<cdiv(s.n * s.r, 256), 256, 0, st>>>(static_cast<const TC*>(b.V), s.n, s.r, V);
+      return cudaGetLastError();
+    });
+  });
+}
+
+cudaError_t launch_ppass(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st) {
+  dim3 grid(s.sweep_grid_x, s.nsplit);
+  return by_prec(fp64, [&](auto tc) {
+    using TC = decltype(tc);
+    return by_rank(s.rp, [&](auto rpc) {
+      constexpr int RP = decltype(rpc)::value;
+      return by_mtype(b.m_dtype, b.M, [&](auto M) {
+        using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
+        ppass_kernel<TC, TMs, RP><<<grid, 256, 0, st>>>(M, s.m, s.n, s.ldm, static_cast<const TC*>(b.V),
+                                                         static_cast<TC*>(b.Qpart), s.cols_per_split, b.st);
+        return cudaGetLastError();
+      });
+    });
+  });
+}
+
+cudaError_t launch_full_end(const Shape& s, const Buffers& b, cudaStream_t st) {
+  full_end_kernel<<<1, 256, 0, st>>>(b.B, b.Bprev, s.rp, s.r, b.st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_import(const Shape& s, const double* src, int64_t rows, void* dst, bool fp64, cudaStream_t st) {
+  return by_prec(fp64, [&](auto tc) {
+    using TC = decltype(tc);
+    return by_rank(s.rp, [&](auto rpc) {
+      constexpr int RP = decltype(rpc)::value;
+      import_kernel<TC, RP><<<cdiv(rows * RP, 256), 256, 0, st>>>(src, rows, s.r, static_cast<TC*>(dst));
       return cudaGetLastError();
     });
   });

@@ -520,12 +520,15 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
 }
 
 // ---------------------------------------------------------------- W pass: W = X^T U on tensor cores
-// CTA: 128 columns j x a chunk of rows i; D (128 x 64) in TMEM.  A = the m x n source (Delta, or
-// M on iteration 1) read row-major as an MN-major operand (M index = column j), B = U^T (K-major).
+// CTA: 128 columns j x a chunk of rows i; D (128 x 64 NS) in TMEM.  A = the m x n source (Delta,
+// or M on iteration 1 and in Algorithm 4) read row-major as an MN-major operand (M index = column
+// j), B = U^T (K-major) as NS bfloat16 terms stacked in 64-row groups (NS = 2 for Algorithm 4:
+// U = U_hi + U_lo, so that the product sees U at about 16 bits), summed in the epilogue.
 constexpr int WSTAGES = 4;
-constexpr uint32_t W_A_BYTES = 16384, W_B_BYTES = 8192, W_STAGE = W_A_BYTES + W_B_BYTES;
-constexpr uint32_t W_OFF_BAR = WSTAGES * W_STAGE;
-constexpr uint32_t WPASS_SMEM = W_OFF_BAR + 128 + 1024;
+constexpr uint32_t W_A_BYTES = 16384, W_B_BYTES = 8192;
+template <int NS> constexpr uint32_t w_stage() { return W_A_BYTES + NS * W_B_BYTES; }
+template <int NS> constexpr uint32_t w_off_bar() { return WSTAGES * w_stage<NS>(); }
+template <int NS> constexpr uint32_t wpass_smem() { return w_off_bar<NS>() + 128 + 1024; }
 
 // MN-major operand in the 128-byte swizzle layout: 64-element atoms along M 8 KB apart (LBO),
 // 8-row groups along K 1024 bytes apart (SBO)
@@ -546,14 +549,16 @@ struct WBars {
   int abort;
 };
 
+template <int NS>
 __global__ void __launch_bounds__(192, 1) wpass_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                           const __grid_constant__ CUtensorMap tmUt, int64_t m,
                                                           int64_t n, int rows_per_chunk, float* __restrict__ Wpart,
                                                           DevState* st) {
+  constexpr uint32_t W_STAGE = w_stage<NS>(), TCOLS = NS == 1 ? 64 : 128;
   if (stopped(st)) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-  WBars& B = *reinterpret_cast<WBars*>(sm + W_OFF_BAR);
+  WBars& B = *reinterpret_cast<WBars*>(sm + w_off_bar<NS>());
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int j0 = blockIdx.x * 128;
   const int r0 = blockIdx.y * rows_per_chunk;
@@ -569,7 +574,7 @@ __global__ void __launch_bounds__(192, 1) wpass_tc_kernel(const __grid_constant_
     B.abort = 0;
     mbar_fence_init();
   }
-  if (warp == 5) tmem_alloc(&B.tmem_base, 64);
+  if (warp == 5) tmem_alloc(&B.tmem_base, TCOLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -596,7 +601,7 @@ __global__ void __launch_bounds__(192, 1) wpass_tc_kernel(const __grid_constant_
     }
   } else if (warp == 5) {
     if (lane == 0) {
-      const uint32_t id = idesc(1, 128, TR) | (1u << 15);  // A MN-major
+      const uint32_t id = idesc(1, 128, TR * NS) | (1u << 15);  // A MN-major
       bool ok = true;
       for (int k = 0; k < nk; ++k) {
         const int s = k % WSTAGES;
@@ -628,8 +633,19 @@ __global__ void __launch_bounds__(192, 1) wpass_tc_kernel(const __grid_constant_
       named_bar(1, 128);  // uniform decision before the warp-collective TMEM loads
       if (!*abort) {
         tc_fence_after();
+        const uint32_t lb = (uint32_t)(warp * 32) << 16;
 #pragma unroll
-        for (int c = 0; c < TR; c += 16) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c, w + c);
+        for (int c = 0; c < TR; c += 16) tmem_ld16(tmem + lb + c, w + c);
+        if constexpr (NS == 2) {
+          float lo[16];
+#pragma unroll
+          for (int c = 0; c < TR; c += 16) {
+            tmem_ld16(tmem + lb + TR + c, lo);
+            tmem_ld_wait();
+#pragma unroll
+            for (int q = 0; q < 16; ++q) w[c + q] += lo[q];
+          }
+        }
         tmem_ld_wait();
         have = true;
       }
@@ -644,7 +660,139 @@ __global__ void __launch_bounds__(192, 1) wpass_tc_kernel(const __grid_constant_
   __syncthreads();
   if (warp == 5) {
     tc_fence_after();
-    tmem_dealloc(tmem, 64);
+    tmem_dealloc(tmem, TCOLS);
+  }
+  if (tid == 0 && B.abort) {
+    st->status = SFR_E_TIMEOUT;
+    st->done = 1;
+  }
+}
+
+// ---------------------------------------------------------------- P pass of Algorithm 4: P = M V
+// The sweep's persistent partition of (128-row block, 64-column tile) pairs: A = the bfloat16 M
+// tile (K-major), B = V^T as two bfloat16 terms V_hi, V_lo stacked into 128 rows, so one N = 128
+// MMA per K step forms M V_hi and M V_lo (M is exact in bfloat16, so the sum sees V at about
+// 16 bits, below the float32 accumulation error).  Each row-block segment of the CTA
+// accumulates in its own 128 TMEM columns over all its tiles; at the end the epilogue adds the
+// two halves and writes the Q partial into slot (CTA - first owner of the block), the layout
+// thin_gram_kernel sums.  Warps 0-3: epilogue (TMEM lanes = rows); warp 4: TMA producer;
+// warp 5: TMEM owner and MMA issuer.
+constexpr int PSTAGES = 6;
+constexpr uint32_t P_A_BYTES = 16384, P_B_BYTES = 16384, P_STAGE = P_A_BYTES + P_B_BYTES;
+constexpr uint32_t P_OFF_BAR = PSTAGES * P_STAGE;
+constexpr uint32_t PPASS_SMEM = P_OFF_BAR + 128 + 1024;
+static_assert(PPASS_SMEM <= 232448, "shared memory per CTA");
+
+struct PBars {
+  uint64_t full[PSTAGES], empty[PSTAGES];
+  uint64_t acc_full;
+  uint32_t tmem_base;
+  int abort;
+};
+static_assert(sizeof(PBars) <= 128, "barrier block");
+
+__global__ void __launch_bounds__(192, 1) ppass_tc_kernel(const __grid_constant__ CUtensorMap tmM,
+                                                          const __grid_constant__ CUtensorMap tmVt, int64_t m,
+                                                          int64_t n, float* __restrict__ Qpart, DevState* st) {
+  if (stopped(st)) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sm = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  PBars& B = *reinterpret_cast<PBars*>(sm + P_OFF_BAR);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // tiles [x0, x1) of the N (row block, column tile) pairs, at most two row blocks (tc_plan)
+  const int64_t T = (n + TBN - 1) / TBN, N = ((m + TBM - 1) / TBM) * T, G = gridDim.x;
+  const int64_t x0 = (int64_t)blockIdx.x * N / G, x1 = ((int64_t)blockIdx.x + 1) * N / G;
+  const int ntiles = (int)(x1 - x0);
+  const int64_t rb0 = x0 / T;
+  const int kb = (int)(((rb0 + 1) * T < x1 ? (rb0 + 1) * T : x1) - x0);
+  const int nseg = kb < ntiles ? 2 : 1;
+  volatile int* abort = &B.abort;
+  if (tid == 0) {
+    for (int s = 0; s < PSTAGES; ++s) {
+      mbar_init(&B.full[s], 1);
+      mbar_init(&B.empty[s], 1);
+    }
+    mbar_init(&B.acc_full, 1);
+    B.abort = 0;
+    mbar_fence_init();
+  }
+  if (warp == 5) tmem_alloc(&B.tmem_base, 256);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = B.tmem_base;
+  if (warp == 4) {
+    if (lane == 0) {
+      prefetch_map(&tmM);
+      int armed[PSTAGES];
+      for (int q = 0; q < PSTAGES; ++q) armed[q] = -1;
+      for (int t = 0; t < ntiles && !*abort; ++t) {
+        const int s = t % PSTAGES;
+        const int i0 = (int)((rb0 + (t >= kb)) * TBM), j0 = (int)((x0 + t - (rb0 + (t >= kb)) * T) * TBN);
+        if (t >= PSTAGES && !mbar_wait(&B.empty[s], ((t / PSTAGES) - 1) & 1, abort)) break;
+        mbar_expect_tx(&B.full[s], P_STAGE);
+        tma_load_2d(sm + s * P_STAGE, &tmM, j0, i0, &B.full[s]);
+        tma_load_2d(sm + s * P_STAGE + P_A_BYTES, &tmVt, j0, 0, &B.full[s]);
+        armed[s] = t;
+      }
+      if (*abort)
+        for (int q = 0; q < PSTAGES; ++q)
+          if (armed[q] >= 0) {
+            int dummy = 0;
+            mbar_wait(&B.full[q], (armed[q] / PSTAGES) & 1, &dummy);
+          }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      const uint32_t id = idesc(1, TBM, 2 * TR);  // bf16, 128 x 128
+      bool ok = true;
+      for (int t = 0; t < ntiles; ++t) {
+        const int s = t % PSTAGES, seg = t >= kb, first = seg ? kb : 0;
+        if (!mbar_wait(&B.full[s], (t / PSTAGES) & 1, abort)) { ok = false; break; }
+        tc_fence_after();
+        for (int kk = 0; kk < TBN / 16; ++kk) {
+          const uint64_t a = desc_sw128(smem_u32(sm + s * P_STAGE) + kk * 32);
+          const uint64_t b = desc_sw128(smem_u32(sm + s * P_STAGE + P_A_BYTES) + kk * 32);
+          mma_bf16(tmem + 2 * TR * seg, a, b, id, (t > first || kk > 0) ? 1u : 0u);
+        }
+        mma_commit(&B.empty[s]);
+      }
+      mma_commit(&B.acc_full);
+      if (!ok) {
+        int dummy = 0;
+        mbar_wait(&B.acc_full, 0, &dummy);
+      }
+    }
+  } else {
+    if (ntiles > 0) mbar_wait(&B.acc_full, 0, abort);
+    named_bar(1, 128);  // uniform decision before the warp-collective TMEM loads
+    if (ntiles > 0 && !*abort) {
+      tc_fence_after();
+      const uint32_t lb = (uint32_t)(warp * 32) << 16;
+      for (int seg = 0; seg < nseg; ++seg) {
+        const int64_t rb = rb0 + seg, gi = rb * TBM + warp * 32 + lane;
+        const int64_t slot = blockIdx.x - tc_tile_owner(rb * T, N, G);
+        for (int c = 0; c < TR; c += 16) {
+          float hi[16], lo[16];
+          tmem_ld16(tmem + lb + 2 * TR * seg + c, hi);
+          tmem_ld16(tmem + lb + 2 * TR * seg + TR + c, lo);
+          tmem_ld_wait();
+          if (gi < m) {
+            float4* dst = reinterpret_cast<float4*>(Qpart + (slot * m + gi) * TR + c);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              dst[q] = make_float4(hi[4 * q] + lo[4 * q], hi[4 * q + 1] + lo[4 * q + 1], hi[4 * q + 2] + lo[4 * q + 2],
+                                   hi[4 * q + 3] + lo[4 * q + 3]);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 5) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 256);
   }
   if (tid == 0 && B.abort) {
     st->status = SFR_E_TIMEOUT;
@@ -704,6 +852,16 @@ bool tc_supported(const Shape& s, int m_dtype, int64_t ldm) {
   return s.rp == 64 && m_dtype == SFR_BF16 && ldm % 8 == 0 && s.n % 8 == 0 && s.m % 8 == 0 && encode_fn() != nullptr;
 }
 
+cudaError_t tc_make_full_maps(const Shape& s, const TcBuffers& t, const void* M, int64_t ldm, TcMaps* maps) {
+  const auto BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  bool ok = true;
+  ok &= make_map(&maps->M, M, BF, s.n, s.m, 2 * ldm, 64, 128);
+  ok &= make_map(&maps->M_w, M, BF, s.n, s.m, 2 * ldm, 64, 64);
+  ok &= make_map(&maps->Ut2, t.Ut, BF, s.m, 128, 2 * t.ldd, 64, 128);
+  ok &= make_map(&maps->Vt2, t.Vt, BF, s.n, 128, 2 * t.ldy, 64, 128);
+  return ok ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t tc_make_maps(const Shape& s, const TcBuffers& t, const void* M, int64_t ldm, TcMaps* maps) {
   const auto BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   bool ok = true;
@@ -721,11 +879,28 @@ cudaError_t tc_make_maps(const Shape& s, const TcBuffers& t, const void* M, int6
 
 cudaError_t tc_launch_wpass(const Shape& s, const TcMaps& mp, bool first, float* Wpart, DevState* dst,
                             cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(wpass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WPASS_SMEM);
+  cudaError_t e =
+      cudaFuncSetAttribute(wpass_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wpass_smem<1>());
   if (e != cudaSuccess) return e;
   dim3 grid(cdiv(s.n, 128), s.nchunk);
-  wpass_tc_kernel<<<grid, 192, WPASS_SMEM, st>>>(first ? mp.M_w : mp.D_w, mp.Ut, s.m, s.n, s.rows_per_chunk, Wpart,
-                                                  dst);
+  wpass_tc_kernel<1><<<grid, 192, wpass_smem<1>(), st>>>(first ? mp.M_w : mp.D_w, mp.Ut, s.m, s.n, s.rows_per_chunk,
+                                                          Wpart, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_full_wpass(const Shape& s, const TcMaps& mp, float* Wpart, DevState* dst, cudaStream_t st) {
+  cudaError_t e =
+      cudaFuncSetAttribute(wpass_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wpass_smem<2>());
+  if (e != cudaSuccess) return e;
+  dim3 grid(cdiv(s.n, 128), s.nchunk);
+  wpass_tc_kernel<2><<<grid, 192, wpass_smem<2>(), st>>>(mp.M_w, mp.Ut2, s.m, s.n, s.rows_per_chunk, Wpart, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_full_ppass(const Shape& s, const TcMaps& mp, float* Qpart, DevState* dst, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(ppass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PPASS_SMEM);
+  if (e != cudaSuccess) return e;
+  ppass_tc_kernel<<<s.sweep_grid_x, 192, PPASS_SMEM, st>>>(mp.M, mp.Vt2, s.m, s.n, Qpart, dst);
   return cudaGetLastError();
 }
 

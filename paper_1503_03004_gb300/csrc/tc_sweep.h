@@ -19,14 +19,16 @@ struct TcBuffers {
   int64_t ldd;         // m rounded up to 64 (leading dimension of U^T)
   float* Uh;           // m x 64: U rounded to TF32
   float* Ul;           // m x 64: U - Uh
-  void* Ut;            // 64 x ldd bfloat16: U^T
+  void* Ut;            // 128 x ldd bfloat16: U^T in rows 0-63 (Algorithm 4: rows 64-127 hold the
+                       // bfloat16 rounding of U^T - rows 0-63)
   float* Ch;           // n x 64: C rounded to TF32
   float* Cl;           // n x 64: C - Ch
-  void* Vt;            // 64 x ldy bfloat16: V^T
+  void* Vt;            // 128 x ldy bfloat16: V^T in rows 0-63 (Algorithm 4: plus its low part)
 };
 
 struct TcMaps {
   CUtensorMap M, M_w, Y[2], D, D_w, Ut, Ch, Cl, Vt;  // *_w: 64 x 64 boxes for the W pass
+  CUtensorMap Ut2, Vt2;  // Algorithm 4: the two-term splits, 64 x 128 boxes
 };
 
 bool tc_supported(const Shape& s, int m_dtype, int64_t ldm);
@@ -38,6 +40,12 @@ cudaError_t tc_launch_wpass(const Shape& s, const TcMaps& mp, bool first, float*
                             cudaStream_t st);
 cudaError_t tc_launch_sweep(const Shape& s, const TcMaps& mp, const TcBuffers& t, int y_in, float* Qpart,
                             double* resid_part, DevState* dst, cudaStream_t st);
+// Algorithm 4 (FixedRankOptFull) on a fixed bfloat16 M: the maps of M and of the split U^T, V^T;
+// P = M V partials (persistent partition of tc_plan, Q-partial layout of the sweep) and
+// W = M^T U partials (the W pass with the two-term split of U).
+cudaError_t tc_make_full_maps(const Shape& s, const TcBuffers& t, const void* M, int64_t ldm, TcMaps* maps);
+cudaError_t tc_launch_full_ppass(const Shape& s, const TcMaps& mp, float* Qpart, DevState* dst, cudaStream_t st);
+cudaError_t tc_launch_full_wpass(const Shape& s, const TcMaps& mp, float* Wpart, DevState* dst, cudaStream_t st);
 // S = P_ST_{1/mu}(M - L + Y / mu) (and L when non-null) from the last iteration's factors, mu
 // and multiplier Y = t.Y[y_in]; S / L are m x n with leading dimension lds, float64 when
 // s_dtype == SFR_F64 else float32.

@@ -50,9 +50,10 @@ def test_binding_signatures_cover_the_header():
 
 def test_struct_layouts_match_the_header():
     # field order and sizes of the ctypes mirrors against the C declarations
-    text = open(os.path.join(ROOT, "include", "sfr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "sfr.h")).read(), flags=re.S)
     for struct, py in (("sfr_config", binding.Config), ("sfr_problem", binding.Problem), ("sfr_result", binding.Result),
-                       ("sfr_kernel_stat", binding.KernelStat)):
+                       ("sfr_kernel_stat", binding.KernelStat), ("sfr_opt_full_problem", binding.OptFullProblem),
+                       ("sfr_opt_full_result", binding.OptFullResult)):
         body = re.search(r"typedef struct \{([^}]*)\}\s*" + struct + ";", text).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
         fields = []
