@@ -41,16 +41,24 @@ FALLBACK_HBM_GBS = 6800.0
 def sweep_traffic(m: int, n: int):
     """DRAM bytes of one sweep launch from the committed ncu summary, scaled by m n.
 
-    The summary records bytes per element and the hash of the kernel source it was measured
-    on; if the source has changed since, the figure no longer applies and None is returned.
+    The summary records bytes per element and the hashes of the kernel's source (the part of
+    its file before `source_until`, which holds the sweep kernel, its constants and helpers) and
+    of the shared tensor-core helpers; if either has changed since, the figure no longer applies
+    and None is returned.
     """
     import hashlib
+    keys = ("traffic_bytes_per_element", "source", "source_until", "source_sha256", "helpers", "helpers_sha256")
     try:
         with open(os.path.join(ROOT, "profiles", "sweep_tc_square8192_r64_bf16.md")) as f:
             kv = dict(line.strip().split(": ", 1) for line in f if line.startswith("    ") and ": " in line
-                      and line.strip().split(": ", 1)[0] in ("traffic_bytes_per_element", "source", "source_sha256"))
-        with open(os.path.join(ROOT, kv["source"]), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != kv["source_sha256"]:
+                      and line.strip().split(": ", 1)[0] in keys)
+        with open(os.path.join(ROOT, kv["source"]), encoding="utf-8") as f:
+            text = f.read()
+        region = text[:text.index(kv["source_until"])]
+        if hashlib.sha256(region.encode("utf-8")).hexdigest() != kv["source_sha256"]:
+            return None
+        with open(os.path.join(ROOT, kv["helpers"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != kv["helpers_sha256"]:
                 return None
         return float(kv["traffic_bytes_per_element"]) * m * n
     except Exception:
@@ -259,6 +267,91 @@ def run_serving(args):
     return 0
 
 
+def run_opt_full(args):
+    """FixedRankOptFull (Algorithm 4) as a truncated-SVD replacement on the benchmark's matrix
+    (16384 x 16384 bf16, r = 64): one step = one call of sfr_fixed_rank_opt_full from V_0 = I,
+    B_0 = I until ||B_i - B_{i-1}||_F <= 1e-6 ||B_i||_F (mixed path: tensor-core P = M V and
+    W = M^T U passes).  Inputs are on the device before timing (M is larger than L2).  Reports
+    TSVDs/s, the two passes against the HBM roofline (each reads M once: 2 B per element), the
+    float64 oracle on a 2048 x 2048 sample, and the same call with host buffers (e2e).  Prints
+    one JSON line (supplementary; the main benchmark line is the default mode)."""
+    import numpy as np
+    import torch
+    from paper_1503_03004_gb300 import binding as B
+    torch.cuda.set_device(0)
+    m = n = args.m
+    r, tol, cap = WORKLOAD["r"], 1e-6, 50
+    prob = make_workload(1001) if m == WORKLOAD["m"] else None
+    if prob is None:
+        from paper_1503_03004_gb300 import synth
+        prob = synth.square_large(m, r, dtype="bf16", seed=1001)
+    Md = torch.from_numpy(prob.M.view(np.int16)).view(torch.bfloat16).cuda()
+    hbm, src = peaks()
+    with B.Context(0, profile=True) as ctx:
+        for _ in range(args.warmup):
+            B.opt_full_torch(ctx, Md, r, tol=tol, max_iter=cap, precision=B.PREC_MIXED)
+        torch.cuda.synchronize()
+        ctx.stats(reset=True)
+        iters = []
+        with ClockSampler(0) as clk:
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                sol = B.opt_full_torch(ctx, Md, r, tol=tol, max_iter=cap, precision=B.PREC_MIXED)
+                iters.append(sol.iters)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        st = ctx.stats()
+        # e2e: the same call with host buffers (H2D of M and D2H of U, B, V inside the timed region)
+        Mh = torch.from_numpy(prob.M.view(np.int16)).pin_memory()
+        U = torch.empty((m, r), dtype=torch.float64).pin_memory()
+        Bh = torch.empty((r, r), dtype=torch.float64).pin_memory()
+        V = torch.empty((n, r), dtype=torch.float64).pin_memory()
+        hp = B.OptFullProblem(m=m, n=n, ldm=n, r=r, m_dtype=B.BF16, M=Mh.data_ptr(), V0=None, B0=None, tol=tol,
+                              max_iter=cap, precision=B.PREC_MIXED, mem=B.MEM_HOST)
+        hr = B.OptFullResult(U=U.data_ptr(), B=Bh.data_ptr(), V=V.data_ptr())
+        ctx.opt_full(hp, hr)
+        t1 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            if ctx.opt_full(hp, hr) != B.OK:
+                raise RuntimeError(ctx.last_error())
+        e2e = args.e2e_steps / (time.perf_counter() - t1)
+    pp, wp = st[B.STAT_PPASS], st[B.STAT_WPASS]
+    p_ms = pp["total_ms"] / max(1, pp["timed"])
+    w_ms = wp["total_ms"] / max(1, wp["timed"])
+    achieved = (pp["bytes"] / max(1, pp["timed"])) / (p_ms * 1e-3) / 1e9
+    line = {"metric": "TSVDs/s", "value": args.steps / dt, "unit": "TSVDs/s", "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True,
+            "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": f"square{m}_r{r}_bf16_opt_full", "m": m, "n": n, "r": r, "storage": "bf16",
+                       "precision": "mixed", "stop": f"||B_i - B_(i-1)||_F <= {tol} ||B_i||_F", "max_iter": cap,
+                       "iters_per_step": sorted(set(iters)), "l2": f"M {m * n * 2 >> 20} MB, larger than L2; no flush"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "kernel": "P pass (ppass_tc_kernel)", "bytes_per_element": 2.0,
+                         "avg_launch_ms": p_ms, "timed_launches": pp["timed"], "peak_source": f"{src} hbm_gbs",
+                         "wpass_avg_ms": w_ms, "wpass_frac": (wp["bytes"] / max(1, wp["timed"])) / (w_ms * 1e-3) / 1e9 / hbm,
+                         "rxr_avg_ms": st[B.STAT_RXR]["total_ms"] / max(1, st[B.STAT_RXR]["timed"])},
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e, "unit": "TSVDs/s", "h2d_bytes_per_step": m * n * 2,
+                    "d2h_bytes_per_step": 8 * (m * r + r * r + n * r)},
+            "gpu_launches": st[B.STAT_ALL]["launches"]}
+    if not args.no_cpu_baseline:
+        # the oracle's Algorithm 4 on the same full-size matrix (float64 copy of the stored values),
+        # for the iteration count the GPU took: a few seconds of BLAS-bound CPU work
+        from oracle import fradm as O
+        Ms = prob.values_f64()
+        k = int(np.median(iters))
+        t2 = time.perf_counter()
+        O.fixed_rank_opt_full(Ms, None, np.eye(r), np.eye(n, r), k)
+        dts = time.perf_counter() - t2
+        del Ms
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        line["cpu_baseline"] = {"value": 1.0 / dts, "unit": "TSVDs/s", "cores": cores, "kind": "oracle",
+                                "sample": f"one run of the FP64 oracle's Algorithm 4 on the same {m}x{n} matrix, "
+                                          f"{k} iterations ({dts:.1f} s)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_setup()
     if rank != 0:
@@ -292,6 +385,8 @@ def main():
                     help="do not time kernels with events (no roofline; for measuring the profiling cost)")
     ap.add_argument("--serving", action="store_true",
                     help="supplementary: the serving-stream workload (submit/poll slots vs per-problem solves)")
+    ap.add_argument("--opt-full", action="store_true",
+                    help="supplementary: FixedRankOptFull (Algorithm 4) as a TSVD of the benchmark matrix")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--budget-gb", type=int, default=64)
@@ -306,6 +401,8 @@ def main():
         return run_reference(args)
     if args.serving:
         return run_serving(args)
+    if args.opt_full:
+        return run_opt_full(args)
 
     import numpy as np
     import torch
