@@ -352,6 +352,181 @@ def run_opt_full(args):
     return 0
 
 
+# The other workloads of the benchmark recipe, one supplementary JSON line each (`--config NAME`).
+OTHER_CONFIGS = {
+    "square500_r25_f64": "500 x 500, r = 25, 10% outliers in [-50, 50], float64 storage, float64 path",
+    "square16384_r64_f32_fp64": "16384 x 16384, r = 64, 5% outliers in [-50, 50], float32 storage, float64 path",
+    "photometric_1048576x40_r3": "1024^2 pixels x 40 images, r = 3, float32 storage, mixed path (float32 sweep)",
+    "affinity_32768_r20_nys2048": "32768^2 symmetric affinity, 20 clusters, 3% outliers, bfloat16 storage, "
+                                  "FR-Nys with l = 2048 sampled columns, mixed path",
+}
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA per clock x 2 flops x max SM clock
+
+
+def affinity_device(n: int, k: int, seed: int, p_out: float = 0.03):
+    """The affinity recipe generated on the device with torch's seeded generator (the float64
+    numpy generator needs tens of GB of host memory at n = 32768): cluster labels shuffled,
+    within 0.8 + N(0, 0.05^2), across 0.05 + N(0, 0.02^2), noise mirrored across the diagonal,
+    3% symmetric additive outliers U[0, 1]; bfloat16 storage.  Same distribution as
+    synth.affinity, different bits."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    sizes = [n // k + (1 if c < n % k else 0) for c in range(k)]
+    labels = torch.repeat_interleave(torch.arange(k, device="cuda"), torch.tensor(sizes, device="cuda"))
+    labels = labels[torch.randperm(n, generator=g, device="cuda")]
+    A = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    out = torch.empty((n, n), dtype=torch.bfloat16, device="cuda")
+    blk = 4096
+    for i0 in range(0, n, blk):  # upper triangle of the noisy block pattern, row block by row block
+        same = labels[i0:i0 + blk, None] == labels[None, :]
+        noise = torch.randn((min(blk, n - i0), n), generator=g, device="cuda")
+        A[i0:i0 + blk] = torch.where(same, 0.8 + 0.05 * noise, 0.05 + 0.02 * noise)
+        hit = torch.rand((min(blk, n - i0), n), generator=g, device="cuda") < p_out
+        d = torch.arange(min(blk, n - i0), device="cuda")
+        hit[d, i0 + d] = False  # no outliers on the diagonal (the recipe draws them off it)
+        A[i0:i0 + blk] += torch.where(hit, torch.rand((min(blk, n - i0), n), generator=g, device="cuda"), 0.0)
+    for i0 in range(0, n, blk):  # mirror: row block i0 takes column block i0 of the upper triangle
+        rows = slice(i0, min(n, i0 + blk))
+        up = torch.triu(A[rows], diagonal=i0)  # entries with j >= i
+        low = torch.tril(A[:, rows].T, diagonal=i0 - 1)  # entries with j < i, from rows j's upper part
+        out[rows] = (up + low).to(torch.bfloat16)
+    del A
+    return out
+
+
+def run_config(args):
+    """Solves/s of one of the other workloads (device-resident inputs, CUDA events on the
+    library stream), the sweep against its roofline (HBM for the float32 / bfloat16 sweeps,
+    FP64 ALU for the float64 path), the oracle on a bounded sample, and the host-buffer call."""
+    import numpy as np
+    import torch
+    from paper_1503_03004_gb300 import binding as B, synth
+    from oracle import fradm as O
+    torch.cuda.set_device(0)
+    name = args.config
+    nys_l, perm = 0, None
+    if name == "square500_r25_f64":
+        prob, prec, mu0, s_dtype = synth.square_fp64_500(1000), B.PREC_FP64, 0.05, B.F64
+    elif name == "square16384_r64_f32_fp64":
+        prob, prec, mu0, s_dtype = synth.square_large(16384, 64, dtype="f32", seed=1001), B.PREC_FP64, 0.05, B.F32
+    elif name == "photometric_1048576x40_r3":
+        prob, prec, mu0, s_dtype = synth.photometric(seed=1002), B.PREC_MIXED, 1.0, B.F32
+    else:
+        prob, prec, mu0, s_dtype = None, B.PREC_MIXED, 1.0, B.F32
+        nys_l = 2048
+    if prob is not None:
+        M_dev = (torch.from_numpy(prob.M.view(np.int16)).view(torch.bfloat16) if prob.dtype == "bf16"
+                 else torch.from_numpy(prob.M)).cuda()
+        r = prob.r
+    else:
+        M_dev, r = affinity_device(32768, 20, seed=1003), 20
+        perm = torch.from_numpy(synth.row_permutation(32768, 5)).cuda()
+    m, n = M_dev.shape
+    code = {torch.float64: B.F64, torch.float32: B.F32, torch.bfloat16: B.BF16}[M_dev.dtype]
+    stream = torch.cuda.Stream()
+    ctx = B.Context(0, stream=stream.cuda_stream, profile=True)
+    f64 = dict(dtype=torch.float64, device="cuda")
+    U, Bm, V = (None, None, None) if nys_l else (torch.empty((m, r), **f64), torch.empty((r, r), **f64),
+                                                  torch.empty((n, r), **f64))
+    sd = torch.float64 if s_dtype == B.F64 else torch.float32
+    S = torch.empty((m, n), dtype=sd, device="cuda")
+    kw = dict(m=m, n=n, r=r, m_dtype=code, mu0=mu0, rho=1.5, tol=1e-9, max_iter=300, precision=prec, nys_l=nys_l)
+    p = B.make_problem(M_ptr=M_dev.data_ptr(), nys_perm_ptr=perm.data_ptr() if perm is not None else 0, **kw)
+    res = B.make_result(U_ptr=U.data_ptr() if U is not None else 0, B_ptr=Bm.data_ptr() if Bm is not None else 0,
+                        V_ptr=V.data_ptr() if V is not None else 0, S_ptr=S.data_ptr(), s_dtype=s_dtype, lds=n)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        if ctx.solve(p, res) != B.OK:
+            raise RuntimeError(ctx.last_error())
+    iters = res.iters
+    ctx.stats(reset=True)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            if ctx.solve(p, res) != B.OK:
+                raise RuntimeError(ctx.last_error())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = ctx.stats(reset=True)
+    sw = st[B.STAT_SWEEP]
+    hbm, src = peaks()
+    avg = sw["total_ms"] / max(1, sw["timed"])
+    if prec == B.PREC_FP64:
+        # float64 sweep: L rebuild (2 r) and (L + Delta) V (2 r) flops per element of the sweep
+        achieved = 4 * pad_rank(r) * m * n / (avg * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "fused sweep (SIMT, float64)",
+                "flops_per_element": 4 * pad_rank(r), "avg_launch_ms": avg, "timed_launches": sw["timed"],
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2.07 GHz"}
+    else:
+        achieved = sw["bytes"] / max(1, sw["timed"]) / (avg * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": "fused sweep", "bytes_per_launch": sw["bytes"] / max(1, sw["timed"]),
+                "avg_launch_ms": avg, "timed_launches": sw["timed"], "peak_source": f"{src} hbm_gbs"}
+    roof["wpass_avg_ms"] = st[B.STAT_WPASS]["total_ms"] / max(1, st[B.STAT_WPASS]["timed"])
+    roof["rxr_avg_ms"] = st[B.STAT_RXR]["total_ms"] / max(1, st[B.STAT_RXR]["timed"])
+    # e2e: host buffers (H2D of M and D2H of S and the factors inside the timed region)
+    Mh = M_dev.cpu().pin_memory()
+    Sh = torch.empty((m, n), dtype=sd).pin_memory()
+    Uh, Bh, Vh = (np.empty((m, r)), np.empty((r, r)), np.empty((n, r))) if not nys_l else (None, None, None)
+    permh = perm.cpu() if perm is not None else None
+    ph = B.make_problem(M_ptr=Mh.data_ptr(), mem=B.MEM_HOST, nys_perm_ptr=permh.data_ptr() if permh is not None else 0,
+                        **kw)
+    rh = B.make_result(U_ptr=Uh.ctypes.data if Uh is not None else 0, B_ptr=Bh.ctypes.data if Bh is not None else 0,
+                       V_ptr=Vh.ctypes.data if Vh is not None else 0, S_ptr=Sh.data_ptr(), s_dtype=s_dtype, lds=n)
+    ctx.solve(ph, rh)
+    t1 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        if ctx.solve(ph, rh) != B.OK:
+            raise RuntimeError(ctx.last_error())
+    e2e = args.e2e_steps / (time.perf_counter() - t1)
+    ctx.close()
+    line = {"metric": "solves/s", "value": 1000.0 / ms, "unit": "solves/s", "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "f64" if prec == B.PREC_FP64 else "f32/f64", "data": "synthetic",
+            "config": {"workload": name, "recipe": OTHER_CONFIGS[name], "m": m, "n": n, "r": r, "nys_l": nys_l,
+                       "mu0": mu0, "rho": 1.5, "tol": 1e-9, "iters_per_solve": iters},
+            "roofline": roof, "clocks": clk.summary(),
+            "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": Mh.numel() * Mh.element_size(),
+                    "d2h_bytes_per_step": Sh.numel() * Sh.element_size() + (0 if nys_l else 8 * (m + n + r) * r)},
+            "gpu_launches": st[B.STAT_ALL]["launches"]}
+    if not args.no_cpu_baseline:
+        # the float64 oracle on a bounded sample of the same recipe, scaled to the full size by
+        # the element count (every step of both methods is O(elements) per iteration)
+        if name == "square500_r25_f64":
+            sp, scale, what = prob, 1.0, "the full 500x500 problem"
+            ref = lambda Ms: O.fr_adm(Ms, r, rho=1.5, mu0=mu0, tol=1e-9, max_iter=300)
+        elif name == "square16384_r64_f32_fp64":
+            sp = synth.planted(2048, 2048, 64, p=0.05, amp=50.0, seed=1001, dtype="f32")
+            scale, what = (m * n) / 2048 ** 2, "a 2048x2048 r=64 sample, scaled by m*n"
+            ref = lambda Ms: O.fr_adm(Ms, r, rho=1.5, mu0=mu0, tol=1e-9, max_iter=300)
+        elif name == "photometric_1048576x40_r3":
+            sp = synth.photometric(side=256, seed=1002)
+            scale, what = m / 256 ** 2, "a 256^2-pixel x 40 sample of the recipe, scaled by m"
+            ref = lambda Ms: O.fr_adm(Ms, r, rho=1.5, mu0=mu0, tol=1e-9, max_iter=300)
+        else:
+            sp = synth.affinity(n=4096, k=20, seed=1003, dtype="bf16")
+            scale, what = (m / 4096) ** 2, "n=4096, l=256 (the same l/n), scaled by n^2"
+            sperm = synth.row_permutation(4096, 5)
+            ref = lambda Ms: O.fr_nys(Ms, r, 256, sperm, rho=1.5, mu0=mu0, tol=1e-9, max_iter=300)
+        Ms = sp.values_f64()
+        t2 = time.perf_counter()
+        ref(Ms)
+        dts = time.perf_counter() - t2
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        line["cpu_baseline"] = {"value": 1.0 / (dts * scale), "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                "sample": f"one FP64 oracle solve of {what} ({dts:.1f} s)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def pad_rank(r: int) -> int:
+    return 8 if r <= 8 else 16 if r <= 16 else 32 if r <= 32 else 64
+
+
 def run_reference(args):
     rank, world, _ = dist_setup()
     if rank != 0:
@@ -387,6 +562,8 @@ def main():
                     help="supplementary: the serving-stream workload (submit/poll slots vs per-problem solves)")
     ap.add_argument("--opt-full", action="store_true",
                     help="supplementary: FixedRankOptFull (Algorithm 4) as a TSVD of the benchmark matrix")
+    ap.add_argument("--config", choices=sorted(OTHER_CONFIGS),
+                    help="supplementary: one of the other workloads of the recipe")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--budget-gb", type=int, default=64)
@@ -403,6 +580,8 @@ def main():
         return run_serving(args)
     if args.opt_full:
         return run_opt_full(args)
+    if args.config:
+        return run_config(args)
 
     import numpy as np
     import torch

@@ -72,7 +72,7 @@ void iteration(const Shape& s, Buffers& b, bool fp64, bool first, cudaStream_t s
   NA_CUDA(launch_rxr(s, b, true, st));
   NA_CUDA(launch_apply_v(s, b, fp64, st));
   NA_CUDA(launch_sweep(s, b, fp64, u_new, st));
-  NA_CUDA(launch_iter_end(s, b, st));
+  NA_CUDA(launch_iter_end(s, b, fp64, st));
   NA_CUDA(launch_gram_p(s, b, fp64, true, st));
   b.u_cur = u_new;
   std::swap(b.Y[0], b.Y[1]);

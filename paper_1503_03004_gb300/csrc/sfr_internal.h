@@ -48,6 +48,8 @@ struct Shape {
   int gp_blocks;        // ceil(m / gram_rows)
   int gw_blocks;        // ceil(n / gram_rows)
   int resid_parts;      // residual partials written by one sweep
+  int num_sms;          // SMs of the device (grid sizing of the persistent-style kernels)
+  int mx_grid_x;        // row-block CTAs of the mixed-path SIMT sweep (64-row blocks, grid-stride)
   int q_ctas;           // > 0: persistent tensor-core sweep over this many CTAs, whose Q partials per
                         // 128-row block are the CTAs owning its tiles (tc_q_slots); nsplit = max slots
 };
@@ -113,7 +115,7 @@ cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first
 cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st);
 cudaError_t launch_apply_v(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st);
 cudaError_t launch_sweep(const Shape& s, const Buffers& b, bool fp64, int u_cur, cudaStream_t st);
-cudaError_t launch_iter_end(const Shape& s, const Buffers& b, cudaStream_t st);
+cudaError_t launch_iter_end(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st);
 cudaError_t launch_finalize(const Shape& s, const Buffers& b, bool fp64, int u_cur, void* S, sfr_dtype s_dtype,
                             int64_t lds, void* L, cudaStream_t st);  // Y is bfloat16 (ld t.ldy) when b.tc
 // Algorithm 4 (FixedRankOptFull): Qpart = split partials of M V (SIMT), the end-of-iteration

@@ -104,7 +104,9 @@ Shape plan_shape(int64_t m, int64_t n, int64_t ldm, int r, int num_sms) {
   const int64_t target = 2LL * num_sms;
   s.sweep_grid_x = (int)((m + kSweepBM - 1) / kSweepBM);
   int64_t tiles = (n + kSweepBN - 1) / kSweepBN;
-  int64_t ns = std::max<int64_t>(1, std::min<int64_t>(tiles, (target + s.sweep_grid_x - 1) / s.sweep_grid_x));
+  // column splits: enough (64-row block, split) pairs for four CTAs per SM
+  const int64_t nrb64 = (m + 63) / 64;
+  int64_t ns = std::max<int64_t>(1, std::min<int64_t>(tiles, (4LL * num_sms + nrb64 - 1) / nrb64));
   int64_t tps = (tiles + ns - 1) / ns;
   s.cols_per_split = (int)(tps * kSweepBN);
   s.nsplit = (int)((n + s.cols_per_split - 1) / s.cols_per_split);
@@ -116,12 +118,18 @@ Shape plan_shape(int64_t m, int64_t n, int64_t ldm, int r, int num_sms) {
   s.rows_per_chunk = (int)(((rtpc * kWBM) + 63) / 64 * 64);
   s.nchunk = (int)((m + s.rows_per_chunk - 1) / s.rows_per_chunk);
   s.gram_rows = kGramRows;
-  // thin kernels loop over 64-row tiles with at most one CTA per SM, which bounds the
-  // number of r x r partials the projector kernels reduce
-  s.gp_blocks = (int)std::min<int64_t>((m + kGramRows - 1) / kGramRows, num_sms);
-  s.gw_blocks = (int)std::min<int64_t>((n + kGramRows - 1) / kGramRows, num_sms);
+  // thin kernels loop over 64-row tiles with at most four CTAs per SM (latency hiding for tall
+  // matrices), which bounds the number of r x r partials the projector kernels reduce
+  auto thin_ctas = [&](int64_t rows) {  // one CTA per SM, four for tall thin matrices
+    const int64_t tiles = (rows + kGramRows - 1) / kGramRows;
+    return (int)std::min<int64_t>(tiles, tiles >= 4LL * num_sms ? 4LL * num_sms : num_sms);
+  };
+  s.gp_blocks = thin_ctas(m);
+  s.gw_blocks = thin_ctas(n);
   s.resid_parts = s.sweep_grid_x * s.nsplit;
   s.q_ctas = 0;
+  s.num_sms = num_sms;
+  s.mx_grid_x = (int)std::max<int64_t>(1, std::min<int64_t>(nrb64, (8LL * num_sms + s.nsplit - 1) / s.nsplit));
   return s;
 }
 
@@ -293,7 +301,7 @@ struct Solver {
     timed_launch(slot, 3, [&] { return launch_rxr(s, b, true, st, fp64); });   // T_V, B_bar, T_C
     SFR_CUDA(launch_apply_v(s, b, fp64, st));                                 // V_bar, C
     timed_launch(slot, 0, [&] { return launch_sweep(s, b, fp64, u_new, st); });  // S/Y steps, Delta, next P
-    SFR_CUDA(launch_iter_end(s, b, st));                                      // residual, mu, stop test
+    SFR_CUDA(launch_iter_end(s, b, fp64, st));                                // residual, mu, stop test
     SFR_CUDA(launch_gram_p(s, b, fp64, true, st));                            // P = sum of partials, G_P
     kernels += first ? 11 : 12;  // as on the tensor-core path below
     b.u_cur = u_new;
@@ -321,7 +329,7 @@ struct Solver {
     timed_launch(slot, 0, [&] {
       return tc_launch_sweep(s, maps, b.t, y_in, static_cast<float*>(b.Qpart), b.resid_part, b.st, st);
     });
-    SFR_CUDA(launch_iter_end(s, b, st));
+    SFR_CUDA(launch_iter_end(s, b, false, st));
     // P_{k+1} = U_bar B_bar + Delta V_bar  (L V_bar = U_bar B_bar since V_bar^T V_bar = I)
     SFR_CUDA(launch_gram_p(s, b, false, true, st, b.U[u_new], b.B));
     // launches: projector 2 + 2 (partial sums, cluster kernel), transforms 2, W pass 1, W final

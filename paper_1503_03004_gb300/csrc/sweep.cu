@@ -15,6 +15,7 @@
 //     Delta_{k+1} = Y_{k+1} (1/mu_k + 1/mu_{k+1}) - Y_k / mu_k,
 // so the sweep writes Delta and accumulates P_{k+1} = X_{k+1} V_{k+1} row by row,
 // and the second pass forms X_{k+1}^T U = C (U_old^T U) + Delta^T U with L = U_old C^T.
+#include <algorithm>
 #include <type_traits>
 
 #include "sfr_internal.h"
@@ -197,6 +198,7 @@ __global__ void __launch_bounds__(256) thin_gram_kernel(const TC* __restrict__ p
         np = min(nparts, tc_q_slots(i0 / 128, q_tiles, nblk * q_tiles, q_ctas));
       }
       load_tile<TC, RP>(parts, i0, rows, t, v);
+#pragma unroll 4
       for (int s = 1; s < np; ++s) {
         TC w[TileIdx<RP>::PER];
         load_tile<TC, RP>(parts + s * part_stride, i0, rows, t, w);
@@ -617,12 +619,612 @@ __global__ void __launch_bounds__(256) sweep_kernel(const TMs* __restrict__ M, i
   if (t == 0) resid_part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = resid;
 }
 
+// ---------------------------------------------------------------- mixed-path SIMT passes (r <= 32)
+// Float32 versions of the sweep and the W pass for the mixed path when the tensor-core kernels do
+// not apply (r <= 32, or M not bfloat16).  The work per element is small (2 r FMAs in the sweep,
+// r in the W pass), so these are built for bandwidth: 128-bit loads and stores along rows, L and
+// the thin products register-blocked (2 x 8 and 2 x r/8 per thread) so that shared-memory
+// operands are mostly broadcasts, and CTAs that loop over row blocks (the C / V tile stays
+// resident when a split is one tile wide, as for tall-skinny M).
+constexpr int kMxBM = 64, kMxBN = 64, kMxLDX = kMxBN + 4;
+
+// 4 consecutive elements of row-major storage as float, j0 a multiple of 4 (VEC: one aligned
+// vector load; else scalar loads of the valid ones, 0 past `lim` columns).
+template <typename T, bool VEC>
+__device__ __forceinline__ void ld4(const T* __restrict__ p, int lim, float (&v)[4]) {
+  if constexpr (VEC) {
+    if constexpr (std::is_same<T, float>::value) {
+      const float4 w = *reinterpret_cast<const float4*>(p);
+      v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
+    } else if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+      const uint2 w = *reinterpret_cast<const uint2*>(p);
+      v[0] = __uint_as_float(w.x << 16); v[1] = __uint_as_float(w.x & 0xFFFF0000u);
+      v[2] = __uint_as_float(w.y << 16); v[3] = __uint_as_float(w.y & 0xFFFF0000u);
+    } else {
+      const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+      v[0] = (float)a.x; v[1] = (float)a.y; v[2] = (float)b.x; v[3] = (float)b.y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] = c < lim ? ld_as<float, T>(p + c) : 0.f;
+  }
+}
+
+__device__ __forceinline__ void st4(float* __restrict__ p, int lim, const float (&v)[4], bool vec) {
+  if (vec) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (c < lim) p[c] = v[c];
+  }
+}
+
+// Sweep (Algorithm 1 S- and Y-steps, next P), float32 arithmetic, float32 Y and Delta (ld n).
+// CTA: column split blockIdx.y, 64-row blocks blockIdx.x, blockIdx.x + gridDim.x, ...
+// Phase A: thread (tr, tc) = (t / 8, t % 8) forms L for rows 2 tr, 2 tr + 1 and columns
+// 8 tc .. 8 tc + 7 of the tile, loads M and Y_k (vector loads issued before the L products),
+// writes Y_{k+1}, Delta and X = L + Delta (into shared memory).  Phase B: thread (qr, qa) adds
+// X V for rows 2 qr, 2 qr + 1 and ranks qa r/8 .. into registers; the Q partial of a row block is
+// stored once.  One residual partial per CTA (slot blockIdx.y * gridDim.x + blockIdx.x).
+template <typename TMs, int RP, bool VEC>
+__global__ void __launch_bounds__(256) sweep_mx_kernel(const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm,
+                                                       const float* __restrict__ Yin, float* __restrict__ Yout,
+                                                       float* __restrict__ D, const float* __restrict__ U,
+                                                       const float* __restrict__ C, const float* __restrict__ V,
+                                                       float* __restrict__ Qpart, int cols_per_split,
+                                                       double* __restrict__ resid_part, const DevState* st) {
+  if (stopped(st)) return;
+  constexpr int BM = kMxBM, BN = kMxBN, QA = RP / 8;
+  __shared__ __align__(16) float UsT[RP][BM];
+  __shared__ __align__(16) float CsT[RP][BN];
+  __shared__ __align__(16) float Vs[BN][RP];
+  __shared__ __align__(16) float Xs[BM][kMxLDX];
+  __shared__ double red[32];
+  const double mu_d = st->mu, mu_next = fmin(st->mu_max, st->rho * mu_d);
+  const float mu = (float)mu_d, inv_mu = (float)(1.0 / mu_d), dcoef = (float)(1.0 / mu_d + 1.0 / mu_next);
+  const int64_t jbeg = (int64_t)blockIdx.y * cols_per_split;
+  const int64_t jend = min(n, jbeg + cols_per_split);
+  const bool one_tile = jend - jbeg <= BN;
+  const int t = threadIdx.x, tr = t >> 3, tc = t & 7;
+  const int64_t nrb = (m + BM - 1) / BM;
+
+  double resid_acc = 0.0;
+  auto load_cv = [&](int64_t j0) {  // C^T and V tiles of columns j0 .. j0 + 63 (0 past jend)
+    for (int e = t; e < BN * RP; e += blockDim.x) {
+      const int jj = e / RP, a = e % RP;
+      const int64_t j = j0 + jj;
+      const bool in = j < jend;
+      CsT[a][jj] = in ? C[j * RP + a] : 0.f;
+      Vs[jj][a] = in ? V[j * RP + a] : 0.f;
+    }
+  };
+  if (one_tile) load_cv(jbeg);
+
+  for (int64_t rb = blockIdx.x; rb < nrb; rb += gridDim.x) {
+    const int64_t i0 = rb * BM;
+    __syncthreads();  // the previous row block's UsT / Xs readers are done
+    for (int e = t; e < BM * RP; e += blockDim.x) {
+      const int ii = e / RP, a = e % RP;
+      const int64_t i = i0 + ii;
+      UsT[a][ii] = i < m ? U[i * RP + a] : 0.f;
+    }
+    float q[2][QA];
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+      for (int k = 0; k < QA; ++k) q[x][k] = 0.f;
+    float resid = 0.f;
+    for (int64_t j0 = jbeg; j0 < jend; j0 += BN) {
+      if (!one_tile) {
+        __syncthreads();  // previous tile's CsT / Vs / Xs consumed
+        load_cv(j0);
+      }
+      // global loads of this thread's M and Y_k first (independent of the L products)
+      float mv[2][8], yv[2][8];
+      const int64_t jc = j0 + 8 * tc;
+      const int lim = (int)(jend - jc < 8 ? jend - jc : 8);  // valid columns among the 8 (may be <= 0)
+#pragma unroll
+      for (int x = 0; x < 2; ++x) {
+        const int64_t i = i0 + 2 * tr + x;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float a4[4], b4[4];
+          if (i < m && lim > 4 * h) {
+            ld4<TMs, VEC>(M + i * ldm + jc + 4 * h, lim - 4 * h, a4);
+            ld4<float, VEC>(Yin + i * n + jc + 4 * h, lim - 4 * h, b4);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) a4[c] = b4[c] = 0.f;
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            mv[x][4 * h + c] = a4[c];
+            yv[x][4 * h + c] = b4[c];
+          }
+        }
+      }
+      __syncthreads();  // UsT (first tile) and CsT / Vs visible
+      float l[2][8];
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) l[x][c] = 0.f;
+#pragma unroll 8
+      for (int a = 0; a < RP; ++a) {
+        const float2 u = *reinterpret_cast<const float2*>(&UsT[a][2 * tr]);
+        const float4 c0 = *reinterpret_cast<const float4*>(&CsT[a][8 * tc]);
+        const float4 c1 = *reinterpret_cast<const float4*>(&CsT[a][8 * tc + 4]);
+        const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          l[0][c] = fmaf(u.x, cv[c], l[0][c]);
+          l[1][c] = fmaf(u.y, cv[c], l[1][c]);
+        }
+      }
+#pragma unroll
+      for (int x = 0; x < 2; ++x) {
+        const int64_t i = i0 + 2 * tr + x;
+        const bool row_ok = i < m;
+        float yn[8], dd[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const bool ok = row_ok && c < lim;
+          const float y = yv[x][c];
+          const float z = mv[x][c] - l[x][c] + y * inv_mu;
+          const float y1 = fminf(1.f, fmaxf(-1.f, mu * z));
+          const float d = y1 * dcoef - y * inv_mu;
+          const float dy = y1 - y;
+          resid += ok ? dy * dy : 0.f;
+          yn[c] = y1;
+          dd[c] = d;
+          l[x][c] = ok ? l[x][c] + d : 0.f;  // X = L + Delta (0 outside the matrix)
+        }
+        *reinterpret_cast<float4*>(&Xs[2 * tr + x][8 * tc]) = make_float4(l[x][0], l[x][1], l[x][2], l[x][3]);
+        *reinterpret_cast<float4*>(&Xs[2 * tr + x][8 * tc + 4]) = make_float4(l[x][4], l[x][5], l[x][6], l[x][7]);
+        if (row_ok)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (lim <= 4 * h) continue;
+            const float y4[4] = {yn[4 * h], yn[4 * h + 1], yn[4 * h + 2], yn[4 * h + 3]};
+            const float d4[4] = {dd[4 * h], dd[4 * h + 1], dd[4 * h + 2], dd[4 * h + 3]};
+            st4(Yout + i * n + jc + 4 * h, lim - 4 * h, y4, VEC);
+            st4(D + i * n + jc + 4 * h, lim - 4 * h, d4, VEC);
+          }
+      }
+      __syncthreads();  // Xs complete
+      // phase B: q += X V over the tile's columns
+#pragma unroll 4
+      for (int jj = 0; jj < BN; ++jj) {
+        const float x0 = Xs[2 * tr][jj], x1 = Xs[2 * tr + 1][jj];
+        float v[QA];
+        if constexpr (QA == 4) {
+          const float4 w = *reinterpret_cast<const float4*>(&Vs[jj][4 * tc]);
+          v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
+        } else if constexpr (QA == 2) {
+          const float2 w = *reinterpret_cast<const float2*>(&Vs[jj][2 * tc]);
+          v[0] = w.x; v[1] = w.y;
+        } else {
+          v[0] = Vs[jj][tc];
+        }
+#pragma unroll
+        for (int k = 0; k < QA; ++k) {
+          q[0][k] = fmaf(x0, v[k], q[0][k]);
+          q[1][k] = fmaf(x1, v[k], q[1][k]);
+        }
+      }
+    }
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+      const int64_t i = i0 + 2 * tr + x;
+      if (i < m)
+#pragma unroll
+        for (int k = 0; k < QA; ++k) Qpart[((int64_t)blockIdx.y * m + i) * RP + QA * tc + k] = q[x][k];
+    }
+    resid_acc += (double)resid;
+  }
+  resid_acc = block_sum(resid_acc, red);
+  if (t == 0) resid_part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = resid_acc;
+}
+
+// cp.async (16-byte, L2 only) global -> shared copy; src_bytes < 16 zero-fills the rest.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// The sweep above with the M and Y_k tiles double-buffered in shared memory by cp.async: the copy
+// of the CTA's next (row block, column tile) pair is in flight while the current one is
+// computed, so HBM latency is hidden without holding the tiles in registers.  Needs the vector
+// conditions (n % 4 == 0, 16-byte aligned rows of M) and float32 or bfloat16 M.
+template <typename TMs, int RP>
+__global__ void __launch_bounds__(256) sweep_mxp_kernel(const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm,
+                                                        const float* __restrict__ Yin, float* __restrict__ Yout,
+                                                        float* __restrict__ D, const float* __restrict__ U,
+                                                        const float* __restrict__ C, const float* __restrict__ V,
+                                                        float* __restrict__ Qpart, int cols_per_split,
+                                                        double* __restrict__ resid_part, int r, const DevState* st) {
+  if (stopped(st)) return;
+  constexpr int BM = kMxBM, BN = kMxBN, QA = RP / 8, EPC = 16 / (int)sizeof(TMs);  // M elements per 16 B
+  constexpr int LDU = RP + 4;  // padded U rows: the four rows a warp reads fall in different banks
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Ys = reinterpret_cast<float*>(smem_raw);                     // [2][BM][BN]
+  TMs* Ms = reinterpret_cast<TMs*>(Ys + 2 * BM * BN);                 // [2][BM][BN]
+  float* Us = reinterpret_cast<float*>(Ms + 2 * BM * BN);             // [2][BM][LDU]: U rows, by row-block parity
+  float* CsT = Us + 2 * BM * LDU;                                     // [RP][BN]
+  float* Vs = CsT + RP * BN;                                          // [BN][RP]
+  float* Xs = Vs + BN * RP;                                           // [BM][kMxLDX]
+  __shared__ double red[32];
+  const double mu_d = st->mu, mu_next = fmin(st->mu_max, st->rho * mu_d);
+  const float mu = (float)mu_d, inv_mu = (float)(1.0 / mu_d), dcoef = (float)(1.0 / mu_d + 1.0 / mu_next);
+  const int64_t jbeg = (int64_t)blockIdx.y * cols_per_split;
+  const int64_t jend = min(n, jbeg + cols_per_split);
+  const int ntile = (int)((jend - jbeg + BN - 1) / BN);
+  const int t = threadIdx.x, tr = t >> 3, tc = t & 7;
+  const int64_t nrb = (m + BM - 1) / BM;
+  const int64_t nmine = blockIdx.x < nrb ? (nrb - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t total = nmine * ntile;  // this CTA's (row block, tile) pairs, row block major
+
+  auto issue = [&](int64_t k) {  // cp.async of pair k into stage k & 1 (and its U rows on tile 0)
+    const int64_t rb = blockIdx.x + (k / ntile) * gridDim.x, i0 = rb * BM;
+    const int64_t j0 = jbeg + (k % ntile) * BN;
+    float* ys = Ys + (k & 1) * BM * BN;
+    TMs* ms = Ms + (k & 1) * BM * BN;
+    if (k % ntile == 0) {
+      float* us = Us + ((k / ntile) & 1) * BM * LDU;
+      for (int e = t; e < BM * (RP / 4); e += blockDim.x) {
+        const int ii = e / (RP / 4), cc = e % (RP / 4);
+        const int64_t i = i0 + ii;
+        cp_async16(us + ii * LDU + 4 * cc, i < m ? (const void*)(U + i * RP + 4 * cc) : (const void*)U, i < m ? 16 : 0);
+      }
+    }
+    for (int e = t; e < BM * (BN / 4); e += blockDim.x) {  // Y: 16-byte chunks of 4 floats
+      const int ii = e / (BN / 4), cc = e % (BN / 4);
+      const int64_t i = i0 + ii, j = j0 + 4 * cc;
+      const bool ok = i < m && j < jend;
+      cp_async16(ys + ii * BN + 4 * cc, ok ? (const void*)(Yin + i * n + j) : (const void*)Yin, ok ? 16 : 0);
+    }
+    for (int e = t; e < BM * (BN / EPC); e += blockDim.x) {  // M: 16-byte chunks
+      const int ii = e / (BN / EPC), cc = e % (BN / EPC);
+      const int64_t i = i0 + ii, j = j0 + EPC * cc;
+      const int64_t left = i < m ? jend - j : 0;
+      const int bytes = left <= 0 ? 0 : (left >= EPC ? 16 : (int)left * (int)sizeof(TMs));
+      cp_async16(ms + ii * BN + EPC * cc, bytes ? (const void*)(M + i * ldm + j) : (const void*)M, bytes);
+    }
+    cp_async_commit();
+  };
+  auto load_cv = [&](int64_t j0) {
+    for (int e = t; e < BN * RP; e += blockDim.x) {
+      const int jj = e / RP, a = e % RP;
+      const int64_t j = j0 + jj;
+      const bool in = j < jend;
+      CsT[a * BN + jj] = in ? C[j * RP + a] : 0.f;
+      Vs[jj * RP + a] = in ? V[j * RP + a] : 0.f;
+    }
+  };
+
+  if (total > 0) issue(0);
+  if (ntile == 1) load_cv(jbeg);
+  float q[2][QA];
+  float resid = 0.f;
+  double resid_acc = 0.0;
+  for (int64_t k = 0; k < total; ++k) {
+    const int64_t rb = blockIdx.x + (k / ntile) * gridDim.x, i0 = rb * BM;
+    const int tile = (int)(k % ntile);
+    const int64_t j0 = jbeg + (int64_t)tile * BN;
+    if (k + 1 < total) issue(k + 1); else cp_async_commit();  // keep one group per iteration
+    cp_async_wait1();  // pair k has landed (this thread's copies)
+    __syncthreads();   // everyone's copies visible; the previous pair's Xs / Vs readers are done
+    if (tile == 0) {
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int c = 0; c < QA; ++c) q[x][c] = 0.f;
+      resid = 0.f;
+    }
+    if (ntile > 1) {
+      load_cv(j0);
+      __syncthreads();
+    }
+    const float* us = Us + ((k / ntile) & 1) * BM * LDU;
+    // phase A: L for rows 2 tr, 2 tr + 1 and columns 8 tc .. 8 tc + 7 (ranks a < r)
+    float l[2][8];
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) l[x][c] = 0.f;
+#pragma unroll 4
+    for (int a = 0; a < r; ++a) {
+      const float2 u = make_float2(us[(2 * tr) * LDU + a], us[(2 * tr + 1) * LDU + a]);
+      const float4 c0 = *reinterpret_cast<const float4*>(&CsT[a * BN + 8 * tc]);
+      const float4 c1 = *reinterpret_cast<const float4*>(&CsT[a * BN + 8 * tc + 4]);
+      const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        l[0][c] = fmaf(u.x, cv[c], l[0][c]);
+        l[1][c] = fmaf(u.y, cv[c], l[1][c]);
+      }
+    }
+    const float* ys = Ys + (k & 1) * BM * BN;
+    const TMs* ms = Ms + (k & 1) * BM * BN;
+    const int64_t jc = j0 + 8 * tc;
+    const int lim = (int)(jend - jc < 8 ? jend - jc : 8);
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+      const int rr = 2 * tr + x;
+      const int64_t i = i0 + rr;
+      float mv[8], yv[8];
+      {
+        const float4 a0 = *reinterpret_cast<const float4*>(ys + rr * BN + 8 * tc);
+        const float4 a1 = *reinterpret_cast<const float4*>(ys + rr * BN + 8 * tc + 4);
+        yv[0] = a0.x; yv[1] = a0.y; yv[2] = a0.z; yv[3] = a0.w; yv[4] = a1.x; yv[5] = a1.y; yv[6] = a1.z; yv[7] = a1.w;
+      }
+      if constexpr (std::is_same<TMs, float>::value) {
+        const float4 a0 = *reinterpret_cast<const float4*>(ms + rr * BN + 8 * tc);
+        const float4 a1 = *reinterpret_cast<const float4*>(ms + rr * BN + 8 * tc + 4);
+        mv[0] = a0.x; mv[1] = a0.y; mv[2] = a0.z; mv[3] = a0.w; mv[4] = a1.x; mv[5] = a1.y; mv[6] = a1.z; mv[7] = a1.w;
+      } else {
+        const uint4 w = *reinterpret_cast<const uint4*>(ms + rr * BN + 8 * tc);
+        const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          mv[2 * c] = __uint_as_float(wv[c] << 16);
+          mv[2 * c + 1] = __uint_as_float(wv[c] & 0xFFFF0000u);
+        }
+      }
+      const bool row_ok = i < m;
+      float yn[8], dd[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const bool ok = row_ok && c < lim;
+        const float y = yv[c];
+        const float z = mv[c] - l[x][c] + y * inv_mu;
+        const float y1 = fminf(1.f, fmaxf(-1.f, mu * z));
+        const float d = y1 * dcoef - y * inv_mu;
+        const float dy = y1 - y;
+        resid += ok ? dy * dy : 0.f;
+        yn[c] = y1;
+        dd[c] = d;
+        l[x][c] = ok ? l[x][c] + d : 0.f;  // X = L + Delta (0 outside the matrix)
+      }
+      *reinterpret_cast<float4*>(&Xs[rr * kMxLDX + 8 * tc]) = make_float4(l[x][0], l[x][1], l[x][2], l[x][3]);
+      *reinterpret_cast<float4*>(&Xs[rr * kMxLDX + 8 * tc + 4]) = make_float4(l[x][4], l[x][5], l[x][6], l[x][7]);
+      if (row_ok)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (lim <= 4 * h) continue;
+          *reinterpret_cast<float4*>(Yout + i * n + jc + 4 * h) =
+              make_float4(yn[4 * h], yn[4 * h + 1], yn[4 * h + 2], yn[4 * h + 3]);
+          *reinterpret_cast<float4*>(D + i * n + jc + 4 * h) =
+              make_float4(dd[4 * h], dd[4 * h + 1], dd[4 * h + 2], dd[4 * h + 3]);
+        }
+    }
+    __syncthreads();  // Xs complete
+    const int jn = (int)(jend - j0 < BN ? jend - j0 : BN);  // valid columns of the tile
+#pragma unroll 4
+    for (int jj = 0; jj < jn; ++jj) {
+      const float x0 = Xs[(2 * tr) * kMxLDX + jj], x1 = Xs[(2 * tr + 1) * kMxLDX + jj];
+      float v[QA];
+      if constexpr (QA == 4) {
+        const float4 w = *reinterpret_cast<const float4*>(&Vs[jj * RP + 4 * tc]);
+        v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
+      } else if constexpr (QA == 2) {
+        const float2 w = *reinterpret_cast<const float2*>(&Vs[jj * RP + 2 * tc]);
+        v[0] = w.x; v[1] = w.y;
+      } else {
+        v[0] = Vs[jj * RP + tc];
+      }
+#pragma unroll
+      for (int c = 0; c < QA; ++c) {
+        q[0][c] = fmaf(x0, v[c], q[0][c]);
+        q[1][c] = fmaf(x1, v[c], q[1][c]);
+      }
+    }
+    if (tile == ntile - 1) {  // row block done: its Q partial and residual
+#pragma unroll
+      for (int x = 0; x < 2; ++x) {
+        const int64_t i = i0 + 2 * tr + x;
+        if (i < m)
+#pragma unroll
+          for (int c = 0; c < QA; ++c) Qpart[((int64_t)blockIdx.y * m + i) * RP + QA * tc + c] = q[x][c];
+      }
+      resid_acc += (double)resid;
+    }
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  resid_acc = block_sum(resid_acc, red);
+  if (t == 0) resid_part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = resid_acc;
+}
+
+template <typename TMs, int RP>
+constexpr size_t mxp_smem() {
+  return (size_t)2 * kMxBM * kMxBN * (4 + sizeof(TMs)) + (size_t)2 * kMxBM * (RP + 4) * 4 +
+         (size_t)RP * 2 * kMxBN * 4 + (size_t)kMxBM * kMxLDX * 4;
+}
+
+// W pass, float32: Wpart[c][j][:] = sum over the rows i of chunk c of src[i][j] U[i][:].  CTA:
+// 64 columns x a chunk of rows, in 32-row tiles (src and U tiles staged in shared memory with
+// vector loads); thread (wc, wa) = (t / 8, t % 8) accumulates columns 2 wc, 2 wc + 1 and ranks
+// wa r/8 .. in registers.
+template <typename TS, int RP, bool VEC>
+__global__ void __launch_bounds__(256) wpass_mx_kernel(const TS* __restrict__ src, int64_t lds, int64_t m, int64_t n,
+                                                       int rows_per_chunk, const float* __restrict__ U,
+                                                       float* __restrict__ Wpart, const DevState* st) {
+  if (stopped(st)) return;
+  constexpr int BR = 32, BN = kMxBN, QA = RP / 8;
+  __shared__ __align__(16) float Xs[BR][kMxLDX];
+  __shared__ __align__(16) float Us[BR][RP];
+  const int64_t j0 = (int64_t)blockIdx.x * BN;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
+  const int64_t r1 = min(m, r0 + rows_per_chunk);
+  const int t = threadIdx.x, wc = t >> 3, wa = t & 7;
+  const int lr = t >> 4, lq = t & 15;  // tile loads: rows lr and lr + 16, columns 4 lq .. 4 lq + 3
+  const int lim = (int)(n - (j0 + 4 * lq) < 4 ? n - (j0 + 4 * lq) : 4);
+  float acc[2][QA];
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int k = 0; k < QA; ++k) acc[x][k] = 0.f;
+  for (int64_t it = r0; it < r1; it += BR) {
+    float v[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t i = it + lr + 16 * h;
+      if (i < r1 && lim > 0) {
+        ld4<TS, VEC>(src + i * lds + j0 + 4 * lq, lim, v[h]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[h][c] = 0.f;
+      }
+    }
+    float uv[(BR * RP + 255) / 256];
+#pragma unroll
+    for (int q2 = 0; q2 < (BR * RP + 255) / 256; ++q2) {
+      const int e = t + 256 * q2, ii = e / RP, a = e % RP;
+      const int64_t i = it + ii;
+      uv[q2] = (e < BR * RP && i < r1) ? U[i * RP + a] : 0.f;
+    }
+    __syncthreads();  // previous tile consumed
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      *reinterpret_cast<float4*>(&Xs[lr + 16 * h][4 * lq]) = make_float4(v[h][0], v[h][1], v[h][2], v[h][3]);
+#pragma unroll
+    for (int q2 = 0; q2 < (BR * RP + 255) / 256; ++q2) {
+      const int e = t + 256 * q2;
+      if (e < BR * RP) Us[e / RP][e % RP] = uv[q2];
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ii = 0; ii < BR; ++ii) {
+      const float2 x = *reinterpret_cast<const float2*>(&Xs[ii][2 * wc]);
+      float u[QA];
+      if constexpr (QA == 4) {
+        const float4 w = *reinterpret_cast<const float4*>(&Us[ii][4 * wa]);
+        u[0] = w.x; u[1] = w.y; u[2] = w.z; u[3] = w.w;
+      } else if constexpr (QA == 2) {
+        const float2 w = *reinterpret_cast<const float2*>(&Us[ii][2 * wa]);
+        u[0] = w.x; u[1] = w.y;
+      } else {
+        u[0] = Us[ii][wa];
+      }
+#pragma unroll
+      for (int k = 0; k < QA; ++k) {
+        acc[0][k] = fmaf(x.x, u[k], acc[0][k]);
+        acc[1][k] = fmaf(x.y, u[k], acc[1][k]);
+      }
+    }
+  }
+#pragma unroll
+  for (int x = 0; x < 2; ++x) {
+    const int64_t j = j0 + 2 * wc + x;
+    if (j < n)
+#pragma unroll
+      for (int k = 0; k < QA; ++k) Wpart[((int64_t)blockIdx.y * n + j) * RP + QA * wa + k] = acc[x][k];
+  }
+}
+
+// The W pass above with cp.async staging: 32-row tiles of src and U in a 4-stage ring, three
+// tiles in flight while one is accumulated.  Needs the vector conditions (src rows 16-byte
+// aligned, n % 4 == 0) and float32 or bfloat16 src.
+constexpr int kWxStages = 4;
+template <typename TS, int RP>
+__global__ void __launch_bounds__(256) wpass_mxp_kernel(const TS* __restrict__ src, int64_t lds, int64_t m, int64_t n,
+                                                        int rows_per_chunk, const float* __restrict__ U,
+                                                        float* __restrict__ Wpart, const DevState* st) {
+  if (stopped(st)) return;
+  constexpr int BR = 32, BN = kMxBN, QA = RP / 8, EPC = 16 / (int)sizeof(TS);
+  constexpr int XS = BR * BN, US = BR * RP;  // elements per stage
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TS* Xs = reinterpret_cast<TS*>(smem_raw);                                  // [stages][BR][BN]
+  float* Us = reinterpret_cast<float*>(Xs + kWxStages * XS);                 // [stages][BR][RP]
+  const int64_t j0 = (int64_t)blockIdx.x * BN;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
+  const int64_t r1 = min(m, r0 + rows_per_chunk);
+  const int ntile = r1 > r0 ? (int)((r1 - r0 + BR - 1) / BR) : 0;
+  const int t = threadIdx.x, wc = t >> 3, wa = t & 7;
+  auto issue = [&](int k) {
+    const int64_t it = r0 + (int64_t)k * BR;
+    TS* xs = Xs + (k % kWxStages) * XS;
+    float* us = Us + (k % kWxStages) * US;
+    for (int e = t; e < BR * (BN / EPC); e += blockDim.x) {
+      const int ii = e / (BN / EPC), cc = e % (BN / EPC);
+      const int64_t i = it + ii, j = j0 + EPC * cc;
+      const int64_t left = i < r1 ? n - j : 0;
+      const int bytes = left <= 0 ? 0 : (left >= EPC ? 16 : (int)left * (int)sizeof(TS));
+      cp_async16(xs + ii * BN + EPC * cc, bytes ? (const void*)(src + i * lds + j) : (const void*)src, bytes);
+    }
+    for (int e = t; e < BR * (RP / 4); e += blockDim.x) {
+      const int ii = e / (RP / 4), cc = e % (RP / 4);
+      const int64_t i = it + ii;
+      cp_async16(us + ii * RP + 4 * cc, i < r1 ? (const void*)(U + i * RP + 4 * cc) : (const void*)U, i < r1 ? 16 : 0);
+    }
+    cp_async_commit();
+  };
+  float acc[2][QA];
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int c = 0; c < QA; ++c) acc[x][c] = 0.f;
+  for (int k = 0; k < kWxStages - 1; ++k) {
+    if (k < ntile) issue(k); else cp_async_commit();
+  }
+  for (int k = 0; k < ntile; ++k) {
+    if (k + kWxStages - 1 < ntile) issue(k + kWxStages - 1); else cp_async_commit();
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kWxStages - 1) : "memory");
+    __syncthreads();
+    const TS* xs = Xs + (k % kWxStages) * XS;
+    const float* us = Us + (k % kWxStages) * US;
+#pragma unroll 4
+    for (int ii = 0; ii < BR; ++ii) {
+      float x0, x1;
+      if constexpr (std::is_same<TS, float>::value) {
+        const float2 w = *reinterpret_cast<const float2*>(xs + ii * BN + 2 * wc);
+        x0 = w.x; x1 = w.y;
+      } else {
+        const uint32_t w = *reinterpret_cast<const uint32_t*>(xs + ii * BN + 2 * wc);
+        x0 = __uint_as_float(w << 16); x1 = __uint_as_float(w & 0xFFFF0000u);
+      }
+      float u[QA];
+      if constexpr (QA == 4) {
+        const float4 w = *reinterpret_cast<const float4*>(us + ii * RP + 4 * wa);
+        u[0] = w.x; u[1] = w.y; u[2] = w.z; u[3] = w.w;
+      } else if constexpr (QA == 2) {
+        const float2 w = *reinterpret_cast<const float2*>(us + ii * RP + 2 * wa);
+        u[0] = w.x; u[1] = w.y;
+      } else {
+        u[0] = us[ii * RP + wa];
+      }
+#pragma unroll
+      for (int c = 0; c < QA; ++c) {
+        acc[0][c] = fmaf(x0, u[c], acc[0][c]);
+        acc[1][c] = fmaf(x1, u[c], acc[1][c]);
+      }
+    }
+    __syncthreads();  // stage k % stages is refilled by the next iteration's issue
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+#pragma unroll
+  for (int x = 0; x < 2; ++x) {
+    const int64_t j = j0 + 2 * wc + x;
+    if (j < n)
+#pragma unroll
+      for (int c = 0; c < QA; ++c) Wpart[((int64_t)blockIdx.y * n + j) * RP + QA * wa + c] = acc[x][c];
+  }
+}
+
+template <typename TS, int RP>
+constexpr size_t wxp_smem() { return (size_t)kWxStages * 32 * (kMxBN * sizeof(TS) + RP * 4); }
+
 // ---------------------------------------------------------------- end of iteration (one CTA)
 // ||M - L - S||_F = ||Y_{k+1} - Y_k||_F / mu_k; continuation mu_{k+1} = min(mu_bar, rho mu_k).
 __global__ void iter_end_kernel(const double* __restrict__ resid_part, int count, DevState* st) {
   __shared__ double red[32];
   if (stopped(st)) return;
   double v = 0.0;
+#pragma unroll 8
   for (int c = threadIdx.x; c < count; c += blockDim.x) v += resid_part[c];
   v = block_sum(v, red);
   if (threadIdx.x == 0) {
@@ -792,6 +1394,13 @@ cudaError_t allow_smem(K kern, size_t bytes) {
 
 }  // namespace
 
+// Mixed path, r <= 32: the float32 passes above.  Vector loads need n % 4 == 0 and M rows on
+// 16-byte boundaries; otherwise the same kernels load element by element.
+static bool mx_vec(const Shape& s, const Buffers& b) {
+  const size_t es = b.m_dtype == SFR_F64 ? 8 : b.m_dtype == SFR_F32 ? 4 : 2;
+  return s.n % 4 == 0 && ((size_t)s.ldm * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(b.M) % 16) == 0;
+}
+
 cudaError_t launch_reduce_parts(const double* parts, int count, int rpsq, double* out, const DevState* dst,
                                 cudaStream_t st) {
   reduce_sq_kernel<<<cdiv(rpsq, 32), 256, 0, st>>>(parts, count, rpsq, out, dst);
@@ -863,6 +1472,41 @@ cudaError_t launch_apply_u(const Shape& s, const Buffers& b, bool fp64, bool fir
 
 cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first, int u_new, cudaStream_t st) {
   dim3 grid(s.wpass_grid_x, s.nchunk);
+  if (!fp64 && s.rp <= 32) {
+    const bool vec = first ? mx_vec(s, b) : s.n % 4 == 0;
+    return by_rank(s.rp, [&](auto rpc) {
+      constexpr int RP = decltype(rpc)::value;
+      if constexpr (RP > 32) {
+        return cudaErrorInvalidValue;
+      } else {
+        const float* U = static_cast<const float*>(b.U[u_new]);
+        float* Wp = static_cast<float*>(b.Wpart);
+        auto go = [&](auto kern, auto src, int64_t lds) {
+          kern<<<grid, 256, 0, st>>>(src, lds, s.m, s.n, s.rows_per_chunk, U, Wp, b.st);
+          return cudaGetLastError();
+        };
+        auto pipelined = [&](auto srcp, int64_t lds) {
+          using TS = std::remove_const_t<std::remove_pointer_t<decltype(srcp)>>;
+          auto kern = wpass_mxp_kernel<TS, RP>;
+          constexpr size_t sm = wxp_smem<TS, RP>();
+          cudaError_t e = allow_smem(kern, sm);
+          if (e != cudaSuccess) return e;
+          kern<<<grid, 256, sm, st>>>(srcp, lds, s.m, s.n, s.rows_per_chunk, U, Wp, b.st);
+          return cudaGetLastError();
+        };
+        if (first)
+          return by_mtype(b.m_dtype, b.M, [&](auto M) {
+            using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
+            if constexpr (!std::is_same<TMs, double>::value) {
+              if (vec) return pipelined(M, s.ldm);
+            }
+            return vec ? go(wpass_mx_kernel<TMs, RP, true>, M, s.ldm) : go(wpass_mx_kernel<TMs, RP, false>, M, s.ldm);
+          });
+        const float* Dp = static_cast<const float*>(b.D);
+        return vec ? pipelined(Dp, s.n) : go(wpass_mx_kernel<float, RP, false>, Dp, s.n);
+      }
+    });
+  }
   return by_prec(fp64, [&](auto tc) {
     using TC = decltype(tc);
     return by_rank(s.rp, [&](auto rpc) {
@@ -928,9 +1572,48 @@ cudaError_t launch_apply_v(const Shape& s, const Buffers& b, bool fp64, cudaStre
   });
 }
 
+static cudaError_t launch_sweep_mx(const Shape& s, const Buffers& b, int u_cur, cudaStream_t st) {
+  dim3 grid(s.mx_grid_x, s.nsplit);
+  const bool vec = mx_vec(s, b);
+  return by_rank(s.rp, [&](auto rpc) {
+    constexpr int RP = decltype(rpc)::value;
+    if constexpr (RP > 32) {
+      return cudaErrorInvalidValue;
+    } else {
+      return by_mtype(b.m_dtype, b.M, [&](auto M) {
+        using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
+        auto go = [&](auto kern) {
+          kern<<<grid, 256, 0, st>>>(M, s.m, s.n, s.ldm, static_cast<const float*>(b.Y[0]),
+                                     static_cast<float*>(b.Y[1]), static_cast<float*>(b.D),
+                                     static_cast<const float*>(b.U[u_cur]), static_cast<const float*>(b.C),
+                                     static_cast<const float*>(b.V), static_cast<float*>(b.Qpart), s.cols_per_split,
+                                     b.resid_part, b.st);
+          return cudaGetLastError();
+        };
+        if constexpr (!std::is_same<TMs, double>::value) {
+          if (vec) {
+            auto kern = sweep_mxp_kernel<TMs, RP>;
+            constexpr size_t sm = mxp_smem<TMs, RP>();
+            cudaError_t e = allow_smem(kern, sm);
+            if (e != cudaSuccess) return e;
+            kern<<<grid, 256, sm, st>>>(M, s.m, s.n, s.ldm, static_cast<const float*>(b.Y[0]),
+                                        static_cast<float*>(b.Y[1]), static_cast<float*>(b.D),
+                                        static_cast<const float*>(b.U[u_cur]), static_cast<const float*>(b.C),
+                                        static_cast<const float*>(b.V), static_cast<float*>(b.Qpart),
+                                        s.cols_per_split, b.resid_part, s.r, b.st);
+            return cudaGetLastError();
+          }
+        }
+        return vec ? go(sweep_mx_kernel<TMs, RP, true>) : go(sweep_mx_kernel<TMs, RP, false>);
+      });
+    }
+  });
+}
+
 cudaError_t launch_sweep(const Shape& s, const Buffers& b, bool fp64, int u_cur, cudaStream_t st) {
   // Y ping-pong: iteration k (0-based count of completed iterations) reads Y[k % 2] and writes
   // Y[(k + 1) % 2].  The host tracks k because graphs are replayed per iteration parity.
+  if (!fp64 && s.rp <= 32) return launch_sweep_mx(s, b, u_cur, st);
   dim3 grid(s.sweep_grid_x, s.nsplit);
   return by_prec(fp64, [&](auto tc) {
     using TC = decltype(tc);
@@ -953,8 +1636,10 @@ cudaError_t launch_sweep(const Shape& s, const Buffers& b, bool fp64, int u_cur,
   });
 }
 
-cudaError_t launch_iter_end(const Shape& s, const Buffers& b, cudaStream_t st) {
-  iter_end_kernel<<<1, 256, 0, st>>>(b.resid_part, s.resid_parts, b.st);
+cudaError_t launch_iter_end(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st) {
+  // the mixed SIMT sweep writes one residual partial per CTA, the others one per 32-row block
+  const int count = (!fp64 && !b.tc && s.rp <= 32) ? s.mx_grid_x * s.nsplit : s.resid_parts;
+  iter_end_kernel<<<1, 1024, 0, st>>>(b.resid_part, count, b.st);
   return cudaGetLastError();
 }
 

@@ -526,9 +526,9 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
 // U = U_hi + U_lo, so that the product sees U at about 16 bits), summed in the epilogue.
 constexpr int WSTAGES = 4;
 constexpr uint32_t W_A_BYTES = 16384, W_B_BYTES = 8192;
-template <int NS> constexpr uint32_t w_stage() { return W_A_BYTES + NS * W_B_BYTES; }
-template <int NS> constexpr uint32_t w_off_bar() { return WSTAGES * w_stage<NS>(); }
-template <int NS> constexpr uint32_t wpass_smem() { return w_off_bar<NS>() + 128 + 1024; }
+template <int NS> __host__ __device__ constexpr uint32_t w_stage() { return W_A_BYTES + NS * W_B_BYTES; }
+template <int NS> __host__ __device__ constexpr uint32_t w_off_bar() { return WSTAGES * w_stage<NS>(); }
+template <int NS> __host__ __device__ constexpr uint32_t wpass_smem() { return w_off_bar<NS>() + 128 + 1024; }
 
 // MN-major operand in the 128-byte swizzle layout: 64-element atoms along M 8 KB apart (LBO),
 // 8-row groups along K 1024 bytes apart (SBO)
