@@ -554,13 +554,47 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
   for (int p = tid; p < r; p += blockDim.x)
     if (lamf[p] < 1e-6f * hi) anysmall = 1.f;
   anysmall = block_reduce_f(anysmall, redf, true);
+  if (anysmall > 0.f && rotated) {
+    // Jacobi stopped at a 1e-3 off-diagonal, so a basis vector of a tiny eigenvalue still mixes
+    // ~1e-3 of the large ones and its Rayleigh quotient sits near 1e-6 hi: two first-order rounds
+    // (near-degenerate pairs are skipped) bring the mixing down to float32 rounding first.
+    for (int round = 0; round < 2; ++round)
+      if (!refine_basis(Kf, S.Qf, S.Af, F1, F2, n2, S.red)) break;
+    for (int e = tid; e < r * r; e += blockDim.x) S.QT[(e % r) * LD + e / r] = S.Qf[(e / r) * LD + e % r];
+    for (int p = tid; p < r; p += blockDim.x) lamf[p] = S.Af[p * LD + p];
+    __syncthreads();
+    hi = 0.f;
+    for (int p = tid; p < r; p += blockDim.x) hi = fmaxf(hi, lamf[p]);
+    hi = block_reduce_f(hi, redf, true);
+  }
+  // A float32 eigenvector carries components of about 1e-7 along the large eigenvectors, which
+  // alone would add ~1e-14 hi to its Rayleigh quotient (the rank threshold): project them out in
+  // float64 first (q <- q - Q_L Q_L^T q over the columns of large eigenvalues).
+  double* qs = S.Z;       // the vector (Z is free until step 4)
+  double* cf = S.Z + LD;  // its coefficients on the large eigenvectors
   for (int p = 0; anysmall > 0.f && p < r; ++p) {
     if (!(lamf[p] < 1e-6f * hi)) continue;  // uniform: lamf is in shared memory
+    if (tid < r) qs[tid] = (double)S.Qf[tid * LD + p];
+    __syncthreads();
+    if (tid < r) {
+      double c = 0.0;
+      if (!(lamf[tid] < 1e-6f * hi))
+        for (int k = 0; k < r; ++k) c = fma((double)S.Qf[k * LD + tid], qs[k], c);
+      cf[tid] = c;
+    }
+    __syncthreads();
+    double qi = 0.0;
+    if (tid < r) {
+      qi = qs[tid];
+      for (int q2 = 0; q2 < r; ++q2) qi = fma(-cf[q2], (double)S.Qf[tid * LD + q2], qi);
+    }
+    __syncthreads();
+    if (tid < r) qs[tid] = qi;
+    __syncthreads();
     double num = 0.0, den = 0.0;
     if (tid < r) {
       double kq = 0.0;
-      for (int k = 0; k < r; ++k) kq = fma(S.K[tid * LD + k], (double)S.Qf[k * LD + p], kq);
-      const double qi = (double)S.Qf[tid * LD + p];
+      for (int k = 0; k < r; ++k) kq = fma(S.K[tid * LD + k], qs[k], kq);
       num = qi * kq;
       den = qi * qi;
     }

@@ -303,7 +303,7 @@ struct Solver {
     timed_launch(slot, 0, [&] { return launch_sweep(s, b, fp64, u_new, st); });  // S/Y steps, Delta, next P
     SFR_CUDA(launch_iter_end(s, b, fp64, st));                                // residual, mu, stop test
     SFR_CUDA(launch_gram_p(s, b, fp64, true, st));                            // P = sum of partials, G_P
-    kernels += first ? 11 : 12;  // as on the tensor-core path below
+    kernels += (first ? 11 : 12) + (s.nchunk >= 32 ? 1 : 0);  // as on the tensor-core path below (+ W pre-sum)
     b.u_cur = u_new;
     std::swap(b.Y[0], b.Y[1]);
     return kernels;
@@ -333,8 +333,9 @@ struct Solver {
     // P_{k+1} = U_bar B_bar + Delta V_bar  (L V_bar = U_bar B_bar since V_bar^T V_bar = I)
     SFR_CUDA(launch_gram_p(s, b, false, true, st, b.U[u_new], b.B));
     // launches: projector 2 + 2 (partial sums, cluster kernel), transforms 2, W pass 1, W final
-    // 1 (+1 H sum after the first), sweep 1, iteration end 1, P / Gram 1
-    kernels += first ? 11 : 12;
+    // 1 (+1 H sum after the first, +1 wide pre-sum of many W partials), sweep 1, iteration end 1,
+    // P / Gram 1
+    kernels += (first ? 11 : 12) + (s.nchunk >= 32 ? 1 : 0);
     b.u_cur = u_new;
     std::swap(b.Y[0], b.Y[1]);
     return kernels;
@@ -533,8 +534,9 @@ struct Solver {
     SFR_CUDA(launch_apply_v(s, b, fp64, st));                                  // V = W T_V
     SFR_CUDA(launch_full_end(s, b, st));
     b.u_cur = u_new;
-    // P pass (or init_p) 1, P sum / Gram 1, projectors 2 + 2, transforms 2, W pass 1, W sum 1, end 1
-    return 11;
+    // P pass (or init_p) 1, P sum / Gram 1, projectors 2 + 2, transforms 2, W pass 1, W sum 1 (+1 wide
+    // pre-sum of many W partials), end 1
+    return 11 + (!b.tc && s.nchunk >= 32 ? 1 : 0);
   }
 
   // Runs Algorithm 4 (FixedRankOptFull) on a device-resident M from V_0 (NULL: I_{n x r}) and

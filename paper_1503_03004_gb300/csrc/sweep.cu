@@ -121,6 +121,62 @@ __device__ __forceinline__ void zero44(T (&acc)[4][4]) {
 // counts so that every load of a thread is in flight before the first shared-memory store.
 constexpr int kThinThreads = 256;
 
+// Gram-type products A^T B of two 64-row tiles (RP x RP output) with the 64-row sum split over
+// all threads: thread t owns output block t % G (4 x 4, G = (RP/4)^2) and the rows congruent to
+// t / G modulo 256 / G, accumulated across tiles; gram_store sums the row groups in a fixed order
+// at the end.  (With one 4 x 4 block per thread only G threads would work: 4 of 256 at RP = 8.)
+template <int RP> struct GramSplit {
+  static constexpr int NB = RP / 4, G = NB * NB, KG = kThinThreads / G;
+};
+
+template <typename T, int RP>
+__device__ __forceinline__ void gram_slice(const T* __restrict__ A, const T* __restrict__ B, int ld, T (&acc)[4][4],
+                                           int t) {
+  using GS = GramSplit<RP>;
+  const int blk = t % GS::G, kg = t / GS::G;
+  const int i0 = 4 * (blk / GS::NB), j0 = 4 * (blk % GS::NB);
+#pragma unroll 4
+  for (int k = kg; k < kGramRows; k += GS::KG) {
+    T a[4], bb[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      a[q] = A[k * ld + i0 + q];
+      bb[q] = B[k * ld + j0 + q];
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * bb[y];
+  }
+}
+
+// out[RP x RP] (float64) = the sum over row groups of the threads' gram_slice accumulators.
+// `red` is shared scratch of 256 x 16 T (unused when the split is 1, RP = 64).
+template <typename T, int RP>
+__device__ __forceinline__ void gram_store(const T (&acc)[4][4], int t, T* red, double* __restrict__ out) {
+  using GS = GramSplit<RP>;
+  if constexpr (GS::KG == 1) {
+    const int i0 = 4 * (t / GS::NB), j0 = 4 * (t % GS::NB);
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) out[(i0 + x) * RP + j0 + y] = (double)acc[x][y];
+  } else {
+    __syncthreads();  // callers' last use of `red` (a tile buffer) is done
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) red[t * 16 + 4 * x + y] = acc[x][y];
+    __syncthreads();
+    for (int o = t; o < GS::G * 16; o += kThinThreads) {
+      const int blk = o / 16, xy = o % 16;
+      double v = 0.0;
+      for (int kg = 0; kg < GS::KG; ++kg) v += (double)red[(kg * GS::G + blk) * 16 + xy];
+      out[(4 * (blk / GS::NB) + xy / 4) * RP + 4 * (blk % GS::NB) + xy % 4] = v;
+    }
+  }
+}
+
 // s[RP x RP] (row stride LDT, type TC) = g[RP x RP] (float64, dense).
 template <typename TC, int RP, int LDT>
 __device__ __forceinline__ void load_rr(const double* __restrict__ g, TC* s, int t) {
@@ -181,6 +237,7 @@ __global__ void __launch_bounds__(256) thin_gram_kernel(const TC* __restrict__ p
   TC* tile = reinterpret_cast<TC*>(smem_raw);   // [kGramRows][LDT]
   TC* arow = tile + kGramRows * LDT;              // [kGramRows][LDT]  addA rows
   TC* Hs = arow + kGramRows * LDT;                // [RP][LDT]
+  TC* red = tile;                                 // after the tiles: 256 x 16 Gram scratch
   const int t = threadIdx.x;
   if (addA) load_rr<TC, RP, LDT>(H, Hs, t);
   TC g[4][4];
@@ -232,44 +289,39 @@ __global__ void __launch_bounds__(256) thin_gram_kernel(const TC* __restrict__ p
         if (i < rows) out[i * RP + a] = tile[ii * LDT + a];
       }
     }
-    block_mm<TC, RP, RP, kGramRows, true>(tile, LDT, tile, LDT, g, t);
+    gram_slice<TC, RP>(tile, tile, LDT, g, t);
   }
-  if (t < (RP / 4) * (RP / 4)) {
-    const int r0 = 4 * (t / (RP / 4)), c0 = 4 * (t % (RP / 4));
-    double* dst = gpart + (int64_t)blockIdx.x * RP * RP;
-#pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 4; ++y) dst[(r0 + x) * RP + c0 + y] = (double)g[x][y];
-  }
+  gram_store<TC, RP>(g, t, red, gpart + (int64_t)blockIdx.x * RP * RP);
 }
 
-// Sum of `count` partials of rpsq doubles into out, in a fixed order: warp w of a CTA adds the
+// Sum of `count` partials of rpsq values into out, in a fixed order: warp w of a CTA adds the
 // partials w, w + 8, w + 16, ... of 32 consecutive entries (four loads in flight), then the
-// eight warp sums are added in warp order.
-__global__ void __launch_bounds__(256) reduce_sq_kernel(const double* __restrict__ parts, int count, int rpsq,
-                                                        double* out, const DevState* st) {
+// eight warp sums are added in warp order.  out may be the first partial (each entry is read
+// and written by one CTA).
+template <typename T>
+__global__ void __launch_bounds__(256) reduce_sq_kernel(const T* parts, int64_t count, int64_t rpsq, T* out,
+                                                        const DevState* st) {
   if (stopped(st)) return;
-  __shared__ double red[8][32];
+  __shared__ T red[8][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int e = blockIdx.x * 32 + lane;
-  double a = 0.0;
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  T a = 0;
   if (e < rpsq) {
-    int c = warp;
+    int64_t c = warp;
     for (; c + 24 < count; c += 32) {
-      const double v0 = parts[(int64_t)c * rpsq + e], v1 = parts[(int64_t)(c + 8) * rpsq + e];
-      const double v2 = parts[(int64_t)(c + 16) * rpsq + e], v3 = parts[(int64_t)(c + 24) * rpsq + e];
+      const T v0 = parts[c * rpsq + e], v1 = parts[(c + 8) * rpsq + e];
+      const T v2 = parts[(c + 16) * rpsq + e], v3 = parts[(c + 24) * rpsq + e];
       a += v0;
       a += v1;
       a += v2;
       a += v3;
     }
-    for (; c < count; c += 8) a += parts[(int64_t)c * rpsq + e];
+    for (; c < count; c += 8) a += parts[c * rpsq + e];
   }
   red[warp][lane] = a;
   __syncthreads();
   if (warp == 0 && e < rpsq) {
-    double s = red[0][lane];
+    T s = red[0][lane];
 #pragma unroll
     for (int w = 1; w < 8; ++w) s += red[w][lane];
     out[e] = s;
@@ -368,7 +420,7 @@ __global__ void __launch_bounds__(256) row_transform_kernel(const TC* __restrict
       }
     }
     if (hpart || trans) __syncthreads();  // drow complete
-    if (hpart) block_mm<TC, RP, RP, kGramRows, true>(orow, LDT, drow, LDT, h, t);
+    if (hpart) gram_slice<TC, RP>(orow, drow, LDT, h, t);
     if constexpr (kF32) {
       if (trans) {  // column a of the tile -> row a of the transpose, 64 consecutive rows i
 #pragma unroll
@@ -385,14 +437,7 @@ __global__ void __launch_bounds__(256) row_transform_kernel(const TC* __restrict
       }
     }
   }
-  if (hpart && t < (RP / 4) * (RP / 4)) {
-    const int a0 = 4 * (t / (RP / 4)), b0 = 4 * (t % (RP / 4));
-    double* out = hpart + (int64_t)blockIdx.x * RP * RP;
-#pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 4; ++y) out[(a0 + x) * RP + b0 + y] = (double)h[x][y];
-  }
+  if (hpart) gram_store<TC, RP>(h, t, srow, hpart + (int64_t)blockIdx.x * RP * RP);
 }
 
 // ---------------------------------------------------------------- W pass
@@ -1383,9 +1428,13 @@ cudaError_t by_prec(bool fp64, F&& f) {
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 template <typename TC, int RP>
-size_t gram_smem() { return sizeof(TC) * (size_t)(2 * kGramRows + RP) * (RP + 4); }
+size_t gram_smem() { return sizeof(TC) * std::max<size_t>((size_t)(2 * kGramRows + RP) * (RP + 4), 16 * kThinThreads); }
 template <typename TC, int RP>
-size_t transform_smem() { return sizeof(TC) * (size_t)(2 * RP + 3 * kGramRows) * (RP + 4); }
+size_t transform_smem() {
+  // the Gram scratch (256 x 16) starts at the source-row tile, 2 RP (RP + 4) elements in
+  return sizeof(TC) * std::max<size_t>((size_t)(2 * RP + 3 * kGramRows) * (RP + 4),
+                                       (size_t)2 * RP * (RP + 4) + 16 * kThinThreads);
+}
 
 template <typename K>
 cudaError_t allow_smem(K kern, size_t bytes) {
@@ -1403,7 +1452,7 @@ static bool mx_vec(const Shape& s, const Buffers& b) {
 
 cudaError_t launch_reduce_parts(const double* parts, int count, int rpsq, double* out, const DevState* dst,
                                 cudaStream_t st) {
-  reduce_sq_kernel<<<cdiv(rpsq, 32), 256, 0, st>>>(parts, count, rpsq, out, dst);
+  reduce_sq_kernel<double><<<cdiv(rpsq, 32), 256, 0, st>>>(parts, count, rpsq, out, dst);
   return cudaGetLastError();
 }
 
@@ -1531,8 +1580,8 @@ cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool firs
   // W = sum_c Wpart[c] (+ C_old H, H = U_old^T U_new), then Gram partials of W.
   // H = sum of the U_old^T U_new partials, reduced into the slot after the partials.
   if (!first) {
-    reduce_sq_kernel<<<cdiv(s.rp * s.rp, 32), 256, 0, st>>>(b.Hpart, s.gp_blocks, s.rp * s.rp, b.Hpart + (size_t)s.gp_blocks * s.rp * s.rp,
-                                        b.st);
+    reduce_sq_kernel<double><<<cdiv(s.rp * s.rp, 32), 256, 0, st>>>(
+        b.Hpart, s.gp_blocks, s.rp * s.rp, b.Hpart + (size_t)s.gp_blocks * s.rp * s.rp, b.st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1544,8 +1593,18 @@ cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool firs
       const size_t sm = gram_smem<TC, RP>();
       cudaError_t e = allow_smem(thin_gram_kernel<TC, RP>, sm);
       if (e != cudaSuccess) return e;
+      // many row chunks over few columns (tall M): sum the chunks' partials into the first one
+      // with a wide reduction first, so the thin kernel does not add hundreds of them per element
+      int nparts = s.nchunk;
+      if (nparts >= 32) {
+        const int64_t len = s.n * RP;
+        reduce_sq_kernel<TC><<<cdiv(len, 32), 256, 0, st>>>(static_cast<const TC*>(b.Wpart), nparts, len,
+                                                             static_cast<TC*>(b.Wpart), b.st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        nparts = 1;
+      }
       thin_gram_kernel<TC, RP><<<s.gw_blocks, 256, sm, st>>>(
-          static_cast<const TC*>(b.Wpart), s.nchunk, s.n * RP, static_cast<TC*>(b.W), s.n,
+          static_cast<const TC*>(b.Wpart), nparts, s.n * RP, static_cast<TC*>(b.W), s.n,
           first ? nullptr : static_cast<const TC*>(b.C), first ? nullptr : H, b.GWpart, b.st);
       return cudaGetLastError();
     });
