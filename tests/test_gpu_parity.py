@@ -117,6 +117,22 @@ def test_mixed_matches_oracle(ctx, dtype):
     assert _rel(_gpu_L(sol), ref.L) <= MIXED_TOL
 
 
+@pytest.mark.parametrize("m,n,r,dtype", [
+    (517, 333, 10, "f32"),    # n % 4 != 0: the element-load variants of the float32 passes
+    (301, 258, 7, "bf16"),    # the same with bfloat16 M
+    (96, 3001, 5, "f32"),     # few rows, many column tiles: several splits, several tiles per split
+    (2048, 1000, 20, "bf16"),  # cp.async-pipelined passes at r = 20 (padded to 32), ragged tiles
+])
+def test_mixed_simt_passes_match_oracle(ctx, m, n, r, dtype):
+    prob = synth.planted(m, n, r, p=0.05, amp=50.0, seed=m * 7 + n, dtype=dtype)
+    M = prob.values_f64()
+    ref = O.fr_adm(M, r, rho=1.5, mu0=0.05, tol=1e-9, max_iter=300)
+    sol = B.solve_torch(ctx, _dev(prob), r, rho=1.5, mu0=0.05, tol=1e-9, max_iter=300, precision=B.PREC_MIXED,
+                        s_dtype=B.F32)
+    assert sol.status == B.OK and sol.rel_residual <= 1e-9
+    assert _rel(_gpu_L(sol), ref.L) <= MIXED_TOL
+
+
 def test_mixed_square_r64_bf16_recipe(ctx):
     # the 16384 x 16384 r = 64 recipe (5% outliers in [-50, 50], bf16 storage) at 1024 x 1024
     prob = synth.planted(1024, 1024, 64, p=0.05, amp=50.0, seed=1001, dtype="bf16")
