@@ -134,6 +134,8 @@ constexpr int kWBM = 32;         // rows per W-pass tile
 constexpr int kGramRows = 64;    // rows per Gram / transform CTA
 
 inline int pad_rank(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 32 ? 32 : 64; }
+// The mixed path's float32 SIMT passes for r <= 32 (sweep_mx*/wpass_mx* kernels).
+inline bool mx_path(const Shape& s, bool fp64) { return !fp64 && s.rp <= 32; }
 
 // ---- host helpers shared by the entry points (solver.cu)
 Shape plan_shape(int64_t m, int64_t n, int64_t ldm, int r, int num_sms);

@@ -8,6 +8,7 @@
 #include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -187,6 +188,85 @@ size_t carve(const Shape& s, bool fp64, void* base, Buffers* b, bool tc, bool fu
   x.st = static_cast<DevState*>(c.take(sizeof(DevState)));
   if (b) *b = x;
   return c.off + 256;
+}
+
+// ---------------------------------------------------------------- launch-shape autotuner
+// The mixed-path SIMT sweep loops each CTA over 64-row blocks, so its grid is free: how many CTAs
+// per SM hide latency best depends on the shape (row length, rank, storage).  The first solve of
+// a size class (m and n bucketed by powers of two, padded rank, dtype of M, vector-load
+// eligibility) times the sweep at 2, 4, 8 and 16 CTAs per SM before it starts and keeps the
+// fastest.  The table is process-wide and an entry never changes once set, so every solve of a
+// class -- through sfr_solve or any serving slot -- uses the same grid and gets the same result
+// (the grid decides the order of the residual partial sums).  SFR_AUTOTUNE=0 disables it (8 per
+// SM); SFR_TUNE_FILE=path loads and appends choices as a flat JSON object {"class": ctas, ...}.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;  // size class -> CTAs per SM
+bool g_tune_loaded = false;
+
+std::string tune_file() {
+  const char* f = getenv("SFR_TUNE_FILE");
+  return f ? std::string(f) : std::string();
+}
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const std::string path = tune_file();
+  if (path.empty()) return;
+  FILE* f = fopen(path.c_str(), "r");
+  if (!f) return;
+  std::string text;
+  char buf[4096];
+  size_t k;
+  while ((k = fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, k);
+  fclose(f);
+  // "key": value pairs of a flat object
+  size_t pos = 0;
+  while ((pos = text.find('"', pos)) != std::string::npos) {
+    const size_t end = text.find('"', pos + 1);
+    if (end == std::string::npos) break;
+    const std::string key = text.substr(pos + 1, end - pos - 1);
+    const size_t colon = text.find(':', end);
+    if (colon == std::string::npos) break;
+    const int v = atoi(text.c_str() + colon + 1);
+    if (v > 0 && v <= 64) g_tune.emplace(key, v);
+    pos = colon + 1;
+  }
+}
+
+void tune_save_locked() {
+  const std::string path = tune_file();
+  if (path.empty()) return;
+  FILE* f = fopen(path.c_str(), "w");
+  if (!f) return;
+  fputs("{", f);
+  bool firstk = true;
+  for (const auto& kv : g_tune) {
+    fprintf(f, "%s\n  \"%s\": %d", firstk ? "" : ",", kv.first.c_str(), kv.second);
+    firstk = false;
+  }
+  fputs("\n}\n", f);
+  fclose(f);
+}
+
+int ilog2(int64_t v) {
+  int k = 0;
+  while (v > 1) {
+    v >>= 1;
+    ++k;
+  }
+  return k;
+}
+}  // namespace
+
+std::string tune_class(const Shape& s, sfr_dtype m_dtype, bool vec) {
+  return fmt("mx_sweep/m2^%d/n2^%d/rp%d/dt%d/v%d", ilog2(s.m), ilog2(s.n), s.rp, (int)m_dtype, (int)vec);
+}
+
+int mx_grid_for(const Shape& s, int ctas_per_sm) {
+  const int64_t nrb64 = (s.m + 63) / 64;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(nrb64, ((int64_t)ctas_per_sm * s.num_sms + s.nsplit - 1) / s.nsplit));
 }
 
 // ---------------------------------------------------------------- one FR-ADM solve
@@ -416,6 +496,52 @@ struct Solver {
     SFR_CUDA(cudaStreamSynchronize(stream));
   }
 
+  // Picks the mixed SIMT sweep's grid for this size class (see the autotuner above).  Runs before
+  // the first iteration: the sweep reads Y_1 = 0 and whatever U, C, V hold, and writes buffers the
+  // first iteration overwrites, so timing it changes nothing.
+  void tune_mx(Shape& s, Buffers& b, sfr_dtype m_dtype) {
+    const char* env = getenv("SFR_AUTOTUNE");
+    const bool vec = ((size_t)s.n % 4 == 0) &&
+                     ((size_t)s.ldm * (m_dtype == SFR_F64 ? 8 : m_dtype == SFR_F32 ? 4 : 2)) % 16 == 0 &&
+                     (reinterpret_cast<uintptr_t>(b.M) % 16) == 0;
+    const std::string cls = tune_class(s, m_dtype, vec);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find(cls);
+    if (it != g_tune.end()) {
+      s.mx_grid_x = mx_grid_for(s, it->second);
+      return;
+    }
+    int best = 8;
+    if (!(env && env[0] == '0')) {
+      cudaEvent_t e0, e1;
+      SFR_CUDA(cudaEventCreate(&e0));
+      SFR_CUDA(cudaEventCreate(&e1));
+      float best_ms = 1e30f;
+      for (int c : {2, 4, 8, 16}) {
+        Shape t = s;
+        t.mx_grid_x = mx_grid_for(s, c);
+        SFR_CUDA(launch_sweep(t, b, false, 0, stream));  // warm-up
+        SFR_CUDA(cudaEventRecord(e0, stream));
+        for (int k = 0; k < 3; ++k) SFR_CUDA(launch_sweep(t, b, false, 0, stream));
+        SFR_CUDA(cudaEventRecord(e1, stream));
+        SFR_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        SFR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms * 0.97f) {  // prefer the earlier (smaller) grid unless clearly faster
+          best_ms = ms;
+          best = c;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      count(SFR_STAT_ALL, 16);
+    }
+    g_tune.emplace(cls, best);
+    tune_save_locked();
+    s.mx_grid_x = mx_grid_for(s, best);
+  }
+
   // Runs Algorithm 1 on a device-resident M.  Returns the final host copy of the state and
   // fills U/V/B/S/L (device pointers) as requested.
   DevState run(const sfr_problem& p, const void* Mdev, double* Udev, double* Bdev, double* Vdev, void* Sdev,
@@ -469,6 +595,7 @@ struct Solver {
     SFR_CUDA(launch_norm_m(s, b, stream));
     count(SFR_STAT_ALL, 2);
     if (profile) make_events();
+    if (!tc && mx_path(s, fp64)) tune_mx(s, b, p.m_dtype);
 
     // iteration 1 (X_1 = M, V_1 = I_{n x r}), eager
     count(SFR_STAT_ALL, enqueue_iteration(s, b, fp64, true, 0));
@@ -478,7 +605,7 @@ struct Solver {
     const Buffers after_first = b;
     const std::string key = fmt("%p/%lld/%lld/%lld/%d/%d/%p", work.ptr, (long long)s.m, (long long)s.n,
                                 (long long)s.ldm, s.r, (int)fp64, Mdev) +
-                            fmt("/%d/%d", (int)p.m_dtype, (int)tc);
+                            fmt("/%d/%d/%d", (int)p.m_dtype, (int)tc, s.mx_grid_x);
     drive(after_first, key, h.max_iter, true,
           [&](Buffers& bb, int slot) { return enqueue_iteration(s, bb, fp64, false, slot); });
     DevState out = *host_state;

@@ -1521,7 +1521,7 @@ cudaError_t launch_apply_u(const Shape& s, const Buffers& b, bool fp64, bool fir
 
 cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first, int u_new, cudaStream_t st) {
   dim3 grid(s.wpass_grid_x, s.nchunk);
-  if (!fp64 && s.rp <= 32) {
+  if (mx_path(s, fp64)) {
     const bool vec = first ? mx_vec(s, b) : s.n % 4 == 0;
     return by_rank(s.rp, [&](auto rpc) {
       constexpr int RP = decltype(rpc)::value;
@@ -1672,7 +1672,7 @@ static cudaError_t launch_sweep_mx(const Shape& s, const Buffers& b, int u_cur, 
 cudaError_t launch_sweep(const Shape& s, const Buffers& b, bool fp64, int u_cur, cudaStream_t st) {
   // Y ping-pong: iteration k (0-based count of completed iterations) reads Y[k % 2] and writes
   // Y[(k + 1) % 2].  The host tracks k because graphs are replayed per iteration parity.
-  if (!fp64 && s.rp <= 32) return launch_sweep_mx(s, b, u_cur, st);
+  if (mx_path(s, fp64)) return launch_sweep_mx(s, b, u_cur, st);
   dim3 grid(s.sweep_grid_x, s.nsplit);
   return by_prec(fp64, [&](auto tc) {
     using TC = decltype(tc);
@@ -1697,7 +1697,7 @@ cudaError_t launch_sweep(const Shape& s, const Buffers& b, bool fp64, int u_cur,
 
 cudaError_t launch_iter_end(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st) {
   // the mixed SIMT sweep writes one residual partial per CTA, the others one per 32-row block
-  const int count = (!fp64 && !b.tc && s.rp <= 32) ? s.mx_grid_x * s.nsplit : s.resid_parts;
+  const int count = mx_path(s, fp64) ? s.mx_grid_x * s.nsplit : s.resid_parts;
   iter_end_kernel<<<1, 1024, 0, st>>>(b.resid_part, count, b.st);
   return cudaGetLastError();
 }
