@@ -582,6 +582,69 @@ def run_paper_tables(args):
     return 0
 
 
+def run_phase(args):
+    """The phase-transition experiment of Fig. 2 for FR-ADM on the GPU: m = n = 800, rank fraction
+    r / 800 in {0.01, 0.02, 0.04, 0.06, 0.08} (the library's r <= 64 caps it there), outlier
+    fraction 0.05 .. 0.50, the Sec. 5.1 entries (A, B ~ N(0, 1), outliers in [-1, 1]), `--reps`
+    repetitions per cell.  All problems go through sfr_submit / sfr_poll (8 slots, mixed path;
+    mu0 = 1.25 / ||M||_2 as in Sec. 7c, rho = 1.5, tol 1e-9).  Per cell: the paper's error
+    measure (1 / K) sum_z sum_ij psi_eps(S_z - S*_z) / (m n), psi_eps(s) = |s| if |s| > eps else 0,
+    eps = 1e-3, and Err.L; plus the batch's throughput.  Prints one JSON line."""
+    import numpy as np
+    import torch
+    from paper_1503_03004_gb300 import binding as B, synth
+    torch.cuda.set_device(0)
+    m = 800
+    fr = [0.01, 0.02, 0.04, 0.06, 0.08]
+    po = [0.05, 0.10, 0.15, 0.20, 0.25, 0.30, 0.35, 0.40, 0.45, 0.50]
+    eps = 1e-3
+    items = []
+    for ri, f in enumerate(fr):
+        r = max(1, int(round(f * m)))
+        for pi, p in enumerate(po):
+            for z in range(args.reps):
+                prob = synth.planted(m, m, r, p=p, amp=1.0, seed=9000 + 1000 * ri + 10 * pi + z, dtype="f64")
+                Md = torch.from_numpy(prob.M).cuda()
+                L0 = torch.from_numpy(prob.U0 @ prob.V0.T).cuda()
+                mu0 = 1.25 / float(torch.linalg.matrix_norm(Md, ord=2))
+                f64 = dict(dtype=torch.float64, device="cuda")
+                out = dict(U=torch.empty((m, r), **f64), B=torch.empty((r, r), **f64), V=torch.empty((m, r), **f64),
+                           S=torch.empty((m, m), **f64))
+                q = B.make_problem(m=m, n=m, r=r, M_ptr=Md.data_ptr(), m_dtype=B.F64, mu0=mu0, rho=1.5, tol=1e-9,
+                                   max_iter=500, precision=B.PREC_MIXED)
+                res = B.make_result(U_ptr=out["U"].data_ptr(), B_ptr=out["B"].data_ptr(), V_ptr=out["V"].data_ptr(),
+                                    S_ptr=out["S"].data_ptr(), s_dtype=B.F64, lds=m)
+                items.append(((f, p, r), Md, L0, out, q, res))
+    torch.cuda.synchronize()
+    with B.Context(0, max_slots=8) as ctx:
+        t0 = time.perf_counter()
+        tickets = [ctx.submit(it[4], it[5]) for it in items]
+        status = [ctx.poll(t, -1) for t in tickets]
+        wall = time.perf_counter() - t0
+    cells = {}
+    for (key, Md, L0, out, q, res), st in zip(items, status):
+        S0 = Md - L0
+        d = (out["S"] - S0).abs()
+        psi = float(torch.where(d > eps, d, torch.zeros_like(d)).sum()) / (m * m)
+        L = out["U"] @ out["B"] @ out["V"].T
+        errl = float(torch.linalg.norm(L - L0) / torch.linalg.norm(L0))
+        c = cells.setdefault(key, {"rank_fraction": key[0], "outlier_fraction": key[1], "r": key[2], "psi": 0.0,
+                                   "err_L": 0.0, "iters": 0, "ok": 0, "count": 0})
+        c["psi"] += psi / args.reps
+        c["err_L"] = max(c["err_L"], errl)
+        c["iters"] += res.iters
+        c["ok"] += int(st == B.OK)
+        c["count"] += 1
+    line = {"metric": "Fig. 2 phase transition, FR-ADM (batched through the serving slots)",
+            "value": len(items) / wall, "unit": "solves/s", "problems": len(items), "slots": 8,
+            "config": {"m": m, "n": m, "rank_fractions": fr, "outlier_fractions": po, "reps": args.reps,
+                       "outliers": "uniform in [-1, 1]", "mu0": "1.25/||M||_2", "rho": 1.5, "tol": 1e-9,
+                       "eps": eps, "precision": "mixed", "storage": "f64"},
+            "cells": list(cells.values())}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_setup()
     if rank != 0:
@@ -621,6 +684,9 @@ def main():
                     help="supplementary: one of the other workloads of the recipe")
     ap.add_argument("--paper-tables", action="store_true",
                     help="supplementary: the Sec. 5.1 scale experiment (Tables 1-2 recipe) on the GPU")
+    ap.add_argument("--phase", action="store_true",
+                    help="supplementary: the Fig. 2 phase transition for FR-ADM, batched through the serving slots")
+    ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--budget-gb", type=int, default=64)
@@ -641,6 +707,8 @@ def main():
         return run_config(args)
     if args.paper_tables:
         return run_paper_tables(args)
+    if args.phase:
+        return run_phase(args)
 
     import numpy as np
     import torch
