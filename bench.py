@@ -155,6 +155,26 @@ def oracle_sample_rate(seed: int = 1001):
             "sample_iters": res.iters, "sample_seconds": dt, "converged": bool(res.converged)}, np
 
 
+def oracle_sample_error(U, Bm, V, S):
+    """Relative error of L = U B V^T and of S at the float64 oracle's sampled positions of the
+    16384^2 r = 64 bf16 workload (tests/golden/square16384_r64_bf16_samples.txt, written by
+    tests/golden/make_fullsize_samples.py from the oracle alone), or None without that file."""
+    import numpy as np
+    import torch
+    path = os.path.join(ROOT, "tests", "golden", "square16384_r64_bf16_samples.txt")
+    if not os.path.exists(path):
+        return None
+    rows = [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
+    a = np.array([[float(x) for x in t] for t in rows if len(t) == 5])
+    ii = torch.from_numpy(a[:, 0].astype(np.int64)).to(U.device)
+    jj = torch.from_numpy(a[:, 1].astype(np.int64)).to(U.device)
+    L = torch.einsum("ka,ab,kb->k", U[ii], Bm, V[jj]).cpu().numpy()
+    Sv = S[ii, jj].double().cpu().numpy()
+    return {"rel_err_L": float(np.linalg.norm(L - a[:, 2]) / np.linalg.norm(a[:, 2])),
+            "rel_err_S": float(np.linalg.norm(Sv - a[:, 3]) / np.linalg.norm(a[:, 3])),
+            "bar": 1e-5, "samples": int(len(a)), "against": "float64 oracle (sampled positions)"}
+
+
 def reduce_max(x: float, device=None) -> float:
     """Max of a float over all ranks (identity without a process group)."""
     import torch
@@ -811,6 +831,10 @@ def main():
     e2e = {"value": world * args.e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 2 * m * n,
            "d2h_bytes_per_step": 4 * m * n + 8 * (m * r + r * r + n * r)}
 
+    # accuracy of the timed solves against the float64 oracle: its L_ij and S_ij at the 4096 seeded
+    # positions stored by tests/golden/make_fullsize_samples.py (oracle and generators only)
+    accuracy = oracle_sample_error(U, Bm, V, S) if (m, n, r) == (16384, 16384, 64) and rank == 0 else None
+
     lat_ms = sorted(x * 1000.0 for x in lat)
     line = {"metric": "solves/s", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -820,7 +844,8 @@ def main():
                                                                                 int(0.99 * len(lat_ms)))]},
             "roofline": roofline, "clocks": clocks, "e2e": e2e,
             "gpu_launches": stats[B.STAT_ALL]["launches"],
-            "cpu_baseline": cpu_base and {k: cpu_base[k] for k in ("value", "unit", "cores", "kind", "sample")}}
+            "cpu_baseline": cpu_base and {k: cpu_base[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "accuracy": accuracy}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
