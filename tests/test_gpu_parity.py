@@ -122,6 +122,8 @@ def test_mixed_matches_oracle(ctx, dtype):
     (301, 258, 7, "bf16"),    # the same with bfloat16 M
     (96, 3001, 5, "f32"),     # few rows, many column tiles: several splits, several tiles per split
     (2048, 1000, 20, "bf16"),  # cp.async-pipelined passes at r = 20 (padded to 32), ragged tiles
+    (517, 336, 10, "f32"),    # pipelined passes with a ragged last row block (m % 64 != 0)
+    (1003, 1024, 24, "bf16"),  # the same with bfloat16 M and r = 24
 ])
 def test_mixed_simt_passes_match_oracle(ctx, m, n, r, dtype):
     prob = synth.planted(m, n, r, p=0.05, amp=50.0, seed=m * 7 + n, dtype=dtype)
