@@ -131,6 +131,30 @@ def make_workload(seed: int):
     return synth.square_large(WORKLOAD["m"], WORKLOAD["r"], dtype="bf16", seed=seed)  # m = n
 
 
+def host_cpu():
+    """(threads available to this process, CPU model name from lscpu or /proc/cpuinfo)."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return cores, model or platform.machine()
+
+
 def oracle_sample_rate(seed: int = 1001):
     """FP64 CPU oracle on a 2048 x 2048 sample of the same recipe, scaled to full-size solves/s.
 
@@ -148,8 +172,8 @@ def oracle_sample_rate(seed: int = 1001):
                    max_iter=WORKLOAD["max_iter"])
     dt = time.perf_counter() - t0
     scale = (WORKLOAD["m"] * WORKLOAD["n"]) / (SAMPLE["m"] * SAMPLE["n"])
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": 1.0 / (dt * scale), "unit": "solves/s", "cores": cores, "kind": "oracle",
+    cores, model = host_cpu()
+    return {"value": 1.0 / (dt * scale), "unit": "solves/s", "cores": cores, "cpu_model": model, "kind": "oracle",
             "sample": (f"one FP64 oracle solve of a {SAMPLE['m']}x{SAMPLE['n']} r=64 sample of the same recipe "
                        f"({res.iters} iterations, {dt:.1f} s), scaled by m*n to 16384x16384"),
             "sample_iters": res.iters, "sample_seconds": dt, "converged": bool(res.converged)}, np
@@ -364,8 +388,9 @@ def run_opt_full(args):
         O.fixed_rank_opt_full(Ms, None, np.eye(r), np.eye(n, r), k)
         dts = time.perf_counter() - t2
         del Ms
-        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-        line["cpu_baseline"] = {"value": 1.0 / dts, "unit": "TSVDs/s", "cores": cores, "kind": "oracle",
+        cores, model = host_cpu()
+        line["cpu_baseline"] = {"value": 1.0 / dts, "unit": "TSVDs/s", "cores": cores, "cpu_model": model,
+                                "kind": "oracle",
                                 "sample": f"one run of the FP64 oracle's Algorithm 4 on the same {m}x{n} matrix, "
                                           f"{k} iterations ({dts:.1f} s)"}
     print(json.dumps(line), flush=True)
@@ -536,8 +561,9 @@ def run_config(args):
         t2 = time.perf_counter()
         ref(Ms)
         dts = time.perf_counter() - t2
-        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-        line["cpu_baseline"] = {"value": 1.0 / (dts * scale), "unit": "solves/s", "cores": cores, "kind": "oracle",
+        cores, model = host_cpu()
+        line["cpu_baseline"] = {"value": 1.0 / (dts * scale), "unit": "solves/s", "cores": cores, "cpu_model": model,
+                                "kind": "oracle",
                                 "sample": f"one FP64 oracle solve of {what} ({dts:.1f} s)"}
     print(json.dumps(line), flush=True)
     return 0
@@ -680,7 +706,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": WORKLOAD,
-            "cpu_baseline": {k: info[k] for k in ("kind", "cores", "sample")} | {"value": value, "unit": "solves/s"},
+            "cpu_baseline": {k: info[k] for k in ("kind", "cores", "cpu_model", "sample")} | {"value": value,
+                                                                                          "unit": "solves/s"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -844,7 +871,8 @@ def main():
                                                                                 int(0.99 * len(lat_ms)))]},
             "roofline": roofline, "clocks": clocks, "e2e": e2e,
             "gpu_launches": stats[B.STAT_ALL]["launches"],
-            "cpu_baseline": cpu_base and {k: cpu_base[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "cpu_baseline": cpu_base and {k: cpu_base[k] for k in ("value", "unit", "cores", "cpu_model", "kind",
+                                                                   "sample")},
             "accuracy": accuracy}
     if rank == 0:
         print(json.dumps(line), flush=True)
