@@ -23,6 +23,13 @@
  *     error; sfr_last_error(ctx) then holds a one-line message.  A per-problem
  *     outcome is also stored in sfr_result.status.
  *   - A context is not thread-safe: use one context per host thread.
+ *   - Launch shapes: the first mixed-precision solve of a size class (m and n by
+ *     powers of two, padded rank, dtype of M) times a few grid sizes of the
+ *     float32 sweep (r <= 32) before it starts and keeps the fastest for the rest
+ *     of the process, so every later solve of that class, in any context or
+ *     serving slot, runs the same kernels and gives bit-identical results.
+ *     Environment: SFR_AUTOTUNE=0 skips the timing (a fixed default grid);
+ *     SFR_TUNE_FILE=path loads the choices from, and saves them to, a JSON file.
  */
 #ifndef SFR_H
 #define SFR_H
