@@ -294,36 +294,35 @@ __global__ void __launch_bounds__(256) thin_gram_kernel(const TC* __restrict__ p
   gram_store<TC, RP>(g, t, red, gpart + (int64_t)blockIdx.x * RP * RP);
 }
 
-// Sum of `count` partials of rpsq values into out, in a fixed order: warp w of a CTA adds the
-// partials w, w + 8, w + 16, ... of 32 consecutive entries (four loads in flight), then the
-// eight warp sums are added in warp order.  out may be the first partial (each entry is read
-// and written by one CTA).
+// Sum of `count` partials of rpsq values into out, in a fixed order: warp w of a CTA of nw warps
+// adds the partials w, w + nw, w + 2 nw, ... of 32 consecutive entries (four loads in flight),
+// then the warp sums are added in warp order.  out may be the first partial (each entry is read
+// and written by one CTA).  nw = blockDim.x / 32 <= 32.
 template <typename T>
-__global__ void __launch_bounds__(256) reduce_sq_kernel(const T* parts, int64_t count, int64_t rpsq, T* out,
-                                                        const DevState* st) {
+__global__ void __launch_bounds__(1024) reduce_sq_kernel(const T* parts, int64_t count, int64_t rpsq, T* out,
+                                                         const DevState* st) {
   if (stopped(st)) return;
-  __shared__ T red[8][32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ T red[32][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int64_t e = (int64_t)blockIdx.x * 32 + lane;
   T a = 0;
   if (e < rpsq) {
     int64_t c = warp;
-    for (; c + 24 < count; c += 32) {
-      const T v0 = parts[c * rpsq + e], v1 = parts[(c + 8) * rpsq + e];
-      const T v2 = parts[(c + 16) * rpsq + e], v3 = parts[(c + 24) * rpsq + e];
+    for (; c + 3 * nw < count; c += 4 * nw) {
+      const T v0 = parts[c * rpsq + e], v1 = parts[(c + nw) * rpsq + e];
+      const T v2 = parts[(c + 2 * nw) * rpsq + e], v3 = parts[(c + 3 * nw) * rpsq + e];
       a += v0;
       a += v1;
       a += v2;
       a += v3;
     }
-    for (; c < count; c += 8) a += parts[c * rpsq + e];
+    for (; c < count; c += nw) a += parts[c * rpsq + e];
   }
   red[warp][lane] = a;
   __syncthreads();
   if (warp == 0 && e < rpsq) {
     T s = red[0][lane];
-#pragma unroll
-    for (int w = 1; w < 8; ++w) s += red[w][lane];
+    for (int w = 1; w < nw; ++w) s += red[w][lane];
     out[e] = s;
   }
 }
@@ -1450,9 +1449,12 @@ static bool mx_vec(const Shape& s, const Buffers& b) {
   return s.n % 4 == 0 && ((size_t)s.ldm * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(b.M) % 16) == 0;
 }
 
+// threads of the partial-sum kernel: 8 warps, 32 when there are many partials to walk
+inline int reduce_threads(int64_t count) { return count >= 256 ? 1024 : 256; }
+
 cudaError_t launch_reduce_parts(const double* parts, int count, int rpsq, double* out, const DevState* dst,
                                 cudaStream_t st) {
-  reduce_sq_kernel<double><<<cdiv(rpsq, 32), 256, 0, st>>>(parts, count, rpsq, out, dst);
+  reduce_sq_kernel<double><<<cdiv(rpsq, 32), reduce_threads(count), 0, st>>>(parts, count, rpsq, out, dst);
   return cudaGetLastError();
 }
 
@@ -1580,7 +1582,7 @@ cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool firs
   // W = sum_c Wpart[c] (+ C_old H, H = U_old^T U_new), then Gram partials of W.
   // H = sum of the U_old^T U_new partials, reduced into the slot after the partials.
   if (!first) {
-    reduce_sq_kernel<double><<<cdiv(s.rp * s.rp, 32), 256, 0, st>>>(
+    reduce_sq_kernel<double><<<cdiv(s.rp * s.rp, 32), reduce_threads(s.gp_blocks), 0, st>>>(
         b.Hpart, s.gp_blocks, s.rp * s.rp, b.Hpart + (size_t)s.gp_blocks * s.rp * s.rp, b.st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1598,8 +1600,9 @@ cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool firs
       int nparts = s.nchunk;
       if (nparts >= 32) {
         const int64_t len = s.n * RP;
-        reduce_sq_kernel<TC><<<cdiv(len, 32), 256, 0, st>>>(static_cast<const TC*>(b.Wpart), nparts, len,
-                                                             static_cast<TC*>(b.Wpart), b.st);
+        reduce_sq_kernel<TC><<<cdiv(len, 32), reduce_threads(nparts), 0, st>>>(static_cast<const TC*>(b.Wpart),
+                                                                                nparts, len, static_cast<TC*>(b.Wpart),
+                                                                                b.st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         nparts = 1;
       }
