@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(workload="square16384_r64_bf16_mixed", m=16384, n=16384, r=64, storage="bf16", precision="mixed",
                 outlier_fraction=0.05, outlier_range=[-50, 50], mu0=0.05, rho=1.5, tol=1e-9, max_iter=300,
                 l2="inputs larger than L2 (M 512 MB, multipliers 2 x 512 MB, Delta 512 MB); no flush")
-SAMPLE = dict(m=2048, n=2048)          # CPU oracle sample of the same recipe (about 10 s of CPU work)
+SAMPLE = dict(m=4096, n=4096)          # CPU oracle sample of the same recipe (about 10 s on 16 Arm cores)
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -156,7 +156,7 @@ def host_cpu():
 
 
 def oracle_sample_rate(seed: int = 1001):
-    """FP64 CPU oracle on a 2048 x 2048 sample of the same recipe, scaled to full-size solves/s.
+    """FP64 CPU oracle on a 4096 x 4096 sample of the same recipe, scaled to full-size solves/s.
 
     FR-ADM costs O(m n r) per iteration and needs a similar iteration count at both sizes,
     so the full-size time is taken as the sample's solve time x (16384^2 / 2048^2).
@@ -317,8 +317,8 @@ def run_opt_full(args):
     B_0 = I until ||B_i - B_{i-1}||_F <= 1e-6 ||B_i||_F (mixed path: tensor-core P = M V and
     W = M^T U passes).  Inputs are on the device before timing (M is larger than L2).  Reports
     TSVDs/s, the two passes against the HBM roofline (each reads M once: 2 B per element), the
-    float64 oracle on a 2048 x 2048 sample, and the same call with host buffers (e2e).  Prints
-    one JSON line (supplementary; the main benchmark line is the default mode)."""
+    float64 oracle's Algorithm 4 on the same matrix, and the same call with host buffers (e2e).
+    Prints one JSON line (supplementary; the main benchmark line is the default mode)."""
     import numpy as np
     import torch
     from paper_1503_03004_gb300 import binding as B
