@@ -35,6 +35,7 @@ WORKLOAD = dict(workload="square16384_r64_bf16_mixed", m=16384, n=16384, r=64, s
                 outlier_fraction=0.05, outlier_range=[-50, 50], mu0=0.05, rho=1.5, tol=1e-9, max_iter=300,
                 l2="inputs larger than L2 (M 512 MB, multipliers 2 x 512 MB, Delta 512 MB); no flush")
 SAMPLE = dict(m=4096, n=4096)          # CPU oracle sample of the same recipe (about 10 s on 16 Arm cores)
+REF_SAMPLE = dict(m=2048, n=2048)      # one step of the reference arm (about 2.5 s on 16 Arm cores)
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -155,28 +156,32 @@ def host_cpu():
     return cores, model or platform.machine()
 
 
-def oracle_sample_rate(seed: int = 1001):
-    """FP64 CPU oracle on a 4096 x 4096 sample of the same recipe, scaled to full-size solves/s.
+def oracle_sample_rate(seed: int = 1001, sample=None):
+    """FP64 CPU oracle on a sample of the same recipe (default SAMPLE, 4096 x 4096), scaled to
+    full-size solves/s.
 
-    FR-ADM costs O(m n r) per iteration and needs a similar iteration count at both sizes,
-    so the full-size time is taken as the sample's solve time x (16384^2 / 2048^2).
+    FR-ADM costs O(m n r) per iteration and needs a similar iteration count at both sizes
+    (42 at 4096^2, 41 at 16384^2), so the full-size time is taken as the sample's solve time x
+    (m n of the workload / m n of the sample).
     """
+    sample = sample or SAMPLE
     import numpy as np
     from oracle import fradm as O
     from paper_1503_03004_gb300 import synth
-    p = synth.planted(SAMPLE["m"], SAMPLE["n"], WORKLOAD["r"], p=WORKLOAD["outlier_fraction"], amp=50.0, seed=seed,
+    p = synth.planted(sample["m"], sample["n"], WORKLOAD["r"], p=WORKLOAD["outlier_fraction"], amp=50.0, seed=seed,
                       dtype="bf16")
     M = p.values_f64()
     t0 = time.perf_counter()
     res = O.fr_adm(M, WORKLOAD["r"], rho=WORKLOAD["rho"], mu0=WORKLOAD["mu0"], tol=WORKLOAD["tol"],
                    max_iter=WORKLOAD["max_iter"])
     dt = time.perf_counter() - t0
-    scale = (WORKLOAD["m"] * WORKLOAD["n"]) / (SAMPLE["m"] * SAMPLE["n"])
+    scale = (WORKLOAD["m"] * WORKLOAD["n"]) / (sample["m"] * sample["n"])
     cores, model = host_cpu()
     return {"value": 1.0 / (dt * scale), "unit": "solves/s", "cores": cores, "cpu_model": model, "kind": "oracle",
-            "sample": (f"one FP64 oracle solve of a {SAMPLE['m']}x{SAMPLE['n']} r=64 sample of the same recipe "
-                       f"({res.iters} iterations, {dt:.1f} s), scaled by m*n to 16384x16384"),
-            "sample_iters": res.iters, "sample_seconds": dt, "converged": bool(res.converged)}, np
+            "sample": (f"one FP64 oracle solve of a {sample['m']}x{sample['n']} r=64 sample of the same recipe "
+                       f"({res.iters} iterations, {dt:.1f} s), scaled by m*n ({scale:g}x) to "
+                       f"{WORKLOAD['m']}x{WORKLOAD['n']}"),
+            "sample_iters": res.iters, "sample_seconds": dt, "scale": scale, "converged": bool(res.converged)}, np
 
 
 def oracle_sample_error(U, Bm, V, S):
@@ -217,6 +222,20 @@ def aggregate(steps: int, elapsed_ms: float) -> float:
     return world * steps / (reduce_max(elapsed_ms) / 1000.0)
 
 
+def relaunch_cmd(argv, nproc: int, port: int):
+    """Command that runs this script as `nproc` replica ranks (one process per GPU) under
+    torch.distributed.run on this node, rendezvous on 127.0.0.1."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={nproc}",
+            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *argv]
+
+
+def free_port() -> int:
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
 def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -224,31 +243,69 @@ def dist_setup():
     return rank, world, local
 
 
+def _serving_item(q):
+    """Stored bfloat16 bits of one serving request's matrix (a pool worker: host work only)."""
+    from paper_1503_03004_gb300 import synth
+    return synth.planted(q.m, q.n, q.r, p=q.p, amp=50.0, seed=q.seed, dtype="bf16").M
+
+
+def _serving_oracle(args):
+    """Float64 oracle (Algorithm 1) of one serving request: L = U B V^T (a pool worker)."""
+    q, kw = args
+    from oracle import fradm as O
+    from paper_1503_03004_gb300 import synth
+    prob = synth.planted(q.m, q.n, q.r, p=q.p, amp=50.0, seed=q.seed, dtype="bf16")
+    ref = O.fr_adm(prob.values_f64(), q.r, **kw)
+    return ref.L, ref.iters, bool(ref.converged)
+
+
 def run_serving(args):
-    """Serving-stream workload: uneven planted requests (m in [256, 8192], n in [16, 512],
-    r in {3, 5, 10, 25}, outliers 2-15 % in [-50, 50], bf16 storage), three ways:
+    """Serving-stream workload: `--requests` uneven planted requests (default 4096: m in [256, 8192],
+    n in [16, 512], r in {3, 5, 10, 25}, outliers 2-15 % in [-50, 50], bf16 storage), three ways:
       * serving: the mixed path through sfr_submit / sfr_poll with --slots slots, all requests
         queued at once (throughput), then again with Poisson arrivals at 70 % of that rate
         (latency p50 / p99 from arrival to completion);
       * per-problem float64: sfr_solve one request at a time on the float64 path;
       * per-problem mixed: sfr_solve one request at a time on the mixed path.
-    Inputs are on the device before timing.  Prints one JSON line (supplementary; the main
-    benchmark line is the default mode)."""
+    Only requests that end with SFR_OK count as solves; the line carries every outcome's count.
+    Accuracy: on `--check` seeded requests (m n <= 2^20) the float64 oracle runs on the host and
+    the serving (mixed) and per-problem float64 results are compared with it (relative error of
+    L = U B V^T).  Inputs are on the device before timing.  Prints one JSON line (supplementary;
+    the main benchmark line is the default mode)."""
+    import multiprocessing as mproc
     import numpy as np
-    import torch
-    from paper_1503_03004_gb300 import binding as B, synth
-    torch.cuda.set_device(0)
+    from paper_1503_03004_gb300 import synth
     reqs = synth.request_stream(args.requests, rate_per_s=1000.0)
+    kw = dict(rho=1.5, mu0=0.05, tol=1e-9, max_iter=300)
+    g = synth.rng(77)
+    small = [i for i, q in enumerate(reqs) if q.m * q.n <= (1 << 20)]
+    check = sorted(int(i) for i in g.choice(small, size=min(args.check, len(small)), replace=False))
+    # host work (inputs, and the oracle on the checked requests) in a spawn pool of single-threaded
+    # workers, all before any CUDA call of this process and outside every timed region
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    os.environ.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
+    try:
+        with mproc.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+            mats = pool.map(_serving_item, reqs, chunksize=16)
+            refs = pool.map(_serving_oracle, [(reqs[i], kw) for i in check])
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    import torch
+    from paper_1503_03004_gb300 import binding as B
+    torch.cuda.set_device(0)
     items = []
-    for q in reqs:
-        prob = synth.planted(q.m, q.n, q.r, p=q.p, amp=50.0, seed=q.seed, dtype="bf16")
-        Md = torch.from_numpy(prob.M.view(np.int16)).view(torch.bfloat16).cuda()
+    for q, bits in zip(reqs, mats):
+        Md = torch.from_numpy(bits.view(np.int16)).view(torch.bfloat16).cuda()
         f64 = dict(dtype=torch.float64, device="cuda")
         out = dict(U=torch.empty((q.m, q.r), **f64), B=torch.empty((q.r, q.r), **f64),
                    V=torch.empty((q.n, q.r), **f64), S=torch.empty((q.m, q.n), dtype=torch.float32, device="cuda"))
         items.append((q, Md, out))
+    del mats
     torch.cuda.synchronize()
-    kw = dict(rho=1.5, mu0=0.05, tol=1e-9, max_iter=300)
 
     def mk(q, Md, out, prec):
         p = B.make_problem(m=q.m, n=q.n, r=q.r, M_ptr=Md.data_ptr(), m_dtype=B.BF16, precision=prec, **kw)
@@ -256,29 +313,45 @@ def run_serving(args):
                             S_ptr=out["S"].data_ptr(), s_dtype=B.F32, lds=q.n)
         return p, res
 
+    def rel_errs(refs):
+        errs = []
+        for k, (Lref, _, _) in zip(check, refs):
+            out = items[k][2]
+            L = (out["U"] @ out["B"] @ out["V"].T).cpu().numpy()
+            errs.append(float(np.linalg.norm(L - Lref) / np.linalg.norm(Lref)))
+        return errs
+
     def sequential(prec):
+        counts = {}
         with B.Context(0) as ctx:
-            for q, Md, out in items[:8]:  # warm-up: graphs, workspaces
+            for q, Md, out in items[:8]:  # warm-up: graphs, workspaces, tuned grids
                 p, res = mk(q, Md, out, prec)
                 ctx.solve(p, res)
             t0 = time.perf_counter()
             for q, Md, out in items:
                 p, res = mk(q, Md, out, prec)
-                if ctx.solve(p, res) not in (B.OK, B.E_NOCONV):
-                    raise RuntimeError(ctx.last_error())
-            return len(items) / (time.perf_counter() - t0)
+                st = ctx.solve(p, res)
+                counts[B.STATUS_NAMES.get(st, str(st))] = counts.get(B.STATUS_NAMES.get(st, str(st)), 0) + 1
+            wall = time.perf_counter() - t0
+        return counts.get("OK", 0) / wall, counts
 
     def serving(rate):
         with B.Context(0, max_slots=args.slots, hbm_budget_bytes=args.budget_gb << 30) as ctx:
             for q, Md, out in items[:args.slots]:
                 p, res = mk(q, Md, out, B.PREC_MIXED)
                 ctx.poll(ctx.submit(p, res), -1)
-            keep, pending, done = [], {}, {}
+            keep, pending, done, counts = [], {}, {}, {}
 
             def reap():
-                for t in [t for t in pending if ctx.poll(t, 0) != B.PENDING]:
+                for t in list(pending):
+                    st = ctx.poll(t, 0)
+                    if st == B.PENDING:
+                        continue
                     k, ts = pending.pop(t)
-                    done[k] = time.perf_counter() - ts
+                    name = B.STATUS_NAMES.get(st, str(st))
+                    counts[name] = counts.get(name, 0) + 1
+                    if st == B.OK:
+                        done[k] = time.perf_counter() - ts
 
             t0 = time.perf_counter()
             for k, (q, Md, out) in enumerate(items):
@@ -294,19 +367,29 @@ def run_serving(args):
                 reap()
                 time.sleep(1e-4)
             wall = time.perf_counter() - t0
-            lat = sorted(v * 1000.0 for v in done.values())
-            return len(items) / wall, lat[len(lat) // 2], lat[min(len(lat) - 1, int(0.99 * len(lat)))]
+            lat = sorted(v * 1000.0 for v in done.values()) or [float("nan")]
+            return (counts.get("OK", 0) / wall, lat[len(lat) // 2], lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                    counts)
 
-    thr, _, _ = serving(None)
+    thr, _, _, counts = serving(None)
+    err_serving = rel_errs(refs)  # results of the throughput run (mixed path, through the slots)
     rate = 0.7 * thr
-    _, p50, p99 = serving(rate)
-    f64 = sequential(B.PREC_FP64)
-    mix = sequential(B.PREC_MIXED)
+    _, p50, p99, counts_lat = serving(rate)
+    f64, counts_f64 = sequential(B.PREC_FP64)
+    err_f64 = rel_errs(refs)
+    mix, counts_mix = sequential(B.PREC_MIXED)
     line = {"metric": "serving solves/s", "requests": len(items), "slots": args.slots,
-            "value": thr, "unit": "solves/s", "per_problem_fp64": f64, "per_problem_mixed": mix,
-            "latency_ms_at_rate": {"rate_per_s": rate, "p50": p50, "p99": p99},
+            "value": thr, "unit": "solves/s", "status_counts": counts,
+            "per_problem_fp64": f64, "per_problem_fp64_status_counts": counts_f64,
+            "per_problem_mixed": mix, "per_problem_mixed_status_counts": counts_mix,
+            "latency_ms_at_rate": {"rate_per_s": rate, "p50": p50, "p99": p99, "status_counts": counts_lat},
+            "accuracy": {"against": "float64 oracle (Algorithm 1) on the host", "requests_checked": check,
+                         "oracle_converged": all(c for _, _, c in refs),
+                         "serving_mixed_max_rel_err_L": max(err_serving), "mixed_bar": 1e-5,
+                         "per_problem_fp64_max_rel_err_L": max(err_f64), "fp64_bar": 1e-9},
             "config": {"workload": "serving_stream", "m": [256, 8192], "n": [16, 512], "r": [3, 5, 10, 25],
-                       "outlier_fraction": [0.02, 0.15], "storage": "bf16", "tol": 1e-9}}
+                       "outlier_fraction": [0.02, 0.15], "storage": "bf16", "tol": 1e-9,
+                       "solves_counted": "status OK only"}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -408,37 +491,6 @@ OTHER_CONFIGS = {
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA per clock x 2 flops x max SM clock
 
 
-def affinity_device(n: int, k: int, seed: int, p_out: float = 0.03):
-    """The affinity recipe generated on the device with torch's seeded generator (the float64
-    numpy generator needs tens of GB of host memory at n = 32768): cluster labels shuffled,
-    within 0.8 + N(0, 0.05^2), across 0.05 + N(0, 0.02^2), noise mirrored across the diagonal,
-    3% symmetric additive outliers U[0, 1]; bfloat16 storage.  Same distribution as
-    synth.affinity, different bits."""
-    import torch
-    g = torch.Generator(device="cuda").manual_seed(seed)
-    sizes = [n // k + (1 if c < n % k else 0) for c in range(k)]
-    labels = torch.repeat_interleave(torch.arange(k, device="cuda"), torch.tensor(sizes, device="cuda"))
-    labels = labels[torch.randperm(n, generator=g, device="cuda")]
-    A = torch.empty((n, n), dtype=torch.float32, device="cuda")
-    out = torch.empty((n, n), dtype=torch.bfloat16, device="cuda")
-    blk = 4096
-    for i0 in range(0, n, blk):  # upper triangle of the noisy block pattern, row block by row block
-        same = labels[i0:i0 + blk, None] == labels[None, :]
-        noise = torch.randn((min(blk, n - i0), n), generator=g, device="cuda")
-        A[i0:i0 + blk] = torch.where(same, 0.8 + 0.05 * noise, 0.05 + 0.02 * noise)
-        hit = torch.rand((min(blk, n - i0), n), generator=g, device="cuda") < p_out
-        d = torch.arange(min(blk, n - i0), device="cuda")
-        hit[d, i0 + d] = False  # no outliers on the diagonal (the recipe draws them off it)
-        A[i0:i0 + blk] += torch.where(hit, torch.rand((min(blk, n - i0), n), generator=g, device="cuda"), 0.0)
-    for i0 in range(0, n, blk):  # mirror: row block i0 takes column block i0 of the upper triangle
-        rows = slice(i0, min(n, i0 + blk))
-        up = torch.triu(A[rows], diagonal=i0)  # entries with j >= i
-        low = torch.tril(A[:, rows].T, diagonal=i0 - 1)  # entries with j < i, from rows j's upper part
-        out[rows] = (up + low).to(torch.bfloat16)
-    del A
-    return out
-
-
 def run_config(args):
     """Solves/s of one of the other workloads (device-resident inputs, CUDA events on the
     library stream), the sweep against its roofline (HBM for the float32 / bfloat16 sweeps,
@@ -457,15 +509,13 @@ def run_config(args):
     elif name == "photometric_1048576x40_r3":
         prob, prec, mu0, s_dtype = synth.photometric(seed=1002), B.PREC_MIXED, 1.0, B.F32
     else:
-        prob, prec, mu0, s_dtype = None, B.PREC_MIXED, 1.0, B.F32
+        # the tile-wise generator: the same bits the oracle's samples were computed from
+        prob, prec, mu0, s_dtype = synth.affinity(n=32768, k=20, seed=1003, dtype="bf16"), B.PREC_MIXED, 1.0, B.F32
         nys_l = 2048
-    if prob is not None:
-        M_dev = (torch.from_numpy(prob.M.view(np.int16)).view(torch.bfloat16) if prob.dtype == "bf16"
-                 else torch.from_numpy(prob.M)).cuda()
-        r = prob.r
-    else:
-        M_dev, r = affinity_device(32768, 20, seed=1003), 20
         perm = torch.from_numpy(synth.row_permutation(32768, 5)).cuda()
+    M_dev = (torch.from_numpy(prob.M.view(np.int16)).view(torch.bfloat16) if prob.dtype == "bf16"
+             else torch.from_numpy(prob.M)).cuda()
+    r = prob.r
     m, n = M_dev.shape
     code = {torch.float64: B.F64, torch.float32: B.F32, torch.bfloat16: B.BF16}[M_dev.dtype]
     stream = torch.cuda.Stream()
@@ -633,7 +683,8 @@ def run_phase(args):
     r / 800 in {0.01, 0.02, 0.04, 0.06, 0.08} (the library's r <= 64 caps it there), outlier
     fraction 0.05 .. 0.50, the Sec. 5.1 entries (A, B ~ N(0, 1), outliers in [-1, 1]), `--reps`
     repetitions per cell.  All problems go through sfr_submit / sfr_poll (8 slots, mixed path;
-    mu0 = 1.25 / ||M||_2 as in Sec. 7c, rho = 1.5, tol 1e-9).  Per cell: the paper's error
+    mu0 = 1.25 / ||M||_2, the scale-aware start of the inexact ALM the paper builds on, rho = 1.5,
+    tol 1e-9).  Per cell: the paper's error
     measure (1 / K) sum_z sum_ij psi_eps(S_z - S*_z) / (m n), psi_eps(s) = |s| if |s| > eps else 0,
     eps = 1e-3, and Err.L; plus the batch's throughput.  Prints one JSON line."""
     import numpy as np
@@ -692,20 +743,29 @@ def run_phase(args):
 
 
 def run_reference(args):
+    """The reference arm: the float64 oracle (the slow reference program) on the host cores.
+
+    Each step is one oracle solve of a REF_SAMPLE-sized sample of the workload's recipe (a
+    bounded sample, so that the run ends within a few minutes); `ms_per_step` is that measured
+    wall time, and `value` is the full workload's rate it implies (sample rate / scale, scale =
+    the ratio of element counts, since the method is O(m n r) per iteration)."""
     rank, world, _ = dist_setup()
     if rank != 0:
         return 0
-    rates = []
-    info = None
+    times, info = [], None
     for i in range(args.warmup + args.steps):
-        info, _ = oracle_sample_rate()
+        info, _ = oracle_sample_rate(sample=REF_SAMPLE)
         if i >= args.warmup:
-            rates.append(info["value"])
-    value = args.steps / sum(1.0 / r for r in rates)
+            times.append(info["sample_seconds"])
+    per_step = sum(times) / len(times)
+    value = 1.0 / (per_step * info["scale"])
     line = {"impl": "reference", "metric": "solves/s", "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": WORKLOAD,
+            "config": WORKLOAD | {"scaled": (f"each step solves a {REF_SAMPLE['m']}x{REF_SAMPLE['n']} sample of "
+                                             f"the recipe; value = its rate / {info['scale']:g} (element count)"),
+                                  "sample_m": REF_SAMPLE["m"], "sample_n": REF_SAMPLE["n"]},
+            "sample_ms_per_step": 1000.0 * per_step, "scale_to_workload": info["scale"],
             "cpu_baseline": {k: info[k] for k in ("kind", "cores", "cpu_model", "sample")} | {"value": value,
                                                                                           "unit": "solves/s"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -734,12 +794,17 @@ def main():
     ap.add_argument("--phase", action="store_true",
                     help="supplementary: the Fig. 2 phase transition for FR-ADM, batched through the serving slots")
     ap.add_argument("--reps", type=int, default=2)
-    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=4096)
+    ap.add_argument("--check", type=int, default=8, help="serving: requests checked against the float64 oracle")
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--budget-gb", type=int, default=64)
     ap.add_argument("--m", type=int, default=WORKLOAD["m"],
                     help="square size of the same recipe (smaller sizes are for profiler captures)")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # --gpus N outside torchrun: start N replica ranks (each solves its own problem on its own
+        # GPU; barrier and max-time reduction only)
+        return subprocess.call(relaunch_cmd(sys.argv[1:], args.gpus, free_port()))
     if args.m != WORKLOAD["m"]:
         mb = args.m * args.m * 2 // (1 << 20)
         WORKLOAD.update(m=args.m, n=args.m, workload=f"square{args.m}_r64_bf16_mixed",

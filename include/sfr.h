@@ -65,6 +65,13 @@ typedef enum { SFR_PREC_FP64 = 0, SFR_PREC_MIXED = 1 } sfr_precision;
 
 typedef enum { SFR_MEM_DEVICE = 0, SFR_MEM_HOST = 1 } sfr_memspace;
 
+/* Bits of sfr_result.path: which kernels a solve ran. */
+typedef enum {
+  SFR_PATH_TC = 1           /* the m x n sweep and W pass ran on the tensor cores (tcgen05, TMA):
+                               mixed precision with bfloat16 M, 33 <= r <= 64, n and ldm multiples
+                               of 8 and a 16-byte aligned M; clear = the SIMT passes            */
+} sfr_path_flag;
+
 typedef struct sfr_ctx sfr_ctx;
 
 typedef struct {
@@ -125,6 +132,8 @@ typedef struct {
   double rel_residual;      /* ||M - L - S||_F / ||M||_F after the last iteration          */
   double lambda_min_B;      /* smallest eigenvalue of the returned B (SPD diagnostic)      */
   sfr_status status;        /* outcome of this problem                                     */
+  int32_t path;             /* sfr_path_flag bits of the kernels this solve ran (FR-Nys: of
+                               either block solve)                                           */
 } sfr_result;
 
 /* FixedRankOptFull (Algorithm 4, Appendix): FixedRankOptStep (Algorithm 3)
@@ -193,20 +202,20 @@ sfr_status sfr_fixed_rank_opt_full(sfr_ctx* ctx, const sfr_opt_full_problem* pro
 sfr_status sfr_stats(sfr_ctx* ctx, sfr_kernel_stat* out, int32_t count, int32_t reset);
 
 /* sfr_solve without any device allocation, for callers that cannot allocate:
- * code that runs while a CUDA graph is being captured, processes whose device
- * memory belongs to a fixed pool or to a framework allocator, and paths that may
- * not take the allocator's locks.  The paper has no counterpart; this is a
- * library convenience.  It runs the same FR-ADM kernels as sfr_solve, eagerly
- * on the context's stream, with all workspace taken from one 32 MiB __device__
- * array built into the library (every GPU that loads libsfr holds it until the
- * process exits).
+ * processes whose device memory belongs to a fixed pool or to a framework
+ * allocator, and latency-critical paths that may not take the allocator's locks.
+ * The paper has no counterpart; this is a library convenience.  It runs the same
+ * FR-ADM kernels as sfr_solve (the SIMT passes, sfr_result.path = 0), eagerly on
+ * the context's stream, with all workspace taken from one 32 MiB __device__ array
+ * built into the library (every GPU that loads libsfr holds it until the process
+ * exits).
  *   - FR-ADM only (nys_l == 0) and device buffers only (mem == SFR_MEM_DEVICE).
  *   - A problem whose workspace exceeds the array is refused with SFR_E_NOMEM.
  *     The workspace is about 24 bytes (float64 path) or 12 bytes (mixed path)
  *     per element of M plus the thin and r x r buffers; 500 x 500 at r = 25
  *     in float64 needs about 10 MiB.
- *   - The first call on a device looks up the array's device address; make that
- *     first call before any stream capture begins.
+ *   - The first call on a device looks up the array's device address and keeps
+ *     it; do not call this entry point after a cudaDeviceReset in the process.
  *   - All calls share the array and it keeps the previous call's contents (the
  *     solve clears what must start at zero).  Calls whose GPU work overlaps --
  *     from two host threads, or two contexts on one device -- race on it.

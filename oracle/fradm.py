@@ -194,8 +194,8 @@ def fr_adm(M, r: int, *, rho: float = 1.5, mu0: float = 1.0, mu_max: float = 1e9
 
 @dataclasses.dataclass
 class FRNysResult:
-    L: np.ndarray            # m x n, in the row order of the input M
-    S: np.ndarray            # m x n, in the row order of the input M
+    L: np.ndarray            # m x n, in the row order of the input M (sampled: L at the samples)
+    S: np.ndarray            # m x n, in the row order of the input M (sampled: S at the samples)
     left: FRADMResult        # FR-ADM on the m x l column block of the shuffled M
     top: FRADMResult         # FR-ADM on the l x n row block of the shuffled M
     perm: np.ndarray         # row permutation: shuffled row i is input row perm[i]
@@ -207,26 +207,40 @@ def truncated_pinv(A: np.ndarray, r: int) -> np.ndarray:
     return (Wt[:r].T / s[:r]) @ Q[:, :r].T
 
 
-def fr_nys(M, r: int, l: int, perm, **adm_kwargs) -> FRNysResult:
+def fr_nys(M, r: int, l: int, perm, *, sample=None, **adm_kwargs) -> FRNysResult:
     """Algorithm 2 (FR-Nys).
 
     M_tilde = rows of M shuffled by `perm` (M_tilde[i] = M[perm[i]]);
     (L_L, S_L) = FR-ADM(M_tilde[:, :l], r); (L_T, S_T) = FR-ADM(M_tilde[:l, :], r);
     L = L_L (L_L[:l, :l])^+ L_T;  S = M_tilde - L.  Both are returned in the
     row order of the input M (the shuffle is undone at the end).
+
+    sample = (ii, jj): instead of the dense m x n L and S, return their entries at the input-order
+    positions (ii[k], jj[k]) only, each from the same formula (row inv[ii[k]] of L_L (L_L[:l, :l])^+
+    times column jj[k] of L_T, inv the inverse shuffle), so that large inputs need no m x n
+    intermediate beyond M itself.
     """
-    M = np.asarray(M, dtype=np.float64)
+    M = np.asarray(M)
     m, n = M.shape
     perm = np.asarray(perm, dtype=np.int64)
-    if sorted(perm.tolist()) != list(range(m)):
+    if not np.array_equal(np.sort(perm), np.arange(m)):
         raise ValueError("perm must be a permutation of range(m)")
     if not (r <= l <= min(m, n)):
         raise ValueError("need r <= l <= min(m, n)")
-    Mt = M[perm]
-    left = fr_adm(Mt[:, :l], r, **adm_kwargs)
-    top = fr_adm(Mt[:l, :], r, **adm_kwargs)
+    # the two blocks of M_tilde: M_tilde[:, :l] = M[perm, :l] and M_tilde[:l, :] = M[perm[:l], :]
+    left = fr_adm(np.asarray(M[perm, :l], dtype=np.float64), r, **adm_kwargs)
+    top = fr_adm(np.asarray(M[perm[:l], :], dtype=np.float64), r, **adm_kwargs)
     L_L, L_T = left.L, top.L
-    Lt = L_L @ truncated_pinv(L_L[:l, :l], r) @ L_T
+    P = L_L @ truncated_pinv(L_L[:l, :l], r)          # m x l: L_L (L_L[:l, :l])^+
+    if sample is not None:
+        ii, jj = (np.asarray(x, dtype=np.int64) for x in sample)
+        inv = np.empty(m, dtype=np.int64)
+        inv[perm] = np.arange(m)
+        Ls = np.einsum("kl,lk->k", P[inv[ii]], L_T[:, jj])
+        Ss = np.asarray(M[ii, jj], dtype=np.float64) - Ls
+        return FRNysResult(L=Ls, S=Ss, left=left, top=top, perm=perm)
+    Mt = np.asarray(M, dtype=np.float64)[perm]
+    Lt = P @ L_T
     St = Mt - Lt
     L = np.empty_like(Lt)
     S = np.empty_like(St)

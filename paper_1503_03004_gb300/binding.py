@@ -54,7 +54,11 @@ class Result(ctypes.Structure):
     _fields_ = [("U", ctypes.c_void_p), ("B", ctypes.c_void_p), ("V", ctypes.c_void_p), ("S", ctypes.c_void_p),
                 ("s_dtype", ctypes.c_int), ("lds", ctypes.c_int64), ("L", ctypes.c_void_p),
                 ("iters", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("lambda_min_B", ctypes.c_double),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("path", ctypes.c_int32)]
+
+
+# sfr_path_flag bits of Result.path
+PATH_TC = 1
 
 
 class OptFullProblem(ctypes.Structure):
@@ -181,7 +185,7 @@ def make_problem(*, m: int, n: int, r: int, M_ptr: int, m_dtype: int, ldm: int |
 
 def make_result(*, U_ptr=0, B_ptr=0, V_ptr=0, S_ptr=0, s_dtype=F64, lds=0, L_ptr=0) -> Result:
     return Result(U=U_ptr or None, B=B_ptr or None, V=V_ptr or None, S=S_ptr or None, s_dtype=s_dtype, lds=lds,
-                  L=L_ptr or None, iters=0, rel_residual=0.0, lambda_min_B=0.0, status=PENDING)
+                  L=L_ptr or None, iters=0, rel_residual=0.0, lambda_min_B=0.0, status=PENDING, path=0)
 
 
 @dataclass
@@ -195,6 +199,7 @@ class Solution:
     rel_residual: float
     lambda_min_B: float
     status: int
+    path: int = 0          # PATH_TC bit: the tensor-core sweep and W pass ran
 
 
 def solve_torch(ctx: Context, M, r: int, *, precision: int = PREC_FP64, want_L: bool = False, s_dtype: int = F64,
@@ -230,7 +235,7 @@ def solve_torch(ctx: Context, M, r: int, *, precision: int = PREC_FP64, want_L: 
     if check and st not in (OK,):
         raise SfrError(st, ctx.last_error())
     return Solution(U=U, B=B, V=V, S=S, L=L, iters=res.iters, rel_residual=res.rel_residual,
-                    lambda_min_B=res.lambda_min_B, status=st)
+                    lambda_min_B=res.lambda_min_B, status=st, path=res.path)
 
 
 @dataclass

@@ -1,20 +1,21 @@
 // sfr_solve_noalloc: FR-ADM for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at solve time: code running while a CUDA
-// graph is being captured, processes whose device memory is handed out by a
-// fixed pool or a framework allocator that must own every byte, and
-// latency-critical paths that may not take the allocator's locks.  For them
-// this entry point runs the same FR-ADM kernels as sfr_solve, but takes every
-// byte of workspace (multiplier buffers, Delta, thin products, reduction
-// partials, r x r matrices and the iteration state) from one file-scope
-// __device__ array of fixed size, so a call allocates nothing: no cudaMalloc,
-// cudaFree, graph instantiation, event or pinned buffer.
+// Some callers cannot call cudaMalloc when they solve: processes whose device memory is
+// handed out by a fixed pool or by a framework allocator that must own every byte, and
+// latency-critical paths that may not take the allocator's locks or risk its
+// fragmentation.  For them this entry point runs the same FR-ADM kernels as sfr_solve,
+// but takes every byte of workspace (multiplier buffers, Delta, thin products, reduction
+// partials, r x r matrices and the iteration state) from one file-scope __device__ array
+// of fixed size, so a call allocates nothing: no cudaMalloc, cudaFree, graph
+// instantiation, event or pinned buffer.
 //
 // The array lives in the module image, so every GPU that loads libsfr holds
-// kStaticScratchBytes of it until the process exits.  All calls share it and
-// it keeps the previous call's contents; the solve clears what must start at
-// zero.  Calls whose work overlaps on the GPU (two host threads, or two
-// contexts on one device) race on the array.
+// kStaticScratchBytes of it until the process exits.  All calls share it and it keeps the
+// previous call's contents; the solve clears what must start at zero.  Calls whose work
+// overlaps on the GPU (two host threads, or two contexts on one device) race on it.
+// The array's device address is looked up once per device (on that device's first call)
+// and kept; a device reset (cudaDeviceReset) reloads the module at a new address, so the
+// entry point must not be used in a process after it reset a device.
 #include <cstring>
 #include <mutex>
 
@@ -33,7 +34,7 @@ void* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of g_static_scratch on `device` (which must be current).  In host code
 // the symbol's name is only a host-side stand-in, not a device address, so it is looked up
-// once per device with cudaGetSymbolAddress and cached.
+// once per device with cudaGetSymbolAddress and cached (valid until a device reset).
 cudaError_t scratch_base(int device, void** out) {
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_scratch_mu);
@@ -171,6 +172,7 @@ extern "C" sfr_status sfr_solve_noalloc(sfr_ctx* ctx, const sfr_problem* prob, s
     res->iters = out.iter;
     res->rel_residual = out.res;
     res->status = (sfr_status)out.status;
+    res->path = 0;  // SIMT passes only (the tensor-core path's operand copies are not in the array)
     res->lambda_min_B = NAN;
     if (res->B && (res->status == SFR_OK || res->status == SFR_E_NOCONV)) {
       std::vector<double> hb((size_t)p.r * p.r);

@@ -22,6 +22,7 @@ DevState solver_run(Solver& sv, const sfr_problem& p, const void* Mdev, double* 
                     sfr_dtype s_dtype, int64_t lds, void* L);
 void* solver_nys_block(Solver& sv, size_t bytes);
 cudaStream_t solver_stream(Solver& sv);
+bool solver_last_tc(const Solver& sv);
 
 namespace {
 
@@ -265,9 +266,11 @@ sfr_status nys_solve_device(Solver& sv, const sfr_problem& p, const void* Mdev, 
   pl.mem = SFR_MEM_DEVICE;
   pl.m = m; pl.n = l; pl.ldm = l; pl.M = Mleft;
   DevState a = solver_run(sv, pl, Mleft, UL, BL, VL, nullptr, SFR_F64, 0, nullptr);
+  res->path |= solver_last_tc(sv) ? SFR_PATH_TC : 0;
   sfr_problem pt = pl;
   pt.m = l; pt.n = n; pt.ldm = n; pt.M = Mtop;
   DevState b = solver_run(sv, pt, Mtop, UT, BT, VT, nullptr, SFR_F64, 0, nullptr);
+  res->path |= solver_last_tc(sv) ? SFR_PATH_TC : 0;
   res->iters = a.iter + b.iter;
   res->rel_residual = std::max(a.res, b.res);
   res->lambda_min_B = NAN;

@@ -817,6 +817,7 @@ void* solver_nys_block(Solver& sv, size_t bytes) {
   return sv.nys.ptr;
 }
 cudaStream_t solver_stream(Solver& sv) { return sv.stream; }
+bool solver_last_tc(const Solver& sv) { return sv.last_tc; }
 
 sfr_status nys_solve_device(Solver& sv, const sfr_problem& p, const void* Mdev, const int64_t* perm_dev,
                             sfr_result* res, void* Sdev, void* Ldev, std::string* err);
@@ -856,6 +857,7 @@ struct Request {
   sfr_result* res;
   bool finished = false;
   sfr_status status = SFR_PENDING;
+  int passed_over = 0;  // times a later request was admitted ahead of this one
 };
 
 struct sfr_ctx {
@@ -886,7 +888,10 @@ namespace sfr {
 int ctx_device(const sfr_ctx* ctx) { return ctx->device; }
 int ctx_num_sms(const sfr_ctx* ctx) { return ctx->solver->num_sms; }
 cudaStream_t ctx_stream(const sfr_ctx* ctx) { return ctx->stream; }
-void ctx_set_error(sfr_ctx* ctx, const std::string& msg) { ctx->last_error = msg; }
+void ctx_set_error(sfr_ctx* ctx, const std::string& msg) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->last_error = msg;
+}
 }  // namespace sfr
 
 sfr_status validate(const sfr_problem* p, const sfr_result* r, std::string* why) {
@@ -915,6 +920,7 @@ sfr_status validate(const sfr_problem* p, const sfr_result* r, std::string* why)
 // Solve on `sv`, staging host buffers when p.mem == SFR_MEM_HOST.
 static sfr_status solve_with(Solver& sv, const sfr_problem& p, sfr_result* res, std::string* err) {
   try {
+    res->path = 0;
     SFR_CUDA(cudaSetDevice(sv.device));
     if (p.nys_l != 0) {
       res->status = sfr_nys_solve(sv, p, res, err);
@@ -948,6 +954,7 @@ static sfr_status solve_with(Solver& sv, const sfr_problem& p, sfr_result* res, 
       if (L) L = st + offL;
     }
     DevState out = sv.run(p, Mdev, U, B, V, S, res->s_dtype, res->lds, L);
+    res->path = sv.last_tc ? SFR_PATH_TC : 0;
     if (p.mem == SFR_MEM_HOST) {
       if (res->U) SFR_CUDA(cudaMemcpyAsync(res->U, U, 8 * (size_t)p.m * p.r, cudaMemcpyDeviceToHost, sv.stream));
       if (res->V) SFR_CUDA(cudaMemcpyAsync(res->V, V, 8 * (size_t)p.n * p.r, cudaMemcpyDeviceToHost, sv.stream));
@@ -1116,23 +1123,48 @@ static void worker_main(sfr_ctx* ctx, int slot) {
           ctx->cv_work.wait(lk);
           continue;
         }
-        need = request_bytes(ctx->queue.front()->prob, sv.num_sms);
-        if (ctx->budget && need > ctx->budget) {  // can never be admitted
-          rq = ctx->queue.front();
-          ctx->queue.pop_front();
-          rq->status = SFR_E_NOMEM;
-          rq->res->status = SFR_E_NOMEM;
-          rq->finished = true;
-          ctx->last_error = fmt("request needs %zu bytes; the HBM budget is %zu", need, ctx->budget);
+        // requests that can never fit the budget fail at once
+        bool refused = false;
+        for (auto it = ctx->queue.begin(); it != ctx->queue.end(); ++it) {
+          const size_t want = request_bytes((*it)->prob, sv.num_sms);
+          if (ctx->budget && want > ctx->budget) {
+            std::shared_ptr<Request> bad = *it;
+            ctx->queue.erase(it);
+            bad->status = SFR_E_NOMEM;
+            bad->res->status = SFR_E_NOMEM;
+            bad->finished = true;
+            ctx->last_error = fmt("request needs %zu bytes; the HBM budget is %zu", want, ctx->budget);
+            refused = true;
+            break;
+          }
+        }
+        if (refused) {
           ctx->cv_done.notify_all();
-          rq.reset();
           continue;
         }
-        if (!ctx->budget || ctx->in_use + need <= ctx->budget) break;
-        ctx->cv_work.wait(lk);  // wait for a running request to release memory
+        // the oldest request that fits the free budget; a request that does not fit yet is passed
+        // over by later, smaller ones at most kMaxPassOver times, after which admission waits for it
+        // (so a large request cannot be starved by a stream of small ones)
+        constexpr int kMaxPassOver = 64;
+        auto pick = ctx->queue.end();
+        for (auto it = ctx->queue.begin(); it != ctx->queue.end(); ++it) {
+          const size_t want = request_bytes((*it)->prob, sv.num_sms);
+          if (!ctx->budget || ctx->in_use + want <= ctx->budget) {
+            pick = it;
+            need = want;
+            break;
+          }
+          if ((*it)->passed_over >= kMaxPassOver) break;  // this one goes next: wait for memory
+        }
+        if (pick == ctx->queue.end()) {
+          ctx->cv_work.wait(lk);  // wait for a running request to release memory
+          continue;
+        }
+        for (auto it = ctx->queue.begin(); it != pick; ++it) ++(*it)->passed_over;
+        rq = *pick;
+        ctx->queue.erase(pick);
+        break;
       }
-      rq = ctx->queue.front();
-      ctx->queue.pop_front();
       ctx->in_use += need;
     }
     std::string err;
@@ -1165,7 +1197,14 @@ const char* sfr_version(void) { return "libsfr 0.1 (sm_103a)"; }
 
 const char* sfr_last_error(const sfr_ctx* ctx) {
   if (!ctx) return g_create_error.c_str();
-  return ctx->last_error.c_str();
+  // serving slots write the message from their threads: hand out a copy taken under the lock,
+  // valid until this thread's next call
+  static thread_local std::string copy;
+  {
+    std::lock_guard<std::mutex> lk(const_cast<sfr_ctx*>(ctx)->mu);
+    copy = ctx->last_error;
+  }
+  return copy.c_str();
 }
 
 sfr_status sfr_create(sfr_ctx** out, const sfr_config* cfg) {
@@ -1228,13 +1267,13 @@ sfr_status sfr_solve(sfr_ctx* ctx, const sfr_problem* prob, sfr_result* res) {
   std::string why;
   sfr_status v = validate(prob, res, &why);
   if (v != SFR_OK) {
-    ctx->last_error = why;
+    ctx_set_error(ctx, why);
     if (res) res->status = v;
     return v;
   }
   std::string err;
   sfr_status s = solve_with(*ctx->solver, *prob, res, &err);
-  if (s < 0) ctx->last_error = err;
+  if (s < 0) ctx_set_error(ctx, err);
   return s;
 }
 
@@ -1243,13 +1282,13 @@ sfr_status sfr_fixed_rank_opt_full(sfr_ctx* ctx, const sfr_opt_full_problem* pro
   std::string why;
   sfr_status v = validate_full(prob, res, &why);
   if (v != SFR_OK) {
-    ctx->last_error = why;
+    ctx_set_error(ctx, why);
     if (res) res->status = v;
     return v;
   }
   std::string err;
   sfr_status s = full_with(*ctx->solver, *prob, res, &err);
-  if (s < 0) ctx->last_error = err;
+  if (s < 0) ctx_set_error(ctx, err);
   return s;
 }
 
@@ -1258,7 +1297,7 @@ sfr_status sfr_submit(sfr_ctx* ctx, const sfr_problem* prob, sfr_result* res, ui
   std::string why;
   sfr_status v = validate(prob, res, &why);
   if (v != SFR_OK) {
-    ctx->last_error = why;
+    ctx_set_error(ctx, why);
     if (res) res->status = v;
     return v;
   }

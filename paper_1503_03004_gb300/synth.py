@@ -148,28 +148,89 @@ def photometric(side: int = 1024, n_images: int = 40, *, p_spec: float = 0.10, s
                    name=f"photometric_{side * side}x{n_images}_r3")
 
 
+AFFINITY_TILE = 2048
+
+
+def _affinity_tile(seed: int, bi: int, bj: int, rows: int, cols: int, p_out: float):
+    """Draws of the upper-triangle tile (bi, bj), bi <= bj, from its own Philox stream: standard
+    normal noise, the outlier mask and the outlier values (U[0, 1])."""
+    g = np.random.Generator(np.random.Philox(key=int(seed), counter=[0, 0, int(bi), int(bj)]))
+    z = g.standard_normal((rows, cols))
+    hit = g.random((rows, cols), dtype=np.float32) < p_out
+    val = g.random((rows, cols))
+    return z, hit, val
+
+
+def affinity_rows(n: int, k: int, i0: int, i1: int, *, p_out: float = 0.03, seed: int = 1003):
+    """Rows [i0, i1) of the affinity recipe in float64 (see `affinity`), plus the outlier mask of
+    those rows.  Memory is O((i1 - i0) n): tiles of the upper triangle are drawn from their own
+    streams, and a lower tile is the mirror of its upper tile."""
+    labels = affinity_labels(n, k, seed)
+    T = AFFINITY_TILE
+    A = np.empty((i1 - i0, n))
+    M = np.zeros((i1 - i0, n), dtype=bool)
+    for bi in range(i0 // T, (i1 - 1) // T + 1):
+        r0, r1 = bi * T, min(n, (bi + 1) * T)
+        for bj in range(n // T + (n % T > 0)):
+            c0, c1 = bj * T, min(n, (bj + 1) * T)
+            if bi <= bj:
+                z, hit, val = _affinity_tile(seed, bi, bj, r1 - r0, c1 - c0, p_out)
+                if bi == bj:  # diagonal tile: mirror its strict upper part, no outliers on the diagonal
+                    up = np.triu(np.ones((r1 - r0, c1 - c0), dtype=bool), 1)
+                    d = np.diag(z).copy()
+                    z = np.where(up, z, 0.0)
+                    z = z + z.T + np.diag(d)
+                    hit = hit & up
+                    val = np.where(hit, val, 0.0)
+                    hit = hit | hit.T
+                    val = val + val.T
+            else:  # lower tile: transpose of the upper tile (bj, bi)
+                z, hit, val = _affinity_tile(seed, bj, bi, c1 - c0, r1 - r0, p_out)
+                z, hit, val = z.T, hit.T, val.T
+            same = labels[r0:r1, None] == labels[None, c0:c1]
+            tile = np.where(same, 0.8 + 0.05 * z, 0.05 + 0.02 * z) + np.where(hit, val, 0.0)
+            a0, a1 = max(i0, r0), min(i1, r1)
+            A[a0 - i0:a1 - i0, c0:c1] = tile[a0 - r0:a1 - r0]
+            M[a0 - i0:a1 - i0, c0:c1] = hit[a0 - r0:a1 - r0]
+    return A, M
+
+
+def affinity_labels(n: int, k: int, seed: int) -> np.ndarray:
+    """Cluster labels of the affinity recipe: k clusters whose sizes differ by at most one,
+    assigned to the nodes in a random order."""
+    sizes = np.full(k, n // k)
+    sizes[: n % k] += 1
+    return rng(seed).permutation(np.repeat(np.arange(k), sizes))
+
+
 def affinity(n: int = 32768, k: int = 20, *, p_out: float = 0.03, seed: int = 1003,
              dtype: str = "bf16") -> Problem:
     """Symmetric n x n affinity of k clusters (sizes differ by at most one, labels shuffled).
 
-    Within-cluster 0.8 + N(0, 0.05^2), across 0.05 + N(0, 0.02^2) (noise mirrored
-    across the diagonal), plus 3% symmetric additive outliers U[0, 1].
+    Within-cluster 0.8 + N(0, 0.05^2), across 0.05 + N(0, 0.02^2) (noise mirrored across the
+    diagonal), plus 3% symmetric additive outliers U[0, 1] off the diagonal.  Generated row block
+    by row block (`affinity_rows`), so the host holds one float64 block at a time plus the stored
+    matrix (2 GB at n = 32768 in bfloat16).
     """
-    g = rng(seed)
-    sizes = np.full(k, n // k)
-    sizes[: n % k] += 1
-    labels = g.permutation(np.repeat(np.arange(k), sizes))
-    same = labels[:, None] == labels[None, :]
-    noise = np.where(same, g.normal(0.0, 0.05, (n, n)), g.normal(0.0, 0.02, (n, n)))
-    noise = np.triu(noise) + np.triu(noise, 1).T
-    A = np.where(same, 0.8, 0.05) + noise
-    mask = np.triu(g.random((n, n), dtype=np.float32) < p_out, 1)
-    out = np.where(mask, g.uniform(0.0, 1.0, (n, n)), 0.0)
-    A = A + out + out.T
+    labels = affinity_labels(n, k, seed)
+    out = np.empty((n, n), dtype=np.float64 if dtype == "f64" else np.float32 if dtype == "f32" else np.uint16)
+    mask = np.zeros((n, n), dtype=bool) if n <= 8192 else None
+    T = AFFINITY_TILE
+
+    def block(i0):
+        A, hit = affinity_rows(n, k, i0, min(n, i0 + T), p_out=p_out, seed=seed)
+        out[i0:i0 + T] = _store(A, dtype)
+        if mask is not None:
+            mask[i0:i0 + T] = hit
+
+    # row blocks are independent (each draws its tiles from their own streams): a few threads
+    # (numpy releases the GIL in its generators and element-wise kernels), same bits in any order
+    import concurrent.futures
+    with concurrent.futures.ThreadPoolExecutor(max_workers=4) as ex:
+        list(ex.map(block, range(0, n, T)))
     Z = np.zeros((n, k))
     Z[np.arange(n), labels] = 1.0
-    return Problem(M=_store(A, dtype), dtype=dtype, r=k, U0=Z, V0=None, S0_mask=mask | mask.T,
-                   name=f"affinity_{n}_k{k}_{dtype}")
+    return Problem(M=out, dtype=dtype, r=k, U0=Z, V0=None, S0_mask=mask, name=f"affinity_{n}_k{k}_{dtype}")
 
 
 def row_permutation(m: int, seed: int) -> np.ndarray:

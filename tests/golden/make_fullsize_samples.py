@@ -9,6 +9,8 @@ path.  Usage (from the repository root):
 
     python tests/golden/make_fullsize_samples.py photometric   # 1048576 x 40, r = 3 (~2 min)
     python tests/golden/make_fullsize_samples.py square16384   # 16384 x 16384, r = 64 (~30 GB RAM)
+    python tests/golden/make_fullsize_samples.py square16384_f32   # the same recipe stored in float32
+    python tests/golden/make_fullsize_samples.py affinity   # 32768^2 FR-Nys, l = 2048 (~20 GB RAM)
 """
 import os
 import sys
@@ -33,6 +35,15 @@ WORKLOADS = {
     "square16384": dict(make=lambda: synth.square_large(16384, 64, dtype="bf16", seed=1001), r=64,
                         kw=dict(rho=1.5, mu0=0.05, tol=1e-9, max_iter=300),
                         out="square16384_r64_bf16_samples.txt"),
+    # the same recipe stored in float32: the workload of the float64 path at full size
+    "square16384_f32": dict(make=lambda: synth.square_large(16384, 64, dtype="f32", seed=1001), r=64,
+                            kw=dict(rho=1.5, mu0=0.05, tol=1e-9, max_iter=300),
+                            out="square16384_r64_f32_samples.txt"),
+    # spectral-clustering affinity, n = 32768, 20 clusters, bf16, through FR-Nys (Algorithm 2) with
+    # l = 2048 sampled columns and the row shuffle synth.row_permutation(32768, 5)
+    "affinity": dict(make=lambda: synth.affinity(n=32768, k=20, seed=1003, dtype="bf16"), r=20, nys_l=2048,
+                     perm_seed=5, kw=dict(rho=1.5, mu0=1.0, tol=1e-9, max_iter=300),
+                     out="affinity_32768_r20_nys2048_samples.txt"),
 }
 
 
@@ -46,23 +57,36 @@ def main(name: str) -> None:
     prob = w["make"]()
     M = prob.values_f64()
     m, n = M.shape
-    t0 = time.time()
-    ref = O.fr_adm(M, w["r"], **w["kw"])
-    dt = time.time() - t0
     ii, jj = sample_positions(m, n)
+    t0 = time.time()
+    if "nys_l" in w:
+        perm = synth.row_permutation(m, w["perm_seed"])
+        ref = O.fr_nys(M, w["r"], w["nys_l"], perm, sample=(ii, jj), **w["kw"])
+        dt = time.time() - t0
+        head = [f"# Float64 oracle (Algorithm 2, FR-Nys, l = {w['nys_l']}, row shuffle "
+                f"synth.row_permutation({m}, {w['perm_seed']})) on {prob.name}, inner FR-ADM parameters {w['kw']}.",
+                f"# oracle time {dt:.0f} s, blocks converged {bool(ref.left.converged)} / {bool(ref.top.converged)}.",
+                f"iters {ref.left.iters + ref.top.iters}", f"iters_left {ref.left.iters}", f"iters_top {ref.top.iters}",
+                "# columns: i j L_ij S_ij 0 (FR-Nys: S = M - L, no threshold)"]
+        rows = zip(ii, jj, ref.L, ref.S, np.zeros(len(ii)))
+    else:
+        ref = O.fr_adm(M, w["r"], **w["kw"])
+        dt = time.time() - t0
+        z = M[ii, jj] - ref.L[ii, jj] + ref.Y_prev[ii, jj] / ref.mu_last
+        head = [f"# Float64 oracle (Algorithm 1, FR-ADM) on {prob.name}, parameters {w['kw']}.",
+                f"# oracle time {dt:.0f} s, converged {bool(ref.converged)}.",
+                f"iters {ref.iters}", f"normL {np.linalg.norm(ref.L):.17g}", f"mu_last {ref.mu_last:.17g}",
+                "# columns: i j L_ij S_ij z_ij (z = M - L + Y_prev / mu_last; S_ij is nonzero iff |z_ij| > 1/mu_last)"]
+        rows = zip(ii, jj, ref.L[ii, jj], ref.S[ii, jj], z)
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), w["out"])
     with open(path, "w") as f:
-        f.write(f"# Float64 oracle (Algorithm 1, FR-ADM) on {prob.name}, parameters {w['kw']}.\n")
+        f.write(head[0] + "\n")
         f.write("# Written by tests/golden/make_fullsize_samples.py (oracle and seeded inputs only);\n")
-        f.write(f"# oracle time {dt:.0f} s, converged {bool(ref.converged)}.\n")
-        f.write(f"iters {ref.iters}\n")
-        f.write(f"normL {np.linalg.norm(ref.L):.17g}\n")
-        f.write(f"mu_last {ref.mu_last:.17g}\n")
-        f.write("# columns: i j L_ij S_ij z_ij (z = M - L + Y_prev / mu_last; S_ij is nonzero iff |z_ij| > 1/mu_last)\n")
-        z = M[ii, jj] - ref.L[ii, jj] + ref.Y_prev[ii, jj] / ref.mu_last
-        for a, b, lv, sv, zv in zip(ii, jj, ref.L[ii, jj], ref.S[ii, jj], z):
+        for h in head[1:]:
+            f.write(h + "\n")
+        for a, b, lv, sv, zv in rows:
             f.write(f"{a} {b} {lv:.17g} {sv:.17g} {zv:.17g}\n")
-    print(path, ref.iters, f"{dt:.0f} s")
+    print(path, f"{dt:.0f} s")
 
 
 if __name__ == "__main__":

@@ -124,6 +124,50 @@ def test_square16384_r64_bf16_mixed_full_size_matches_oracle_samples(ctx):
     assert 0 <= sol.iters - int(meta["iters"]) <= 4
 
 
+def test_square16384_r64_f32_fp64_full_size_matches_oracle_samples(ctx):
+    # the 16384 x 16384 rank-64 recipe stored in float32, solved on the float64 path
+    path = os.path.join(GOLDEN, "square16384_r64_f32_samples.txt")
+    if not os.path.exists(path):
+        pytest.skip("oracle samples for the 16384 x 16384 float32 workload not generated")
+    meta, ii, jj, L_ref, S_ref, z_ref = _golden("square16384_r64_f32_samples.txt")
+    prob = synth.square_large(16384, 64, dtype="f32", seed=1001)
+    sol = B.solve_torch(ctx, _dev(prob), 64, rho=1.5, mu0=0.05, tol=1e-9, max_iter=300, precision=B.PREC_FP64,
+                        s_dtype=B.F64)
+    assert sol.status == B.OK and sol.rel_residual <= 1e-9
+    assert sol.iters == int(meta["iters"])
+    L = _sampled_L(sol, ii, jj)
+    S = _sampled_S(sol, ii, jj)
+    assert _rel(L, L_ref) <= 1e-9
+    thr = 1.0 / meta["mu_last"]
+    near = np.abs(np.abs(z_ref) - thr) <= 1e-9 * max(1.0, np.abs(z_ref).max())
+    assert np.count_nonzero(((S != 0) != (S_ref != 0)) & ~near) == 0
+    assert np.linalg.norm(S - S_ref) <= 1e-9 * np.linalg.norm(L_ref)
+    _invariants(sol, 1e-10)
+
+
+def test_affinity_nystrom_32768_full_size_matches_oracle_samples(ctx):
+    # the spectral-clustering workload at its full size: n = 32768, 20 clusters, bf16, FR-Nys with
+    # l = 2048 on the mixed path (the call bench.py --config affinity_32768_r20_nys2048 times)
+    path = os.path.join(GOLDEN, "affinity_32768_r20_nys2048_samples.txt")
+    if not os.path.exists(path):
+        pytest.skip("oracle samples for the 32768^2 affinity workload not generated")
+    meta, ii, jj, L_ref, S_ref, _ = _golden("affinity_32768_r20_nys2048_samples.txt")
+    prob = synth.affinity(n=32768, k=20, seed=1003, dtype="bf16")
+    Md = _dev(prob)
+    del prob
+    perm = torch.from_numpy(synth.row_permutation(32768, 5)).cuda()
+    sol = B.solve_torch(ctx, Md, 20, nys_l=2048, nys_perm=perm, rho=1.5, mu0=1.0, tol=1e-9, max_iter=300,
+                        precision=B.PREC_MIXED, s_dtype=B.F32, want_L=True)
+    assert sol.status == B.OK
+    assert abs(sol.iters - int(meta["iters"])) <= 8
+    it = torch.from_numpy(ii).cuda()
+    jt = torch.from_numpy(jj).cuda()
+    L = sol.L[it, jt].double().cpu().numpy()
+    S = sol.S[it, jt].double().cpu().numpy()
+    assert _rel(L, L_ref) <= 1e-5
+    assert np.linalg.norm(S - S_ref) <= 1e-5 * np.linalg.norm(L_ref)
+
+
 def test_affinity_nystrom_8192_matches_oracle(ctx):
     # the spectral-clustering workload through FR-Nys at n = 8192 with l = 512 (the full
     # workload's l / n = 2048 / 32768); the oracle runs here (about 30 s)

@@ -53,3 +53,14 @@ def test_single_process_reduction_is_identity():
     import bench
     assert bench.reduce_max(3.5) == 3.5
     assert bench.aggregate(4, 2000.0) == pytest.approx(2.0)
+
+
+def test_gpus_flag_relaunches_as_replica_ranks():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    cmd = bench.relaunch_cmd(["--gpus", "2", "--steps", "3"], 2, 29511)
+    assert cmd[1:4] == ["-m", "torch.distributed.run", "--nnodes=1"]
+    assert "--nproc-per-node=2" in cmd and cmd[cmd.index("--master-addr") + 1] == "127.0.0.1"
+    assert cmd[cmd.index("--master-port") + 1] == "29511"
+    assert cmd[-4:] == ["--gpus", "2", "--steps", "3"] and cmd[-5].endswith("bench.py")

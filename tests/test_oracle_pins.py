@@ -308,3 +308,18 @@ def test_frnys_recovers_planted_low_rank():
 def test_truncated_pinv_matches_numpy_pinv_on_full_rank():
     A = _rand(93, 6, 6)
     np.testing.assert_allclose(O.truncated_pinv(A, 6), np.linalg.pinv(A), atol=1e-12)
+
+
+def test_frnys_sampled_output_equals_dense_output():
+    # the sampled form (used at sizes where the dense m x n L cannot be formed) takes the same
+    # entries of the same L_L (L_L[:l, :l])^+ L_T and M - L as the dense form
+    m, n, r, l = 260, 230, 4, 40
+    prob = synth.planted(m, n, r, p=0.05, amp=1.0, seed=44, dtype="f64")
+    M = prob.values_f64()
+    perm = synth.row_permutation(m, 45)
+    dense = O.fr_nys(M, r, l, perm, rho=1.5, mu0=0.1, tol=1e-10)
+    g = synth.rng(46)
+    ii, jj = g.integers(0, m, 500), g.integers(0, n, 500)
+    samp = O.fr_nys(M, r, l, perm, sample=(ii, jj), rho=1.5, mu0=0.1, tol=1e-10)
+    np.testing.assert_allclose(samp.L, dense.L[ii, jj], rtol=0, atol=1e-12 * np.abs(dense.L).max())
+    np.testing.assert_allclose(samp.S, dense.S[ii, jj], rtol=0, atol=1e-12 * np.abs(dense.L).max())

@@ -1,11 +1,12 @@
 """sfr_solve_noalloc: the solve for callers that cannot allocate device memory.
 
-Such callers (code running during CUDA graph capture, processes whose device
-memory belongs to a fixed pool or a framework allocator) get all workspace from
-a fixed __device__ array inside the library.  This checks, through the C ABI,
-that two calls in a row give the same factors and S as sfr_solve within the
-float64 parity tolerance, and that an oversized problem is refused.  The file
-is named to be collected last.
+Such callers (processes whose device memory belongs to a fixed pool or a
+framework allocator, paths that may not take the allocator's locks) get all
+workspace from a fixed __device__ array inside the library.  This checks,
+through the C ABI, that two calls in a row give the same factors and S as
+sfr_solve within the parity tolerance of each precision path (float64: 1e-9,
+mixed: 1e-5), and that an oversized problem is refused.  The file is named to
+be collected last.
 """
 import numpy as np
 import pytest
@@ -25,9 +26,9 @@ def _buffers(m, n, r):
     return (torch.empty((m, r), **f), torch.empty((r, r), **f), torch.empty((n, r), **f), torch.empty((m, n), **f))
 
 
-def _run(call, Md, m, n, r, **kw):
+def _run(call, Md, m, n, r, m_dtype=B.F64, **kw):
     U, Bm, V, S = _buffers(m, n, r)
-    p = B.make_problem(m=m, n=n, r=r, M_ptr=Md.data_ptr(), m_dtype=B.F64, **kw)
+    p = B.make_problem(m=m, n=n, r=r, M_ptr=Md.data_ptr(), m_dtype=m_dtype, **kw)
     res = B.make_result(U_ptr=U.data_ptr(), B_ptr=Bm.data_ptr(), V_ptr=V.data_ptr(), S_ptr=S.data_ptr(),
                         s_dtype=B.F64, lds=n)
     st = call(p, res)
@@ -56,6 +57,27 @@ def test_noalloc_matches_solve_twice(kw):
             assert _rel(U @ Bm @ V.T, L0) <= TOL
             assert _rel(S, S0) <= 1e-8
             assert abs(res.rel_residual - ref.rel_residual) <= 1e-6 * max(ref.rel_residual, 1e-300)
+
+
+@pytest.mark.parametrize("m,n,r", [(500, 500, 25), (384, 640, 64)])
+def test_noalloc_mixed_matches_solve_twice(m, n, r):
+    # mixed path with bfloat16 M: the no-alloc call runs the SIMT passes (also at r = 64, where
+    # sfr_solve takes the tensor-core kernels); both must reach tol and agree to the mixed bar
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    prob = synth.planted(m, n, r, p=0.05, amp=50.0, seed=m + n + r, dtype="bf16")
+    Md = torch.from_numpy(prob.M.view(np.int16)).view(torch.bfloat16).cuda()
+    kw = dict(m_dtype=B.BF16, mu0=0.05, rho=1.5, tol=1e-9, max_iter=300, precision=B.PREC_MIXED)
+    with B.Context(0) as ctx:
+        st, ref, U0, B0, V0, S0 = _run(ctx.solve, Md, m, n, r, **kw)
+        assert st == B.OK, ctx.last_error()
+        L0 = U0 @ B0 @ V0.T
+        for _ in range(2):
+            st, res, U, Bm, V, S = _run(ctx.solve_noalloc, Md, m, n, r, **kw)
+            assert st == B.OK, ctx.last_error()
+            assert res.path == 0 and res.rel_residual <= 1e-9
+            assert _rel(U @ Bm @ V.T, L0) <= 1e-5
+            assert _rel(S, S0) <= 1e-4
 
 
 def test_noalloc_refuses_oversized_problem():
