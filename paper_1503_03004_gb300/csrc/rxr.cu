@@ -35,31 +35,56 @@ namespace sfr {
 namespace {
 
 constexpr int RPMAX = kMaxRank;
-constexpr int LD = RPMAX + 4;  // row stride of the r x r arrays: 16-byte aligned float rows
+constexpr int LD = RPMAX + 4;  // row stride of the float r x r arrays: 16-byte aligned rows
+constexpr int LDD = RPMAX;     // row stride of the float64 r x r arrays (read along rows only)
 constexpr int kThreads = 512;
 
 __device__ __forceinline__ bool stopped(const DevState* st) { return *(volatile const int32_t*)&st->done != 0; }
 
-// C = op(A) op(B) on the leading r x r blocks of [RPMAX][LD] shared arrays.
-template <typename T, bool TA, bool TB>
-__device__ void mm(const T* A, const T* B, T* C, int r) {
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    const int i = e / r, j = e % r;
-    T acc = 0;
-    for (int k = 0; k < r; ++k) {
-      const T a = TA ? A[k * LD + i] : A[i * LD + k];
-      const T b = TB ? B[j * LD + k] : B[k * LD + j];
-      acc = fma(a, b, acc);
-    }
-    C[i * LD + j] = acc;
-  }
-  __syncthreads();
+// GB300 issues float64 arithmetic at about two operations per clock per SM, so every float64
+// instruction that all 512 threads execute costs ~0.1 us.  The kernel therefore keeps float64 to
+// the products and the few element-wise steps that need it, takes scalar float64 math on one
+// thread, and does comparisons and float64 <-> float32 conversions with integer operations.
+
+// |x| as an integer (ordered like |x| for non-NaN values; NaN sorts above +inf).
+__device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
+constexpr long long kInfBits = 0x7ff0000000000000LL;
+
+// float32 value of x 2^-e, rounded to nearest even, for |x 2^-e| < 2; results below the float32
+// normal range flush to zero.  Integer operations only.
+__device__ __forceinline__ float f64_to_f32_shift(double x, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const int ex = (int)((b >> 52) & 0x7ff) - 1023 - e + 127;
+  if (ex <= 0 || ((b >> 52) & 0x7ff) == 0) return __uint_as_float(sign);
+  const unsigned long long mant = b & 0xfffffffffffffULL;
+  const unsigned long long rest = mant & ((1ULL << 29) - 1);
+  unsigned bits = ((unsigned)ex << 23) | (unsigned)(mant >> 29);
+  if (rest > (1ULL << 28) || (rest == (1ULL << 28) && (bits & 1u))) bits += 1;  // carries into the exponent
+  return __uint_as_float(bits | sign);
 }
 
-// C = op(A) op(B) for float64, rows split across the cluster and broadcast through DSMEM.
-// C must not alias A or B.  On return every CTA holds the full product.
-template <bool TA, bool TB>
-__device__ void mm_dist(const double* A, const double* B, double* C, int r, double scale = 1.0) {
+// Exact float64 value of f 2^e (f a normal float32 or zero; subnormals flush to zero).  Integer
+// operations only.
+__device__ __forceinline__ double f32_to_f64_shift(float f, int e) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xff;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  if (ex == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long b = sign | ((unsigned long long)(ex - 127 + 1023 + e) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f32_to_f64_shift(x, 0); }
+
+// C = epi(op(A) B) with float64 arithmetic, rows split across the cluster and broadcast through
+// DSMEM.  A is a float64 array (row stride LDD); B is float64 (LDD) or float (LD), converted on
+// load; C is float64 (LDD) or float (LD) and receives epi(i, j, (op(A) B)_ij).  C must not alias A
+// or B.  On return every CTA holds the full product.
+template <bool TA, typename TB, typename TCo, typename Epi>
+__device__ __noinline__ void mm_dist(const double* A, const TB* B, TCo* C, int r, Epi epi) {
+  constexpr int ldb = sizeof(TB) == 8 ? LDD : LD;
+  constexpr int ldc = sizeof(TCo) == 8 ? LDD : LD;
   cg::cluster_group cl = cg::this_cluster();
   const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int rpc = (r + cs - 1) / cs, i0 = min(r, rank * rpc), i1 = min(r, i0 + rpc);
@@ -72,28 +97,27 @@ __device__ void mm_dist(const double* A, const double* B, double* C, int r, doub
     for (; k + 4 <= r; k += 4)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const double a = TA ? A[(k + q) * LD + i] : A[i * LD + k + q];
-        const double b = TB ? B[j * LD + k + q] : B[(k + q) * LD + j];
-        acc[q] = fma(a, b, acc[q]);
+        const double a = TA ? A[(k + q) * LDD + i] : A[i * LDD + k + q];
+        acc[q] = fma(a, to_f64(B[(k + q) * ldb + j]), acc[q]);
       }
     for (; k < r; ++k) {
-      const double a = TA ? A[k * LD + i] : A[i * LD + k];
-      const double b = TB ? B[j * LD + k] : B[k * LD + j];
-      acc[0] = fma(a, b, acc[0]);
+      const double a = TA ? A[k * LDD + i] : A[i * LDD + k];
+      acc[0] = fma(a, to_f64(B[k * ldb + j]), acc[0]);
     }
-    C[i * LD + j] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) * scale;
+    C[i * ldc + j] = epi(i, j, (acc[0] + acc[1]) + (acc[2] + acc[3]));
   }
   __syncthreads();
   if (cs > 1) {
     cl.sync();  // every CTA is past its earlier reads of C
-    // push this CTA's rows to the other CTAs in 16-byte pieces (column pairs; with r odd the
-    // last pair carries column r, which no product reads)
-    const int np2 = (r + 1) / 2, per = (i1 - i0) * np2;
+    // push this CTA's rows to the other CTAs in 16-byte pieces (column pairs of float64 or quads of
+    // float; the last piece of a row may carry columns >= r, which no product or loop reads)
+    constexpr int per16 = 16 / sizeof(TCo);
+    const int npc = (r + per16 - 1) / per16, per = (i1 - i0) * npc;
     for (int e = threadIdx.x; e < (cs - 1) * per; e += blockDim.x) {
       const int q = 1 + e / per, w = e % per;
-      const int i = i0 + w / np2, j = 2 * (w % np2);
-      double* Cq = cl.map_shared_rank(C, (rank + q) % cs);
-      *reinterpret_cast<double2*>(Cq + i * LD + j) = *reinterpret_cast<const double2*>(C + i * LD + j);
+      const int i = i0 + w / npc, j = per16 * (w % npc);
+      TCo* Cq = cl.map_shared_rank(C, (rank + q) % cs);
+      *reinterpret_cast<float4*>(Cq + i * ldc + j) = *reinterpret_cast<const float4*>(C + i * ldc + j);
     }
     cl.sync();  // all rows have arrived everywhere
   }
@@ -104,7 +128,7 @@ __device__ void mm_dist(const double* A, const double* B, double* C, int r, doub
 // sum over k runs in order.  Reads may touch rows and columns beyond r (inside the RPMAX x LD
 // arrays); only outputs inside r x r are written.
 template <bool TA, bool TB>
-__device__ void mmf(const float* A, const float* B, float* C, int r) {
+__device__ __noinline__ void mmf(const float* A, const float* B, float* C, int r) {
   const int nb = (r + 3) / 4, r4 = r & ~3;
   for (int blk = threadIdx.x; blk < nb * nb; blk += blockDim.x) {
     const int i0 = 4 * (blk / nb), j0 = 4 * (blk % nb);
@@ -172,33 +196,53 @@ __device__ __forceinline__ void load_sq(const TS* __restrict__ src, int rp, int 
   }
 }
 
-__device__ double block_reduce(double v, double* red, bool take_max) {
+// Block-wide sum or max: shuffles within each warp, one shared slot per warp, then every thread
+// reduces the (at most 32) warp values with shuffles again; the closing barrier lets `red` be
+// reused at once.
+__device__ __noinline__ double block_reduce(double v, double* red, bool take_max) {
   for (int o = 16; o > 0; o >>= 1) {
     const double w = __shfl_xor_sync(0xffffffffu, v, o);
     v = take_max ? fmax(v, w) : v + w;
   }
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
-  __syncthreads();
   if (l == 0) red[w] = v;
   __syncthreads();
-  double t = red[0];
-  for (int i = 1; i < nw; ++i) t = take_max ? fmax(t, red[i]) : t + red[i];
+  double t = l < nw ? red[l] : (take_max ? -INFINITY : 0.0);
+  for (int o = 16; o > 0; o >>= 1) {
+    const double u = __shfl_xor_sync(0xffffffffu, t, o);
+    t = take_max ? fmax(t, u) : t + u;
+  }
+  __syncthreads();
+  return t;
+}
+
+// Block-wide maximum of 64-bit integers (same scheme).
+__device__ __noinline__ long long block_max_ll(long long v, double* red) {
+  long long* rl = reinterpret_cast<long long*>(red);
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  if (l == 0) rl[w] = v;
+  __syncthreads();
+  long long t = l < nw ? rl[l] : 0LL;
+  for (int o = 16; o > 0; o >>= 1) t = max(t, __shfl_xor_sync(0xffffffffu, t, o));
   __syncthreads();
   return t;
 }
 
 // float version (the sums and maxima it serves steer decisions only)
-__device__ float block_reduce_f(float v, float* red, bool take_max) {
+__device__ __noinline__ float block_reduce_f(float v, float* red, bool take_max) {
   for (int o = 16; o > 0; o >>= 1) {
     const float w = __shfl_xor_sync(0xffffffffu, v, o);
     v = take_max ? fmaxf(v, w) : v + w;
   }
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
-  __syncthreads();
   if (l == 0) red[w] = v;
   __syncthreads();
-  float t = red[0];
-  for (int i = 1; i < nw; ++i) t = take_max ? fmaxf(t, red[i]) : t + red[i];
+  float t = l < nw ? red[l] : (take_max ? -INFINITY : 0.f);
+  for (int o = 16; o > 0; o >>= 1) {
+    const float u = __shfl_xor_sync(0xffffffffu, t, o);
+    t = take_max ? fmaxf(t, u) : t + u;
+  }
   __syncthreads();
   return t;
 }
@@ -206,7 +250,7 @@ __device__ float block_reduce_f(float v, float* red, bool take_max) {
 // Cyclic two-sided Jacobi on the symmetric n2 x n2 float matrix A (n2 even; rows/cols
 // beyond r are zero), accumulating the rotations into Q (A_final = Q^T A_init Q).
 // Round-robin ordering: n2/2 disjoint rotations per step, n2-1 steps per sweep.
-__device__ void jacobi_f32(float* A, float* Q, int n2, int max_sweeps, double* red, float* cs, float* sn, int* pp,
+__device__ __noinline__ void jacobi_f32(float* A, float* Q, int n2, int max_sweeps, double* red, float* cs, float* sn, int* pp,
                            int* qq) {
   const int np = n2 / 2;
   const bool pow2 = (np & (np - 1)) == 0;
@@ -389,7 +433,7 @@ __device__ void jacobi_f32(float* A, float* Q, int n2, int max_sweeps, double* r
 // Returns false (leaving Q, A unchanged) when some |E_pq| > 0.25, i.e. A is not close enough
 // to diagonal for the first-order step; pairs with (relative) gaps below 1e-5 are left alone,
 // since any basis of a cluster serves the Newton preconditioner.
-__device__ bool refine_basis(const float* Kf, float* Q, float* A, float* F1, float* F2, int r, double* red) {
+__device__ __noinline__ bool refine_basis(const float* Kf, float* Q, float* A, float* F1, float* F2, int r, double* red) {
   float big = 0.f;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int p = e / r, q = e % r;
@@ -425,7 +469,7 @@ __device__ bool refine_basis(const float* Kf, float* Q, float* A, float* F1, flo
 }
 
 // Off-diagonal mass of A below tol^2 of its diagonal mass (Frobenius), float32 sums.
-__device__ bool near_diagonal(const float* A, int r, double* red, double tol2 = 1e-9) {
+__device__ __noinline__ bool near_diagonal(const float* A, int r, double* red, double tol2 = 1e-9) {
   float off = 0.f, dia = 0.f;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
@@ -438,147 +482,179 @@ __device__ bool near_diagonal(const float* A, int r, double* red, double tol2 = 
 }
 
 struct RxrSmem {
-  double K[RPMAX * LD];    // B G B / s
-  double B[RPMAX * LD];
-  double Z[RPMAX * LD];    // K^{-1/2} iterate
-  double T1[RPMAX * LD];   // scratch; also holds two float scratch arrays
-  double T2[RPMAX * LD];   // scratch
-  float Af[RPMAX * LD];    // Jacobi matrix / float scratch
-  float Qf[RPMAX * LD];    // approximate eigenbasis
-  float QT[RPMAX * LD];    // its transpose (keeps every float32 product in the conflict-free forms)
-  double lam[RPMAX];
-  double sq[RPMAX];
+  double G[RPMAX * LDD];   // Gram of the thin factor (float64 sum of the partials); later B_bar
+  double T[RPMAX * LDD];   // T_hat = B Z_hat (Newton iterate); scratch vectors of the rank test
+  double W[RPMAX * LDD];   // B (until T_hat exists), then G T_hat
+  float Gf[RPMAX * LD];    // G 2^-eg (float32; the power of two keeps K = B G B finite)
+  float Bf[RPMAX * LD];    // B 2^-eb
+  float Kf[RPMAX * LD];    // K / s in float32 (until Z0), then Q^T
+  float Af[RPMAX * LD];    // Q^T K Q / s, the Jacobi matrix, then the Newton correction in that basis
+  float Qf[RPMAX * LD];    // approximate eigenbasis of K
+  float F1[RPMAX * LD];    // scratch
+  float F2[RPMAX * LD];    // scratch
+  float lam[RPMAX], sq[RPMAX], isq[RPMAX];
   double red[32];
   float cs[RPMAX / 2], sn[RPMAX / 2];
   int pp[RPMAX / 2], qq[RPMAX / 2];
-  double scale;
-  int bad;
+  double scale, inv_s, rs;  // s = trace(B G B) / r, 1 / s, 1 / sqrt(s)  (written by thread 0)
+  float kn;                 // r / trace of the scaled float32 K
+  int ok;
+};
+
+// Epilogues of mm_dist: the product itself, or I - product / s rounded to float32.
+struct PlainEpi {
+  __device__ double operator()(int, int, double v) const { return v; }
+};
+struct ResidEpi {
+  double inv_s;
+  __device__ float operator()(int i, int j, double v) const { return (float)((i == j ? 1.0 : 0.0) - v * inv_s); }
 };
 
 __device__ void fail(DevState* st, int code) {
   if (threadIdx.x == 0 && cg::this_cluster().block_rank() == 0) { st->status = code; st->done = 1; }
 }
 
+// Unbiased binary exponent of the largest |x| whose bits are `bits` (0 for 0).
+__device__ __forceinline__ int exponent_of(long long bits) { return bits ? (int)(bits >> 52) - 1023 : 0; }
+
 // v_side = false: T_U = B (B G_P B)^{-1/2}.
 // v_side = true:  T_V = B (B G_W B)^{-1/2}, B <- Sym(G_W T_V), T_C = T_V B.
-// float64: K = B G B, the Newton residual, T, B_bar, T_C (G: the float64 sum of the partials).
-// float32: the eigenbasis, eigenvalue estimates, Z0 and the Newton corrections, which only
-// steer the iteration (their error shrinks with each Newton step).
-__global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict__ G, int rp, int r,
+//
+// With K = B G B and s = trace(K) / r, let Z be (K / s)^{-1/2}; then T = B Z / sqrt(s).  The kernel
+// carries T_hat = B Z instead of Z: Newton's residual for Z K Z = I is
+//     R = I - Z K Z = I - T_hat^T (G T_hat) / s,
+// so float64 products form T_hat, W = G T_hat and T_hat^T W only, and K itself is needed in
+// float32 alone (for the eigenbasis that preconditions Newton).  A Newton correction Delta of Z
+// (float32, small) moves T_hat by B Delta and W by G B Delta, formed in float32: their rounding
+// is float32-relative to the correction, and the next residual is formed in float64 again.
+// float64: G, B, T_hat, W, R, B_bar, T_C.  float32: K, the eigenbasis, eigenvalue estimates, Z0
+// and the Newton corrections, which only steer the iteration.  Outputs are written by rows, each
+// CTA of the cluster its own slice.
+__global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict__ Gg, int rp, int r,
                                                        double* __restrict__ Bg, double* __restrict__ Tout,
                                                        double* __restrict__ TCout, float* __restrict__ Qeig,
                                                        int v_side, int mixed, DevState* st) {
   if (stopped(st)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RxrSmem& S = *reinterpret_cast<RxrSmem*>(smem_raw);
-  float* F1 = reinterpret_cast<float*>(S.T1);            // float scratch inside T1
-  float* F2 = F1 + RPMAX * LD;
-  float* Kf = reinterpret_cast<float*>(S.T2);            // float copy of K inside T2 (until Z0)
-  float* lamf = reinterpret_cast<float*>(S.lam);         // float eigenvalue estimates
-  float* sqf = lamf + RPMAX;                             // sqrt(lambda)
-  float* isqf = reinterpret_cast<float*>(S.sq);          // 1 / sqrt(lambda)
+  float* redf = reinterpret_cast<float*>(S.red);
+  cg::cluster_group cl = cg::this_cluster();
   const int tid = threadIdx.x;
-  const int rpsq = rp * rp;
-  const bool writer = cg::this_cluster().block_rank() == 0;
-  // 1. Gram of the thin matrix and B; K = B G B (symmetrised) scaled by s = trace / r
-  load_sq(G, rp, r, r, S.T2, 0.0);
-  load_sq(Bg, rp, r, r, S.B, 0.0);
-  __syncthreads();
-  mm_dist<false, false>(S.T2, S.B, S.T1, r);
-  mm_dist<false, false>(S.B, S.T1, S.Z, r);
-  double tr = 0.0;  // trace of B G B: float64 sums within the first two warps (r <= 64)
-  if (tid < 64) {
-    tr = tid < r ? S.Z[tid * LD + tid] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-    if ((tid & 31) == 0) S.red[tid >> 5] = tr;
-  }
-  __syncthreads();
-  tr = S.red[0] + S.red[1];
-  __syncthreads();
-  const double scale = tr / r;
-  if (!(scale > 0.0) || !(scale < 1e300)) { fail(st, SFR_E_NAN); return; }
-  const double inv_s = 1.0 / scale;
-  for (int e = tid; e < r * r; e += blockDim.x) {  // B (G B) is symmetric to float64 rounding
-    const int i = e / r, j = e % r;
-    const double v = S.Z[i * LD + j] * inv_s;
-    S.K[i * LD + j] = v;
-    Kf[i * LD + j] = (float)v;
-  }
-  // 2. float32 Jacobi, warm-started from the previous eigenbasis Qw: A = Qw^T K Qw
-  const int n2 = (r + 1) & ~1;
-  for (int e = tid; e < n2 * n2; e += blockDim.x) {
-    const int i = e / n2, j = e % n2;
-    if (i >= r || j >= r) Kf[i * LD + j] = 0.f;
+  const int cs = (int)cl.num_blocks(), crank = (int)cl.block_rank();
+  const bool writer = crank == 0;
+  const int rpc = (r + cs - 1) / cs, row0 = min(r, crank * rpc), row1 = min(r, row0 + rpc);  // own rows
+  const int n2 = (r + 1) & ~1;  // Jacobi works on an even size (row / column r zero when r is odd)
+  // 1. G and B in float64 (B in W until T_hat exists), their power-of-two-scaled float32 copies,
+  //    and the previous call's eigenbasis
+  constexpr int PER = RPMAX * RPMAX / kThreads;
+  double gv[PER], bv[PER];
+  long long gmax = 0, bmax = 0;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = tid + q * kThreads, i = e / RPMAX, j = e % RPMAX;
+    const bool in = i < r && j < r;
+    gv[q] = in ? Gg[i * rp + j] : 0.0;
+    bv[q] = in ? Bg[i * rp + j] : 0.0;
+    gmax = max(gmax, abs_bits(gv[q]));
+    bmax = max(bmax, abs_bits(bv[q]));
   }
   load_sq(Qeig, rp, r, n2, S.Qf, 1.f);
+  gmax = block_max_ll(gmax, S.red);
+  bmax = block_max_ll(bmax, S.red);
+  if (gmax >= kInfBits || bmax >= kInfBits || bmax == 0) { fail(st, SFR_E_NAN); return; }
+  const int eg = exponent_of(gmax), eb = exponent_of(bmax);
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = tid + q * kThreads, i = e / RPMAX, j = e % RPMAX;
+    S.G[i * LDD + j] = gv[q];
+    S.W[i * LDD + j] = bv[q];
+    S.Gf[i * LD + j] = f64_to_f32_shift(gv[q], eg);
+    S.Bf[i * LD + j] = f64_to_f32_shift(bv[q], eb);
+  }
   __syncthreads();
-  mmf<false, false>(Kf, S.Qf, F2, n2);
-  mmf<true, false>(S.Qf, F2, S.Af, n2);
-  // the basis of the previous call is usually close: refine it to first order (cheap), and fall
-  // back to Jacobi sweeps only when that does not converge
-  // at least one refinement round: a basis accurate to float32 rounding lets one Newton step
-  // (two float64 products) replace two
+  // 2. K = B G B in float32 (the scaled copies give K 2^-(eg + 2 eb)), s = trace(K) / r, Kf = K / s
+  mmf<false, false>(S.Gf, S.Bf, S.F1, r);
+  mmf<false, false>(S.Bf, S.F1, S.Kf, r);
+  const float trf = block_reduce_f(tid < r ? S.Kf[tid * LD + tid] : 0.f, redf, false);
+  if (tid == 0) {
+    const double scale = ldexp((double)trf / r, eg + 2 * eb);  // trace(B G B) / r
+    S.ok = scale > 0.0 && scale < 1e300;
+    S.scale = scale;
+    S.inv_s = 1.0 / scale;
+    S.rs = 1.0 / sqrt(scale);
+    S.kn = r / trf;
+  }
+  __syncthreads();
+  if (!S.ok) { fail(st, SFR_E_NAN); return; }
+  const float kn = S.kn;
+  for (int e = tid; e < n2 * n2; e += blockDim.x) {
+    const int i = e / n2, j = e % n2;
+    S.Kf[i * LD + j] = (i < r && j < r) ? S.Kf[i * LD + j] * kn : 0.f;
+  }
+  __syncthreads();
+  // 3. eigenbasis: A = Qw^T (K / s) Qw from the previous basis Qw, refined to first order (cheap);
+  //    float32 Jacobi sweeps only when that does not converge
+  mmf<false, false>(S.Kf, S.Qf, S.F2, n2);
+  mmf<true, false>(S.Qf, S.F2, S.Af, n2);
+  // at least one refinement round: a basis accurate to float32 rounding lets one Newton step do
   bool diag = false;
   for (int round = 0; round < 3; ++round) {
-    if (!refine_basis(Kf, S.Qf, S.Af, F1, F2, n2, S.red)) break;
+    if (!refine_basis(S.Kf, S.Qf, S.Af, S.F1, S.F2, n2, S.red)) break;
     diag = near_diagonal(S.Af, n2, S.red);
     if (diag) break;
   }
   const bool rotated = !diag;
-  if (rotated) jacobi_f32(S.Af, S.Qf, n2, 10, S.red, S.cs, S.sn, S.pp, S.qq);
   if (rotated) {
+    jacobi_f32(S.Af, S.Qf, n2, 10, S.red, S.cs, S.sn, S.pp, S.qq);
     // re-orthonormalise the float basis: Q <- Q (3I - Q^T Q) / 2
-    mmf<true, false>(S.Qf, S.Qf, F1, r);
+    mmf<true, false>(S.Qf, S.Qf, S.F1, r);
     for (int e = tid; e < r * r; e += blockDim.x) {
       const int i = e / r, j = e % r;
-      F1[i * LD + j] = 0.5f * ((i == j ? 3.f : 0.f) - F1[i * LD + j]);
+      S.F1[i * LD + j] = 0.5f * ((i == j ? 3.f : 0.f) - S.F1[i * LD + j]);
     }
     __syncthreads();
-    mmf<false, false>(S.Qf, F1, F2, r);
-    for (int e = tid; e < r * r; e += blockDim.x) S.Qf[(e / r) * LD + e % r] = F2[(e / r) * LD + e % r];
+    mmf<false, false>(S.Qf, S.F1, S.F2, r);
+    for (int e = tid; e < r * r; e += blockDim.x) S.Qf[(e / r) * LD + e % r] = S.F2[(e / r) * LD + e % r];
     __syncthreads();
   }
-  for (int e = tid; e < r * r; e += blockDim.x) S.QT[(e % r) * LD + e / r] = S.Qf[(e / r) * LD + e % r];
-  // 3. eigenvalue estimates: the diagonal of A = Q^T K Q (Rayleigh quotients of the basis, to
-  //    float32 rounding); those far below the largest are recomputed in float64 for the rank
-  //    test (Eq. 9 needs rank r)
-  for (int p = tid; p < r; p += blockDim.x) lamf[p] = S.Af[p * LD + p];
+  // 4. eigenvalue estimates: the diagonal of A = Q^T K Q / s (Rayleigh quotients of the basis, to
+  //    float32 rounding); those far below the largest are recomputed in float64 for the rank test
+  //    (Eq. 9 needs rank r)
+  for (int p = tid; p < r; p += blockDim.x) S.lam[p] = S.Af[p * LD + p];
   __syncthreads();
-  float* redf = reinterpret_cast<float*>(S.red);
   float hi = 0.f;
-  for (int p = tid; p < r; p += blockDim.x) hi = fmaxf(hi, lamf[p]);
+  for (int p = tid; p < r; p += blockDim.x) hi = fmaxf(hi, S.lam[p]);
   hi = block_reduce_f(hi, redf, true);
-  // the float32 estimates carry errors near 1e-7 hi: below 1e-6 hi, recompute q_p^T K q_p in
-  // float64 (every thread takes one row of K q_p, then a block sum)
   float anysmall = 0.f;
   for (int p = tid; p < r; p += blockDim.x)
-    if (lamf[p] < 1e-6f * hi) anysmall = 1.f;
+    if (S.lam[p] < 1e-6f * hi) anysmall = 1.f;
   anysmall = block_reduce_f(anysmall, redf, true);
   if (anysmall > 0.f && rotated) {
     // Jacobi stopped at a 1e-3 off-diagonal, so a basis vector of a tiny eigenvalue still mixes
     // ~1e-3 of the large ones and its Rayleigh quotient sits near 1e-6 hi: two first-order rounds
     // (near-degenerate pairs are skipped) bring the mixing down to float32 rounding first.
     for (int round = 0; round < 2; ++round)
-      if (!refine_basis(Kf, S.Qf, S.Af, F1, F2, n2, S.red)) break;
-    for (int e = tid; e < r * r; e += blockDim.x) S.QT[(e % r) * LD + e / r] = S.Qf[(e / r) * LD + e % r];
-    for (int p = tid; p < r; p += blockDim.x) lamf[p] = S.Af[p * LD + p];
+      if (!refine_basis(S.Kf, S.Qf, S.Af, S.F1, S.F2, n2, S.red)) break;
+    for (int p = tid; p < r; p += blockDim.x) S.lam[p] = S.Af[p * LD + p];
     __syncthreads();
     hi = 0.f;
-    for (int p = tid; p < r; p += blockDim.x) hi = fmaxf(hi, lamf[p]);
+    for (int p = tid; p < r; p += blockDim.x) hi = fmaxf(hi, S.lam[p]);
     hi = block_reduce_f(hi, redf, true);
   }
   // A float32 eigenvector carries components of about 1e-7 along the large eigenvectors, which
   // alone would add ~1e-14 hi to its Rayleigh quotient (the rank threshold): project them out in
-  // float64 first (q <- q - Q_L Q_L^T q over the columns of large eigenvalues).
-  double* qs = S.Z;       // the vector (Z is free until step 4)
-  double* cf = S.Z + LD;  // its coefficients on the large eigenvectors
+  // float64 first (q <- q - Q_L Q_L^T q over the columns of large eigenvalues), then take
+  // q^T K q / (s q^T q) = (B q)^T G (B q) / (s q^T q) with float64 matrix-vector products.
+  double* qs = S.T;            // the vector (T_hat is free until step 6)
+  double* cf = S.T + LDD;      // its coefficients on the large eigenvectors
+  double* bq = S.T + 2 * LDD;  // B q
   for (int p = 0; anysmall > 0.f && p < r; ++p) {
-    if (!(lamf[p] < 1e-6f * hi)) continue;  // uniform: lamf is in shared memory
+    if (!(S.lam[p] < 1e-6f * hi)) continue;  // uniform: lam is in shared memory
     if (tid < r) qs[tid] = (double)S.Qf[tid * LD + p];
     __syncthreads();
     if (tid < r) {
       double c = 0.0;
-      if (!(lamf[tid] < 1e-6f * hi))
+      if (!(S.lam[tid] < 1e-6f * hi))
         for (int k = 0; k < r; ++k) c = fma((double)S.Qf[k * LD + tid], qs[k], c);
       cf[tid] = c;
     }
@@ -591,111 +667,165 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
     __syncthreads();
     if (tid < r) qs[tid] = qi;
     __syncthreads();
+    if (tid < r) {
+      double v = 0.0;
+      for (int k = 0; k < r; ++k) v = fma(S.W[tid * LDD + k], qs[k], v);  // (B q)_tid
+      bq[tid] = v;
+    }
+    __syncthreads();
     double num = 0.0, den = 0.0;
     if (tid < r) {
-      double kq = 0.0;
-      for (int k = 0; k < r; ++k) kq = fma(S.K[tid * LD + k], qs[k], kq);
-      num = qi * kq;
+      double gq = 0.0;
+      for (int k = 0; k < r; ++k) gq = fma(S.G[tid * LDD + k], bq[k], gq);  // (G B q)_tid
+      num = bq[tid] * gq;
       den = qi * qi;
     }
-    num = block_reduce(num, S.red, false);
-    den = block_reduce(den, S.red, false);
-    if (tid == 0) lamf[p] = (float)(num / den);
+    if (tid >= 64) num = den = 0.0;  // r <= 64: the first two warps hold every term
+    if (tid < 64) {
+      for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+      }
+    }
+    if (tid == 0) S.red[0] = num, S.red[1] = den;
+    __syncthreads();
+    if (tid == 32) S.red[2] = num, S.red[3] = den;
+    __syncthreads();
+    if (tid == 0) S.lam[p] = (float)((S.red[0] + S.red[2]) / (S.red[1] + S.red[3]) * S.inv_s);
     __syncthreads();
   }
   float nlo = -hi, badf = 0.f;  // max of -lambda and of the rank-failure flag
   for (int p = tid; p < r; p += blockDim.x) {
-    nlo = fmaxf(nlo, -lamf[p]);
-    if (!(lamf[p] > 1e-14f * hi)) badf = 1.f;
+    nlo = fmaxf(nlo, -S.lam[p]);
+    if (!(S.lam[p] > 1e-14f * hi)) badf = 1.f;
   }
   const float lo = -block_reduce_f(nlo, redf, true);
   const bool bad = block_reduce_f(badf, redf, true) > 0.f || !(hi > 0.f);
   if (writer && tid == 0) {
-    if (v_side) st->lam_min_v = (double)lo * scale; else st->lam_min_u = (double)lo * scale;
+    if (v_side) st->lam_min_v = (double)lo * S.scale; else st->lam_min_u = (double)lo * S.scale;
   }
   if (bad) { fail(st, SFR_E_RANK); return; }
   for (int p = tid; p < r; p += blockDim.x) {
-    const float sq = sqrtf(lamf[p]);
-    sqf[p] = sq;
-    isqf[p] = 1.f / sq;
+    const float sq = sqrtf(S.lam[p]);
+    S.sq[p] = sq;
+    S.isq[p] = 1.f / sq;
   }
+  float* QT = S.Kf;  // K is no longer needed: its storage holds Q^T
+  for (int e = tid; e < r * r; e += blockDim.x) QT[(e % r) * LD + e / r] = S.Qf[(e / r) * LD + e % r];
   __syncthreads();
-  // 4. Z0 = Q diag(lambda^{-1/2}) Q^T (float32 start; Newton below brings it to float64 accuracy)
+  // 5. Z0 = Q diag(lambda^{-1/2}) Q^T (float32 start; Newton below brings it to float64 accuracy)
   for (int e = tid; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
-    F2[i * LD + j] = S.Qf[i * LD + j] * isqf[j];
+    S.F2[i * LD + j] = S.Qf[i * LD + j] * S.isq[j];
   }
   __syncthreads();
-  mmf<false, false>(F2, S.QT, F1, r);
+  mmf<false, false>(S.F2, QT, S.F1, r);
   for (int e = tid; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
-    S.Z[i * LD + j] = (double)(0.5f * (F1[i * LD + j] + F1[j * LD + i]));
+    S.F2[i * LD + j] = 0.5f * (S.F1[i * LD + j] + S.F1[j * LD + i]);
   }
   __syncthreads();
-  // 5. Newton steps on Z K Z = I (residual in float64, correction in float32)
+  // 6. T_hat = B Z0 (float64 products of B with the float32 values of Z0)
+  const PlainEpi plain;
+  mm_dist<false>(S.W, S.F2, S.T, r, plain);
+  // 7. Newton steps on Z K Z = I: R = I - T_hat^T (G T_hat) / s in float64, correction in float32
+  bool w_stale = false;  // W lags T_hat by G (B Delta)
   for (int it = 0; it < 6; ++it) {
-    mm_dist<false, false>(S.K, S.Z, S.T1, r);
-    mm_dist<false, false>(S.Z, S.T1, S.T2, r);
+    mm_dist<false>(S.G, S.T, S.W, r, plain);                  // W = G T_hat
+    mm_dist<true>(S.T, S.W, S.F1, r, ResidEpi{S.inv_s});     // I - Z K Z, rounded to float32
+    w_stale = false;
     float rmax = 0.f;
-    for (int e = tid; e < r * r; e += blockDim.x) {  // I - Z K Z, rounded to float32
-      const int i = e / r, j = e % r;
-      const float v = (float)((i == j ? 1.0 : 0.0) - S.T2[i * LD + j]);
-      F1[i * LD + j] = v;
-      rmax = fmaxf(rmax, fabsf(v));
-    }
+    for (int e = tid; e < r * r; e += blockDim.x) rmax = fmaxf(rmax, fabsf(S.F1[(e / r) * LD + e % r]));
     const float rm = block_reduce_f(rmax, redf, true);
     if (!(rm == rm)) { fail(st, SFR_E_NAN); return; }
     if (rm < 4e-16f * r) break;
     for (int e = tid; e < r * r; e += blockDim.x) {  // R = Sym(I - Z K Z)
       const int i = e / r, j = e % r;
-      F2[i * LD + j] = 0.5f * (F1[i * LD + j] + F1[j * LD + i]);
+      S.F2[i * LD + j] = 0.5f * (S.F1[i * LD + j] + S.F1[j * LD + i]);
     }
     __syncthreads();
-    mmf<false, false>(F2, S.Qf, F1, r);     // R Q
-    mmf<true, false>(S.Qf, F1, S.Af, r);    // Q^T R Q
+    mmf<false, false>(S.F2, S.Qf, S.F1, r);    // R Q
+    mmf<true, false>(S.Qf, S.F1, S.Af, r);     // Q^T R Q
     for (int e = tid; e < r * r; e += blockDim.x) {
       const int p = e / r, q = e % r;
-      S.Af[p * LD + q] = __fdividef(S.Af[p * LD + q], sqf[p] + sqf[q]);
+      S.Af[p * LD + q] = __fdividef(S.Af[p * LD + q], S.sq[p] + S.sq[q]);
     }
     __syncthreads();
-    mmf<false, false>(S.Af, S.QT, F2, r);   // Dt Q^T
-    mmf<false, false>(S.Qf, F2, F1, r);     // Q Dt Q^T
+    mmf<false, false>(S.Af, QT, S.F2, r);      // Dt Q^T
+    mmf<false, false>(S.Qf, S.F2, S.F1, r);    // Q Dt Q^T
     for (int e = tid; e < r * r; e += blockDim.x) {
       const int i = e / r, j = e % r;
-      S.Z[i * LD + j] += (double)(0.5f * (F1[i * LD + j] + F1[j * LD + i]));
+      S.F2[i * LD + j] = 0.5f * (S.F1[i * LD + j] + S.F1[j * LD + i]);  // Delta (symmetric)
     }
     __syncthreads();
+    mmf<false, false>(S.Bf, S.F2, S.F1, r);    // B Delta 2^-eb
     // The step just taken leaves a residual of about (eigenbasis error + float32 rounding of the
     // correction) x rm + O(rm^2): from rm < 3e-6 about 1e-11 (mixed path, whose Gram carries
-    // float32 rounding), from rm < 1e-7 about 1e-14 (float64 path), so stop without forming it again.
-    if (rm < (mixed ? 3e-6 : 1e-7)) break;
+    // float32 rounding), from rm < 1e-7 about 1e-14 (float64 path), so stop without forming it again
+    // and update only this CTA's rows of T_hat (the rows it writes).
+    const bool last = rm < (mixed ? 3e-6f : 1e-7f) || it == 5;
+    const int e0 = last ? row0 * r : 0, e1 = last ? row1 * r : r * r;
+    for (int e = e0 + tid; e < e1; e += blockDim.x) {
+      const int i = e / r, j = e % r;
+      S.T[i * LDD + j] += f32_to_f64_shift(S.F1[i * LD + j], eb);
+    }
+    __syncthreads();
+    w_stale = true;
+    if (last) break;
   }
-  // 6. (B G B)^{-1/2} = Z / sqrt(s); T = B (B G B)^{-1/2}
-  mm_dist<false, false>(S.B, S.Z, S.T1, r, 1.0 / sqrt(scale));
+  // 8. T = B (B G B)^{-1/2} = T_hat / sqrt(s): this CTA's rows, and its rows of the basis
+  const double rs = S.rs;
+  for (int e = row0 * rp + tid; e < row1 * rp; e += blockDim.x) {
+    const int i = e / rp, j = e % rp;
+    Tout[e] = j < r ? S.T[i * LDD + j] * rs : 0.0;
+    Qeig[e] = j < r ? S.Qf[i * LD + j] : (i == j ? 1.f : 0.f);
+  }
   if (writer)
-    for (int e = tid; e < rpsq; e += blockDim.x) {
+    for (int e = r * rp + tid; e < rp * rp; e += blockDim.x) {  // padding rows
       const int i = e / rp, j = e % rp;
-      const bool in = i < r && j < r;
-      Tout[e] = in ? S.T1[i * LD + j] : 0.0;
-      Qeig[e] = in ? S.Qf[i * LD + j] : (i == j ? 1.f : 0.f);
+      Tout[e] = 0.0;
+      Qeig[e] = i == j ? 1.f : 0.f;
     }
   if (!v_side) return;
-  // 7. B_bar = Sym(G_W T_V) (Eq. 10 with W = X^T U_bar), T_C = T_V B_bar
-  load_sq(G, rp, r, r, S.K, 0.0);
-  __syncthreads();
-  mm_dist<false, false>(S.K, S.T1, S.T2, r);
-  for (int e = tid; e < r * r; e += blockDim.x) {
+  // 9. B_bar = Sym(G_W T_V) (Eq. 10 with W = X^T U_bar) = Sym(G T_hat) / sqrt(s), T_C = T_V B_bar.
+  //    W lags T_hat by the last correction: W + G (B Delta), the latter in float32.  Every CTA forms
+  //    its rows of B_bar and sends them to the others (nobody reads G after the last W product).
+  if (w_stale) mmf<false, false>(S.Gf, S.F1, S.F2, r);  // G B Delta 2^-(eg + eb)
+  for (int e = row0 * r + tid; e < row1 * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
-    S.Z[i * LD + j] = 0.5 * (S.T2[i * LD + j] + S.T2[j * LD + i]);
+    double v = S.W[i * LDD + j] + S.W[j * LDD + i];
+    if (w_stale) v += f32_to_f64_shift(S.F2[i * LD + j] + S.F2[j * LD + i], eg + eb);
+    S.G[i * LDD + j] = 0.5 * rs * v;
   }
   __syncthreads();
-  mm_dist<false, false>(S.T1, S.Z, S.T2, r);
+  if (cs > 1) {
+    const int npc = (r + 1) / 2, per = (row1 - row0) * npc;
+    for (int e = tid; e < (cs - 1) * per; e += blockDim.x) {
+      const int q = 1 + e / per, w = e % per;
+      const int i = row0 + w / npc, j = 2 * (w % npc);
+      double* Gq = cl.map_shared_rank(S.G, (crank + q) % cs);
+      *reinterpret_cast<double2*>(Gq + i * LDD + j) = *reinterpret_cast<const double2*>(S.G + i * LDD + j);
+    }
+    cl.sync();
+  }
+  // this CTA's rows: B_bar, and T_C = T_V B_bar = (T_hat rows) B_bar / sqrt(s)
+  for (int e = row0 * rp + tid; e < row1 * rp; e += blockDim.x) {
+    const int i = e / rp, j = e % rp;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (j < r) {
+      int k = 0;
+      for (; k + 4 <= r; k += 4)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = fma(S.T[i * LDD + k + q], S.G[(k + q) * LDD + j], acc[q]);
+      for (; k < r; ++k) acc[0] = fma(S.T[i * LDD + k], S.G[k * LDD + j], acc[0]);
+    }
+    Bg[e] = j < r ? S.G[i * LDD + j] : 0.0;
+    TCout[e] = j < r ? ((acc[0] + acc[1]) + (acc[2] + acc[3])) * rs : 0.0;
+  }
   if (writer)
-    for (int e = tid; e < rpsq; e += blockDim.x) {
-      const int i = e / rp, j = e % rp;
-      const bool in = i < r && j < r;
-      Bg[e] = in ? S.Z[i * LD + j] : 0.0;
-      TCout[e] = in ? S.T2[i * LD + j] : 0.0;
+    for (int e = r * rp + tid; e < rp * rp; e += blockDim.x) {
+      Bg[e] = 0.0;
+      TCout[e] = 0.0;
     }
 }
 
