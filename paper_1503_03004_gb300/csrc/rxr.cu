@@ -81,7 +81,9 @@ __device__ __forceinline__ double to_f64(float x) { return f32_to_f64_shift(x, 0
 // DSMEM.  A is a float64 array (row stride LDD); B is float64 (LDD) or float (LD), converted on
 // load; C is float64 (LDD) or float (LD) and receives epi(i, j, (op(A) B)_ij).  C must not alias A
 // or B.  On return every CTA holds the full product.
-template <bool TA, typename TB, typename TCo, typename Epi>
+// PRE = false skips the barrier before the broadcast: allowed when no CTA has read C since the
+// last cluster barrier.
+template <bool TA, bool PRE = true, typename TB, typename TCo, typename Epi>
 __device__ __noinline__ void mm_dist(const double* A, const TB* B, TCo* C, int r, Epi epi) {
   constexpr int ldb = sizeof(TB) == 8 ? LDD : LD;
   constexpr int ldc = sizeof(TCo) == 8 ? LDD : LD;
@@ -108,7 +110,7 @@ __device__ __noinline__ void mm_dist(const double* A, const TB* B, TCo* C, int r
   }
   __syncthreads();
   if (cs > 1) {
-    cl.sync();  // every CTA is past its earlier reads of C
+    if (PRE) cl.sync();  // every CTA is past its earlier reads of C
     // push this CTA's rows to the other CTAs in 16-byte pieces (column pairs of float64 or quads of
     // float; the last piece of a row may carry columns >= r, which no product or loop reads)
     constexpr int per16 = 16 / sizeof(TCo);
@@ -427,13 +429,29 @@ __device__ __noinline__ void jacobi_f32(float* A, float* Q, int n2, int max_swee
   }
 }
 
-// One first-order eigenbasis refinement round for a nearly diagonal A = Q^T K Q (float32):
+// A = (B Q)^T G (B Q) kn = kn Q^T K Q for the float32 copies Bf, Gf (three products; K itself is
+// never formed).  The padding row and column r of an odd-sized Jacobi problem (n2 = r + 1) are zero.
+__device__ __noinline__ void gram_in_basis(const float* Bf, const float* Gf, const float* Q, float* A, float* F1,
+                                           float* F2, int r, int n2, float kn) {
+  mmf<false, false>(Bf, Q, F1, r);   // B Q
+  mmf<false, false>(Gf, F1, F2, r);  // G B Q
+  mmf<true, false>(F1, F2, A, r);    // (B Q)^T G B Q
+  for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
+    const int i = e / n2, j = e % n2;
+    A[i * LD + j] = (i < r && j < r) ? A[i * LD + j] * kn : 0.f;
+  }
+  __syncthreads();
+}
+
+// One first-order eigenbasis refinement round for a nearly diagonal A = Q^T K Q / s (float32):
 // Q <- Q (I + E), E_pq = A_pq / (A_qq - A_pp) for p != q (the small-angle Jacobi rotation of
-// every pair at once), then one Newton-Schulz re-orthonormalisation and A <- Q^T K Q.
-// Returns false (leaving Q, A unchanged) when some |E_pq| > 0.25, i.e. A is not close enough
-// to diagonal for the first-order step; pairs with (relative) gaps below 1e-5 are left alone,
-// since any basis of a cluster serves the Newton preconditioner.
-__device__ __noinline__ bool refine_basis(const float* Kf, float* Q, float* A, float* F1, float* F2, int r, double* red) {
+// every pair at once), then one Newton-Schulz re-orthonormalisation, and the second-order
+// eigenvalue estimates lam_p = A_pp - sum_q A_pq E_pq (A itself is not recomputed).  Pairs with
+// (relative) gaps below 1e-5 are left alone, since any basis of a cluster serves the Newton
+// preconditioner.  Returns max |E|; above 0.25 (A not close enough to diagonal for the
+// first-order step) nothing is changed.
+__device__ __noinline__ float refine_round(float* Q, const float* A, float* F1, float* F2, float* lam, int r,
+                                           double* red) {
   float big = 0.f;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int p = e / r, q = e % r;
@@ -447,8 +465,16 @@ __device__ __noinline__ bool refine_basis(const float* Kf, float* Q, float* A, f
     big = fmaxf(big, fabsf(v));
   }
   big = block_reduce_f(big, reinterpret_cast<float*>(red), true);
-  if (!(big <= 0.25f)) return false;
-  mmf<false, false>(Q, F1, F2, r);                  // Q E
+  if (!(big <= 0.25f)) return big;
+  // lam_p = A_pp - sum_q A_pq E_pq: one warp per row
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int p = threadIdx.x >> 5; p < r; p += nw) {
+    float acc = 0.f;
+    for (int q = lane; q < r; q += 32) acc = fmaf(A[p * LD + q], F1[p * LD + q], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) lam[p] = A[p * LD + p] - acc;
+  }
+  mmf<false, false>(Q, F1, F2, r);                  // Q E (ends with a barrier)
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
     Q[i * LD + j] += F2[i * LD + j];
@@ -463,22 +489,7 @@ __device__ __noinline__ bool refine_basis(const float* Kf, float* Q, float* A, f
   mmf<false, false>(Q, F1, F2, r);                  // Q (3I - Q^T Q) / 2
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) Q[(e / r) * LD + e % r] = F2[(e / r) * LD + e % r];
   __syncthreads();
-  mmf<false, false>(Kf, Q, F1, r);                  // A = Q^T K Q
-  mmf<true, false>(Q, F1, A, r);
-  return true;
-}
-
-// Off-diagonal mass of A below tol^2 of its diagonal mass (Frobenius), float32 sums.
-__device__ __noinline__ bool near_diagonal(const float* A, int r, double* red, double tol2 = 1e-9) {
-  float off = 0.f, dia = 0.f;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    const int i = e / r, j = e % r;
-    const float v = A[i * LD + j];
-    if (i == j) dia = fmaf(v, v, dia); else off = fmaf(v, v, off);
-  }
-  const float o = block_reduce_f(off, reinterpret_cast<float*>(red), false);
-  const float d = block_reduce_f(dia, reinterpret_cast<float*>(red), false);
-  return !((double)o > tol2 * (double)d);
+  return big;
 }
 
 struct RxrSmem {
@@ -487,8 +498,8 @@ struct RxrSmem {
   double W[RPMAX * LDD];   // B (until T_hat exists), then G T_hat
   float Gf[RPMAX * LD];    // G 2^-eg (float32; the power of two keeps K = B G B finite)
   float Bf[RPMAX * LD];    // B 2^-eb
-  float Kf[RPMAX * LD];    // K / s in float32 (until Z0), then Q^T
-  float Af[RPMAX * LD];    // Q^T K Q / s, the Jacobi matrix, then the Newton correction in that basis
+  float QT[RPMAX * LD];    // Q^T
+  float Af[RPMAX * LD];    // Q^T K Q / s (K = B G B), the Jacobi matrix, then the Newton correction in that basis
   float Qf[RPMAX * LD];    // approximate eigenbasis of K
   float F1[RPMAX * LD];    // scratch
   float F2[RPMAX * LD];    // scratch
@@ -572,10 +583,10 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
     S.Bf[i * LD + j] = f64_to_f32_shift(bv[q], eb);
   }
   __syncthreads();
-  // 2. K = B G B in float32 (the scaled copies give K 2^-(eg + 2 eb)), s = trace(K) / r, Kf = K / s
-  mmf<false, false>(S.Gf, S.Bf, S.F1, r);
-  mmf<false, false>(S.Bf, S.F1, S.Kf, r);
-  const float trf = block_reduce_f(tid < r ? S.Kf[tid * LD + tid] : 0.f, redf, false);
+  // 2. A = Q^T K Q in the previous call's basis Q (float32, from the scaled copies:
+  //    K 2^-(eg + 2 eb)); s = trace(K) / r = trace(A) / r; A <- A / s
+  gram_in_basis(S.Bf, S.Gf, S.Qf, S.Af, S.F1, S.F2, r, n2, 1.f);
+  const float trf = block_reduce_f(tid < r ? S.Af[tid * LD + tid] : 0.f, redf, false);
   if (tid == 0) {
     const double scale = ldexp((double)trf / r, eg + 2 * eb);  // trace(B G B) / r
     S.ok = scale > 0.0 && scale < 1e300;
@@ -587,23 +598,19 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
   __syncthreads();
   if (!S.ok) { fail(st, SFR_E_NAN); return; }
   const float kn = S.kn;
-  for (int e = tid; e < n2 * n2; e += blockDim.x) {
-    const int i = e / n2, j = e % n2;
-    S.Kf[i * LD + j] = (i < r && j < r) ? S.Kf[i * LD + j] * kn : 0.f;
-  }
+  for (int e = tid; e < r * r; e += blockDim.x) S.Af[(e / r) * LD + e % r] *= kn;
   __syncthreads();
-  // 3. eigenbasis: A = Qw^T (K / s) Qw from the previous basis Qw, refined to first order (cheap);
-  //    float32 Jacobi sweeps only when that does not converge
-  mmf<false, false>(S.Kf, S.Qf, S.F2, n2);
-  mmf<true, false>(S.Qf, S.F2, S.Af, n2);
-  // at least one refinement round: a basis accurate to float32 rounding lets one Newton step do
-  bool diag = false;
-  for (int round = 0; round < 3; ++round) {
-    if (!refine_basis(S.Kf, S.Qf, S.Af, S.F1, S.F2, n2, S.red)) break;
-    diag = near_diagonal(S.Af, n2, S.red);
-    if (diag) break;
+  // 3. eigenbasis: refine the previous basis to first order (cheap) while its rotation is small;
+  //    a round whose rotation is at most 1e-3 leaves the basis accurate to ~1e-6 and is the last,
+  //    a larger one is followed by a fresh A; float32 Jacobi sweeps only when that does not converge
+  bool accepted = false;
+  for (int round = 0; round < 3 && !accepted; ++round) {
+    const float big = refine_round(S.Qf, S.Af, S.F1, S.F2, S.lam, n2, S.red);
+    if (!(big <= 0.25f)) break;                      // A unchanged, Q unchanged
+    accepted = big <= 1e-3f;
+    if (!accepted) gram_in_basis(S.Bf, S.Gf, S.Qf, S.Af, S.F1, S.F2, r, n2, kn);
   }
-  const bool rotated = !diag;
+  const bool rotated = !accepted;
   if (rotated) {
     jacobi_f32(S.Af, S.Qf, n2, 10, S.red, S.cs, S.sn, S.pp, S.qq);
     // re-orthonormalise the float basis: Q <- Q (3I - Q^T Q) / 2
@@ -616,11 +623,11 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
     mmf<false, false>(S.Qf, S.F1, S.F2, r);
     for (int e = tid; e < r * r; e += blockDim.x) S.Qf[(e / r) * LD + e % r] = S.F2[(e / r) * LD + e % r];
     __syncthreads();
+    // 4. eigenvalue estimates after Jacobi: the diagonal of A (Rayleigh quotients of the basis)
+    for (int p = tid; p < r; p += blockDim.x) S.lam[p] = S.Af[p * LD + p];
   }
-  // 4. eigenvalue estimates: the diagonal of A = Q^T K Q / s (Rayleigh quotients of the basis, to
-  //    float32 rounding); those far below the largest are recomputed in float64 for the rank test
-  //    (Eq. 9 needs rank r)
-  for (int p = tid; p < r; p += blockDim.x) S.lam[p] = S.Af[p * LD + p];
+  // (after a refinement round lam holds its second-order estimates); those far below the largest
+  // are recomputed in float64 for the rank test (Eq. 9 needs rank r)
   __syncthreads();
   float hi = 0.f;
   for (int p = tid; p < r; p += blockDim.x) hi = fmaxf(hi, S.lam[p]);
@@ -633,9 +640,13 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
     // Jacobi stopped at a 1e-3 off-diagonal, so a basis vector of a tiny eigenvalue still mixes
     // ~1e-3 of the large ones and its Rayleigh quotient sits near 1e-6 hi: two first-order rounds
     // (near-degenerate pairs are skipped) bring the mixing down to float32 rounding first.
-    for (int round = 0; round < 2; ++round)
-      if (!refine_basis(S.Kf, S.Qf, S.Af, S.F1, S.F2, n2, S.red)) break;
-    for (int p = tid; p < r; p += blockDim.x) S.lam[p] = S.Af[p * LD + p];
+    for (int round = 0; round < 2; ++round) {
+      gram_in_basis(S.Bf, S.Gf, S.Qf, S.Af, S.F1, S.F2, r, n2, kn);
+      if (!(refine_round(S.Qf, S.Af, S.F1, S.F2, S.lam, n2, S.red) <= 0.25f)) {
+        for (int p = tid; p < r; p += blockDim.x) S.lam[p] = S.Af[p * LD + p];
+        break;
+      }
+    }
     __syncthreads();
     hi = 0.f;
     for (int p = tid; p < r; p += blockDim.x) hi = fmaxf(hi, S.lam[p]);
@@ -710,7 +721,7 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
     S.sq[p] = sq;
     S.isq[p] = 1.f / sq;
   }
-  float* QT = S.Kf;  // K is no longer needed: its storage holds Q^T
+  float* QT = S.QT;
   for (int e = tid; e < r * r; e += blockDim.x) QT[(e % r) * LD + e / r] = S.Qf[(e / r) * LD + e % r];
   __syncthreads();
   // 5. Z0 = Q diag(lambda^{-1/2}) Q^T (float32 start; Newton below brings it to float64 accuracy)
@@ -731,8 +742,10 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
   // 7. Newton steps on Z K Z = I: R = I - T_hat^T (G T_hat) / s in float64, correction in float32
   bool w_stale = false;  // W lags T_hat by G (B Delta)
   for (int it = 0; it < 6; ++it) {
-    mm_dist<false>(S.G, S.T, S.W, r, plain);                  // W = G T_hat
-    mm_dist<true>(S.T, S.W, S.F1, r, ResidEpi{S.inv_s});     // I - Z K Z, rounded to float32
+    // W was last read by the previous product (T_hat0 = B Z0 or the residual), F1 by this CTA
+    // alone before that product's closing barrier: neither needs a barrier before its broadcast
+    mm_dist<false, false>(S.G, S.T, S.W, r, plain);               // W = G T_hat
+    mm_dist<true, false>(S.T, S.W, S.F1, r, ResidEpi{S.inv_s});  // I - Z K Z, rounded to float32
     w_stale = false;
     float rmax = 0.f;
     for (int e = tid; e < r * r; e += blockDim.x) rmax = fmaxf(rmax, fabsf(S.F1[(e / r) * LD + e % r]));
