@@ -79,9 +79,10 @@ typedef struct {
   size_t hbm_budget_bytes;  /* cap on workspace bytes the context may hold; 0 = no cap     */
   int max_slots;            /* concurrent requests for sfr_submit; 0 = default (8)         */
   void* cuda_stream;        /* cudaStream_t for sfr_solve; NULL = a stream the ctx creates */
-  int profile;              /* nonzero: time the sweep (or P pass), W-pass and r x r kernels of
+  int profile;              /* 1: time the sweep (or P pass), W-pass and r x r kernels of
                                sfr_solve / sfr_fixed_rank_opt_full with CUDA events on the
-                               solve stream (see sfr_stats)                                */
+                               solve stream (see sfr_stats); 2: time the sweep (or P pass) only
+                               (fewer event records inside the iteration); 0: no timing    */
 } sfr_config;
 
 /* Kernel classes counted by sfr_stats. */

@@ -118,7 +118,8 @@ class Context:
     """An sfr_ctx on one device (sfr_create / sfr_destroy)."""
 
     def __init__(self, device: int = 0, stream: int | None = None, hbm_budget_bytes: int = 0, max_slots: int = 0,
-                 profile: bool = False):
+                 profile: int = 0):
+        """profile: 0 none, 1 (or True) sweep, W pass and r x r kernels timed, 2 the sweep only."""
         self.lib = load()
         self.handle = ctypes.c_void_p()
         cfg = Config(device=device, hbm_budget_bytes=hbm_budget_bytes, max_slots=max_slots,

@@ -29,6 +29,7 @@ namespace {
 template <typename T>
 __global__ void gather_cols_kernel(const T* __restrict__ M, int64_t ldm, const int64_t* __restrict__ perm, int64_t m,
                                    int64_t l, T* __restrict__ out) {
+  pdl_enter();
   // out[i][j] = M[perm[i]][j], j < l   (left block of M~, m x l, dense)
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m * l) return;
@@ -39,6 +40,7 @@ __global__ void gather_cols_kernel(const T* __restrict__ M, int64_t ldm, const i
 template <typename T>
 __global__ void gather_rows_kernel(const T* __restrict__ M, int64_t ldm, const int64_t* __restrict__ perm, int64_t l,
                                    int64_t n, T* __restrict__ out) {
+  pdl_enter();
   // out[i][j] = M[perm[i]][j], i < l   (top block of M~, l x n, dense)
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= l * n) return;
@@ -48,6 +50,7 @@ __global__ void gather_rows_kernel(const T* __restrict__ M, int64_t ldm, const i
 
 // flag = 1 when some perm[i] lies outside [0, m): checked before any gather or scatter.
 __global__ void check_perm_kernel(const int64_t* __restrict__ perm, int64_t m, int* __restrict__ flag) {
+  pdl_enter();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
     if (perm[i] < 0 || perm[i] >= m) atomicExch(flag, 1);
 }
@@ -59,6 +62,7 @@ constexpr int CLD = CR + 1;
 __global__ void nys_core_kernel(const double* __restrict__ UL, const double* __restrict__ BL,
                                 const double* __restrict__ UT, const double* __restrict__ BT, int64_t l, int r,
                                 double* __restrict__ core, int* __restrict__ bad) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* G1 = reinterpret_cast<double*>(smem_raw);
   double* G2 = G1 + CR * CLD;
@@ -164,6 +168,7 @@ __global__ void nys_core_kernel(const double* __restrict__ UL, const double* __r
 // Uo[perm[i]][:] = U_L[i][:] Core   (m x r, dense, M's row order)
 __global__ void nys_rows_kernel(const double* __restrict__ UL, const double* __restrict__ core,
                                 const int64_t* __restrict__ perm, int64_t m, int r, double* __restrict__ Uo) {
+  pdl_enter();
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m * r) return;
   int64_t i = idx / r;
@@ -179,6 +184,7 @@ __global__ void __launch_bounds__(256) nys_residual_kernel(const TMs* __restrict
                                                            int64_t ldm, const double* __restrict__ Uo,
                                                            const double* __restrict__ VT, int r, TSo* __restrict__ S,
                                                            TSo* __restrict__ L, int64_t lds) {
+  pdl_enter();
   __shared__ TC us[8][CR];
   __shared__ TC vs[32][CR + 1];
   const int64_t nbx = (n + 31) / 32;  // 1-D grid over (8-row, 32-column) blocks, columns fastest
@@ -246,7 +252,7 @@ sfr_status nys_solve_device(Solver& sv, const sfr_problem& p, const void* Mdev, 
   int hflag = 0;
   cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
   if (e == cudaSuccess) {
-    check_perm_kernel<<<256, 256, 0, st>>>(perm_dev, m, flag);
+    launch_pdl(check_perm_kernel, 256, 256, 0, st, perm_dev, m, flag);
     e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -254,8 +260,8 @@ sfr_status nys_solve_device(Solver& sv, const sfr_problem& p, const void* Mdev, 
   if (hflag) { *err = "FR-Nys: nys_perm has an entry outside [0, m)"; return SFR_E_INVAL; }
   e = by_mtype(p.m_dtype, Mdev, [&](auto M) {
     using T = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
-    gather_cols_kernel<T><<<cdiv(m * l, 256), 256, 0, st>>>(M, p.ldm, perm_dev, m, l, static_cast<T*>(Mleft));
-    gather_rows_kernel<T><<<cdiv(l * n, 256), 256, 0, st>>>(M, p.ldm, perm_dev, l, n, static_cast<T*>(Mtop));
+    launch_pdl(gather_cols_kernel<T>, cdiv(m * l, 256), 256, 0, st, M, p.ldm, perm_dev, m, l, static_cast<T*>(Mleft));
+    launch_pdl(gather_rows_kernel<T>, cdiv(l * n, 256), 256, 0, st, M, p.ldm, perm_dev, l, n, static_cast<T*>(Mtop));
     return cudaGetLastError();
   });
   if (e != cudaSuccess) { *err = cudaGetErrorString(e); return SFR_E_CUDA; }
@@ -283,8 +289,8 @@ sfr_status nys_solve_device(Solver& sv, const sfr_problem& p, const void* Mdev, 
   const int core_smem = (int)(4 * sizeof(double) * CR * CLD);
   e = cudaFuncSetAttribute(nys_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, core_smem);
   if (e != cudaSuccess) { *err = cudaGetErrorString(e); return SFR_E_CUDA; }
-  nys_core_kernel<<<1, 256, core_smem, st>>>(UL, BL, UT, BT, l, r, core, flag);
-  nys_rows_kernel<<<cdiv(m * r, 256), 256, 0, st>>>(UL, core, perm_dev, m, r, Uo);
+  launch_pdl(nys_core_kernel, 1, 256, core_smem, st, UL, BL, UT, BT, l, r, core, flag);
+  launch_pdl(nys_rows_kernel, cdiv(m * r, 256), 256, 0, st, UL, core, perm_dev, m, r, Uo);
   cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { *err = cudaGetErrorString(e); return SFR_E_CUDA; }
@@ -297,11 +303,11 @@ sfr_status nys_solve_device(Solver& sv, const sfr_problem& p, const void* Mdev, 
     e = by_mtype(p.m_dtype, Mdev, [&](auto M) {
       using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
       if (res->s_dtype == SFR_F64) {
-        if (fp64) nys_residual_kernel<double, TMs, double><<<grid, 256, 0, st>>>(M, m, n, p.ldm, Uo, VT, r, (double*)Sdev, (double*)Ldev, res->lds);
-        else nys_residual_kernel<float, TMs, double><<<grid, 256, 0, st>>>(M, m, n, p.ldm, Uo, VT, r, (double*)Sdev, (double*)Ldev, res->lds);
+        if (fp64) launch_pdl(nys_residual_kernel<double, TMs, double>, grid, 256, 0, st, M, m, n, p.ldm, Uo, VT, r, (double*)Sdev, (double*)Ldev, res->lds);
+        else launch_pdl(nys_residual_kernel<float, TMs, double>, grid, 256, 0, st, M, m, n, p.ldm, Uo, VT, r, (double*)Sdev, (double*)Ldev, res->lds);
       } else {
-        if (fp64) nys_residual_kernel<double, TMs, float><<<grid, 256, 0, st>>>(M, m, n, p.ldm, Uo, VT, r, (float*)Sdev, (float*)Ldev, res->lds);
-        else nys_residual_kernel<float, TMs, float><<<grid, 256, 0, st>>>(M, m, n, p.ldm, Uo, VT, r, (float*)Sdev, (float*)Ldev, res->lds);
+        if (fp64) launch_pdl(nys_residual_kernel<double, TMs, float>, grid, 256, 0, st, M, m, n, p.ldm, Uo, VT, r, (float*)Sdev, (float*)Ldev, res->lds);
+        else launch_pdl(nys_residual_kernel<float, TMs, float>, grid, 256, 0, st, M, m, n, p.ldm, Uo, VT, r, (float*)Sdev, (float*)Ldev, res->lds);
       }
       return cudaGetLastError();
     });

@@ -198,27 +198,9 @@ __device__ __forceinline__ void load_sq(const TS* __restrict__ src, int rp, int 
   }
 }
 
-// Block-wide sum or max: shuffles within each warp, one shared slot per warp, then every thread
-// reduces the (at most 32) warp values with shuffles again; the closing barrier lets `red` be
-// reused at once.
-__device__ __noinline__ double block_reduce(double v, double* red, bool take_max) {
-  for (int o = 16; o > 0; o >>= 1) {
-    const double w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = take_max ? fmax(v, w) : v + w;
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  double t = l < nw ? red[l] : (take_max ? -INFINITY : 0.0);
-  for (int o = 16; o > 0; o >>= 1) {
-    const double u = __shfl_xor_sync(0xffffffffu, t, o);
-    t = take_max ? fmax(t, u) : t + u;
-  }
-  __syncthreads();
-  return t;
-}
-
-// Block-wide maximum of 64-bit integers (same scheme).
+// Block-wide maximum of 64-bit integers: shuffles within each warp, one shared slot per warp, then
+// every thread reduces the (at most 32) warp values with shuffles again; the closing barrier lets
+// `red` be reused at once.
 __device__ __noinline__ long long block_max_ll(long long v, double* red) {
   long long* rl = reinterpret_cast<long long*>(red);
   for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -545,6 +527,7 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
                                                        double* __restrict__ Bg, double* __restrict__ Tout,
                                                        double* __restrict__ TCout, float* __restrict__ Qeig,
                                                        int v_side, int mixed, DevState* st) {
+  pdl_enter();
   if (stopped(st)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RxrSmem& S = *reinterpret_cast<RxrSmem*>(smem_raw);
@@ -890,13 +873,15 @@ cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute at;
-  at.id = cudaLaunchAttributeClusterDimension;
-  at.val.clusterDim.x = cs;
-  at.val.clusterDim.y = 1;
-  at.val.clusterDim.z = 1;
-  cfg.attrs = &at;
-  cfg.numAttrs = 1;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // see pdl_enter
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, rxr_kernel, (const double*)b.Gsum, s.rp, s.r, b.B, v_side ? b.TV : b.TU,
                             v_side ? b.TCm : (double*)nullptr, v_side ? b.Qeig_v : b.Qeig_u, v_side ? 1 : 0,
                             fp64 ? 0 : 1, b.st);

@@ -15,6 +15,36 @@ namespace sfr {
 
 constexpr int kMaxRank = 64;  // r <= 64: r x r blocks live in shared memory
 
+// Programmatic dependent launch.  The kernels of an iteration are launched with
+// cudaLaunchAttributeProgrammaticStreamSerialization (launch_pdl), so that the next kernel is
+// launched while the current one runs.  Every kernel of the library starts with pdl_enter():
+// griddepcontrol.wait blocks until the preceding kernel has completed and its writes are
+// visible (it returns at once for a kernel launched without the attribute), so no global
+// memory is touched before that; then griddepcontrol.launch_dependents lets the following
+// kernel be scheduled.  A grid triggers only once all its CTAs run, so waiting dependents
+// never hold resources that the triggering grid still needs.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// kern<<<grid, block, smem, st>>>(args...) with the programmatic-serialization attribute.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at.val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Per-problem scalars, device resident, read and written by the iteration kernels.
 struct DevState {
   double mu;          // mu_k: penalty of the iteration about to run (Algorithm 1)

@@ -289,6 +289,7 @@ struct Solver {
   bool last_tc = false; // whether the last solve took the tensor-core path
   // profiling: kernel counters and events (slot 0: eager iteration, slots 1-2: the graph's two)
   bool profile = false;
+  bool profile_pass_only = false;  // time only the m x n pass (sweep or P pass), not W pass / r x r
   bool count_stats = false;
   bool capturing = false;
   int64_t launches[SFR_STAT_COUNT] = {};
@@ -333,9 +334,10 @@ struct Solver {
     // inside stream capture an event record becomes a graph node only with the external flag,
     // and that flag is refused outside capture
     const unsigned flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-    if (profile) SFR_CUDA(cudaEventRecordWithFlags(ev[slot][k][0], stream, flags));
+    const bool timed = profile && (k == 0 || !profile_pass_only);
+    if (timed) SFR_CUDA(cudaEventRecordWithFlags(ev[slot][k][0], stream, flags));
     SFR_CUDA(f());
-    if (profile) SFR_CUDA(cudaEventRecordWithFlags(ev[slot][k][1], stream, flags));
+    if (timed) SFR_CUDA(cudaEventRecordWithFlags(ev[slot][k][1], stream, flags));
   }
 
   // Accumulate the event durations of the iterations that ran in `slot`s [first, first + count).
@@ -347,6 +349,7 @@ struct Solver {
       total_ms[pass_kind] += ms;
       timed[pass_kind] += 1;
       bytes[pass_kind] += sweep_bytes;
+      if (profile_pass_only) continue;
       SFR_CUDA(cudaEventElapsedTime(&ms, ev[sl][1][0], ev[sl][1][1]));
       total_ms[SFR_STAT_WPASS] += ms;
       timed[SFR_STAT_WPASS] += 1;
@@ -1241,6 +1244,7 @@ sfr_status sfr_create(sfr_ctx** out, const sfr_config* cfg) {
       sv->stream = stream;
       sv->budget = main ? cfg->hbm_budget_bytes : 0;  // slots are admitted by the context's budget
       sv->profile = main && cfg->profile != 0;
+      sv->profile_pass_only = cfg->profile == 2;
       sv->count_stats = main;
       SFR_CUDA(cudaMallocHost(&sv->host_state, sizeof(DevState)));
       return sv;

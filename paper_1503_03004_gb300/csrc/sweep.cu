@@ -46,6 +46,7 @@ __device__ double block_sum(double v, double* red) {
 // ---------------------------------------------------------------- ||M||_F
 template <typename TMs>
 __global__ void norm_m_kernel(const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm, double* part) {
+  pdl_enter();
   __shared__ double red[32];
   double acc = 0.0;
   for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
@@ -62,6 +63,7 @@ __global__ void norm_m_kernel(const TMs* __restrict__ M, int64_t m, int64_t n, i
 
 template <>
 __global__ void norm_m_kernel<double>(const double* __restrict__ M, int64_t m, int64_t n, int64_t ldm, double* part) {
+  pdl_enter();
   __shared__ double red[32];
   double acc = 0.0;
   for (int64_t i = blockIdx.x; i < m; i += gridDim.x)
@@ -77,6 +79,7 @@ __global__ void norm_m_kernel<double>(const double* __restrict__ M, int64_t m, i
 // Iteration 1: X_1 = M (S = Y = 0), V_1 = I_{n x r}, so P = X_1 V_1 = M[:, 0:r].
 template <typename TC, typename TMs>
 __global__ void init_p_kernel(const TMs* __restrict__ M, int64_t m, int64_t ldm, int r, int rp, TC* P) {
+  pdl_enter();
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m * rp) return;
   int64_t i = idx / rp;
@@ -230,7 +233,8 @@ template <typename TC, int RP>
 __global__ void __launch_bounds__(256) thin_gram_kernel(const TC* __restrict__ parts, int nparts, int64_t part_stride,
                                                         TC* __restrict__ out, int64_t rows, const TC* __restrict__ addA,
                                                         const double* __restrict__ H, double* __restrict__ gpart,
-                                                        const DevState* st, int q_ctas = 0, int64_t q_tiles = 0) {
+                                                        const DevState* st, int q_ctas, int64_t q_tiles) {
+  pdl_enter();
   if (stopped(st)) return;
   constexpr int LDT = RP + 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -301,6 +305,7 @@ __global__ void __launch_bounds__(256) thin_gram_kernel(const TC* __restrict__ p
 template <typename T>
 __global__ void __launch_bounds__(1024) reduce_sq_kernel(const T* parts, int64_t count, int64_t rpsq, T* out,
                                                          const DevState* st) {
+  pdl_enter();
   if (stopped(st)) return;
   __shared__ T red[32][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -346,6 +351,7 @@ __global__ void __launch_bounds__(256) row_transform_kernel(const TC* __restrict
                                                             float* __restrict__ sp_lo = nullptr,
                                                             __nv_bfloat16* __restrict__ trans = nullptr,
                                                             int64_t ldt = 0, int trans_lo = 0) {
+  pdl_enter();
   // Tensor-core path extras (float, RP = 64): sp_hi / sp_lo = TF32 split (hi = x rounded to TF32,
   // lo = x - hi) of dst2 (or of dst without T2), trans = dst transposed in bfloat16 (ld ldt);
   // trans_lo != 0: also the bfloat16 rounding of x - hi into row RP + a (a two-term split).
@@ -446,6 +452,7 @@ template <typename TC, typename TS, int RP>
 __global__ void __launch_bounds__(256) wpass_kernel(const TS* __restrict__ src, int64_t lds, int64_t m, int64_t n,
                                                     int rows_per_chunk, const TC* __restrict__ U, TC* __restrict__ Wpart,
                                                     const DevState* st) {
+  pdl_enter();
   if (stopped(st)) return;
   constexpr int APT = RP / 4;  // accumulators per thread
   __shared__ TC xs[kWBM][kWBN + 1];
@@ -499,6 +506,7 @@ template <typename TC, typename TMs, int RP>
 __global__ void __launch_bounds__(256) ppass_kernel(const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm,
                                                     const TC* __restrict__ V, TC* __restrict__ Qpart,
                                                     int cols_per_split, const DevState* st) {
+  pdl_enter();
   if (stopped(st)) return;
   constexpr int BM = kSweepBM, QPT = RP / 8;  // 8 warps split the rank
   __shared__ TC Xs[BM][kPBN + 1];
@@ -556,6 +564,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const TMs* __restrict__ M, i
                                                     const TC* __restrict__ C, const TC* __restrict__ V,
                                                     TC* __restrict__ Qpart, int cols_per_split,
                                                     double* __restrict__ resid_part, const DevState* st) {
+  pdl_enter();
   if (stopped(st)) return;
   constexpr int BM = kSweepBM, BN = kSweepBN;
   constexpr int QPT = RP / 8;  // Q accumulators per thread (8 warps split the rank)
@@ -718,6 +727,7 @@ __global__ void __launch_bounds__(256) sweep_mx_kernel(const TMs* __restrict__ M
                                                        const float* __restrict__ C, const float* __restrict__ V,
                                                        float* __restrict__ Qpart, int cols_per_split,
                                                        double* __restrict__ resid_part, const DevState* st) {
+  pdl_enter();
   if (stopped(st)) return;
   constexpr int BM = kMxBM, BN = kMxBN, QA = RP / 8;
   __shared__ __align__(16) float UsT[RP][BM];
@@ -891,6 +901,7 @@ __global__ void __launch_bounds__(256) sweep_mxp_kernel(const TMs* __restrict__ 
                                                         const float* __restrict__ C, const float* __restrict__ V,
                                                         float* __restrict__ Qpart, int cols_per_split,
                                                         double* __restrict__ resid_part, int r, const DevState* st) {
+  pdl_enter();
   if (stopped(st)) return;
   constexpr int BM = kMxBM, BN = kMxBN, QA = RP / 8, EPC = 16 / (int)sizeof(TMs);  // M elements per 16 B
   constexpr int LDU = RP + 4;  // padded U rows: the four rows a warp reads fall in different banks
@@ -1097,6 +1108,7 @@ template <typename TS, int RP, bool VEC>
 __global__ void __launch_bounds__(256) wpass_mx_kernel(const TS* __restrict__ src, int64_t lds, int64_t m, int64_t n,
                                                        int rows_per_chunk, const float* __restrict__ U,
                                                        float* __restrict__ Wpart, const DevState* st) {
+  pdl_enter();
   if (stopped(st)) return;
   constexpr int BR = 32, BN = kMxBN, QA = RP / 8;
   __shared__ __align__(16) float Xs[BR][kMxLDX];
@@ -1178,6 +1190,7 @@ template <typename TS, int RP>
 __global__ void __launch_bounds__(256) wpass_mxp_kernel(const TS* __restrict__ src, int64_t lds, int64_t m, int64_t n,
                                                         int rows_per_chunk, const float* __restrict__ U,
                                                         float* __restrict__ Wpart, const DevState* st) {
+  pdl_enter();
   if (stopped(st)) return;
   constexpr int BR = 32, BN = kMxBN, QA = RP / 8, EPC = 16 / (int)sizeof(TS);
   constexpr int XS = BR * BN, US = BR * RP;  // elements per stage
@@ -1265,6 +1278,7 @@ constexpr size_t wxp_smem() { return (size_t)kWxStages * 32 * (kMxBN * sizeof(TS
 // ---------------------------------------------------------------- end of iteration (one CTA)
 // ||M - L - S||_F = ||Y_{k+1} - Y_k||_F / mu_k; continuation mu_{k+1} = min(mu_bar, rho mu_k).
 __global__ void iter_end_kernel(const double* __restrict__ resid_part, int count, DevState* st) {
+  pdl_enter();
   __shared__ double red[32];
   if (stopped(st)) return;
   double v = 0.0;
@@ -1293,6 +1307,7 @@ __global__ void iter_end_kernel(const double* __restrict__ resid_part, int count
 }
 
 __global__ void norm_finish_kernel(const double* __restrict__ part, int count, DevState* st) {
+  pdl_enter();
   __shared__ double red[32];
   double v = 0.0;
   for (int c = threadIdx.x; c < count; c += blockDim.x) v += part[c];
@@ -1311,6 +1326,7 @@ __global__ void norm_finish_kernel(const double* __restrict__ part, int count, D
 // of B, ||B_i - B_{i-1}||_F / ||B_i||_F, over the leading r x r block; then B_prev = B_i.
 __global__ void full_end_kernel(const double* __restrict__ B, double* __restrict__ Bprev, int rp, int r,
                                 DevState* st) {
+  pdl_enter();
   __shared__ double red[32];
   if (stopped(st)) return;
   double d2 = 0.0, b2 = 0.0;
@@ -1349,6 +1365,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const TMs* __restrict__ M
                                                        const TY* __restrict__ Yprev, int64_t ldy, const TC* __restrict__ U,
                                                        const TC* __restrict__ C, TSo* __restrict__ S, TSo* __restrict__ L,
                                                        int64_t lds, const DevState* st) {
+  pdl_enter();
   __shared__ TC us[8][RP];
   __shared__ TC cs[32][RP + 1];
   // 1-D grid over (8-row, 32-column) blocks, columns fastest (a 2-D grid would cap m at 65535 x 8)
@@ -1379,6 +1396,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const TMs* __restrict__ M
 
 template <typename TC, int RP>
 __global__ void export_kernel(const TC* __restrict__ src, int64_t rows, int r, double* __restrict__ dst) {
+  pdl_enter();
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= rows * r) return;
   int64_t i = idx / r;
@@ -1389,6 +1407,7 @@ __global__ void export_kernel(const TC* __restrict__ src, int64_t rows, int r, d
 // dst (rows x RP, TC) = src (rows x r, float64), padding columns r .. RP-1 with zeros.
 template <typename TC, int RP>
 __global__ void import_kernel(const double* __restrict__ src, int64_t rows, int r, TC* __restrict__ dst) {
+  pdl_enter();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= rows * RP) return;
   const int64_t i = idx / RP;
@@ -1454,7 +1473,7 @@ inline int reduce_threads(int64_t count) { return count >= 256 ? 1024 : 256; }
 
 cudaError_t launch_reduce_parts(const double* parts, int count, int rpsq, double* out, const DevState* dst,
                                 cudaStream_t st) {
-  reduce_sq_kernel<double><<<cdiv(rpsq, 32), reduce_threads(count), 0, st>>>(parts, count, rpsq, out, dst);
+  launch_pdl(reduce_sq_kernel<double>, cdiv(rpsq, 32), reduce_threads(count), 0, st, parts, count, rpsq, out, dst);
   return cudaGetLastError();
 }
 
@@ -1462,11 +1481,11 @@ cudaError_t launch_norm_m(const Shape& s, const Buffers& b, cudaStream_t st) {
   const int blocks = (int)std::min<int64_t>(s.m, 1024);
   cudaError_t e = by_mtype(b.m_dtype, b.M, [&](auto M) {
     using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
-    norm_m_kernel<TMs><<<blocks, 256, 0, st>>>(M, s.m, s.n, s.ldm, b.normm_part);
+    launch_pdl(norm_m_kernel<TMs>, blocks, 256, 0, st, M, s.m, s.n, s.ldm, b.normm_part);
     return cudaGetLastError();
   });
   if (e != cudaSuccess) return e;
-  norm_finish_kernel<<<1, 256, 0, st>>>(b.normm_part, blocks, b.st);
+  launch_pdl(norm_finish_kernel, 1, 256, 0, st, b.normm_part, blocks, b.st);
   return cudaGetLastError();
 }
 
@@ -1475,7 +1494,7 @@ cudaError_t launch_init_p(const Shape& s, const Buffers& b, bool fp64, cudaStrea
     using TC = decltype(tc);
     return by_mtype(b.m_dtype, b.M, [&](auto M) {
       using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
-      init_p_kernel<TC, TMs><<<cdiv(s.m * s.rp, 256), 256, 0, st>>>(M, s.m, s.ldm, s.r, s.rp, static_cast<TC*>(b.P));
+      launch_pdl(init_p_kernel<TC, TMs>, cdiv(s.m * s.rp, 256), 256, 0, st, M, s.m, s.ldm, s.r, s.rp, static_cast<TC*>(b.P));
       return cudaGetLastError();
     });
   });
@@ -1490,7 +1509,7 @@ cudaError_t launch_gram_p(const Shape& s, const Buffers& b, bool fp64, bool sum_
       const size_t sm = gram_smem<TC, RP>();
       cudaError_t e = allow_smem(thin_gram_kernel<TC, RP>, sm);
       if (e != cudaSuccess) return e;
-      thin_gram_kernel<TC, RP><<<s.gp_blocks, 256, sm, st>>>(
+      launch_pdl(thin_gram_kernel<TC, RP>, s.gp_blocks, 256, sm, st,
           static_cast<const TC*>(b.Qpart), sum_parts ? s.nsplit : 0, s.m * RP, static_cast<TC*>(b.P), s.m,
           static_cast<const TC*>(addA), H, b.GPpart, b.st, s.q_ctas, (s.n + 63) / 64);
       return cudaGetLastError();
@@ -1511,7 +1530,7 @@ cudaError_t launch_apply_u(const Shape& s, const Buffers& b, bool fp64, bool fir
       // tensor-core path: also the TF32 split of U_new and its bfloat16 transpose (MMA operands)
       // (Algorithm 4: the two-term bfloat16 split of U^T instead, the B operand of M^T U)
       const bool tcx = b.tc && RP == 64 && !fp64, tf = tcx && !b.full;
-      row_transform_kernel<TC, RP><<<s.gp_blocks, 256, sm, st>>>(
+      launch_pdl(row_transform_kernel<TC, RP>, s.gp_blocks, 256, sm, st,
           static_cast<const TC*>(b.P), s.m, b.TU, static_cast<TC*>(b.U[u_new]), nullptr, nullptr,
           first ? nullptr : static_cast<const TC*>(b.U[u_old]), first ? nullptr : b.Hpart, b.st,
           tf ? b.t.Uh : nullptr, tf ? b.t.Ul : nullptr, tcx ? static_cast<__nv_bfloat16*>(b.t.Ut) : nullptr,
@@ -1533,7 +1552,7 @@ cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first
         const float* U = static_cast<const float*>(b.U[u_new]);
         float* Wp = static_cast<float*>(b.Wpart);
         auto go = [&](auto kern, auto src, int64_t lds) {
-          kern<<<grid, 256, 0, st>>>(src, lds, s.m, s.n, s.rows_per_chunk, U, Wp, b.st);
+          launch_pdl(kern, grid, 256, 0, st, src, lds, s.m, s.n, s.rows_per_chunk, U, Wp, b.st);
           return cudaGetLastError();
         };
         auto pipelined = [&](auto srcp, int64_t lds) {
@@ -1542,7 +1561,7 @@ cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first
           constexpr size_t sm = wxp_smem<TS, RP>();
           cudaError_t e = allow_smem(kern, sm);
           if (e != cudaSuccess) return e;
-          kern<<<grid, 256, sm, st>>>(srcp, lds, s.m, s.n, s.rows_per_chunk, U, Wp, b.st);
+          launch_pdl(kern, grid, 256, sm, st, srcp, lds, s.m, s.n, s.rows_per_chunk, U, Wp, b.st);
           return cudaGetLastError();
         };
         if (first)
@@ -1567,11 +1586,11 @@ cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first
       if (first) {
         return by_mtype(b.m_dtype, b.M, [&](auto M) {
           using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
-          wpass_kernel<TC, TMs, RP><<<grid, 256, 0, st>>>(M, s.ldm, s.m, s.n, s.rows_per_chunk, U, Wp, b.st);
+          launch_pdl(wpass_kernel<TC, TMs, RP>, grid, 256, 0, st, M, s.ldm, s.m, s.n, s.rows_per_chunk, U, Wp, b.st);
           return cudaGetLastError();
         });
       }
-      wpass_kernel<TC, TC, RP><<<grid, 256, 0, st>>>(static_cast<const TC*>(b.D), s.n, s.m, s.n, s.rows_per_chunk, U, Wp,
+      launch_pdl(wpass_kernel<TC, TC, RP>, grid, 256, 0, st, static_cast<const TC*>(b.D), s.n, s.m, s.n, s.rows_per_chunk, U, Wp,
                                                      b.st);
       return cudaGetLastError();
     });
@@ -1582,7 +1601,7 @@ cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool firs
   // W = sum_c Wpart[c] (+ C_old H, H = U_old^T U_new), then Gram partials of W.
   // H = sum of the U_old^T U_new partials, reduced into the slot after the partials.
   if (!first) {
-    reduce_sq_kernel<double><<<cdiv(s.rp * s.rp, 32), reduce_threads(s.gp_blocks), 0, st>>>(
+    launch_pdl(reduce_sq_kernel<double>, cdiv(s.rp * s.rp, 32), reduce_threads(s.gp_blocks), 0, st,
         b.Hpart, s.gp_blocks, s.rp * s.rp, b.Hpart + (size_t)s.gp_blocks * s.rp * s.rp, b.st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1600,15 +1619,15 @@ cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool firs
       int nparts = s.nchunk;
       if (nparts >= 32) {
         const int64_t len = s.n * RP;
-        reduce_sq_kernel<TC><<<cdiv(len, 32), reduce_threads(nparts), 0, st>>>(static_cast<const TC*>(b.Wpart),
+        launch_pdl(reduce_sq_kernel<TC>, cdiv(len, 32), reduce_threads(nparts), 0, st, static_cast<const TC*>(b.Wpart),
                                                                                 nparts, len, static_cast<TC*>(b.Wpart),
                                                                                 b.st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         nparts = 1;
       }
-      thin_gram_kernel<TC, RP><<<s.gw_blocks, 256, sm, st>>>(
+      launch_pdl(thin_gram_kernel<TC, RP>, s.gw_blocks, 256, sm, st,
           static_cast<const TC*>(b.Wpart), nparts, s.n * RP, static_cast<TC*>(b.W), s.n,
-          first ? nullptr : static_cast<const TC*>(b.C), first ? nullptr : H, b.GWpart, b.st);
+          first ? nullptr : static_cast<const TC*>(b.C), first ? nullptr : H, b.GWpart, b.st, 0, (int64_t)0);
       return cudaGetLastError();
     });
   });
@@ -1625,7 +1644,7 @@ cudaError_t launch_apply_v(const Shape& s, const Buffers& b, bool fp64, cudaStre
       // tensor-core path: also the TF32 split of C and the bfloat16 transpose of V
       // (Algorithm 4: the two-term bfloat16 split of V^T instead, the B operand of M V)
       const bool tcx = b.tc && RP == 64 && !fp64, tf = tcx && !b.full;
-      row_transform_kernel<TC, RP><<<s.gw_blocks, 256, sm, st>>>(
+      launch_pdl(row_transform_kernel<TC, RP>, s.gw_blocks, 256, sm, st,
           static_cast<const TC*>(b.W), s.n, b.TV, static_cast<TC*>(b.V), b.TCm, static_cast<TC*>(b.C), nullptr, nullptr,
           b.st, tf ? b.t.Ch : nullptr, tf ? b.t.Cl : nullptr, tcx ? static_cast<__nv_bfloat16*>(b.t.Vt) : nullptr,
           b.t.ldy, b.full ? 1 : 0);
@@ -1645,7 +1664,7 @@ static cudaError_t launch_sweep_mx(const Shape& s, const Buffers& b, int u_cur, 
       return by_mtype(b.m_dtype, b.M, [&](auto M) {
         using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
         auto go = [&](auto kern) {
-          kern<<<grid, 256, 0, st>>>(M, s.m, s.n, s.ldm, static_cast<const float*>(b.Y[0]),
+          launch_pdl(kern, grid, 256, 0, st, M, s.m, s.n, s.ldm, static_cast<const float*>(b.Y[0]),
                                      static_cast<float*>(b.Y[1]), static_cast<float*>(b.D),
                                      static_cast<const float*>(b.U[u_cur]), static_cast<const float*>(b.C),
                                      static_cast<const float*>(b.V), static_cast<float*>(b.Qpart), s.cols_per_split,
@@ -1658,7 +1677,7 @@ static cudaError_t launch_sweep_mx(const Shape& s, const Buffers& b, int u_cur, 
             constexpr size_t sm = mxp_smem<TMs, RP>();
             cudaError_t e = allow_smem(kern, sm);
             if (e != cudaSuccess) return e;
-            kern<<<grid, 256, sm, st>>>(M, s.m, s.n, s.ldm, static_cast<const float*>(b.Y[0]),
+            launch_pdl(kern, grid, 256, sm, st, M, s.m, s.n, s.ldm, static_cast<const float*>(b.Y[0]),
                                         static_cast<float*>(b.Y[1]), static_cast<float*>(b.D),
                                         static_cast<const float*>(b.U[u_cur]), static_cast<const float*>(b.C),
                                         static_cast<const float*>(b.V), static_cast<float*>(b.Qpart),
@@ -1688,7 +1707,7 @@ cudaError_t launch_sweep(const Shape& s, const Buffers& b, bool fp64, int u_cur,
         auto kern = sweep_kernel<TC, TMs, RP>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<grid, 256, smem, st>>>(M, s.m, s.n, s.ldm, static_cast<const TC*>(b.Y[0]), static_cast<TC*>(b.Y[1]),
+        launch_pdl(kern, grid, 256, smem, st, M, s.m, s.n, s.ldm, static_cast<const TC*>(b.Y[0]), static_cast<TC*>(b.Y[1]),
                                       static_cast<TC*>(b.D), static_cast<const TC*>(b.U[u_cur]),
                                       static_cast<const TC*>(b.C), static_cast<const TC*>(b.V),
                                       static_cast<TC*>(b.Qpart), s.cols_per_split, b.resid_part, b.st);
@@ -1701,7 +1720,7 @@ cudaError_t launch_sweep(const Shape& s, const Buffers& b, bool fp64, int u_cur,
 cudaError_t launch_iter_end(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st) {
   // the mixed SIMT sweep writes one residual partial per CTA, the others one per 32-row block
   const int count = mx_path(s, fp64) ? s.mx_grid_x * s.nsplit : s.resid_parts;
-  iter_end_kernel<<<1, 1024, 0, st>>>(b.resid_part, count, b.st);
+  launch_pdl(iter_end_kernel, 1, 1024, 0, st, b.resid_part, count, b.st);
   return cudaGetLastError();
 }
 
@@ -1720,11 +1739,11 @@ cudaError_t launch_finalize(const Shape& s, const Buffers& b, bool fp64, int u_c
         auto go = [&](auto yptr, int64_t ldy) {
           using TY = std::remove_const_t<std::remove_pointer_t<decltype(yptr)>>;
           if (s_dtype == SFR_F64)
-            finalize_kernel<TC, TMs, double, TY, RP><<<grid, 256, 0, st>>>(
+            launch_pdl(finalize_kernel<TC, TMs, double, TY, RP>, grid, 256, 0, st,
                 M, s.m, s.n, s.ldm, yptr, ldy, static_cast<const TC*>(b.U[u_cur]), static_cast<const TC*>(b.C),
                 static_cast<double*>(S), static_cast<double*>(L), lds, b.st);
           else
-            finalize_kernel<TC, TMs, float, TY, RP><<<grid, 256, 0, st>>>(
+            launch_pdl(finalize_kernel<TC, TMs, float, TY, RP>, grid, 256, 0, st,
                 M, s.m, s.n, s.ldm, yptr, ldy, static_cast<const TC*>(b.U[u_cur]), static_cast<const TC*>(b.C),
                 static_cast<float*>(S), static_cast<float*>(L), lds, b.st);
           return cudaGetLastError();
@@ -1742,8 +1761,8 @@ cudaError_t launch_export_factors(const Shape& s, const Buffers& b, bool fp64, i
     using TC = decltype(tc);
     return by_rank(s.rp, [&](auto rpc) {
       constexpr int RP = decltype(rpc)::value;
-      if (U) export_kernel<TC, RP><<<cdiv(s.m * s.r, 256), 256, 0, st>>>(static_cast<const TC*>(b.U[u_cur]), s.m, s.r, U);
-      if (V) export_kernel<TC, RP><<<cdiv(s.n * s.r, 256), 256, 0, st>>>(static_cast<const TC*>(b.V), s.n, s.r, V);
+      if (U) launch_pdl(export_kernel<TC, RP>, cdiv(s.m * s.r, 256), 256, 0, st, static_cast<const TC*>(b.U[u_cur]), s.m, s.r, U);
+      if (V) launch_pdl(export_kernel<TC, RP>, cdiv(s.n * s.r, 256), 256, 0, st, static_cast<const TC*>(b.V), s.n, s.r, V);
       return cudaGetLastError();
     });
   });
@@ -1757,7 +1776,7 @@ cudaError_t launch_ppass(const Shape& s, const Buffers& b, bool fp64, cudaStream
       constexpr int RP = decltype(rpc)::value;
       return by_mtype(b.m_dtype, b.M, [&](auto M) {
         using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
-        ppass_kernel<TC, TMs, RP><<<grid, 256, 0, st>>>(M, s.m, s.n, s.ldm, static_cast<const TC*>(b.V),
+        launch_pdl(ppass_kernel<TC, TMs, RP>, grid, 256, 0, st, M, s.m, s.n, s.ldm, static_cast<const TC*>(b.V),
                                                          static_cast<TC*>(b.Qpart), s.cols_per_split, b.st);
         return cudaGetLastError();
       });
@@ -1766,7 +1785,7 @@ cudaError_t launch_ppass(const Shape& s, const Buffers& b, bool fp64, cudaStream
 }
 
 cudaError_t launch_full_end(const Shape& s, const Buffers& b, cudaStream_t st) {
-  full_end_kernel<<<1, 256, 0, st>>>(b.B, b.Bprev, s.rp, s.r, b.st);
+  launch_pdl(full_end_kernel, 1, 256, 0, st, b.B, b.Bprev, s.rp, s.r, b.st);
   return cudaGetLastError();
 }
 
@@ -1775,7 +1794,7 @@ cudaError_t launch_import(const Shape& s, const double* src, int64_t rows, void*
     using TC = decltype(tc);
     return by_rank(s.rp, [&](auto rpc) {
       constexpr int RP = decltype(rpc)::value;
-      import_kernel<TC, RP><<<cdiv(rows * RP, 256), 256, 0, st>>>(src, rows, s.r, static_cast<TC*>(dst));
+      launch_pdl(import_kernel<TC, RP>, cdiv(rows * RP, 256), 256, 0, st, src, rows, s.r, static_cast<TC*>(dst));
       return cudaGetLastError();
     });
   });

@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
                                                                    double* __restrict__ resid_part, DevState* st,
                                                                    TSo* __restrict__ Sout, TSo* __restrict__ Lout,
                                                                    int64_t lds, int vec_out) {
+  pdl_enter();
   if (!FINAL && stopped(st)) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -554,6 +555,7 @@ __global__ void __launch_bounds__(192, 1) wpass_tc_kernel(const __grid_constant_
                                                           const __grid_constant__ CUtensorMap tmUt, int64_t m,
                                                           int64_t n, int rows_per_chunk, float* __restrict__ Wpart,
                                                           DevState* st) {
+  pdl_enter();
   constexpr uint32_t W_STAGE = w_stage<NS>(), TCOLS = NS == 1 ? 64 : 128;
   if (stopped(st)) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -694,6 +696,7 @@ static_assert(sizeof(PBars) <= 128, "barrier block");
 __global__ void __launch_bounds__(192, 1) ppass_tc_kernel(const __grid_constant__ CUtensorMap tmM,
                                                           const __grid_constant__ CUtensorMap tmVt, int64_t m,
                                                           int64_t n, float* __restrict__ Qpart, DevState* st) {
+  pdl_enter();
   if (stopped(st)) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -883,7 +886,7 @@ cudaError_t tc_launch_wpass(const Shape& s, const TcMaps& mp, bool first, float*
       cudaFuncSetAttribute(wpass_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wpass_smem<1>());
   if (e != cudaSuccess) return e;
   dim3 grid(cdiv(s.n, 128), s.nchunk);
-  wpass_tc_kernel<1><<<grid, 192, wpass_smem<1>(), st>>>(first ? mp.M_w : mp.D_w, mp.Ut, s.m, s.n, s.rows_per_chunk,
+  launch_pdl(wpass_tc_kernel<1>, grid, 192, wpass_smem<1>(), st, first ? mp.M_w : mp.D_w, mp.Ut, s.m, s.n, s.rows_per_chunk,
                                                           Wpart, dst);
   return cudaGetLastError();
 }
@@ -893,14 +896,14 @@ cudaError_t tc_launch_full_wpass(const Shape& s, const TcMaps& mp, float* Wpart,
       cudaFuncSetAttribute(wpass_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wpass_smem<2>());
   if (e != cudaSuccess) return e;
   dim3 grid(cdiv(s.n, 128), s.nchunk);
-  wpass_tc_kernel<2><<<grid, 192, wpass_smem<2>(), st>>>(mp.M_w, mp.Ut2, s.m, s.n, s.rows_per_chunk, Wpart, dst);
+  launch_pdl(wpass_tc_kernel<2>, grid, 192, wpass_smem<2>(), st, mp.M_w, mp.Ut2, s.m, s.n, s.rows_per_chunk, Wpart, dst);
   return cudaGetLastError();
 }
 
 cudaError_t tc_launch_full_ppass(const Shape& s, const TcMaps& mp, float* Qpart, DevState* dst, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(ppass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PPASS_SMEM);
   if (e != cudaSuccess) return e;
-  ppass_tc_kernel<<<s.sweep_grid_x, 192, PPASS_SMEM, st>>>(mp.M, mp.Vt2, s.m, s.n, Qpart, dst);
+  launch_pdl(ppass_tc_kernel, s.sweep_grid_x, 192, PPASS_SMEM, st, mp.M, mp.Vt2, s.m, s.n, Qpart, dst);
   return cudaGetLastError();
 }
 
@@ -909,7 +912,7 @@ cudaError_t tc_launch_sweep(const Shape& s, const TcMaps& mp, const TcBuffers& t
   auto kern = sweep_tc_kernel<false, float>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
   if (e != cudaSuccess) return e;
-  kern<<<s.sweep_grid_x, kSweepThreads, SWEEP_SMEM, st>>>(mp.M, mp.Y[y_in], mp.Y[1 - y_in], mp.D, mp.Ch, mp.Cl, mp.Vt,
+  launch_pdl(kern, s.sweep_grid_x, kSweepThreads, SWEEP_SMEM, st, mp.M, mp.Y[y_in], mp.Y[1 - y_in], mp.D, mp.Ch, mp.Cl, mp.Vt,
                                                          t.Uh, t.Ul, s.m, s.n, Qpart, resid_part, dst, nullptr,
                                                          nullptr, 0, 0);
   return cudaGetLastError();
@@ -924,7 +927,7 @@ cudaError_t tc_launch_finalize(const Shape& s, const TcMaps& mp, const TcBuffers
     auto kern = sweep_tc_kernel<true, TSo>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
     if (e != cudaSuccess) return e;
-    kern<<<s.sweep_grid_x, kSweepThreads, SWEEP_SMEM, st>>>(mp.M, mp.Y[y_in], mp.Y[1 - y_in], mp.D, mp.Ch, mp.Cl,
+    launch_pdl(kern, s.sweep_grid_x, kSweepThreads, SWEEP_SMEM, st, mp.M, mp.Y[y_in], mp.Y[1 - y_in], mp.D, mp.Ch, mp.Cl,
                                                            mp.Vt, t.Uh, t.Ul, s.m, s.n, nullptr, nullptr, dst,
                                                            static_cast<TSo*>(S), static_cast<TSo*>(L), lds,
                                                            vec ? 1 : 0);
