@@ -361,7 +361,16 @@ def run_serving(args):
                         time.sleep(wait)
                 p, res = mk(q, Md, out, B.PREC_MIXED)
                 keep.append((p, res))
-                pending[ctx.submit(p, res)] = (k, time.perf_counter())
+                ts = time.perf_counter()  # arrival (latency counts queueing at the client too)
+                while True:
+                    try:
+                        pending[ctx.submit(p, res)] = (k, ts)
+                        break
+                    except B.SfrError as e:  # the library's queue is full: wait for completions
+                        if e.status != B.E_BUSY:
+                            raise
+                        reap()
+                        time.sleep(1e-4)
                 reap()
             while pending:
                 reap()

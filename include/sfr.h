@@ -122,14 +122,18 @@ typedef struct {
 } sfr_problem;
 
 typedef struct {
-  double* U;                /* m x r (FR-Nys: NULL, factors are not returned)              */
-  double* B;                /* r x r                                                       */
-  double* V;                /* n x r                                                       */
+  double* U;                /* m x r, orthonormal columns; NULL = do not return            */
+  double* B;                /* r x r, symmetric (FR-Nys: diagonal, see below)              */
+  double* V;                /* n x r, orthonormal columns.  L = U B V^T.  FR-Nys returns its
+                               L = U_L Core V_T^T (Algorithm 2, r x r core) in this form through
+                               the SVD Core = A diag(sigma) C^T: U = U_L A (rows in M's order),
+                               B = diag(sigma) (decreasing), V = V_T C                      */
   void* S;                  /* m x n sparse part; NULL = do not write S                    */
   sfr_dtype s_dtype;        /* SFR_F64 or SFR_F32                                          */
   int64_t lds;              /* leading dimension of S, >= n                                */
   void* L;                  /* optional m x n low-rank part (same dtype/ld as S); NULL = skip */
-  int32_t iters;            /* iterations run (FR-Nys: sum over the two block solves)      */
+  int32_t iters;            /* iterations run (FR-Nys: sum over the two block solves, which
+                               run concurrently on two streams)                            */
   double rel_residual;      /* ||M - L - S||_F / ||M||_F after the last iteration          */
   double lambda_min_B;      /* smallest eigenvalue of the returned B (SPD diagnostic)      */
   sfr_status status;        /* outcome of this problem                                     */

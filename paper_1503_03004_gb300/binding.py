@@ -215,11 +215,9 @@ def solve_torch(ctx: Context, M, r: int, *, precision: int = PREC_FP64, want_L: 
     m, n = M.shape
     dev = M.device
     sd = torch.float64 if s_dtype == F64 else torch.float32
-    U = B = V = None
-    if nys_l == 0:
-        U = torch.empty((m, r), dtype=torch.float64, device=dev)
-        B = torch.empty((r, r), dtype=torch.float64, device=dev)
-        V = torch.empty((n, r), dtype=torch.float64, device=dev)
+    U = torch.empty((m, r), dtype=torch.float64, device=dev)
+    B = torch.empty((r, r), dtype=torch.float64, device=dev)
+    V = torch.empty((n, r), dtype=torch.float64, device=dev)
     S = torch.empty((m, n), dtype=sd, device=dev)
     L = torch.empty((m, n), dtype=sd, device=dev) if want_L else None
     perm_ptr = 0
@@ -228,9 +226,8 @@ def solve_torch(ctx: Context, M, r: int, *, precision: int = PREC_FP64, want_L: 
         perm_ptr = nys_perm.data_ptr()
     prob = make_problem(m=m, n=n, r=r, M_ptr=M.data_ptr(), m_dtype=code, ldm=M.stride(0), precision=precision,
                         mem=MEM_DEVICE, nys_l=nys_l, nys_perm_ptr=perm_ptr, **kw)
-    res = make_result(U_ptr=U.data_ptr() if U is not None else 0, B_ptr=B.data_ptr() if B is not None else 0,
-                      V_ptr=V.data_ptr() if V is not None else 0, S_ptr=S.data_ptr(), s_dtype=s_dtype, lds=n,
-                      L_ptr=L.data_ptr() if L is not None else 0)
+    res = make_result(U_ptr=U.data_ptr(), B_ptr=B.data_ptr(), V_ptr=V.data_ptr(), S_ptr=S.data_ptr(),
+                      s_dtype=s_dtype, lds=n, L_ptr=L.data_ptr() if L is not None else 0)
     torch.cuda.synchronize(dev)
     st = ctx.solve(prob, res)
     if check and st not in (OK,):

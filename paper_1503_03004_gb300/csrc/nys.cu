@@ -9,7 +9,14 @@
 //   (L_L[:l, :l])^+ = (A V_L^T)^+ = V_L (A^T A)^{-1} A^T,
 // so L = U_L B_L (A^T A)^{-1} B_L (U_L[:l]^T U_T) B_T V_T^T = U_L Core V_T^T,
 // an r x r core; no l x l pseudo-inverse is formed.  The m x n pass then writes
-// S = M - (U_L Core) V_T^T row by row in M's original order.
+// S = M - (U_L Core) V_T^T row by row in M's original order.  With the SVD
+// Core = A diag(sigma) C^T (r x r, one-sided Jacobi on the host), L = (U_L A) diag(sigma) (V_T C)^T
+// is returned in the polar form of the other entry points: U = U_L A, B = diag(sigma),
+// V = V_T C, U and V orthonormal.  The two block solves run concurrently, the second on an
+// auxiliary solver with its own stream and workspace.
+#include <algorithm>
+#include <cmath>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -23,6 +30,10 @@ DevState solver_run(Solver& sv, const sfr_problem& p, const void* Mdev, double* 
 void* solver_nys_block(Solver& sv, size_t bytes);
 cudaStream_t solver_stream(Solver& sv);
 bool solver_last_tc(const Solver& sv);
+Solver* solver_aux(Solver& sv);
+bool solver_reserve(Solver& sv, const sfr_problem& p, const void* Mdev, size_t* held, size_t budget);
+size_t* solver_held(Solver& sv);
+size_t solver_budget(const Solver& sv);
 
 namespace {
 
@@ -165,7 +176,7 @@ __global__ void nys_core_kernel(const double* __restrict__ UL, const double* __r
   if (tid == 0) *bad = 0;
 }
 
-// Uo[perm[i]][:] = U_L[i][:] Core   (m x r, dense, M's row order)
+// Uo[perm[i]][:] = U_L[i][:] Core   (m x r, dense, M's row order; perm == nullptr: identity)
 __global__ void nys_rows_kernel(const double* __restrict__ UL, const double* __restrict__ core,
                                 const int64_t* __restrict__ perm, int64_t m, int r, double* __restrict__ Uo) {
   pdl_enter();
@@ -175,7 +186,7 @@ __global__ void nys_rows_kernel(const double* __restrict__ UL, const double* __r
   int b = (int)(idx % r);
   double v = 0.0;
   for (int a = 0; a < r; ++a) v = fma(UL[i * r + a], core[a * r + b], v);
-  Uo[perm[i] * r + b] = v;
+  Uo[(perm ? perm[i] : i) * r + b] = v;
 }
 
 // S = M - Uo V_T^T (and optionally L), Algorithm 2's S = M~ - L in M's row order.
@@ -222,11 +233,94 @@ cudaError_t by_mtype(sfr_dtype dt, const void* M, F&& f) {
 
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
+// SVD of the r x r core, K = A diag(sigma) C^T (host, float64), by one-sided (Hestenes) Jacobi:
+// plane rotations J applied to the columns of W = K until they are mutually orthogonal, so that
+// K C = W with C the product of the rotations; then sigma_j = ||w_j||, a_j = w_j / sigma_j.
+// Columns come out sorted by decreasing sigma; a column with sigma = 0 gets a unit vector
+// orthogonal to the others, so that A is orthogonal in every case.
+void core_svd(const std::vector<double>& K, int r, std::vector<double>& A, std::vector<double>& sig,
+              std::vector<double>& C) {
+  std::vector<double> W = K;  // row-major r x r
+  C.assign((size_t)r * r, 0.0);
+  for (int i = 0; i < r; ++i) C[(size_t)i * r + i] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < r - 1; ++p)
+      for (int q = p + 1; q < r; ++q) {
+        double alpha = 0.0, beta = 0.0, gamma = 0.0;
+        for (int i = 0; i < r; ++i) {
+          const double wp = W[(size_t)i * r + p], wq = W[(size_t)i * r + q];
+          alpha += wp * wp;
+          beta += wq * wq;
+          gamma += wp * wq;
+        }
+        if (gamma == 0.0 || std::fabs(gamma) <= 1e-17 * std::sqrt(alpha * beta)) continue;
+        off = std::max(off, std::fabs(gamma) / std::sqrt(alpha * beta));
+        const double zeta = (beta - alpha) / (2.0 * gamma);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+        for (int i = 0; i < r; ++i) {
+          double* w = &W[(size_t)i * r];
+          const double wp = w[p], wq = w[q];
+          w[p] = c * wp - sn * wq;
+          w[q] = sn * wp + c * wq;
+          double* cc = &C[(size_t)i * r];
+          const double cp = cc[p], cq = cc[q];
+          cc[p] = c * cp - sn * cq;
+          cc[q] = sn * cp + c * cq;
+        }
+      }
+    if (off < 1e-15) break;
+  }
+  std::vector<double> norms(r);
+  for (int j = 0; j < r; ++j) {
+    double v = 0.0;
+    for (int i = 0; i < r; ++i) v += W[(size_t)i * r + j] * W[(size_t)i * r + j];
+    norms[j] = std::sqrt(v);
+  }
+  std::vector<int> order(r);
+  for (int j = 0; j < r; ++j) order[j] = j;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return norms[a] > norms[b]; });
+  const double big = norms[order[0]];
+  A.assign((size_t)r * r, 0.0);
+  sig.assign(r, 0.0);
+  std::vector<double> Cs((size_t)r * r);
+  for (int jj = 0; jj < r; ++jj) {
+    const int j = order[jj];
+    sig[jj] = norms[j];
+    for (int i = 0; i < r; ++i) Cs[(size_t)i * r + jj] = C[(size_t)i * r + j];
+    if (norms[j] > 1e-300 && norms[j] > 1e-15 * big) {
+      for (int i = 0; i < r; ++i) A[(size_t)i * r + jj] = W[(size_t)i * r + j] / norms[j];
+    } else {
+      sig[jj] = 0.0;
+      for (int e = 0; e < r; ++e) {  // first unit vector not in the span of the columns so far
+        std::vector<double> v(r, 0.0);
+        v[e] = 1.0;
+        for (int k = 0; k < jj; ++k) {
+          double d = 0.0;
+          for (int i = 0; i < r; ++i) d += A[(size_t)i * r + k] * v[i];
+          for (int i = 0; i < r; ++i) v[i] -= d * A[(size_t)i * r + k];
+        }
+        double nv = 0.0;
+        for (int i = 0; i < r; ++i) nv += v[i] * v[i];
+        nv = std::sqrt(nv);
+        if (nv > 0.5) {
+          for (int i = 0; i < r; ++i) A[(size_t)i * r + jj] = v[i] / nv;
+          break;
+        }
+      }
+    }
+  }
+  C = Cs;
+}
+
 }  // namespace
 
-// Returns SFR status; fills res (S, L; factors are not returned for FR-Nys).
+// Returns SFR status; fills res (iterations, residual, lambda_min_B) and writes S, L and the
+// factors U, B, V where the device pointers are non-null.
 sfr_status nys_solve_device(Solver& sv, const sfr_problem& p, const void* Mdev, const int64_t* perm_dev,
-                            sfr_result* res, void* Sdev, void* Ldev, std::string* err) {
+                            sfr_result* res, void* Sdev, void* Ldev, double* Udev, double* Bdev, double* Vdev,
+                            std::string* err) {
   cudaStream_t st = solver_stream(sv);
   const int64_t m = p.m, n = p.n, l = p.nys_l;
   const int r = p.r;
@@ -234,7 +328,7 @@ sfr_status nys_solve_device(Solver& sv, const sfr_problem& p, const void* Mdev, 
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t bL = al(es * m * l), bT = al(es * l * n);
   const size_t bUL = al(8 * m * r), bVL = al(8 * l * r), bUT = al(8 * l * r), bVT = al(8 * n * r), bB = al(8 * r * r);
-  const size_t total = bL + bT + bUL + bVL + bUT + bVT + 2 * bB + al(8 * r * r) + al(8 * m * r) + 512;
+  const size_t total = bL + bT + bUL + bVL + bUT + bVT + 2 * bB + 3 * al(8 * r * r) + al(8 * m * r) + 512;
   char* base = static_cast<char*>(solver_nys_block(sv, total));
   char* q = base;
   void* Mleft = q; q += bL;
@@ -246,6 +340,8 @@ sfr_status nys_solve_device(Solver& sv, const sfr_problem& p, const void* Mdev, 
   double* BL = reinterpret_cast<double*>(q); q += bB;
   double* BT = reinterpret_cast<double*>(q); q += bB;
   double* core = reinterpret_cast<double*>(q); q += al(8 * r * r);
+  double* Asvd = reinterpret_cast<double*>(q); q += al(8 * r * r);   // left singular vectors of the core
+  double* Csvd = reinterpret_cast<double*>(q); q += al(8 * r * r);   // right singular vectors
   double* Uo = reinterpret_cast<double*>(q); q += al(8 * m * r);
   int* flag = reinterpret_cast<int*>(q);
 
@@ -271,12 +367,56 @@ sfr_status nys_solve_device(Solver& sv, const sfr_problem& p, const void* Mdev, 
   pl.nys_perm = nullptr;
   pl.mem = SFR_MEM_DEVICE;
   pl.m = m; pl.n = l; pl.ldm = l; pl.M = Mleft;
-  DevState a = solver_run(sv, pl, Mleft, UL, BL, VL, nullptr, SFR_F64, 0, nullptr);
-  res->path |= solver_last_tc(sv) ? SFR_PATH_TC : 0;
   sfr_problem pt = pl;
   pt.m = l; pt.n = n; pt.ldm = n; pt.M = Mtop;
-  DevState b = solver_run(sv, pt, Mtop, UT, BT, VT, nullptr, SFR_F64, 0, nullptr);
+  // The two block solves (Algorithm 2) are independent: the top block runs on the auxiliary
+  // solver in a second host thread while this one solves the left block, when the budget holds
+  // both workspaces (their memory is reserved here, before either starts); else one after the
+  // other.
+  Solver* aux = solver_aux(sv);
+  bool concurrent = solver_reserve(sv, pl, Mleft, solver_held(sv), solver_budget(sv)) &&
+                    solver_reserve(*aux, pt, Mtop, solver_held(sv), solver_budget(sv));
+  cudaEvent_t gathered = nullptr;
+  if (concurrent) {
+    e = cudaEventCreateWithFlags(&gathered, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(gathered, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(solver_stream(*aux), gathered, 0);
+    if (gathered) cudaEventDestroy(gathered);
+    if (e != cudaSuccess) { *err = cudaGetErrorString(e); return SFR_E_CUDA; }
+  }
+  DevState a{}, b{};
+  bool top_tc = false, top_failed = false;
+  std::string top_err;
+  std::thread top;
+  if (concurrent) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    top = std::thread([&, dev] {
+      cudaSetDevice(dev);
+      try {
+        b = solver_run(*aux, pt, Mtop, UT, BT, VT, nullptr, SFR_F64, 0, nullptr);
+        top_tc = solver_last_tc(*aux);
+      } catch (...) {
+        top_failed = true;
+        top_err = "FR-Nys: the top block solve failed";
+      }
+    });
+  }
+  try {
+    a = solver_run(sv, pl, Mleft, UL, BL, VL, nullptr, SFR_F64, 0, nullptr);
+  } catch (...) {
+    if (top.joinable()) top.join();
+    throw;
+  }
   res->path |= solver_last_tc(sv) ? SFR_PATH_TC : 0;
+  if (concurrent) {
+    top.join();
+    if (top_failed) { *err = top_err; return SFR_E_CUDA; }
+  } else {
+    b = solver_run(sv, pt, Mtop, UT, BT, VT, nullptr, SFR_F64, 0, nullptr);
+    top_tc = solver_last_tc(sv);
+  }
+  res->path |= top_tc ? SFR_PATH_TC : 0;
   res->iters = a.iter + b.iter;
   res->rel_residual = std::max(a.res, b.res);
   res->lambda_min_B = NAN;
@@ -295,6 +435,29 @@ sfr_status nys_solve_device(Solver& sv, const sfr_problem& p, const void* Mdev, 
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { *err = cudaGetErrorString(e); return SFR_E_CUDA; }
   if (hflag) { *err = "FR-Nys: singular l x l block"; return SFR_E_RANK; }
+  {
+    // polar factors of L = U_L Core V_T^T from the SVD of the r x r core (host)
+    std::vector<double> hk((size_t)r * r), A, sig, C;
+    e = cudaMemcpy(hk.data(), core, 8 * hk.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { *err = cudaGetErrorString(e); return SFR_E_CUDA; }
+    core_svd(hk, r, A, sig, C);
+    res->lambda_min_B = sig[r - 1];
+    if (Udev || Vdev) {
+      e = cudaMemcpyAsync(Asvd, A.data(), 8 * A.size(), cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(Csvd, C.data(), 8 * C.size(), cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess && Udev) e = launch_pdl(nys_rows_kernel, cdiv(m * r, 256), 256, 0, st, UL, Asvd, perm_dev, m, r, Udev);
+      if (e == cudaSuccess && Vdev)
+        e = launch_pdl(nys_rows_kernel, cdiv(n * r, 256), 256, 0, st, VT, Csvd, (const int64_t*)nullptr, n, r, Vdev);
+      if (e != cudaSuccess) { *err = cudaGetErrorString(e); return SFR_E_CUDA; }
+    }
+    if (Bdev) {
+      std::vector<double> hb((size_t)r * r, 0.0);
+      for (int i = 0; i < r; ++i) hb[(size_t)i * r + i] = sig[i];
+      e = cudaMemcpyAsync(Bdev, hb.data(), 8 * hb.size(), cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // hb is a stack buffer
+      if (e != cudaSuccess) { *err = cudaGetErrorString(e); return SFR_E_CUDA; }
+    }
+  }
   if (Sdev || Ldev) {
     const int64_t nblk = (int64_t)cdiv(n, 32) * cdiv(m, 8);
     if (nblk > 0x7fffffffLL) { *err = "FR-Nys output: m x n too large for one launch"; return SFR_E_INVAL; }

@@ -274,6 +274,7 @@ struct Solver {
   int device = 0;
   int num_sms = 152;
   cudaStream_t stream = nullptr;
+  bool own_stream = false;  // the auxiliary solver's stream is created and destroyed by it
   size_t budget = 0;
   size_t held = 0;
   DeviceBlock work;
@@ -301,12 +302,15 @@ struct Solver {
   cudaEvent_t ev[5][4][2] = {};       // slot 0: eager iteration; 1-2: graph A; 3-4: graph B
   cudaEvent_t done_ev[2] = {};        // completion of the last launch of graph A / B
   DevState* host_state2 = nullptr;    // pinned state copies taken after graph A / B
+  std::unique_ptr<Solver> aux;        // FR-Nys: solves the second block concurrently (own stream)
 
   ~Solver() {
+    if (aux) aux.reset();
     if (graph) cudaGraphExecDestroy(graph);
     if (graph_b) cudaGraphExecDestroy(graph_b);
     if (host_state) cudaFreeHost(host_state);
     if (host_state2) cudaFreeHost(host_state2);
+    if (own_stream && stream) cudaStreamDestroy(stream);
     for (auto& e : done_ev)
       if (e) cudaEventDestroy(e);
     for (auto& a : ev)
@@ -822,28 +826,69 @@ void* solver_nys_block(Solver& sv, size_t bytes) {
 cudaStream_t solver_stream(Solver& sv) { return sv.stream; }
 bool solver_last_tc(const Solver& sv) { return sv.last_tc; }
 
+// The auxiliary solver of sv (created on first use): its own stream, workspace and graph cache.
+Solver* solver_aux(Solver& sv) {
+  if (!sv.aux) {
+    auto a = std::make_unique<Solver>();
+    a->device = sv.device;
+    a->num_sms = sv.num_sms;
+    SFR_CUDA(cudaStreamCreateWithFlags(&a->stream, cudaStreamNonBlocking));
+    a->own_stream = true;
+    SFR_CUDA(cudaMallocHost(&a->host_state, sizeof(DevState)));
+    sv.aux = std::move(a);
+  }
+  return sv.aux.get();
+}
+
+// Reserves, from the calling thread, the workspace that `sv.run` will need for problem p on the
+// device matrix at Mdev, counted against the holder's budget (`held` / `budget`).  False when the
+// budget or the device refuses it.
+bool solver_reserve(Solver& sv, const sfr_problem& p, const void* Mdev, size_t* held, size_t budget) {
+  const bool fp64 = p.precision == SFR_PREC_FP64;
+  Shape s = plan_shape(p.m, p.n, p.ldm, p.r, sv.num_sms);
+  const bool tc = !fp64 && tc_supported(s, p.m_dtype, p.ldm) && ((uintptr_t)Mdev % 16) == 0;
+  if (tc) tc_plan(&s, sv.num_sms);
+  try {
+    sv.work.ensure(carve(s, fp64, nullptr, nullptr, tc), held, budget);
+  } catch (const Fail&) {
+    return false;
+  }
+  return true;
+}
+size_t* solver_held(Solver& sv) { return &sv.held; }
+size_t solver_budget(const Solver& sv) { return sv.budget; }
+
 sfr_status nys_solve_device(Solver& sv, const sfr_problem& p, const void* Mdev, const int64_t* perm_dev,
-                            sfr_result* res, void* Sdev, void* Ldev, std::string* err);
+                            sfr_result* res, void* Sdev, void* Ldev, double* Udev, double* Bdev, double* Vdev,
+                            std::string* err);
 
 // FR-Nys entry: stage host buffers when needed, then run on the device.
 sfr_status sfr_nys_solve(Solver& sv, const sfr_problem& p, sfr_result* res, std::string* err) {
   const size_t mbytes = dtype_size(p.m_dtype) * (size_t)((p.m - 1) * p.ldm + p.n);
   const size_t outbytes = dtype_size(res->s_dtype) * (size_t)((p.m - 1) * res->lds + p.n);
   if (p.mem == SFR_MEM_DEVICE)
-    return nys_solve_device(sv, p, p.M, p.nys_perm, res, res->S, res->L, err);
+    return nys_solve_device(sv, p, p.M, p.nys_perm, res, res->S, res->L, res->U, res->B, res->V, err);
   size_t need = 0;
   auto add = [&](size_t bytes) { need = (need + 255) & ~size_t(255); size_t o = need; need += bytes; return o; };
   const size_t offM = add(mbytes), offP = add(8 * (size_t)p.m);
   const size_t offS = res->S ? add(outbytes) : 0, offL = res->L ? add(outbytes) : 0;
+  const size_t ub = 8 * (size_t)p.m * p.r, vb = 8 * (size_t)p.n * p.r, bb = 8 * (size_t)p.r * p.r;
+  const size_t offU = res->U ? add(ub) : 0, offV = res->V ? add(vb) : 0, offB = res->B ? add(bb) : 0;
   sv.staging.ensure(need + 256, &sv.held, sv.budget);
   char* st = static_cast<char*>(sv.staging.ptr);
   SFR_CUDA(cudaMemcpyAsync(st + offM, p.M, mbytes, cudaMemcpyHostToDevice, sv.stream));
   SFR_CUDA(cudaMemcpyAsync(st + offP, p.nys_perm, 8 * (size_t)p.m, cudaMemcpyHostToDevice, sv.stream));
   sfr_status s = nys_solve_device(sv, p, st + offM, reinterpret_cast<const int64_t*>(st + offP), res,
-                                  res->S ? st + offS : nullptr, res->L ? st + offL : nullptr, err);
+                                  res->S ? st + offS : nullptr, res->L ? st + offL : nullptr,
+                                  res->U ? reinterpret_cast<double*>(st + offU) : nullptr,
+                                  res->B ? reinterpret_cast<double*>(st + offB) : nullptr,
+                                  res->V ? reinterpret_cast<double*>(st + offV) : nullptr, err);
   if (s == SFR_OK) {
     if (res->S) SFR_CUDA(cudaMemcpyAsync(res->S, st + offS, outbytes, cudaMemcpyDeviceToHost, sv.stream));
     if (res->L) SFR_CUDA(cudaMemcpyAsync(res->L, st + offL, outbytes, cudaMemcpyDeviceToHost, sv.stream));
+    if (res->U) SFR_CUDA(cudaMemcpyAsync(res->U, st + offU, ub, cudaMemcpyDeviceToHost, sv.stream));
+    if (res->V) SFR_CUDA(cudaMemcpyAsync(res->V, st + offV, vb, cudaMemcpyDeviceToHost, sv.stream));
+    if (res->B) SFR_CUDA(cudaMemcpyAsync(res->B, st + offB, bb, cudaMemcpyDeviceToHost, sv.stream));
     SFR_CUDA(cudaStreamSynchronize(sv.stream));
   }
   return s;
@@ -1100,8 +1145,8 @@ static size_t request_bytes(const sfr_problem& p, int num_sms) {
     if (tc) tc_plan(&s, num_sms);
     return carve(s, fp64, nullptr, nullptr, tc);
   };
-  if (p.nys_l) {
-    total = std::max(one(p.m, p.nys_l), one(p.nys_l, p.n));
+  if (p.nys_l) {  // the two block solves run concurrently
+    total = one(p.m, p.nys_l) + one(p.nys_l, p.n);
     total += dtype_size(p.m_dtype) * (size_t)(p.m * p.nys_l + p.nys_l * p.n) + 8 * (size_t)(2 * p.m + 2 * p.nys_l + p.n) * p.r;
   } else {
     total = one(p.m, p.n);
@@ -1181,6 +1226,10 @@ static void worker_main(sfr_ctx* ctx, int slot) {
       sv.work.release(&sv.held);
       sv.staging.release(&sv.held);
       sv.nys.release(&sv.held);
+      if (sv.aux) {
+        sv.aux->graph_key.clear();
+        sv.aux->work.release(&sv.held);  // reserved against this slot's count
+      }
     }
     {
       std::lock_guard<std::mutex> lk(ctx->mu);

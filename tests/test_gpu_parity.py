@@ -197,6 +197,15 @@ def test_frnys_matches_oracle(ctx):
     assert sol.iters == ref.left.iters + ref.top.iters
     assert _rel(sol.L.cpu().numpy(), ref.L) <= FP64_TOL
     assert _rel(sol.S.cpu().numpy(), ref.S) <= 1e-6
+    # the factors: L = U B V^T with U, V orthonormal and B = diag(sigma), sigma decreasing
+    U, Bm, V = (x.cpu().numpy() for x in (sol.U, sol.B, sol.V))
+    assert _rel(U @ Bm @ V.T, ref.L) <= FP64_TOL
+    np.testing.assert_allclose(U.T @ U, np.eye(r), atol=1e-12)
+    np.testing.assert_allclose(V.T @ V, np.eye(r), atol=1e-12)
+    sig = np.diag(Bm)
+    assert np.count_nonzero(Bm - np.diag(sig)) == 0 and np.all(np.diff(sig) <= 0) and sig[-1] > 0
+    assert sol.lambda_min_B == pytest.approx(sig[-1])
+    np.testing.assert_allclose(sig, np.linalg.svd(ref.L, compute_uv=False)[:r], rtol=1e-9)
 
 
 def test_submit_poll_equals_solve(ctx):
