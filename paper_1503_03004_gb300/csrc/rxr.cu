@@ -523,11 +523,12 @@ __device__ __forceinline__ int exponent_of(long long bits) { return bits ? (int)
 // float64: G, B, T_hat, W, R, B_bar, T_C.  float32: K, the eigenbasis, eigenvalue estimates, Z0
 // and the Newton corrections, which only steer the iteration.  Outputs are written by rows, each
 // CTA of the cluster its own slice.
-__global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict__ Gg, int rp, int r,
-                                                       double* __restrict__ Bg, double* __restrict__ Tout,
-                                                       double* __restrict__ TCout, float* __restrict__ Qeig,
-                                                       int v_side, int mixed, DevState* st) {
+__device__ __forceinline__ void rxr_body(const VGrid& vg__, const double* __restrict__ Gg, int rp, int r,
+                                         double* __restrict__ Bg, double* __restrict__ Tout,
+                                         double* __restrict__ TCout, float* __restrict__ Qeig, int v_side, int mixed,
+                                         DevState* st) {
   pdl_enter();
+  SFR_VGRID(vg__);
   if (stopped(st)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RxrSmem& S = *reinterpret_cast<RxrSmem*>(smem_raw);
@@ -829,13 +830,16 @@ __global__ void __launch_bounds__(kThreads) rxr_kernel(const double* __restrict_
 }  // namespace
 
 // Cluster size for the r x r kernel: 16 CTAs (non-portable size) when the device accepts it
-// with this kernel's shared memory, else 8, else a single CTA.
+// with this kernel's shared memory, else 8, else a single CTA.  The result does not depend on
+// it (every float64 product element is one thread's loop; the float32 work is redundant).
 static int rxr_cluster_size(size_t smem) {
   static int cached = 0;
   if (cached) return cached;
+  auto kern = body_kernel_of<&rxr_body, kThreads>();
   int best = 1;
-  if (cudaFuncSetAttribute(rxr_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
     cudaGetLastError();
+  if (set_smem_attr(reinterpret_cast<const void*>(kern), smem) != cudaSuccess) cudaGetLastError();
   for (int cs : {16, 8}) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs);
@@ -849,7 +853,7 @@ static int rxr_cluster_size(size_t smem) {
     cfg.attrs = &at;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, rxr_kernel, &cfg) == cudaSuccess && nclusters > 0) {
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters > 0) {
       best = cs;
       break;
     }
@@ -865,26 +869,10 @@ cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream
   cudaError_t e = launch_reduce_parts(parts, count, s.rp * s.rp, b.Gsum, b.st, st);
   if (e != cudaSuccess) return e;
   const size_t smem = sizeof(RxrSmem);
-  e = cudaFuncSetAttribute(rxr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   const int cs = rxr_cluster_size(smem);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cs);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute at[2];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = cs;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // see pdl_enter
-  at[1].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 2;
-  return cudaLaunchKernelEx(&cfg, rxr_kernel, (const double*)b.Gsum, s.rp, s.r, b.B, v_side ? b.TV : b.TU,
-                            v_side ? b.TCm : (double*)nullptr, v_side ? b.Qeig_v : b.Qeig_u, v_side ? 1 : 0,
-                            fp64 ? 0 : 1, b.st);
+  return launch_k_cluster<&rxr_body, kThreads>(cs, kThreads, smem, st, (const double*)b.Gsum, s.rp, s.r, b.B,
+                                              v_side ? b.TV : b.TU, v_side ? b.TCm : (double*)nullptr,
+                                              v_side ? b.Qeig_v : b.Qeig_u, v_side ? 1 : 0, fp64 ? 0 : 1, b.st);
 }
 
 }  // namespace sfr

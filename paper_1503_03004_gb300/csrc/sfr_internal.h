@@ -45,6 +45,12 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
   return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
+}  // namespace sfr
+
+#include "launch.cuh"
+
+namespace sfr {
+
 // Per-problem scalars, device resident, read and written by the iteration kernels.
 struct DevState {
   double mu;          // mu_k: penalty of the iteration about to run (Algorithm 1)

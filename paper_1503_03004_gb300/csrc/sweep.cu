@@ -230,11 +230,12 @@ __device__ __forceinline__ void store_tile(TC* s, int t, const TC (&v)[TileIdx<R
 // come from the persistent tensor-core sweep (q_tiles column tiles per 128-row block), and rows of
 // block rb have tc_q_slots(rb) of them.
 template <typename TC, int RP>
-__global__ void __launch_bounds__(256) thin_gram_kernel(const TC* __restrict__ parts, int nparts, int64_t part_stride,
+__device__ __forceinline__ void thin_gram_body(const VGrid& vg__, const TC* __restrict__ parts, int nparts, int64_t part_stride,
                                                         TC* __restrict__ out, int64_t rows, const TC* __restrict__ addA,
                                                         const double* __restrict__ H, double* __restrict__ gpart,
                                                         const DevState* st, int q_ctas, int64_t q_tiles) {
   pdl_enter();
+  SFR_VGRID(vg__);
   if (stopped(st)) return;
   constexpr int LDT = RP + 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -303,9 +304,10 @@ __global__ void __launch_bounds__(256) thin_gram_kernel(const TC* __restrict__ p
 // then the warp sums are added in warp order.  out may be the first partial (each entry is read
 // and written by one CTA).  nw = blockDim.x / 32 <= 32.
 template <typename T>
-__global__ void __launch_bounds__(1024) reduce_sq_kernel(const T* parts, int64_t count, int64_t rpsq, T* out,
+__device__ __forceinline__ void reduce_sq_body(const VGrid& vg__, const T* parts, int64_t count, int64_t rpsq, T* out,
                                                          const DevState* st) {
   pdl_enter();
+  SFR_VGRID(vg__);
   if (stopped(st)) return;
   __shared__ T red[32][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -343,15 +345,16 @@ __device__ __forceinline__ float to_tf32(float x) {
 // dst2 = src T2, and optional partial hpart[cta] = sum over the CTA's rows of old[i]^T dst[i].
 // Each CTA handles 64-row tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 template <typename TC, int RP>
-__global__ void __launch_bounds__(256) row_transform_kernel(const TC* __restrict__ src, int64_t rows,
+__device__ __forceinline__ void row_transform_body(const VGrid& vg__, const TC* __restrict__ src, int64_t rows,
                                                             const double* __restrict__ T, TC* __restrict__ dst,
                                                             const double* __restrict__ T2, TC* __restrict__ dst2,
                                                             const TC* __restrict__ old, double* __restrict__ hpart,
-                                                            const DevState* st, float* __restrict__ sp_hi = nullptr,
-                                                            float* __restrict__ sp_lo = nullptr,
-                                                            __nv_bfloat16* __restrict__ trans = nullptr,
-                                                            int64_t ldt = 0, int trans_lo = 0) {
+                                                            const DevState* st, float* __restrict__ sp_hi,
+                                                            float* __restrict__ sp_lo,
+                                                            __nv_bfloat16* __restrict__ trans,
+                                                            int64_t ldt, int trans_lo) {
   pdl_enter();
+  SFR_VGRID(vg__);
   // Tensor-core path extras (float, RP = 64): sp_hi / sp_lo = TF32 split (hi = x rounded to TF32,
   // lo = x - hi) of dst2 (or of dst without T2), trans = dst transposed in bfloat16 (ld ldt);
   // trans_lo != 0: also the bfloat16 rounding of x - hi into row RP + a (a two-term split).
@@ -721,13 +724,14 @@ __device__ __forceinline__ void st4(float* __restrict__ p, int lim, const float 
 // X V for rows 2 qr, 2 qr + 1 and ranks qa r/8 .. into registers; the Q partial of a row block is
 // stored once.  One residual partial per CTA (slot blockIdx.y * gridDim.x + blockIdx.x).
 template <typename TMs, int RP, bool VEC>
-__global__ void __launch_bounds__(256) sweep_mx_kernel(const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm,
+__device__ __forceinline__ void sweep_mx_body(const VGrid& vg__, const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm,
                                                        const float* __restrict__ Yin, float* __restrict__ Yout,
                                                        float* __restrict__ D, const float* __restrict__ U,
                                                        const float* __restrict__ C, const float* __restrict__ V,
                                                        float* __restrict__ Qpart, int cols_per_split,
                                                        double* __restrict__ resid_part, const DevState* st) {
   pdl_enter();
+  SFR_VGRID(vg__);
   if (stopped(st)) return;
   constexpr int BM = kMxBM, BN = kMxBN, QA = RP / 8;
   __shared__ __align__(16) float UsT[RP][BM];
@@ -895,13 +899,14 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 // computed, so HBM latency is hidden without holding the tiles in registers.  Needs the vector
 // conditions (n % 4 == 0, 16-byte aligned rows of M) and float32 or bfloat16 M.
 template <typename TMs, int RP>
-__global__ void __launch_bounds__(256) sweep_mxp_kernel(const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm,
+__device__ __forceinline__ void sweep_mxp_body(const VGrid& vg__, const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm,
                                                         const float* __restrict__ Yin, float* __restrict__ Yout,
                                                         float* __restrict__ D, const float* __restrict__ U,
                                                         const float* __restrict__ C, const float* __restrict__ V,
                                                         float* __restrict__ Qpart, int cols_per_split,
                                                         double* __restrict__ resid_part, int r, const DevState* st) {
   pdl_enter();
+  SFR_VGRID(vg__);
   if (stopped(st)) return;
   constexpr int BM = kMxBM, BN = kMxBN, QA = RP / 8, EPC = 16 / (int)sizeof(TMs);  // M elements per 16 B
   constexpr int LDU = RP + 4;  // padded U rows: the four rows a warp reads fall in different banks
@@ -1105,10 +1110,11 @@ constexpr size_t mxp_smem() {
 // vector loads); thread (wc, wa) = (t / 8, t % 8) accumulates columns 2 wc, 2 wc + 1 and ranks
 // wa r/8 .. in registers.
 template <typename TS, int RP, bool VEC>
-__global__ void __launch_bounds__(256) wpass_mx_kernel(const TS* __restrict__ src, int64_t lds, int64_t m, int64_t n,
+__device__ __forceinline__ void wpass_mx_body(const VGrid& vg__, const TS* __restrict__ src, int64_t lds, int64_t m, int64_t n,
                                                        int rows_per_chunk, const float* __restrict__ U,
                                                        float* __restrict__ Wpart, const DevState* st) {
   pdl_enter();
+  SFR_VGRID(vg__);
   if (stopped(st)) return;
   constexpr int BR = 32, BN = kMxBN, QA = RP / 8;
   __shared__ __align__(16) float Xs[BR][kMxLDX];
@@ -1187,10 +1193,11 @@ __global__ void __launch_bounds__(256) wpass_mx_kernel(const TS* __restrict__ sr
 // aligned, n % 4 == 0) and float32 or bfloat16 src.
 constexpr int kWxStages = 4;
 template <typename TS, int RP>
-__global__ void __launch_bounds__(256) wpass_mxp_kernel(const TS* __restrict__ src, int64_t lds, int64_t m, int64_t n,
+__device__ __forceinline__ void wpass_mxp_body(const VGrid& vg__, const TS* __restrict__ src, int64_t lds, int64_t m, int64_t n,
                                                         int rows_per_chunk, const float* __restrict__ U,
                                                         float* __restrict__ Wpart, const DevState* st) {
   pdl_enter();
+  SFR_VGRID(vg__);
   if (stopped(st)) return;
   constexpr int BR = 32, BN = kMxBN, QA = RP / 8, EPC = 16 / (int)sizeof(TS);
   constexpr int XS = BR * BN, US = BR * RP;  // elements per stage
@@ -1277,8 +1284,9 @@ constexpr size_t wxp_smem() { return (size_t)kWxStages * 32 * (kMxBN * sizeof(TS
 
 // ---------------------------------------------------------------- end of iteration (one CTA)
 // ||M - L - S||_F = ||Y_{k+1} - Y_k||_F / mu_k; continuation mu_{k+1} = min(mu_bar, rho mu_k).
-__global__ void iter_end_kernel(const double* __restrict__ resid_part, int count, DevState* st) {
+__device__ __forceinline__ void iter_end_body(const VGrid& vg__, const double* __restrict__ resid_part, int count, DevState* st) {
   pdl_enter();
+  SFR_VGRID(vg__);
   __shared__ double red[32];
   if (stopped(st)) return;
   double v = 0.0;
@@ -1473,7 +1481,8 @@ inline int reduce_threads(int64_t count) { return count >= 256 ? 1024 : 256; }
 
 cudaError_t launch_reduce_parts(const double* parts, int count, int rpsq, double* out, const DevState* dst,
                                 cudaStream_t st) {
-  launch_pdl(reduce_sq_kernel<double>, cdiv(rpsq, 32), reduce_threads(count), 0, st, parts, count, rpsq, out, dst);
+  launch_k<&reduce_sq_body<double>, 1024>(cdiv(rpsq, 32), reduce_threads(count), 0, st, parts, (int64_t)count,
+                                           (int64_t)rpsq, out, dst);
   return cudaGetLastError();
 }
 
@@ -1507,9 +1516,7 @@ cudaError_t launch_gram_p(const Shape& s, const Buffers& b, bool fp64, bool sum_
     return by_rank(s.rp, [&](auto rpc) {
       constexpr int RP = decltype(rpc)::value;
       const size_t sm = gram_smem<TC, RP>();
-      cudaError_t e = allow_smem(thin_gram_kernel<TC, RP>, sm);
-      if (e != cudaSuccess) return e;
-      launch_pdl(thin_gram_kernel<TC, RP>, s.gp_blocks, 256, sm, st,
+      launch_k<&thin_gram_body<TC, RP>, 256>(s.gp_blocks, 256, sm, st,
           static_cast<const TC*>(b.Qpart), sum_parts ? s.nsplit : 0, s.m * RP, static_cast<TC*>(b.P), s.m,
           static_cast<const TC*>(addA), H, b.GPpart, b.st, s.q_ctas, (s.n + 63) / 64);
       return cudaGetLastError();
@@ -1525,16 +1532,14 @@ cudaError_t launch_apply_u(const Shape& s, const Buffers& b, bool fp64, bool fir
     return by_rank(s.rp, [&](auto rpc) {
       constexpr int RP = decltype(rpc)::value;
       const size_t sm = transform_smem<TC, RP>();
-      cudaError_t e = allow_smem(row_transform_kernel<TC, RP>, sm);
-      if (e != cudaSuccess) return e;
       // tensor-core path: also the TF32 split of U_new and its bfloat16 transpose (MMA operands)
       // (Algorithm 4: the two-term bfloat16 split of U^T instead, the B operand of M^T U)
       const bool tcx = b.tc && RP == 64 && !fp64, tf = tcx && !b.full;
-      launch_pdl(row_transform_kernel<TC, RP>, s.gp_blocks, 256, sm, st,
+      launch_k<&row_transform_body<TC, RP>, 256>(s.gp_blocks, 256, sm, st,
           static_cast<const TC*>(b.P), s.m, b.TU, static_cast<TC*>(b.U[u_new]), nullptr, nullptr,
           first ? nullptr : static_cast<const TC*>(b.U[u_old]), first ? nullptr : b.Hpart, b.st,
           tf ? b.t.Uh : nullptr, tf ? b.t.Ul : nullptr, tcx ? static_cast<__nv_bfloat16*>(b.t.Ut) : nullptr,
-          b.t.ldd, b.full ? 1 : 0);
+          (int64_t)b.t.ldd, b.full ? 1 : 0);
       return cudaGetLastError();
     });
   });
@@ -1551,18 +1556,15 @@ cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first
       } else {
         const float* U = static_cast<const float*>(b.U[u_new]);
         float* Wp = static_cast<float*>(b.Wpart);
-        auto go = [&](auto kern, auto src, int64_t lds) {
-          launch_pdl(kern, grid, 256, 0, st, src, lds, s.m, s.n, s.rows_per_chunk, U, Wp, b.st);
-          return cudaGetLastError();
+        auto go = [&](auto tag, auto src, int64_t lds) {
+          return launch_k<decltype(tag)::value, 256>(grid, 256, 0, st, src, lds, s.m, s.n, s.rows_per_chunk, U, Wp,
+                                                      b.st);
         };
         auto pipelined = [&](auto srcp, int64_t lds) {
           using TS = std::remove_const_t<std::remove_pointer_t<decltype(srcp)>>;
-          auto kern = wpass_mxp_kernel<TS, RP>;
           constexpr size_t sm = wxp_smem<TS, RP>();
-          cudaError_t e = allow_smem(kern, sm);
-          if (e != cudaSuccess) return e;
-          launch_pdl(kern, grid, 256, sm, st, srcp, lds, s.m, s.n, s.rows_per_chunk, U, Wp, b.st);
-          return cudaGetLastError();
+          return launch_k<&wpass_mxp_body<TS, RP>, 256>(grid, 256, sm, st, srcp, lds, s.m, s.n, s.rows_per_chunk, U,
+                                                         Wp, b.st);
         };
         if (first)
           return by_mtype(b.m_dtype, b.M, [&](auto M) {
@@ -1570,10 +1572,11 @@ cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first
             if constexpr (!std::is_same<TMs, double>::value) {
               if (vec) return pipelined(M, s.ldm);
             }
-            return vec ? go(wpass_mx_kernel<TMs, RP, true>, M, s.ldm) : go(wpass_mx_kernel<TMs, RP, false>, M, s.ldm);
+            return vec ? go(BodyTag<&wpass_mx_body<TMs, RP, true>>{}, M, s.ldm)
+                       : go(BodyTag<&wpass_mx_body<TMs, RP, false>>{}, M, s.ldm);
           });
         const float* Dp = static_cast<const float*>(b.D);
-        return vec ? pipelined(Dp, s.n) : go(wpass_mx_kernel<float, RP, false>, Dp, s.n);
+        return vec ? pipelined(Dp, s.n) : go(BodyTag<&wpass_mx_body<float, RP, false>>{}, Dp, s.n);
       }
     });
   }
@@ -1601,7 +1604,7 @@ cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool firs
   // W = sum_c Wpart[c] (+ C_old H, H = U_old^T U_new), then Gram partials of W.
   // H = sum of the U_old^T U_new partials, reduced into the slot after the partials.
   if (!first) {
-    launch_pdl(reduce_sq_kernel<double>, cdiv(s.rp * s.rp, 32), reduce_threads(s.gp_blocks), 0, st,
+    launch_k<&reduce_sq_body<double>, 1024>(cdiv(s.rp * s.rp, 32), reduce_threads(s.gp_blocks), 0, st,
         b.Hpart, s.gp_blocks, s.rp * s.rp, b.Hpart + (size_t)s.gp_blocks * s.rp * s.rp, b.st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1612,20 +1615,19 @@ cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool firs
     return by_rank(s.rp, [&](auto rpc) {
       constexpr int RP = decltype(rpc)::value;
       const size_t sm = gram_smem<TC, RP>();
-      cudaError_t e = allow_smem(thin_gram_kernel<TC, RP>, sm);
-      if (e != cudaSuccess) return e;
+      cudaError_t e;
       // many row chunks over few columns (tall M): sum the chunks' partials into the first one
       // with a wide reduction first, so the thin kernel does not add hundreds of them per element
       int nparts = s.nchunk;
       if (nparts >= 32) {
         const int64_t len = s.n * RP;
-        launch_pdl(reduce_sq_kernel<TC>, cdiv(len, 32), reduce_threads(nparts), 0, st, static_cast<const TC*>(b.Wpart),
-                                                                                nparts, len, static_cast<TC*>(b.Wpart),
-                                                                                b.st);
+        launch_k<&reduce_sq_body<TC>, 1024>(cdiv(len, 32), reduce_threads(nparts), 0, st,
+                                            static_cast<const TC*>(b.Wpart), (int64_t)nparts, len,
+                                            static_cast<TC*>(b.Wpart), b.st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         nparts = 1;
       }
-      launch_pdl(thin_gram_kernel<TC, RP>, s.gw_blocks, 256, sm, st,
+      launch_k<&thin_gram_body<TC, RP>, 256>(s.gw_blocks, 256, sm, st,
           static_cast<const TC*>(b.Wpart), nparts, s.n * RP, static_cast<TC*>(b.W), s.n,
           first ? nullptr : static_cast<const TC*>(b.C), first ? nullptr : H, b.GWpart, b.st, 0, (int64_t)0);
       return cudaGetLastError();
@@ -1639,15 +1641,13 @@ cudaError_t launch_apply_v(const Shape& s, const Buffers& b, bool fp64, cudaStre
     return by_rank(s.rp, [&](auto rpc) {
       constexpr int RP = decltype(rpc)::value;
       const size_t sm = transform_smem<TC, RP>();
-      cudaError_t e = allow_smem(row_transform_kernel<TC, RP>, sm);
-      if (e != cudaSuccess) return e;
       // tensor-core path: also the TF32 split of C and the bfloat16 transpose of V
       // (Algorithm 4: the two-term bfloat16 split of V^T instead, the B operand of M V)
       const bool tcx = b.tc && RP == 64 && !fp64, tf = tcx && !b.full;
-      launch_pdl(row_transform_kernel<TC, RP>, s.gw_blocks, 256, sm, st,
+      launch_k<&row_transform_body<TC, RP>, 256>(s.gw_blocks, 256, sm, st,
           static_cast<const TC*>(b.W), s.n, b.TV, static_cast<TC*>(b.V), b.TCm, static_cast<TC*>(b.C), nullptr, nullptr,
           b.st, tf ? b.t.Ch : nullptr, tf ? b.t.Cl : nullptr, tcx ? static_cast<__nv_bfloat16*>(b.t.Vt) : nullptr,
-          b.t.ldy, b.full ? 1 : 0);
+          (int64_t)b.t.ldy, b.full ? 1 : 0);
       return cudaGetLastError();
     });
   });
@@ -1663,29 +1663,25 @@ static cudaError_t launch_sweep_mx(const Shape& s, const Buffers& b, int u_cur, 
     } else {
       return by_mtype(b.m_dtype, b.M, [&](auto M) {
         using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
-        auto go = [&](auto kern) {
-          launch_pdl(kern, grid, 256, 0, st, M, s.m, s.n, s.ldm, static_cast<const float*>(b.Y[0]),
-                                     static_cast<float*>(b.Y[1]), static_cast<float*>(b.D),
-                                     static_cast<const float*>(b.U[u_cur]), static_cast<const float*>(b.C),
-                                     static_cast<const float*>(b.V), static_cast<float*>(b.Qpart), s.cols_per_split,
-                                     b.resid_part, b.st);
-          return cudaGetLastError();
+        auto go = [&](auto tag) {
+          return launch_k<decltype(tag)::value, 256>(grid, 256, 0, st, M, s.m, s.n, s.ldm,
+                                                      static_cast<const float*>(b.Y[0]), static_cast<float*>(b.Y[1]),
+                                                      static_cast<float*>(b.D), static_cast<const float*>(b.U[u_cur]),
+                                                      static_cast<const float*>(b.C), static_cast<const float*>(b.V),
+                                                      static_cast<float*>(b.Qpart), s.cols_per_split, b.resid_part,
+                                                      b.st);
         };
         if constexpr (!std::is_same<TMs, double>::value) {
           if (vec) {
-            auto kern = sweep_mxp_kernel<TMs, RP>;
             constexpr size_t sm = mxp_smem<TMs, RP>();
-            cudaError_t e = allow_smem(kern, sm);
-            if (e != cudaSuccess) return e;
-            launch_pdl(kern, grid, 256, sm, st, M, s.m, s.n, s.ldm, static_cast<const float*>(b.Y[0]),
-                                        static_cast<float*>(b.Y[1]), static_cast<float*>(b.D),
-                                        static_cast<const float*>(b.U[u_cur]), static_cast<const float*>(b.C),
-                                        static_cast<const float*>(b.V), static_cast<float*>(b.Qpart),
-                                        s.cols_per_split, b.resid_part, s.r, b.st);
-            return cudaGetLastError();
+            return launch_k<&sweep_mxp_body<TMs, RP>, 256>(
+                grid, 256, sm, st, M, s.m, s.n, s.ldm, static_cast<const float*>(b.Y[0]), static_cast<float*>(b.Y[1]),
+                static_cast<float*>(b.D), static_cast<const float*>(b.U[u_cur]), static_cast<const float*>(b.C),
+                static_cast<const float*>(b.V), static_cast<float*>(b.Qpart), s.cols_per_split, b.resid_part, s.r,
+                b.st);
           }
         }
-        return vec ? go(sweep_mx_kernel<TMs, RP, true>) : go(sweep_mx_kernel<TMs, RP, false>);
+        return vec ? go(BodyTag<&sweep_mx_body<TMs, RP, true>>{}) : go(BodyTag<&sweep_mx_body<TMs, RP, false>>{});
       });
     }
   });
@@ -1720,7 +1716,7 @@ cudaError_t launch_sweep(const Shape& s, const Buffers& b, bool fp64, int u_cur,
 cudaError_t launch_iter_end(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st) {
   // the mixed SIMT sweep writes one residual partial per CTA, the others one per 32-row block
   const int count = mx_path(s, fp64) ? s.mx_grid_x * s.nsplit : s.resid_parts;
-  launch_pdl(iter_end_kernel, 1, 1024, 0, st, b.resid_part, count, b.st);
+  launch_k<&iter_end_body, 1024>(1, 1024, 0, st, b.resid_part, count, b.st);
   return cudaGetLastError();
 }
 
