@@ -262,8 +262,10 @@ def _serving_oracle(args):
 def run_serving(args):
     """Serving-stream workload: `--requests` uneven planted requests (default 4096: m in [256, 8192],
     n in [16, 512], r in {3, 5, 10, 25}, outliers 2-15 % in [-50, 50], bf16 storage), three ways:
-      * serving: the mixed path through sfr_submit / sfr_poll with --slots slots, all requests
-        queued at once (throughput), then again with Poisson arrivals at 70 % of that rate
+      * serving: the mixed path through sfr_submit / sfr_poll, all requests queued at once
+        (throughput), first through --slots slots (one solve per stream), then through the
+        grouped engine (--max-batch problems iterated together, one grouped launch per kernel
+        and iteration step), then again with Poisson arrivals at 70 % of the grouped rate
         (latency p50 / p99 from arrival to completion);
       * per-problem float64: sfr_solve one request at a time on the float64 path;
       * per-problem mixed: sfr_solve one request at a time on the mixed path.
@@ -335,9 +337,9 @@ def run_serving(args):
             wall = time.perf_counter() - t0
         return counts.get("OK", 0) / wall, counts
 
-    def serving(rate):
-        with B.Context(0, max_slots=args.slots, hbm_budget_bytes=args.budget_gb << 30) as ctx:
-            for q, Md, out in items[:args.slots]:
+    def serving(rate, batch):
+        with B.Context(0, max_slots=args.slots, hbm_budget_bytes=args.budget_gb << 30, max_batch=batch) as ctx:
+            for q, Md, out in items[:max(args.slots, min(batch, 64))]:
                 p, res = mk(q, Md, out, B.PREC_MIXED)
                 ctx.poll(ctx.submit(p, res), -1)
             keep, pending, done, counts = [], {}, {}, {}
@@ -380,15 +382,22 @@ def run_serving(args):
             return (counts.get("OK", 0) / wall, lat[len(lat) // 2], lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                     counts)
 
-    thr, _, _, counts = serving(None)
-    err_serving = rel_errs(refs)  # results of the throughput run (mixed path, through the slots)
+    thr_slots, _, _, counts_slots = serving(None, 0)
+    err_slots = rel_errs(refs)  # results of the throughput run (mixed path, through the slots)
+    if args.max_batch > 0:
+        thr, _, _, counts = serving(None, args.max_batch)
+        err_serving = rel_errs(refs)  # the grouped engine's results
+    else:
+        thr, counts, err_serving = thr_slots, counts_slots, err_slots
     rate = 0.7 * thr
-    _, p50, p99, counts_lat = serving(rate)
+    _, p50, p99, counts_lat = serving(rate, args.max_batch)
     f64, counts_f64 = sequential(B.PREC_FP64)
     err_f64 = rel_errs(refs)
     mix, counts_mix = sequential(B.PREC_MIXED)
     line = {"metric": "serving solves/s", "requests": len(items), "slots": args.slots,
-            "value": thr, "unit": "solves/s", "status_counts": counts,
+            "max_batch": args.max_batch, "value": thr, "unit": "solves/s", "status_counts": counts,
+            "slots_only": {"value": thr_slots, "status_counts": counts_slots,
+                           "max_rel_err_L": max(err_slots)},
             "per_problem_fp64": f64, "per_problem_fp64_status_counts": counts_f64,
             "per_problem_mixed": mix, "per_problem_mixed_status_counts": counts_mix,
             "latency_ms_at_rate": {"rate_per_s": rate, "p50": p50, "p99": p99, "status_counts": counts_lat},
@@ -806,6 +815,8 @@ def main():
     ap.add_argument("--requests", type=int, default=4096)
     ap.add_argument("--check", type=int, default=8, help="serving: requests checked against the float64 oracle")
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--max-batch", type=int, default=256,
+                    help="serving: problems the grouped engine iterates together (0: slots only)")
     ap.add_argument("--budget-gb", type=int, default=64)
     ap.add_argument("--m", type=int, default=WORKLOAD["m"],
                     help="square size of the same recipe (smaller sizes are for profiler captures)")

@@ -83,6 +83,11 @@ typedef struct {
                                sfr_solve / sfr_fixed_rank_opt_full with CUDA events on the
                                solve stream (see sfr_stats); 2: time the sweep (or P pass) only
                                (fewer event records inside the iteration); 0: no timing    */
+  int max_batch;            /* > 0: sfr_submit runs requests on the mixed-precision SIMT path
+                               (FR-ADM, device buffers, r <= 32) in a grouped engine with up to
+                               this many live problems: every step advances each of them by one
+                               iteration with one grouped launch per kernel; results equal
+                               sfr_solve's.  Other requests go to the slots.  0: slots only  */
 } sfr_config;
 
 /* Kernel classes counted by sfr_stats. */

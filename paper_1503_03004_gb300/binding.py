@@ -30,7 +30,7 @@ DTYPE_CODES = {"f64": F64, "f32": F32, "bf16": BF16}
 
 class Config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p), ("profile", ctypes.c_int)]
+                ("cuda_stream", ctypes.c_void_p), ("profile", ctypes.c_int), ("max_batch", ctypes.c_int)]
 
 
 # sfr_stat_kind
@@ -118,12 +118,14 @@ class Context:
     """An sfr_ctx on one device (sfr_create / sfr_destroy)."""
 
     def __init__(self, device: int = 0, stream: int | None = None, hbm_budget_bytes: int = 0, max_slots: int = 0,
-                 profile: int = 0):
-        """profile: 0 none, 1 (or True) sweep, W pass and r x r kernels timed, 2 the sweep only."""
+                 profile: int = 0, max_batch: int = 0):
+        """profile: 0 none, 1 (or True) sweep, W pass and r x r kernels timed, 2 the sweep only.
+        max_batch > 0: the grouped serving engine for sfr_submit (see include/sfr.h)."""
         self.lib = load()
         self.handle = ctypes.c_void_p()
         cfg = Config(device=device, hbm_budget_bytes=hbm_budget_bytes, max_slots=max_slots,
-                     cuda_stream=ctypes.c_void_p(stream) if stream else None, profile=int(profile))
+                     cuda_stream=ctypes.c_void_p(stream) if stream else None, profile=int(profile),
+                     max_batch=max_batch)
         st = self.lib.sfr_create(ctypes.byref(self.handle), ctypes.byref(cfg))
         if st != OK:
             raise SfrError(st, self.lib.sfr_last_error(None).decode())

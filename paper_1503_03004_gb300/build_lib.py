@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsfr.so")
-SOURCES = ["solver.cu", "sweep.cu", "rxr.cu", "nys.cu", "noalloc.cu", "tc_sweep.cu"]
+SOURCES = ["solver.cu", "sweep.cu", "rxr.cu", "nys.cu", "noalloc.cu", "tc_sweep.cu", "batch.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]

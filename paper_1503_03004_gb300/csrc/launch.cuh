@@ -123,9 +123,25 @@ struct LaunchRecorder {
 // While non-null, launch_k records into this recorder instead of launching (per host thread).
 inline thread_local LaunchRecorder* g_recorder = nullptr;
 
-inline cudaError_t set_smem_attr(const void* kern, size_t smem) {
-  if (smem <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// Static shared memory of a kernel, queried once.
+template <auto Kern>
+size_t static_smem() {
+  static const size_t v = [] {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(Kern)) == cudaSuccess) return fa.sharedSizeBytes;
+    cudaGetLastError();
+    return size_t(0);
+  }();
+  return v;
+}
+
+// Opts the kernel in to `smem` bytes of dynamic shared memory where static + dynamic exceed the
+// default 48 KB (a grouped kernel adds a few bytes of its own to the body's static use).
+template <auto Kern>
+cudaError_t set_smem_attr(size_t smem) {
+  if (smem == 0 || smem + static_smem<Kern>() <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(reinterpret_cast<const void*>(Kern), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
 }
 
 template <typename F> struct BodyTraits;
@@ -152,7 +168,7 @@ template <typename... T> struct BodyTraits<void (*)(const VGrid&, T...)> {
       return cudaSuccess;
     }
     auto k = body_kernel<Body, NT, T...>;
-    cudaError_t e = set_smem_attr(reinterpret_cast<const void*>(k), smem);
+    cudaError_t e = set_smem_attr<&body_kernel<Body, NT, T...>>(smem);
     if (e != cudaSuccess) return e;
     return launch_pdl(k, grid, block, smem, st, static_cast<T>(a)...);
   }
@@ -162,7 +178,7 @@ template <typename... T> struct BodyTraits<void (*)(const VGrid&, T...)> {
   static cudaError_t launch_cluster(unsigned cluster, dim3 block, size_t smem, cudaStream_t st, A... a) {
     if (g_recorder) return launch<Body, NT>(dim3(1), block, smem, st, a...);
     auto k = body_kernel<Body, NT, T...>;
-    cudaError_t e = set_smem_attr(reinterpret_cast<const void*>(k), smem);
+    cudaError_t e = set_smem_attr<&body_kernel<Body, NT, T...>>(smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cluster);
@@ -184,7 +200,7 @@ template <typename... T> struct BodyTraits<void (*)(const VGrid&, T...)> {
   static cudaError_t launch_grouped(const int* starts, const void* entries, int count, unsigned total, unsigned block,
                                     size_t smem, cudaStream_t st) {
     auto k = grouped_kernel<Body, NT, T...>;
-    cudaError_t e = set_smem_attr(reinterpret_cast<const void*>(k), smem);
+    cudaError_t e = set_smem_attr<&grouped_kernel<Body, NT, T...>>(smem);
     if (e != cudaSuccess) return e;
     return launch_pdl(k, dim3(total), dim3(block), smem, st, starts, static_cast<const GroupEntry<T...>*>(entries),
                       count);

@@ -839,7 +839,7 @@ static int rxr_cluster_size(size_t smem) {
   int best = 1;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
     cudaGetLastError();
-  if (set_smem_attr(reinterpret_cast<const void*>(kern), smem) != cudaSuccess) cudaGetLastError();
+  if (set_smem_attr<body_kernel_of<&rxr_body, kThreads>()>(smem) != cudaSuccess) cudaGetLastError();
   for (int cs : {16, 8}) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs);

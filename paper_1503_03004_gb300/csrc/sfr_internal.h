@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -178,6 +179,23 @@ Shape plan_shape(int64_t m, int64_t n, int64_t ldm, int r, int num_sms);
 // base == nullptr: size only.  full: the buffers of Algorithm 4 (no m x n workspace).
 size_t carve(const Shape& s, bool fp64, void* base, Buffers* b, bool tc = false, bool full = false);
 double host_lambda_min(std::vector<double> A, int r);
+
+// ---- grouped serving engine (batch.cu)
+// One request handed to the engine: the problem, where its results go, the workspace bytes the
+// context admitted it with, and the context's handle for it.
+struct BatchJob {
+  sfr_problem prob;
+  sfr_result* res;
+  size_t bytes;
+  void* token;
+};
+class BatchEngine;
+// take(job, block): the next admissible request (block = wait for one; false when stopping with
+// nothing queued); done(job, status, message): the request finished.
+BatchEngine* batch_create(int device, int capacity, std::function<bool(BatchJob*, bool)> take,
+                          std::function<void(BatchJob&, sfr_status, const std::string&)> done);
+void batch_destroy(BatchEngine* e);  // waits until every admitted request is answered
+bool batch_eligible(const sfr_problem& p);
 int ctx_device(const sfr_ctx* ctx);
 int ctx_num_sms(const sfr_ctx* ctx);
 cudaStream_t ctx_stream(const sfr_ctx* ctx);

@@ -269,6 +269,53 @@ int mx_grid_for(const Shape& s, int ctas_per_sm) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(nrb64, ((int64_t)ctas_per_sm * s.num_sms + s.nsplit - 1) / s.nsplit));
 }
 
+// Sets s.mx_grid_x for the mixed SIMT sweep from the process-wide table, timing the candidates on
+// b (on stream st) when the size class is new; true when it launched timing sweeps.
+bool tune_mx_grid(Shape& s, Buffers& b, sfr_dtype m_dtype, cudaStream_t st) {
+  const char* env = getenv("SFR_AUTOTUNE");
+  const bool vec = ((size_t)s.n % 4 == 0) &&
+                   ((size_t)s.ldm * (m_dtype == SFR_F64 ? 8 : m_dtype == SFR_F32 ? 4 : 2)) % 16 == 0 &&
+                   (reinterpret_cast<uintptr_t>(b.M) % 16) == 0;
+  const std::string cls = tune_class(s, m_dtype, vec);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load_locked();
+  auto it = g_tune.find(cls);
+  if (it != g_tune.end()) {
+    s.mx_grid_x = mx_grid_for(s, it->second);
+    return false;
+  }
+  int best = 8;
+  bool timed = false;
+  if (!(env && env[0] == '0')) {
+    cudaEvent_t e0, e1;
+    SFR_CUDA(cudaEventCreate(&e0));
+    SFR_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    for (int c : {2, 4, 8, 16}) {
+      Shape t = s;
+      t.mx_grid_x = mx_grid_for(s, c);
+      SFR_CUDA(launch_sweep(t, b, false, 0, st));  // warm-up
+      SFR_CUDA(cudaEventRecord(e0, st));
+      for (int k = 0; k < 3; ++k) SFR_CUDA(launch_sweep(t, b, false, 0, st));
+      SFR_CUDA(cudaEventRecord(e1, st));
+      SFR_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      SFR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms * 0.97f) {  // prefer the earlier (smaller) grid unless clearly faster
+        best_ms = ms;
+        best = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    timed = true;
+  }
+  g_tune.emplace(cls, best);
+  tune_save_locked();
+  s.mx_grid_x = mx_grid_for(s, best);
+  return timed;
+}
+
 // ---------------------------------------------------------------- one FR-ADM solve
 struct Solver {
   int device = 0;
@@ -507,46 +554,7 @@ struct Solver {
   // the first iteration: the sweep reads Y_1 = 0 and whatever U, C, V hold, and writes buffers the
   // first iteration overwrites, so timing it changes nothing.
   void tune_mx(Shape& s, Buffers& b, sfr_dtype m_dtype) {
-    const char* env = getenv("SFR_AUTOTUNE");
-    const bool vec = ((size_t)s.n % 4 == 0) &&
-                     ((size_t)s.ldm * (m_dtype == SFR_F64 ? 8 : m_dtype == SFR_F32 ? 4 : 2)) % 16 == 0 &&
-                     (reinterpret_cast<uintptr_t>(b.M) % 16) == 0;
-    const std::string cls = tune_class(s, m_dtype, vec);
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    tune_load_locked();
-    auto it = g_tune.find(cls);
-    if (it != g_tune.end()) {
-      s.mx_grid_x = mx_grid_for(s, it->second);
-      return;
-    }
-    int best = 8;
-    if (!(env && env[0] == '0')) {
-      cudaEvent_t e0, e1;
-      SFR_CUDA(cudaEventCreate(&e0));
-      SFR_CUDA(cudaEventCreate(&e1));
-      float best_ms = 1e30f;
-      for (int c : {2, 4, 8, 16}) {
-        Shape t = s;
-        t.mx_grid_x = mx_grid_for(s, c);
-        SFR_CUDA(launch_sweep(t, b, false, 0, stream));  // warm-up
-        SFR_CUDA(cudaEventRecord(e0, stream));
-        for (int k = 0; k < 3; ++k) SFR_CUDA(launch_sweep(t, b, false, 0, stream));
-        SFR_CUDA(cudaEventRecord(e1, stream));
-        SFR_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        SFR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best_ms * 0.97f) {  // prefer the earlier (smaller) grid unless clearly faster
-          best_ms = ms;
-          best = c;
-        }
-      }
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      count(SFR_STAT_ALL, 16);
-    }
-    g_tune.emplace(cls, best);
-    tune_save_locked();
-    s.mx_grid_x = mx_grid_for(s, best);
+    if (tune_mx_grid(s, b, m_dtype, stream)) count(SFR_STAT_ALL, 16);
   }
 
   // Runs Algorithm 1 on a device-resident M.  Returns the final host copy of the state and
@@ -928,6 +936,10 @@ struct sfr_ctx {
   std::vector<std::thread> workers;
   std::vector<std::unique_ptr<Solver>> slot_solvers;
   std::vector<cudaStream_t> slot_streams;
+  // grouped engine (max_batch > 0): its own queue of the requests it can run
+  int max_batch = 0;
+  std::deque<std::shared_ptr<Request>> bqueue;
+  BatchEngine* batch = nullptr;
 };
 
 static thread_local std::string g_create_error;
@@ -1155,6 +1167,54 @@ static size_t request_bytes(const sfr_problem& p, int num_sms) {
   return total;
 }
 
+// The grouped engine's side of the queue: the oldest batched request that the free budget admits
+// (passing over one that does not fit yet at most kMaxPassOver times, as the slots do).
+static bool batch_take(sfr_ctx* ctx, BatchJob* job, bool block, int num_sms) {
+  constexpr int kMaxPassOver = 64;
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  for (;;) {
+    auto pick = ctx->bqueue.end();
+    size_t need = 0;
+    for (auto it = ctx->bqueue.begin(); it != ctx->bqueue.end(); ++it) {
+      const size_t want = request_bytes((*it)->prob, num_sms);
+      if (!ctx->budget || ctx->in_use + want <= ctx->budget) {
+        pick = it;
+        need = want;
+        break;
+      }
+      if ((*it)->passed_over >= kMaxPassOver) break;
+    }
+    if (pick != ctx->bqueue.end()) {
+      for (auto it = ctx->bqueue.begin(); it != pick; ++it) ++(*it)->passed_over;
+      std::shared_ptr<Request> rq = *pick;
+      ctx->bqueue.erase(pick);
+      ctx->in_use += need;
+      job->prob = rq->prob;
+      job->res = rq->res;
+      job->bytes = need;
+      job->token = rq.get();  // kept alive by ctx->live until polled
+      return true;
+    }
+    if (!block) return false;
+    if (ctx->stopping && ctx->bqueue.empty()) return false;
+    ctx->cv_work.wait(lk);
+  }
+}
+
+static void batch_done(sfr_ctx* ctx, BatchJob& job, sfr_status st, const std::string& msg) {
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->in_use -= job.bytes;
+    Request* rq = static_cast<Request*>(job.token);
+    job.res->status = st;
+    rq->status = st;
+    rq->finished = true;
+    if (st < 0) ctx->last_error = msg;
+  }
+  ctx->cv_done.notify_all();
+  ctx->cv_work.notify_all();
+}
+
 // One slot: take the oldest request once the HBM budget admits it, solve it on this slot's
 // stream, release its workspace share, take the next (continuous batching of independent solves).
 static void worker_main(sfr_ctx* ctx, int slot) {
@@ -1311,6 +1371,13 @@ sfr_status sfr_create(sfr_ctx** out, const sfr_config* cfg) {
   }
   sfr_ctx* raw = ctx.release();
   for (int w = 0; w < raw->max_slots; ++w) raw->workers.emplace_back(worker_main, raw, w);
+  if (cfg->max_batch > 0) {
+    raw->max_batch = std::min(cfg->max_batch, 1024);
+    const int sms = raw->solver->num_sms;
+    raw->batch = batch_create(
+        raw->device, raw->max_batch, [raw, sms](BatchJob* j, bool block) { return batch_take(raw, j, block, sms); },
+        [raw](BatchJob& j, sfr_status st, const std::string& m) { batch_done(raw, j, st, m); });
+  }
   *out = raw;
   return SFR_OK;
 }
@@ -1359,17 +1426,20 @@ sfr_status sfr_submit(sfr_ctx* ctx, const sfr_problem* prob, sfr_result* res, ui
   rq->res = res;
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
-    if ((int)ctx->queue.size() >= 64 * ctx->max_slots) {
+    const bool batched = ctx->batch && batch_eligible(*prob);
+    auto& q = batched ? ctx->bqueue : ctx->queue;
+    const int limit = batched ? 4 * ctx->max_batch : 64 * ctx->max_slots;
+    if ((int)q.size() >= limit) {
       ctx->last_error = "request queue full";
       return SFR_E_BUSY;
     }
     rq->ticket = ctx->next_ticket++;
     res->status = SFR_PENDING;
-    ctx->queue.push_back(rq);
+    q.push_back(rq);
     ctx->live[rq->ticket] = rq;
     *ticket = rq->ticket;
   }
-  ctx->cv_work.notify_one();
+  ctx->cv_work.notify_all();
   return SFR_OK;
 }
 
@@ -1422,6 +1492,7 @@ sfr_status sfr_destroy(sfr_ctx* ctx) {
   ctx->cv_work.notify_all();
   for (auto& w : ctx->workers)
     if (w.joinable()) w.join();
+  if (ctx->batch) batch_destroy(ctx->batch);  // answers every request it holds first
   cudaSetDevice(ctx->device);
   ctx->solver.reset();
   ctx->slot_solvers.clear();
