@@ -159,6 +159,7 @@ class BatchEngine {
     q->job = job;
     const sfr_problem& p = job.prob;
     q->s = plan_shape(p.m, p.n, p.ldm, p.r, num_sms_);
+    plan_mcopy(&q->s, false, false, p.m_dtype, p.M);
     const size_t bytes = carve(q->s, false, nullptr, nullptr);
     if (cudaMallocAsync(&q->mem, bytes, st_) != cudaSuccess) {
       cudaGetLastError();
@@ -182,6 +183,11 @@ class BatchEngine {
     carve(q->s, false, q->mem, &b);
     b.st = d_states_ + q->slot;
     b.M = p.M;
+    if (q->s.mc_ld > 0) {  // rows of M not 16-byte aligned: the passes read an aligned copy
+      BT_CUDA(launch_copy_m(q->s, p.M, p.ldm, b.Mc, st_));
+      b.M = b.Mc;
+      q->s.ldm = q->s.mc_ld;
+    }
     b.m_dtype = p.m_dtype;
     b.u_cur = 0;
     DevState h{};
@@ -194,7 +200,7 @@ class BatchEngine {
     h.max_iter = p.fixed_iters > 0 ? p.fixed_iters : p.max_iter;
     h.status = SFR_OK;
     BT_CUDA(launch_pdl(batch_init_kernel, 1, 256, 0, st_, b.st, h, b.B, b.Qeig_u, b.Qeig_v, q->s.rp));
-    BT_CUDA(cudaMemsetAsync(b.Y[0], 0, 4 * (size_t)q->s.m * q->s.n, st_));  // Y_1 = 0
+    BT_CUDA(cudaMemsetAsync(b.Y[0], 0, 4 * (size_t)q->s.m * b.ldy, st_));  // Y_1 = 0
     BT_CUDA(launch_norm_m(q->s, b, st_));
     try {
       tune_mx_grid(q->s, b, p.m_dtype, st_);  // the grid sfr_solve uses for this size class

@@ -127,7 +127,7 @@ extern "C" sfr_status sfr_solve_noalloc(sfr_ctx* ctx, const sfr_problem* prob, s
     h.max_iter = p.fixed_iters > 0 ? p.fixed_iters : p.max_iter;
     h.status = SFR_OK;
     NA_CUDA(cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, st));
-    NA_CUDA(cudaMemsetAsync(b.Y[0], 0, (fp64 ? 8 : 4) * (size_t)s.m * s.n, st));
+    NA_CUDA(cudaMemsetAsync(b.Y[0], 0, (fp64 ? 8 : 4) * (size_t)s.m * b.ldy, st));
     double eye[kMaxRank * kMaxRank];
     float eyef[kMaxRank * kMaxRank];
     memset(eye, 0, sizeof eye);

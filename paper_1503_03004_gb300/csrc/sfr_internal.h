@@ -89,6 +89,9 @@ struct Shape {
   int mx_grid_x;        // row-block CTAs of the mixed-path SIMT sweep (64-row blocks, grid-stride)
   int q_ctas;           // > 0: persistent tensor-core sweep over this many CTAs, whose Q partials per
                         // 128-row block are the CTAs owning its tiles (tc_q_slots); nsplit = max slots
+  int64_t mc_ld;        // > 0: the SIMT mixed passes read an aligned copy of M with this leading
+                        // dimension (rows 16-byte aligned, zero padding), made once per solve
+  int mc_es;            // element size of that copy
 };
 
 // Persistent tensor-core sweep: the N = R T (128-row block, 64-column tile) pairs, row-major,
@@ -102,10 +105,13 @@ __host__ __device__ inline int tc_q_slots(int64_t rb, int64_t T, int64_t N, int6
 // Device buffers of one solve.  TC is double (FP64 path) or float (mixed path);
 // the pointers below are typed void* and cast by the launchers.
 struct Buffers {
-  const void* M;        // caller's m x n matrix (device)
+  const void* M;        // m x n matrix the passes read (device): the caller's, or its aligned copy Mc
   sfr_dtype m_dtype;
-  void* Y[2];           // multiplier ping-pong, m x n dense (ld = n), TC
-  void* D;              // Delta = X_{k+1} - L_{k+1}, m x n dense, TC
+  void* Mc;             // aligned copy of M (Shape::mc_ld > 0), else null
+  int64_t ldy;          // leading dimension of Y[] and D: n, rounded up to 4 on the SIMT mixed path
+                        // (16-byte aligned rows for its vector and cp.async accesses)
+  void* Y[2];           // multiplier ping-pong, m x ldy, TC
+  void* D;              // Delta = X_{k+1} - L_{k+1}, m x ldy, TC
   void* P;              // m x rp, TC: X_k V_k
   void* U[2];           // m x rp, TC: U_bar ping-pong
   void* W;              // n x rp, TC: X_k^T U_bar
@@ -173,6 +179,21 @@ constexpr int kGramRows = 64;    // rows per Gram / transform CTA
 inline int pad_rank(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 32 ? 32 : 64; }
 // The mixed path's float32 SIMT passes for r <= 32 (sweep_mx*/wpass_mx* kernels).
 inline bool mx_path(const Shape& s, bool fp64) { return !fp64 && s.rp <= 32; }
+// Leading dimension of the aligned copy of M that the SIMT mixed passes read when the caller's rows
+// are not 16-byte aligned (0: no copy; the tensor-core path has its own alignment rule).
+inline int64_t mcopy_ld(const Shape& s, bool fp64, bool tc, sfr_dtype m_dtype, const void* M) {
+  if (tc || !mx_path(s, fp64)) return 0;
+  const int64_t es = m_dtype == SFR_F64 ? 8 : m_dtype == SFR_F32 ? 4 : 2;
+  if ((s.ldm * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(M) % 16) == 0) return 0;
+  const int64_t per = 16 / es;
+  return (s.n + per - 1) / per * per;
+}
+inline void plan_mcopy(Shape* s, bool fp64, bool tc, sfr_dtype m_dtype, const void* M) {
+  s->mc_ld = mcopy_ld(*s, fp64, tc, m_dtype, M);
+  s->mc_es = m_dtype == SFR_F64 ? 8 : m_dtype == SFR_F32 ? 4 : 2;
+}
+// M -> b.Mc (zero padding past column n); the passes then read b.Mc with leading dimension s.mc_ld.
+cudaError_t launch_copy_m(const Shape& s, const void* M, int64_t ldm, void* Mc, cudaStream_t st);
 
 // ---- host helpers shared by the entry points (solver.cu)
 Shape plan_shape(int64_t m, int64_t n, int64_t ldm, int r, int num_sms);

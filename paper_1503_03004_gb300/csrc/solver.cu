@@ -160,10 +160,12 @@ size_t carve(const Shape& s, bool fp64, void* base, Buffers* b, bool tc, bool fu
     x.t.Ut = c.take(2 * 128 * x.t.ldd);
     x.t.Vt = c.take(2 * 128 * x.t.ldy);
   } else if (!full) {
-    x.Y[0] = c.take(tcb * s.m * s.n);
-    x.Y[1] = c.take(tcb * s.m * s.n);
-    x.D = c.take(tcb * s.m * s.n);
+    x.ldy = mx_path(s, fp64) ? (s.n + 3) / 4 * 4 : s.n;
+    x.Y[0] = c.take(tcb * s.m * x.ldy);
+    x.Y[1] = c.take(tcb * s.m * x.ldy);
+    x.D = c.take(tcb * s.m * x.ldy);
   }
+  if (s.mc_ld > 0) x.Mc = c.take((size_t)s.mc_es * s.m * s.mc_ld);
   x.P = c.take(tcb * s.m * rp);
   x.U[0] = c.take(tcb * s.m * rp);
   x.U[1] = c.take(tcb * s.m * rp);
@@ -273,7 +275,7 @@ int mx_grid_for(const Shape& s, int ctas_per_sm) {
 // b (on stream st) when the size class is new; true when it launched timing sweeps.
 bool tune_mx_grid(Shape& s, Buffers& b, sfr_dtype m_dtype, cudaStream_t st) {
   const char* env = getenv("SFR_AUTOTUNE");
-  const bool vec = ((size_t)s.n % 4 == 0) &&
+  const bool vec = (b.ldy % 4 == 0) &&
                    ((size_t)s.ldm * (m_dtype == SFR_F64 ? 8 : m_dtype == SFR_F32 ? 4 : 2)) % 16 == 0 &&
                    (reinterpret_cast<uintptr_t>(b.M) % 16) == 0;
   const std::string cls = tune_class(s, m_dtype, vec);
@@ -567,6 +569,7 @@ struct Solver {
     last_tc = tc;
     Shape s = s0;
     if (tc) tc_plan(&s, num_sms);  // persistent sweep over the SMs
+    plan_mcopy(&s, fp64, tc, p.m_dtype, Mdev);
     Buffers b{};
     const size_t bytes = carve(s, fp64, nullptr, nullptr, tc);
     work.ensure(bytes, &held, budget);
@@ -583,6 +586,11 @@ struct Solver {
       wpass_first_bytes = mn * bm;
     }
     b.M = Mdev;
+    if (s.mc_ld > 0) {  // rows of M not 16-byte aligned: the passes read an aligned copy
+      SFR_CUDA(launch_copy_m(s, Mdev, p.ldm, b.Mc, stream));
+      b.M = b.Mc;
+      s.ldm = s.mc_ld;
+    }
     b.m_dtype = p.m_dtype;
     b.u_cur = 0;
 
@@ -596,7 +604,7 @@ struct Solver {
     h.max_iter = p.fixed_iters > 0 ? p.fixed_iters : p.max_iter;
     h.status = SFR_OK;
     SFR_CUDA(cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, stream));
-    const size_t ybytes = tc ? 2 * (size_t)s.m * b.t.ldy : (fp64 ? 8 : 4) * (size_t)s.m * s.n;
+    const size_t ybytes = tc ? 2 * (size_t)s.m * b.t.ldy : (fp64 ? 8 : 4) * (size_t)s.m * b.ldy;
     SFR_CUDA(cudaMemsetAsync(b.Y[0], 0, ybytes, stream));  // Y_1 = 0
     std::vector<double> eye(s.rp * s.rp, 0.0);
     std::vector<float> eyef(s.rp * s.rp, 0.f);
@@ -856,6 +864,7 @@ bool solver_reserve(Solver& sv, const sfr_problem& p, const void* Mdev, size_t* 
   Shape s = plan_shape(p.m, p.n, p.ldm, p.r, sv.num_sms);
   const bool tc = !fp64 && tc_supported(s, p.m_dtype, p.ldm) && ((uintptr_t)Mdev % 16) == 0;
   if (tc) tc_plan(&s, sv.num_sms);
+  plan_mcopy(&s, fp64, tc, p.m_dtype, Mdev);
   try {
     sv.work.ensure(carve(s, fp64, nullptr, nullptr, tc), held, budget);
   } catch (const Fail&) {
@@ -1151,17 +1160,21 @@ static sfr_status full_with(Solver& sv, const sfr_opt_full_problem& p, sfr_opt_f
 static size_t request_bytes(const sfr_problem& p, int num_sms) {
   const bool fp64 = p.precision == SFR_PREC_FP64;
   size_t total = 0;
-  auto one = [&](int64_t m, int64_t n) {
-    Shape s = plan_shape(m, n, n, p.r, num_sms);
-    const bool tc = !fp64 && tc_supported(s, p.m_dtype, n);
+  // (the aligned copy of M is planned from M's own rows where the solve reads them in place)
+  auto one = [&](int64_t m, int64_t n, int64_t ldm, const void* M) {
+    Shape s = plan_shape(m, n, ldm, p.r, num_sms);
+    const bool tc = !fp64 && tc_supported(s, p.m_dtype, ldm);
     if (tc) tc_plan(&s, num_sms);
+    plan_mcopy(&s, fp64, tc, p.m_dtype, M);
     return carve(s, fp64, nullptr, nullptr, tc);
   };
-  if (p.nys_l) {  // the two block solves run concurrently
-    total = one(p.m, p.nys_l) + one(p.nys_l, p.n);
+  if (p.nys_l) {  // the two block solves run concurrently on gathered (dense) blocks
+    total = one(p.m, p.nys_l, p.nys_l, nullptr) + one(p.nys_l, p.n, p.n, nullptr);
     total += dtype_size(p.m_dtype) * (size_t)(p.m * p.nys_l + p.nys_l * p.n) + 8 * (size_t)(2 * p.m + 2 * p.nys_l + p.n) * p.r;
+  } else if (p.mem == SFR_MEM_DEVICE) {
+    total = one(p.m, p.n, p.ldm, p.M);
   } else {
-    total = one(p.m, p.n);
+    total = one(p.m, p.n, p.ldm, nullptr);  // the staging copy keeps ldm
   }
   if (p.mem == SFR_MEM_HOST) total += dtype_size(p.m_dtype) * (size_t)(p.m * p.ldm) + 16 * (size_t)p.m * p.n;
   return total;

@@ -725,7 +725,7 @@ __device__ __forceinline__ void st4(float* __restrict__ p, int lim, const float 
 // stored once.  One residual partial per CTA (slot blockIdx.y * gridDim.x + blockIdx.x).
 template <typename TMs, int RP, bool VEC>
 __device__ __forceinline__ void sweep_mx_body(const VGrid& vg__, const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm,
-                                                       const float* __restrict__ Yin, float* __restrict__ Yout,
+                                                       int64_t ldy, const float* __restrict__ Yin, float* __restrict__ Yout,
                                                        float* __restrict__ D, const float* __restrict__ U,
                                                        const float* __restrict__ C, const float* __restrict__ V,
                                                        float* __restrict__ Qpart, int cols_per_split,
@@ -790,7 +790,7 @@ __device__ __forceinline__ void sweep_mx_body(const VGrid& vg__, const TMs* __re
           float a4[4], b4[4];
           if (i < m && lim > 4 * h) {
             ld4<TMs, VEC>(M + i * ldm + jc + 4 * h, lim - 4 * h, a4);
-            ld4<float, VEC>(Yin + i * n + jc + 4 * h, lim - 4 * h, b4);
+            ld4<float, VEC>(Yin + i * ldy + jc + 4 * h, lim - 4 * h, b4);
           } else {
 #pragma unroll
             for (int c = 0; c < 4; ++c) a4[c] = b4[c] = 0.f;
@@ -846,8 +846,8 @@ __device__ __forceinline__ void sweep_mx_body(const VGrid& vg__, const TMs* __re
             if (lim <= 4 * h) continue;
             const float y4[4] = {yn[4 * h], yn[4 * h + 1], yn[4 * h + 2], yn[4 * h + 3]};
             const float d4[4] = {dd[4 * h], dd[4 * h + 1], dd[4 * h + 2], dd[4 * h + 3]};
-            st4(Yout + i * n + jc + 4 * h, lim - 4 * h, y4, VEC);
-            st4(D + i * n + jc + 4 * h, lim - 4 * h, d4, VEC);
+            st4(Yout + i * ldy + jc + 4 * h, lim - 4 * h, y4, VEC);
+            st4(D + i * ldy + jc + 4 * h, lim - 4 * h, d4, VEC);
           }
       }
       __syncthreads();  // Xs complete
@@ -900,7 +900,7 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 // conditions (n % 4 == 0, 16-byte aligned rows of M) and float32 or bfloat16 M.
 template <typename TMs, int RP>
 __device__ __forceinline__ void sweep_mxp_body(const VGrid& vg__, const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm,
-                                                        const float* __restrict__ Yin, float* __restrict__ Yout,
+                                                        int64_t ldy, const float* __restrict__ Yin, float* __restrict__ Yout,
                                                         float* __restrict__ D, const float* __restrict__ U,
                                                         const float* __restrict__ C, const float* __restrict__ V,
                                                         float* __restrict__ Qpart, int cols_per_split,
@@ -945,7 +945,7 @@ __device__ __forceinline__ void sweep_mxp_body(const VGrid& vg__, const TMs* __r
       const int ii = e / (BN / 4), cc = e % (BN / 4);
       const int64_t i = i0 + ii, j = j0 + 4 * cc;
       const bool ok = i < m && j < jend;
-      cp_async16(ys + ii * BN + 4 * cc, ok ? (const void*)(Yin + i * n + j) : (const void*)Yin, ok ? 16 : 0);
+      cp_async16(ys + ii * BN + 4 * cc, ok ? (const void*)(Yin + i * ldy + j) : (const void*)Yin, ok ? 16 : 0);
     }
     for (int e = t; e < BM * (BN / EPC); e += blockDim.x) {  // M: 16-byte chunks
       const int ii = e / (BN / EPC), cc = e % (BN / EPC);
@@ -1056,9 +1056,9 @@ __device__ __forceinline__ void sweep_mxp_body(const VGrid& vg__, const TMs* __r
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           if (lim <= 4 * h) continue;
-          *reinterpret_cast<float4*>(Yout + i * n + jc + 4 * h) =
+          *reinterpret_cast<float4*>(Yout + i * ldy + jc + 4 * h) =
               make_float4(yn[4 * h], yn[4 * h + 1], yn[4 * h + 2], yn[4 * h + 3]);
-          *reinterpret_cast<float4*>(D + i * n + jc + 4 * h) =
+          *reinterpret_cast<float4*>(D + i * ldy + jc + 4 * h) =
               make_float4(dd[4 * h], dd[4 * h + 1], dd[4 * h + 2], dd[4 * h + 3]);
         }
     }
@@ -1473,7 +1473,36 @@ cudaError_t allow_smem(K kern, size_t bytes) {
 // 16-byte boundaries; otherwise the same kernels load element by element.
 static bool mx_vec(const Shape& s, const Buffers& b) {
   const size_t es = b.m_dtype == SFR_F64 ? 8 : b.m_dtype == SFR_F32 ? 4 : 2;
-  return s.n % 4 == 0 && ((size_t)s.ldm * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(b.M) % 16) == 0;
+  return b.ldy % 4 == 0 && ((size_t)s.ldm * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(b.M) % 16) == 0;
+}
+
+// Aligned copy of M: dst[i][j] = src[i][j] for j < n, 0 for n <= j < ldd (one thread per
+// destination element, elements moved as raw bits).
+template <typename T>
+__global__ void copy_m_kernel(const T* __restrict__ src, int64_t ldm, int64_t m, int64_t n, T* __restrict__ dst,
+                              int64_t ldd) {
+  pdl_enter();
+  const int64_t total = m * ldd;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ldd, j = e % ldd;
+    dst[e] = j < n ? src[i * ldm + j] : T(0);
+  }
+}
+
+cudaError_t launch_copy_m(const Shape& s, const void* M, int64_t ldm, void* Mc, cudaStream_t st) {
+  const int64_t total = s.m * s.mc_ld;
+  const int blocks = (int)std::min<int64_t>(cdiv(total, 256), 8LL * s.num_sms);
+  if (total == 0) return cudaSuccess;
+  if (s.mc_es == 8)
+    launch_pdl(copy_m_kernel<uint64_t>, blocks, 256, 0, st, static_cast<const uint64_t*>(M), ldm, s.m, s.n,
+               static_cast<uint64_t*>(Mc), s.mc_ld);
+  else if (s.mc_es == 4)
+    launch_pdl(copy_m_kernel<uint32_t>, blocks, 256, 0, st, static_cast<const uint32_t*>(M), ldm, s.m, s.n,
+               static_cast<uint32_t*>(Mc), s.mc_ld);
+  else
+    launch_pdl(copy_m_kernel<uint16_t>, blocks, 256, 0, st, static_cast<const uint16_t*>(M), ldm, s.m, s.n,
+               static_cast<uint16_t*>(Mc), s.mc_ld);
+  return cudaGetLastError();
 }
 
 // threads of the partial-sum kernel: 8 warps, 32 when there are many partials to walk
@@ -1548,7 +1577,7 @@ cudaError_t launch_apply_u(const Shape& s, const Buffers& b, bool fp64, bool fir
 cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first, int u_new, cudaStream_t st) {
   dim3 grid(s.wpass_grid_x, s.nchunk);
   if (mx_path(s, fp64)) {
-    const bool vec = first ? mx_vec(s, b) : s.n % 4 == 0;
+    const bool vec = first ? mx_vec(s, b) : b.ldy % 4 == 0;
     return by_rank(s.rp, [&](auto rpc) {
       constexpr int RP = decltype(rpc)::value;
       if constexpr (RP > 32) {
@@ -1576,7 +1605,7 @@ cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first
                        : go(BodyTag<&wpass_mx_body<TMs, RP, false>>{}, M, s.ldm);
           });
         const float* Dp = static_cast<const float*>(b.D);
-        return vec ? pipelined(Dp, s.n) : go(BodyTag<&wpass_mx_body<float, RP, false>>{}, Dp, s.n);
+        return vec ? pipelined(Dp, b.ldy) : go(BodyTag<&wpass_mx_body<float, RP, false>>{}, Dp, b.ldy);
       }
     });
   }
@@ -1664,7 +1693,7 @@ static cudaError_t launch_sweep_mx(const Shape& s, const Buffers& b, int u_cur, 
       return by_mtype(b.m_dtype, b.M, [&](auto M) {
         using TMs = std::remove_const_t<std::remove_pointer_t<decltype(M)>>;
         auto go = [&](auto tag) {
-          return launch_k<decltype(tag)::value, 256>(grid, 256, 0, st, M, s.m, s.n, s.ldm,
+          return launch_k<decltype(tag)::value, 256>(grid, 256, 0, st, M, s.m, s.n, s.ldm, b.ldy,
                                                       static_cast<const float*>(b.Y[0]), static_cast<float*>(b.Y[1]),
                                                       static_cast<float*>(b.D), static_cast<const float*>(b.U[u_cur]),
                                                       static_cast<const float*>(b.C), static_cast<const float*>(b.V),
@@ -1675,7 +1704,7 @@ static cudaError_t launch_sweep_mx(const Shape& s, const Buffers& b, int u_cur, 
           if (vec) {
             constexpr size_t sm = mxp_smem<TMs, RP>();
             return launch_k<&sweep_mxp_body<TMs, RP>, 256>(
-                grid, 256, sm, st, M, s.m, s.n, s.ldm, static_cast<const float*>(b.Y[0]), static_cast<float*>(b.Y[1]),
+                grid, 256, sm, st, M, s.m, s.n, s.ldm, b.ldy, static_cast<const float*>(b.Y[0]), static_cast<float*>(b.Y[1]),
                 static_cast<float*>(b.D), static_cast<const float*>(b.U[u_cur]), static_cast<const float*>(b.C),
                 static_cast<const float*>(b.V), static_cast<float*>(b.Qpart), s.cols_per_split, b.resid_part, s.r,
                 b.st);
@@ -1745,7 +1774,7 @@ cudaError_t launch_finalize(const Shape& s, const Buffers& b, bool fp64, int u_c
           return cudaGetLastError();
         };
         if (b.tc) return go(static_cast<const __nv_bfloat16*>(b.Y[0]), b.t.ldy);
-        return go(static_cast<const TC*>(b.Y[0]), s.n);
+        return go(static_cast<const TC*>(b.Y[0]), b.ldy);
       });
     });
   });

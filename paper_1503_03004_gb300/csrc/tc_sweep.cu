@@ -60,7 +60,7 @@ struct SweepBars {
   uint64_t q_full;
   uint32_t tmem_base;
   int abort;
-  float red[16];
+  double red[16];
 };
 static_assert(sizeof(SweepBars) <= 512, "barrier block");
 
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
     const float inv_mu_last = (float)(1.0 / st->mu_last);
     const double mu_next_d = fmin(st->mu_max, st->rho * st->mu);
     const float inv_mu = (float)(1.0 / st->mu), dcoef = (float)(1.0 / st->mu + 1.0 / mu_next_d);
-    float resid = 0.f;
+    double resid = 0.0;  // float64 sum of the per-tile float32 partials
     bool ok = true;
     for (int t = 0; t < ntiles; ++t) {
       const int s = t % NSTAGE, b = t & 1, i0 = tile_i0(t), j0 = tile_j0(t);
@@ -451,11 +451,13 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
       unsigned char* yo = sm + OFF_YO;
       const int ncol = (int)(n - j0 - cbase);  // valid columns among this thread's (may be <= 0)
       uint4 yn[kEpiChunks], dd[kEpiChunks];
+      float rt = 0.f;  // this thread's part of the tile (at most 64 terms)
 #pragma unroll
       for (int cc = 0; cc < kEpiChunks; ++cc) {  // 16-byte chunk c = columns 8c .. 8c+7
-        if (ncol >= kEpiCols) epi_chunk<true>(mwr[cc], ywr[cc], L + 8 * cc, 0, mu, inv_mu, dcoef, yn[cc], dd[cc], resid);
-        else epi_chunk<false>(mwr[cc], ywr[cc], L + 8 * cc, ncol - 8 * cc, mu, inv_mu, dcoef, yn[cc], dd[cc], resid);
+        if (ncol >= kEpiCols) epi_chunk<true>(mwr[cc], ywr[cc], L + 8 * cc, 0, mu, inv_mu, dcoef, yn[cc], dd[cc], rt);
+        else epi_chunk<false>(mwr[cc], ywr[cc], L + 8 * cc, ncol - 8 * cc, mu, inv_mu, dcoef, yn[cc], dd[cc], rt);
       }
+      resid += (double)rt;
       // the single Delta / Y_{k+1} tiles are free once Delta V of tile t - 1 is done and the TMA
       // stores of tile t - 1 have read them (long done by now: the waits come after the compute)
       if (t >= 1) mbar_wait(&B.d_empty, (t - 1) & 1, abort);
@@ -504,7 +506,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
     named_bar(1, kEpiThreads);
     if (!FINAL && tid == 0) {
       double tot = 0.0;
-      for (int w = 0; w < kEpiWarps; ++w) tot += (double)B.red[w];
+      for (int w = 0; w < kEpiWarps; ++w) tot += B.red[w];
       resid_part[blockIdx.x] = tot;
     }
   }
