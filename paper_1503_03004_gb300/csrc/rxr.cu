@@ -262,10 +262,12 @@ __device__ __noinline__ void jacobi_f32(float* A, float* Q, int n2, int max_swee
         const int p = lane == 0 ? 63 : (step + lane) % 63, q = lane == 0 ? step : (step - lane + 63) % 63;
         const float apq = A[p * LD + q], app = A[p * LD + p], aqq = A[q * LD + q];
         float c = 1.f, sn_ = 0.f;
-        if (fabsf(apq) > 1e-9f * sqrtf(fabsf(app * aqq)) && apq != 0.f) {
+        if (apq * apq > 1e-18f * fabsf(app * aqq) && apq != 0.f) {
+          // the angle only steers convergence (c^2 + s^2 = 1 holds for any t): fast approximations
           const float th = __fdividef(aqq - app, 2.f * apq);
+          const float h = 1.f + th * th;
           const float t = fabsf(th) > 1e15f ? __fdividef(0.5f, th)
-                                           : copysignf(1.f, th) * __frcp_rn(fabsf(th) + sqrtf(1.f + th * th));
+                                           : __fdividef(copysignf(1.f, th), fabsf(th) + h * rsqrtf(h));
           c = rsqrtf(1.f + t * t);
           sn_ = t * c;
         }
@@ -323,11 +325,12 @@ __device__ __noinline__ void jacobi_f32(float* A, float* Q, int n2, int max_swee
         else { p = (step + k) % (n2 - 1); q = (step - k + n2 - 1) % (n2 - 1); }
         const float apq = A[p * LD + q], app = A[p * LD + p], aqq = A[q * LD + q];
         float c = 1.f, s = 0.f;
-        if (fabsf(apq) > 1e-9f * sqrtf(fabsf(app * aqq)) && apq != 0.f) {
+        if (apq * apq > 1e-18f * fabsf(app * aqq) && apq != 0.f) {
           const float th = __fdividef(aqq - app, 2.f * apq);
+          const float h = 1.f + th * th;
           float t;
           if (fabsf(th) > 1e15f) t = __fdividef(0.5f, th);
-          else t = copysignf(1.f, th) * __frcp_rn(fabsf(th) + sqrtf(1.f + th * th));
+          else t = __fdividef(copysignf(1.f, th), fabsf(th) + h * rsqrtf(h));
           c = rsqrtf(1.f + t * t);
           s = t * c;
         }
@@ -521,8 +524,9 @@ __device__ __forceinline__ int exponent_of(long long bits) { return bits ? (int)
 // (float32, small) moves T_hat by B Delta and W by G B Delta, formed in float32: their rounding
 // is float32-relative to the correction, and the next residual is formed in float64 again.
 // float64: G, B, T_hat, W, R, B_bar, T_C.  float32: K, the eigenbasis, eigenvalue estimates, Z0
-// and the Newton corrections, which only steer the iteration.  Outputs are written by rows, each
-// CTA of the cluster its own slice.
+// and the Newton corrections, which only steer the iteration.  The mixed path also forms the
+// starting T_hat = B Z0 and T_C in float32 (its U, V and C are float32).  Outputs are written by
+// rows, each CTA of the cluster its own slice.
 __device__ __forceinline__ void rxr_body(const VGrid& vg__, const double* __restrict__ Gg, int rp, int r,
                                          double* __restrict__ Bg, double* __restrict__ Tout,
                                          double* __restrict__ TCout, float* __restrict__ Qeig, int v_side, int mixed,
@@ -572,12 +576,19 @@ __device__ __forceinline__ void rxr_body(const VGrid& vg__, const double* __rest
   gram_in_basis(S.Bf, S.Gf, S.Qf, S.Af, S.F1, S.F2, r, n2, 1.f);
   const float trf = block_reduce_f(tid < r ? S.Af[tid * LD + tid] : 0.f, redf, false);
   if (tid == 0) {
-    const double scale = ldexp((double)trf / r, eg + 2 * eb);  // trace(B G B) / r
-    S.ok = scale > 0.0 && scale < 1e300;
-    S.scale = scale;
-    S.inv_s = 1.0 / scale;
-    S.rs = 1.0 / sqrt(scale);
-    S.kn = r / trf;
+    // s = 2^(2k), the even power of two nearest below trace(B G B) / r (within a factor 4 of
+    // it), so that 1 / s and 1 / sqrt(s) are exact and need no float64 division or square root;
+    // A is scaled by K's power-of-two scale over s, exactly, so that its eigenvalues are those
+    // of K / s.
+    int e1 = 0;
+    frexpf(trf / (float)r, &e1);  // trf / r = f 2^e1, f in [0.5, 1)
+    const int tot = e1 + eg + 2 * eb, k = (tot >= 0 ? tot : tot - 1) / 2;  // floor(tot / 2)
+    S.ok = trf > 0.f && trf < 3e38f && 2 * k > -1000 && 2 * k < 1000;
+    auto pow2 = [](int e) { return __longlong_as_double((long long)(1023 + e) << 52); };
+    S.scale = pow2(2 * k);
+    S.inv_s = pow2(-2 * k);
+    S.rs = pow2(-k);
+    S.kn = ldexpf(1.f, eg + 2 * eb - 2 * k);
   }
   __syncthreads();
   if (!S.ok) { fail(st, SFR_E_NAN); return; }
@@ -720,9 +731,23 @@ __device__ __forceinline__ void rxr_body(const VGrid& vg__, const double* __rest
     S.F2[i * LD + j] = 0.5f * (S.F1[i * LD + j] + S.F1[j * LD + i]);
   }
   __syncthreads();
-  // 6. T_hat = B Z0 (float64 products of B with the float32 values of Z0)
+  // 6. T_hat = B Z0.  Float64 path: float64 products of B with the float32 values of Z0, rows
+  //    split across the cluster.  Mixed path: a float32 product of the scaled copy of B, in every
+  //    CTA.  Newton below corrects the symmetric part of Z only, so the float32 rounding of T_hat
+  //    stays as a rotation of the polar factor of about 1e-7, the size of the mixed path's own
+  //    rounding of U and V.
   const PlainEpi plain;
-  mm_dist<false>(S.W, S.F2, S.T, r, plain);
+  if (mixed) {
+    mmf<false, false>(S.Bf, S.F2, S.F1, r);  // B Z0 2^-eb
+    for (int e = tid; e < r * r; e += blockDim.x) {
+      const int i = e / r, j = e % r;
+      S.T[i * LDD + j] = f32_to_f64_shift(S.F1[i * LD + j], eb);
+    }
+    __syncthreads();
+    if (cs > 1) cl.sync();  // every CTA is past its reads of W (still B) before W rows arrive
+  } else {
+    mm_dist<false>(S.W, S.F2, S.T, r, plain);
+  }
   // 7. Newton steps on Z K Z = I: R = I - T_hat^T (G T_hat) / s in float64, correction in float32
   bool w_stale = false;  // W lags T_hat by G (B Delta)
   for (int it = 0; it < 6; ++it) {
@@ -805,19 +830,41 @@ __device__ __forceinline__ void rxr_body(const VGrid& vg__, const double* __rest
     }
     cl.sync();
   }
-  // this CTA's rows: B_bar, and T_C = T_V B_bar = (T_hat rows) B_bar / sqrt(s)
+  // this CTA's rows: B_bar, and T_C = T_V B_bar = (T_hat rows) B_bar / sqrt(s).  T_C only forms
+  // C = W T_C, which the mixed path stores in float32: there float32 products suffice.
+  if (mixed) {
+    for (int e = tid; e < r * r; e += blockDim.x) {
+      const int i = e / r, j = e % r;
+      S.Af[i * LD + j] = f64_to_f32_shift(S.G[i * LDD + j], 0);
+    }
+    for (int e = row0 * r + tid; e < row1 * r; e += blockDim.x) {
+      const int i = e / r, j = e % r;
+      S.F2[i * LD + j] = f64_to_f32_shift(S.T[i * LDD + j], 0);
+    }
+    __syncthreads();
+  }
   for (int e = row0 * rp + tid; e < row1 * rp; e += blockDim.x) {
     const int i = e / rp, j = e % rp;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    if (j < r) {
+    double tc = 0.0;
+    if (j < r && mixed) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      int k = 0;
+      for (; k + 4 <= r; k += 4)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = fmaf(S.F2[i * LD + k + q], S.Af[(k + q) * LD + j], acc[q]);
+      for (; k < r; ++k) acc[0] = fmaf(S.F2[i * LD + k], S.Af[k * LD + j], acc[0]);
+      tc = f32_to_f64_shift((acc[0] + acc[1]) + (acc[2] + acc[3]), 0);
+    } else if (j < r) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
       int k = 0;
       for (; k + 4 <= r; k += 4)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[q] = fma(S.T[i * LDD + k + q], S.G[(k + q) * LDD + j], acc[q]);
       for (; k < r; ++k) acc[0] = fma(S.T[i * LDD + k], S.G[k * LDD + j], acc[0]);
+      tc = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
     Bg[e] = j < r ? S.G[i * LDD + j] : 0.0;
-    TCout[e] = j < r ? ((acc[0] + acc[1]) + (acc[2] + acc[3])) * rs : 0.0;
+    TCout[e] = j < r ? tc * rs : 0.0;
   }
   if (writer)
     for (int e = r * rp + tid; e < rp * rp; e += blockDim.x) {
