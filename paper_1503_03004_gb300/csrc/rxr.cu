@@ -529,8 +529,8 @@ __device__ __forceinline__ int exponent_of(long long bits) { return bits ? (int)
 // rows, each CTA of the cluster its own slice.
 __device__ __forceinline__ void rxr_body(const VGrid& vg__, const double* __restrict__ Gg, int rp, int r,
                                          double* __restrict__ Bg, double* __restrict__ Tout,
-                                         double* __restrict__ TCout, float* __restrict__ Qeig, int v_side, int mixed,
-                                         DevState* st) {
+                                         double* __restrict__ TCout, const float* __restrict__ Qin,
+                                         float* __restrict__ Qeig, int v_side, int mixed, DevState* st) {
   pdl_enter();
   SFR_VGRID(vg__);
   if (stopped(st)) return;
@@ -544,7 +544,7 @@ __device__ __forceinline__ void rxr_body(const VGrid& vg__, const double* __rest
   const int rpc = (r + cs - 1) / cs, row0 = min(r, crank * rpc), row1 = min(r, row0 + rpc);  // own rows
   const int n2 = (r + 1) & ~1;  // Jacobi works on an even size (row / column r zero when r is odd)
   // 1. G and B in float64 (B in W until T_hat exists), their power-of-two-scaled float32 copies,
-  //    and the previous call's eigenbasis
+  //    and the warm-start eigenbasis (Qin)
   constexpr int PER = RPMAX * RPMAX / kThreads;
   double gv[PER], bv[PER];
   long long gmax = 0, bmax = 0;
@@ -557,7 +557,7 @@ __device__ __forceinline__ void rxr_body(const VGrid& vg__, const double* __rest
     gmax = max(gmax, abs_bits(gv[q]));
     bmax = max(bmax, abs_bits(bv[q]));
   }
-  load_sq(Qeig, rp, r, n2, S.Qf, 1.f);
+  load_sq(Qin, rp, r, n2, S.Qf, 1.f);
   gmax = block_max_ll(gmax, S.red);
   bmax = block_max_ll(bmax, S.red);
   if (gmax >= kInfBits || bmax >= kInfBits || bmax == 0) { fail(st, SFR_E_NAN); return; }
@@ -917,9 +917,13 @@ cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream
   if (e != cudaSuccess) return e;
   const size_t smem = sizeof(RxrSmem);
   const int cs = rxr_cluster_size(smem);
+  // warm start: the U side from its own basis of the previous iteration; the V side from the U
+  // side's basis of this iteration (both K share B, and their eigenbases meet as the iteration
+  // settles, so the V side's first-order refinement holds from the fourth iteration on)
   return launch_k_cluster<&rxr_body, kThreads>(cs, kThreads, smem, st, (const double*)b.Gsum, s.rp, s.r, b.B,
                                               v_side ? b.TV : b.TU, v_side ? b.TCm : (double*)nullptr,
-                                              v_side ? b.Qeig_v : b.Qeig_u, v_side ? 1 : 0, fp64 ? 0 : 1, b.st);
+                                              (const float*)b.Qeig_u, v_side ? b.Qeig_v : b.Qeig_u,
+                                              v_side ? 1 : 0, fp64 ? 0 : 1, b.st);
 }
 
 }  // namespace sfr
