@@ -27,8 +27,6 @@
 
 namespace sfr {
 
-bool tune_mx_grid(Shape& s, Buffers& b, sfr_dtype m_dtype, cudaStream_t st);
-
 namespace {
 
 struct BatchFail {
@@ -202,11 +200,10 @@ class BatchEngine {
     BT_CUDA(launch_pdl(batch_init_kernel, 1, 256, 0, st_, b.st, h, b.B, b.Qeig_u, b.Qeig_v, q->s.rp));
     BT_CUDA(cudaMemsetAsync(b.Y[0], 0, 4 * (size_t)q->s.m * b.ldy, st_));  // Y_1 = 0
     BT_CUDA(launch_norm_m(q->s, b, st_));
-    try {
-      tune_mx_grid(q->s, b, p.m_dtype, st_);  // the grid sfr_solve uses for this size class
-    } catch (...) {
-      throw BatchFail{"launch-shape timing of a batched request failed"};
-    }
+    // Sweep grid: with many problems per launch, each CTA takes 8 row blocks of its column split
+    // (the cp.async pipeline then runs over them) instead of the one-problem grid sfr_solve tunes.
+    // The sweep's partials are per row block and split, so its results do not depend on this.
+    q->s.mx_grid_x = (int)std::max<int64_t>(1, ((q->s.m + 63) / 64 + 7) / 8);
     BT_CUDA(launch_init_p(q->s, b, false, st_));  // X_1 = M, V_1 = I_{n x r}: P = M[:, :r]
     q->admitted_at = seq_;
     BProblem* raw = q.get();

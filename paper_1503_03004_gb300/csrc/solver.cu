@@ -127,7 +127,7 @@ Shape plan_shape(int64_t m, int64_t n, int64_t ldm, int r, int num_sms) {
   };
   s.gp_blocks = thin_ctas(m);
   s.gw_blocks = thin_ctas(n);
-  s.resid_parts = s.sweep_grid_x * s.nsplit;
+  s.resid_parts = s.nsplit * (int)std::max<int64_t>(s.sweep_grid_x, 8 * nrb64);  // see launch_iter_end
   s.q_ctas = 0;
   s.num_sms = num_sms;
   s.mx_grid_x = (int)std::max<int64_t>(1, std::min<int64_t>(nrb64, (8LL * num_sms + s.nsplit - 1) / s.nsplit));

@@ -31,6 +31,16 @@ template <> __device__ __forceinline__ double ld_as<double, __nv_bfloat16>(const
 __device__ __forceinline__ bool stopped(const DevState* st) { return *(volatile const int32_t*)&st->done != 0; }
 
 // Block-wide sum of a double; every thread gets the result.  blockDim.x <= 1024.
+// Residual partial of one warp over one row block of a column split of the SIMT mixed sweeps:
+// slot (split, row block, warp), so that the partials (and their fixed-order sum in the
+// iteration end) do not depend on how many CTAs the sweep runs.
+__device__ __forceinline__ void resid_store_warp(float resid, double* __restrict__ resid_part, int64_t split,
+                                                 int64_t nrb, int64_t rb) {
+  double v = (double)resid;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) resid_part[(split * nrb + rb) * 8 + (threadIdx.x >> 5)] = v;
+}
+
 __device__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
@@ -722,7 +732,7 @@ __device__ __forceinline__ void st4(float* __restrict__ p, int lim, const float 
 // 8 tc .. 8 tc + 7 of the tile, loads M and Y_k (vector loads issued before the L products),
 // writes Y_{k+1}, Delta and X = L + Delta (into shared memory).  Phase B: thread (qr, qa) adds
 // X V for rows 2 qr, 2 qr + 1 and ranks qa r/8 .. into registers; the Q partial of a row block is
-// stored once.  One residual partial per CTA (slot blockIdx.y * gridDim.x + blockIdx.x).
+// stored once.  One residual partial per (column split, row block, warp) (resid_store_warp).
 template <typename TMs, int RP, bool VEC>
 __device__ __forceinline__ void sweep_mx_body(const VGrid& vg__, const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm,
                                                        int64_t ldy, const float* __restrict__ Yin, float* __restrict__ Yout,
@@ -738,7 +748,6 @@ __device__ __forceinline__ void sweep_mx_body(const VGrid& vg__, const TMs* __re
   __shared__ __align__(16) float CsT[RP][BN];
   __shared__ __align__(16) float Vs[BN][RP];
   __shared__ __align__(16) float Xs[BM][kMxLDX];
-  __shared__ double red[32];
   const double mu_d = st->mu, mu_next = fmin(st->mu_max, st->rho * mu_d);
   const float mu = (float)mu_d, inv_mu = (float)(1.0 / mu_d), dcoef = (float)(1.0 / mu_d + 1.0 / mu_next);
   const int64_t jbeg = (int64_t)blockIdx.y * cols_per_split;
@@ -747,7 +756,6 @@ __device__ __forceinline__ void sweep_mx_body(const VGrid& vg__, const TMs* __re
   const int t = threadIdx.x, tr = t >> 3, tc = t & 7;
   const int64_t nrb = (m + BM - 1) / BM;
 
-  double resid_acc = 0.0;
   auto load_cv = [&](int64_t j0) {  // C^T and V tiles of columns j0 .. j0 + 63 (0 past jend)
     for (int e = t; e < BN * RP; e += blockDim.x) {
       const int jj = e / RP, a = e % RP;
@@ -879,10 +887,8 @@ __device__ __forceinline__ void sweep_mx_body(const VGrid& vg__, const TMs* __re
 #pragma unroll
         for (int k = 0; k < QA; ++k) Qpart[((int64_t)blockIdx.y * m + i) * RP + QA * tc + k] = q[x][k];
     }
-    resid_acc += (double)resid;
+    resid_store_warp(resid, resid_part, blockIdx.y, nrb, rb);
   }
-  resid_acc = block_sum(resid_acc, red);
-  if (t == 0) resid_part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = resid_acc;
 }
 
 // cp.async (16-byte, L2 only) global -> shared copy; src_bytes < 16 zero-fills the rest.
@@ -917,7 +923,6 @@ __device__ __forceinline__ void sweep_mxp_body(const VGrid& vg__, const TMs* __r
   float* CsT = Us + 2 * BM * LDU;                                     // [RP][BN]
   float* Vs = CsT + RP * BN;                                          // [BN][RP]
   float* Xs = Vs + BN * RP;                                           // [BM][kMxLDX]
-  __shared__ double red[32];
   const double mu_d = st->mu, mu_next = fmin(st->mu_max, st->rho * mu_d);
   const float mu = (float)mu_d, inv_mu = (float)(1.0 / mu_d), dcoef = (float)(1.0 / mu_d + 1.0 / mu_next);
   const int64_t jbeg = (int64_t)blockIdx.y * cols_per_split;
@@ -970,7 +975,6 @@ __device__ __forceinline__ void sweep_mxp_body(const VGrid& vg__, const TMs* __r
   if (ntile == 1) load_cv(jbeg);
   float q[2][QA];
   float resid = 0.f;
-  double resid_acc = 0.0;
   for (int64_t k = 0; k < total; ++k) {
     const int64_t rb = blockIdx.x + (k / ntile) * gridDim.x, i0 = rb * BM;
     const int tile = (int)(k % ntile);
@@ -1091,12 +1095,10 @@ __device__ __forceinline__ void sweep_mxp_body(const VGrid& vg__, const TMs* __r
 #pragma unroll
           for (int c = 0; c < QA; ++c) Qpart[((int64_t)blockIdx.y * m + i) * RP + QA * tc + c] = q[x][c];
       }
-      resid_acc += (double)resid;
+      resid_store_warp(resid, resid_part, blockIdx.y, nrb, rb);
     }
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  resid_acc = block_sum(resid_acc, red);
-  if (t == 0) resid_part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = resid_acc;
 }
 
 template <typename TMs, int RP>
@@ -1743,8 +1745,10 @@ cudaError_t launch_sweep(const Shape& s, const Buffers& b, bool fp64, int u_cur,
 }
 
 cudaError_t launch_iter_end(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st) {
-  // the mixed SIMT sweep writes one residual partial per CTA, the others one per 32-row block
-  const int count = mx_path(s, fp64) ? s.mx_grid_x * s.nsplit : s.resid_parts;
+  // the mixed SIMT sweep writes one residual partial per (column split, 64-row block, warp), the
+  // float64 SIMT sweep one per 32-row block and split, the tensor-core sweep one per CTA
+  const int count = mx_path(s, fp64) ? s.nsplit * (int)((s.m + 63) / 64) * 8
+                                     : (b.tc ? s.resid_parts : s.sweep_grid_x * s.nsplit);
   launch_k<&iter_end_body, 1024>(1, 1024, 0, st, b.resid_part, count, b.st);
   return cudaGetLastError();
 }
