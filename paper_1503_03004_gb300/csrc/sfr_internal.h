@@ -145,8 +145,9 @@ struct Buffers {
 
 cudaError_t launch_norm_m(const Shape& s, const Buffers& b, cudaStream_t st);
 cudaError_t launch_init_p(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st);
+// pt: also write P^T as a two-term bfloat16 split into b.t.Ut (the tensor-core W pass operand)
 cudaError_t launch_gram_p(const Shape& s, const Buffers& b, bool fp64, bool sum_parts, cudaStream_t st,
-                          const void* addA = nullptr, const double* H = nullptr);
+                          const void* addA = nullptr, const double* H = nullptr, bool pt = false);
 // Sums the Gram partials into b.Gsum, then runs the r x r projector; fp64 = false (mixed path)
 // stops Newton at the float32 resolution of its Gram.
 cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream_t st, bool fp64 = true);
@@ -155,7 +156,7 @@ cudaError_t launch_reduce_parts(const double* parts, int count, int rpsq, double
                                 cudaStream_t st);
 cudaError_t launch_apply_u(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st);
 cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first, int u_new, cudaStream_t st);
-cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st);
+cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st, bool wp = false);
 cudaError_t launch_apply_v(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st);
 cudaError_t launch_sweep(const Shape& s, const Buffers& b, bool fp64, int u_cur, cudaStream_t st);
 cudaError_t launch_iter_end(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st);

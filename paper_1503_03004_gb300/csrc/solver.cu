@@ -352,9 +352,14 @@ struct Solver {
   cudaEvent_t done_ev[2] = {};        // completion of the last launch of graph A / B
   DevState* host_state2 = nullptr;    // pinned state copies taken after graph A / B
   std::unique_ptr<Solver> aux;        // FR-Nys: solves the second block concurrently (own stream)
+  cudaStream_t side = nullptr;        // tensor-core path: the W pass, beside the U-side projector
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 
   ~Solver() {
     if (aux) aux.reset();
+    if (side) cudaStreamDestroy(side);
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    if (join_ev) cudaEventDestroy(join_ev);
     if (graph) cudaGraphExecDestroy(graph);
     if (graph_b) cudaGraphExecDestroy(graph_b);
     if (host_state) cudaFreeHost(host_state);
@@ -374,6 +379,12 @@ struct Solver {
     if (!host_state2) SFR_CUDA(cudaMallocHost(&host_state2, 2 * sizeof(DevState)));
   }
 
+  void ensure_side() {
+    if (!side) SFR_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    if (!fork_ev) SFR_CUDA(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+    if (!join_ev) SFR_CUDA(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
+  }
+
   void make_events() {
     for (auto& a : ev)
       for (auto& b : a)
@@ -384,13 +395,17 @@ struct Solver {
   // Timed launch of one kernel class: events around it when profiling.
   template <typename F>
   void timed_launch(int slot, int k, F&& f) {
+    timed_launch_on(stream, slot, k, f);
+  }
+  template <typename F>
+  void timed_launch_on(cudaStream_t on, int slot, int k, F&& f) {
     // inside stream capture an event record becomes a graph node only with the external flag,
     // and that flag is refused outside capture
     const unsigned flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     const bool timed = profile && (k == 0 || !profile_pass_only);
-    if (timed) SFR_CUDA(cudaEventRecordWithFlags(ev[slot][k][0], stream, flags));
+    if (timed) SFR_CUDA(cudaEventRecordWithFlags(ev[slot][k][0], on, flags));
     SFR_CUDA(f());
-    if (timed) SFR_CUDA(cudaEventRecordWithFlags(ev[slot][k][1], stream, flags));
+    if (timed) SFR_CUDA(cudaEventRecordWithFlags(ev[slot][k][1], on, flags));
   }
 
   // Accumulate the event durations of the iterations that ran in `slot`s [first, first + count).
@@ -454,11 +469,28 @@ struct Solver {
       SFR_CUDA(launch_gram_p(s, b, false, false, st));
       kernels += 2;
     }
-    timed_launch(slot, 2, [&] { return launch_rxr(s, b, false, st, false); });  // T_U
-    SFR_CUDA(launch_apply_u(s, b, false, first, st));  // U_bar = P T_U, with its TF32 split and U^T
     const int u_new = 1 - b.u_cur;
-    timed_launch(slot, 1, [&] { return tc_launch_wpass(s, maps, first, static_cast<float*>(b.Wpart), b.st, st); });
-    SFR_CUDA(launch_wfinal(s, b, false, first, st));                          // W, G_W partials
+    if (first) {  // W = M^T U_bar
+      timed_launch(slot, 2, [&] { return launch_rxr(s, b, false, st, false); });  // T_U
+      SFR_CUDA(launch_apply_u(s, b, false, first, st));  // U_bar = P T_U, its TF32 split and U^T
+      timed_launch(slot, 1, [&] { return tc_launch_wpass(s, maps, true, static_cast<float*>(b.Wpart), b.st, st); });
+      SFR_CUDA(launch_wfinal(s, b, false, true, st));  // W, G_W partials
+    } else {
+      // W = X^T U_bar = X^T P T_U = (C_old (U_old^T P) + Delta^T P) T_U: the W pass forms
+      // Delta^T P, which does not wait for the U-side projector, so it runs on the side stream
+      // beside it; W = (Delta^T P) T_U + C_old H (H = U_old^T U_bar) after both.  (Issuing the
+      // projector on a high-priority side stream instead measured slower.)
+      ensure_side();
+      SFR_CUDA(cudaEventRecord(fork_ev, st));
+      SFR_CUDA(cudaStreamWaitEvent(side, fork_ev, 0));
+      timed_launch_on(side, slot, 1,
+                      [&] { return tc_launch_wpass_p(s, maps, static_cast<float*>(b.Wpart), b.st, side); });
+      SFR_CUDA(cudaEventRecord(join_ev, side));
+      timed_launch(slot, 2, [&] { return launch_rxr(s, b, false, st, false); });  // T_U
+      SFR_CUDA(launch_apply_u(s, b, false, false, st));  // U_bar = P T_U, its TF32 split, H partials
+      SFR_CUDA(cudaStreamWaitEvent(st, join_ev, 0));
+      SFR_CUDA(launch_wfinal(s, b, false, false, st, true));  // W, G_W partials
+    }
     timed_launch(slot, 3, [&] { return launch_rxr(s, b, true, st, false); });  // T_V, B_bar, T_C
     SFR_CUDA(launch_apply_v(s, b, false, st));  // V_bar, C, with the TF32 split of C and V^T
     const int y_in = b.Y[0] == b.t.Y[0] ? 0 : 1;
@@ -466,8 +498,9 @@ struct Solver {
       return tc_launch_sweep(s, maps, b.t, y_in, static_cast<float*>(b.Qpart), b.resid_part, b.st, st);
     });
     SFR_CUDA(launch_iter_end(s, b, false, st));
-    // P_{k+1} = U_bar B_bar + Delta V_bar  (L V_bar = U_bar B_bar since V_bar^T V_bar = I)
-    SFR_CUDA(launch_gram_p(s, b, false, true, st, b.U[u_new], b.B));
+    // P_{k+1} = U_bar B_bar + Delta V_bar  (L V_bar = U_bar B_bar since V_bar^T V_bar = I), with
+    // P^T for the next W pass
+    SFR_CUDA(launch_gram_p(s, b, false, true, st, b.U[u_new], b.B, true));
     // launches: projector 2 + 2 (partial sums, cluster kernel), transforms 2, W pass 1, W final
     // 1 (+1 H sum after the first, +1 wide pre-sum of many W partials), sweep 1, iteration end 1,
     // P / Gram 1

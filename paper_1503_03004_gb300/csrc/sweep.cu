@@ -234,16 +234,20 @@ __device__ __forceinline__ void store_tile(TC* s, int t, const TC (&v)[TileIdx<R
 
 // ---------------------------------------------------------------- thin reduce + Gram partials
 // For every 64-row tile handled by this CTA (tiles blockIdx.x, blockIdx.x + gridDim.x, ...):
-// out[i][:] = sum_s parts[s][i][:]  (+ addA[i][:] H when addA != nullptr), then the CTA's
-// Gram partial gpart[cta] = sum over its rows of out[i]^T out[i]  (r x r).
-// nparts == 0 leaves `out` as it is and only forms the Gram partial.  q_ctas > 0: the partials
-// come from the persistent tensor-core sweep (q_tiles column tiles per 128-row block), and rows of
-// block rb have tc_q_slots(rb) of them.
+// out[i][:] = sum_s parts[s][i][:] (times T2 when T2 != nullptr) (+ addA[i][:] H when
+// addA != nullptr), then the CTA's Gram partial gpart[cta] = sum over its rows of
+// out[i]^T out[i]  (r x r).  With `trans` (float, RP = 64), out is also written transposed as a
+// two-term bfloat16 split: row a holds x rounded to bfloat16, row RP + a the rounding of the rest
+// (ld ldt).  nparts == 0 leaves `out` as it is and only forms the Gram partial.  q_ctas > 0: the
+// partials come from the persistent tensor-core sweep (q_tiles column tiles per 128-row block),
+// and rows of block rb have tc_q_slots(rb) of them.
 template <typename TC, int RP>
 __device__ __forceinline__ void thin_gram_body(const VGrid& vg__, const TC* __restrict__ parts, int nparts, int64_t part_stride,
                                                         TC* __restrict__ out, int64_t rows, const TC* __restrict__ addA,
                                                         const double* __restrict__ H, double* __restrict__ gpart,
-                                                        const DevState* st, int q_ctas, int64_t q_tiles) {
+                                                        const DevState* st, int q_ctas, int64_t q_tiles,
+                                                        const double* __restrict__ T2, __nv_bfloat16* __restrict__ trans,
+                                                        int64_t ldt) {
   pdl_enter();
   SFR_VGRID(vg__);
   if (stopped(st)) return;
@@ -252,9 +256,11 @@ __device__ __forceinline__ void thin_gram_body(const VGrid& vg__, const TC* __re
   TC* tile = reinterpret_cast<TC*>(smem_raw);   // [kGramRows][LDT]
   TC* arow = tile + kGramRows * LDT;              // [kGramRows][LDT]  addA rows
   TC* Hs = arow + kGramRows * LDT;                // [RP][LDT]
+  TC* T2s = Hs + RP * LDT;                        // [RP][LDT]
   TC* red = tile;                                 // after the tiles: 256 x 16 Gram scratch
   const int t = threadIdx.x;
   if (addA) load_rr<TC, RP, LDT>(H, Hs, t);
+  if (T2) load_rr<TC, RP, LDT>(T2, T2s, t);
   TC g[4][4];
   zero44(g);
   const int64_t ntiles = (rows + kGramRows - 1) / kGramRows;
@@ -285,6 +291,20 @@ __device__ __forceinline__ void thin_gram_body(const VGrid& vg__, const TC* __re
     if (addA) store_tile<TC, RP, LDT>(arow, t, av);
     __syncthreads();
     if (nparts > 0) {
+      if (T2) {  // tile <- (sum of the partials) T2
+        TC acc[4][4];
+        zero44(acc);
+        block_mm<TC, kGramRows, RP, RP, false>(tile, LDT, T2s, LDT, acc, t);
+        __syncthreads();  // every read of the tile is done
+        if (t < (kGramRows / 4) * (RP / 4)) {
+          const int r0 = 4 * (t / (RP / 4)), c0 = 4 * (t % (RP / 4));
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) tile[(r0 + x) * LDT + c0 + y] = acc[x][y];
+        }
+        __syncthreads();
+      }
       if (addA) {
         TC acc[4][4];
         zero44(acc);
@@ -302,6 +322,21 @@ __device__ __forceinline__ void thin_gram_body(const VGrid& vg__, const TC* __re
         const int ii = e / RP, a = e % RP;
         const int64_t i = i0 + ii;
         if (i < rows) out[i * RP + a] = tile[ii * LDT + a];
+      }
+    }
+    if constexpr (std::is_same<TC, float>::value) {
+      if (trans) {  // column a of the tile -> rows a (hi) and RP + a (lo) of the transpose
+#pragma unroll
+        for (int q = 0; q < TileIdx<RP>::PER; ++q) {
+          const int e = t + q * kThinThreads, a = e / kGramRows, ii = e % kGramRows;
+          const int64_t i = i0 + ii;
+          if (i < rows) {
+            const float x = tile[ii * LDT + a];
+            const __nv_bfloat16 hb = __float2bfloat16_rn(x);
+            trans[(int64_t)a * ldt + i] = hb;
+            trans[(int64_t)(RP + a) * ldt + i] = __float2bfloat16_rn(x - __bfloat162float(hb));
+          }
+        }
       }
     }
     gram_slice<TC, RP>(tile, tile, LDT, g, t);
@@ -1456,7 +1491,7 @@ cudaError_t by_prec(bool fp64, F&& f) {
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 template <typename TC, int RP>
-size_t gram_smem() { return sizeof(TC) * std::max<size_t>((size_t)(2 * kGramRows + RP) * (RP + 4), 16 * kThinThreads); }
+size_t gram_smem() { return sizeof(TC) * std::max<size_t>((size_t)(2 * kGramRows + 2 * RP) * (RP + 4), 16 * kThinThreads); }
 template <typename TC, int RP>
 size_t transform_smem() {
   // the Gram scratch (256 x 16) starts at the source-row tile, 2 RP (RP + 4) elements in
@@ -1541,7 +1576,7 @@ cudaError_t launch_init_p(const Shape& s, const Buffers& b, bool fp64, cudaStrea
 }
 
 cudaError_t launch_gram_p(const Shape& s, const Buffers& b, bool fp64, bool sum_parts, cudaStream_t st,
-                          const void* addA, const double* H) {
+                          const void* addA, const double* H, bool pt) {
   return by_prec(fp64, [&](auto tc) {
     using TC = decltype(tc);
     return by_rank(s.rp, [&](auto rpc) {
@@ -1549,7 +1584,8 @@ cudaError_t launch_gram_p(const Shape& s, const Buffers& b, bool fp64, bool sum_
       const size_t sm = gram_smem<TC, RP>();
       launch_k<&thin_gram_body<TC, RP>, 256>(s.gp_blocks, 256, sm, st,
           static_cast<const TC*>(b.Qpart), sum_parts ? s.nsplit : 0, s.m * RP, static_cast<TC*>(b.P), s.m,
-          static_cast<const TC*>(addA), H, b.GPpart, b.st, s.q_ctas, (s.n + 63) / 64);
+          static_cast<const TC*>(addA), H, b.GPpart, b.st, s.q_ctas, (s.n + 63) / 64, (const double*)nullptr,
+          pt ? static_cast<__nv_bfloat16*>(b.t.Ut) : nullptr, (int64_t)b.t.ldd);
       return cudaGetLastError();
     });
   });
@@ -1563,14 +1599,16 @@ cudaError_t launch_apply_u(const Shape& s, const Buffers& b, bool fp64, bool fir
     return by_rank(s.rp, [&](auto rpc) {
       constexpr int RP = decltype(rpc)::value;
       const size_t sm = transform_smem<TC, RP>();
-      // tensor-core path: also the TF32 split of U_new and its bfloat16 transpose (MMA operands)
+      // tensor-core path: also the TF32 split of U_new (the sweep's operand) and, for the first
+      // W pass, its bfloat16 transpose (later W passes take P^T from the P / Gram kernel)
       // (Algorithm 4: the two-term bfloat16 split of U^T instead, the B operand of M^T U)
       const bool tcx = b.tc && RP == 64 && !fp64, tf = tcx && !b.full;
       launch_k<&row_transform_body<TC, RP>, 256>(s.gp_blocks, 256, sm, st,
           static_cast<const TC*>(b.P), s.m, b.TU, static_cast<TC*>(b.U[u_new]), nullptr, nullptr,
           first ? nullptr : static_cast<const TC*>(b.U[u_old]), first ? nullptr : b.Hpart, b.st,
-          tf ? b.t.Uh : nullptr, tf ? b.t.Ul : nullptr, tcx ? static_cast<__nv_bfloat16*>(b.t.Ut) : nullptr,
-          (int64_t)b.t.ldd, b.full ? 1 : 0);
+          tf ? b.t.Uh : nullptr, tf ? b.t.Ul : nullptr,
+          (tcx && (first || b.full)) ? static_cast<__nv_bfloat16*>(b.t.Ut) : nullptr, (int64_t)b.t.ldd,
+          b.full ? 1 : 0);
       return cudaGetLastError();
     });
   });
@@ -1631,8 +1669,9 @@ cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first
   });
 }
 
-cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st) {
-  // W = sum_c Wpart[c] (+ C_old H, H = U_old^T U_new), then Gram partials of W.
+cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st, bool wp) {
+  // W = sum_c Wpart[c] (+ C_old H, H = U_old^T U_new), then Gram partials of W.  wp: the partials
+  // hold Delta^T P instead of Delta^T U_new, and W = (sum_c Wpart[c]) T_U + C_old H.
   // H = sum of the U_old^T U_new partials, reduced into the slot after the partials.
   if (!first) {
     launch_k<&reduce_sq_body<double>, 1024>(cdiv(s.rp * s.rp, 32), reduce_threads(s.gp_blocks), 0, st,
@@ -1660,7 +1699,8 @@ cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool firs
       }
       launch_k<&thin_gram_body<TC, RP>, 256>(s.gw_blocks, 256, sm, st,
           static_cast<const TC*>(b.Wpart), nparts, s.n * RP, static_cast<TC*>(b.W), s.n,
-          first ? nullptr : static_cast<const TC*>(b.C), first ? nullptr : H, b.GWpart, b.st, 0, (int64_t)0);
+          first ? nullptr : static_cast<const TC*>(b.C), first ? nullptr : H, b.GWpart, b.st, 0, (int64_t)0,
+          wp ? (const double*)b.TU : (const double*)nullptr, (__nv_bfloat16*)nullptr, (int64_t)0);
       return cudaGetLastError();
     });
   });

@@ -876,6 +876,7 @@ cudaError_t tc_make_maps(const Shape& s, const TcBuffers& t, const void* M, int6
   ok &= make_map(&maps->D, t.D, BF, s.n, s.m, 2 * t.ldy, 64, 128);
   ok &= make_map(&maps->D_w, t.D, BF, s.n, s.m, 2 * t.ldy, 64, 64);
   ok &= make_map(&maps->Ut, t.Ut, BF, s.m, 64, 2 * t.ldd, 64, 64);
+  ok &= make_map(&maps->Ut2, t.Ut, BF, s.m, 128, 2 * t.ldd, 64, 128);  // P^T as a two-term split
   ok &= make_map(&maps->Ch, t.Ch, F32, 64, s.n, 256, 32, 64);
   ok &= make_map(&maps->Cl, t.Cl, F32, 64, s.n, 256, 32, 64);
   ok &= make_map(&maps->Vt, t.Vt, BF, s.n, 64, 2 * t.ldy, 64, 64);
@@ -890,6 +891,15 @@ cudaError_t tc_launch_wpass(const Shape& s, const TcMaps& mp, bool first, float*
   dim3 grid(cdiv(s.n, 128), s.nchunk);
   launch_pdl(wpass_tc_kernel<1>, grid, 192, wpass_smem<1>(), st, first ? mp.M_w : mp.D_w, mp.Ut, s.m, s.n, s.rows_per_chunk,
                                                           Wpart, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_wpass_p(const Shape& s, const TcMaps& mp, float* Wpart, DevState* dst, cudaStream_t st) {
+  cudaError_t e =
+      cudaFuncSetAttribute(wpass_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wpass_smem<2>());
+  if (e != cudaSuccess) return e;
+  dim3 grid(cdiv(s.n, 128), s.nchunk);
+  launch_pdl(wpass_tc_kernel<2>, grid, 192, wpass_smem<2>(), st, mp.D_w, mp.Ut2, s.m, s.n, s.rows_per_chunk, Wpart, dst);
   return cudaGetLastError();
 }
 

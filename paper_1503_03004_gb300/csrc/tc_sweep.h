@@ -19,8 +19,9 @@ struct TcBuffers {
   int64_t ldd;         // m rounded up to 64 (leading dimension of U^T)
   float* Uh;           // m x 64: U rounded to TF32
   float* Ul;           // m x 64: U - Uh
-  void* Ut;            // 128 x ldd bfloat16: U^T in rows 0-63 (Algorithm 4: rows 64-127 hold the
-                       // bfloat16 rounding of U^T - rows 0-63)
+  void* Ut;            // 128 x ldd bfloat16, the B operand of the W pass: U_1^T in rows 0-63 for
+                       // FR-ADM's first W pass, then P^T as a two-term split (rows 64-127 hold the
+                       // bfloat16 rounding of P^T - rows 0-63); Algorithm 4: the same split of U^T
   float* Ch;           // n x 64: C rounded to TF32
   float* Cl;           // n x 64: C - Ch
   void* Vt;            // 128 x ldy bfloat16: V^T in rows 0-63 (Algorithm 4: plus its low part)
@@ -28,7 +29,7 @@ struct TcBuffers {
 
 struct TcMaps {
   CUtensorMap M, M_w, Y[2], D, D_w, Ut, Ch, Cl, Vt;  // *_w: 64 x 64 boxes for the W pass
-  CUtensorMap Ut2, Vt2;  // Algorithm 4: the two-term splits, 64 x 128 boxes
+  CUtensorMap Ut2, Vt2;  // two-term splits, 64 x 128 boxes (FR-ADM: P^T in Ut; Algorithm 4: U^T, V^T)
 };
 
 bool tc_supported(const Shape& s, int m_dtype, int64_t ldm);
@@ -45,6 +46,8 @@ cudaError_t tc_launch_sweep(const Shape& s, const TcMaps& mp, const TcBuffers& t
 // W = M^T U partials (the W pass with the two-term split of U).
 cudaError_t tc_make_full_maps(const Shape& s, const TcBuffers& t, const void* M, int64_t ldm, TcMaps* maps);
 cudaError_t tc_launch_full_ppass(const Shape& s, const TcMaps& mp, float* Qpart, DevState* dst, cudaStream_t st);
+// W pass partials Delta^T P from the two-term bfloat16 split of P^T (W = Delta^T P T_U + C H).
+cudaError_t tc_launch_wpass_p(const Shape& s, const TcMaps& mp, float* Wpart, DevState* dst, cudaStream_t st);
 cudaError_t tc_launch_full_wpass(const Shape& s, const TcMaps& mp, float* Wpart, DevState* dst, cudaStream_t st);
 // S = P_ST_{1/mu}(M - L + Y / mu) (and L when non-null) from the last iteration's factors, mu
 // and multiplier Y = t.Y[y_in]; S / L are m x n with leading dimension lds, float64 when
