@@ -231,8 +231,9 @@ class BatchEngine {
     stage(2, [&] { return launch_rxr(s, b, false, st_, false); });   // T_U = B (B G_P B)^{-1/2}
     stage(3, [&] { return launch_apply_u(s, b, false, first, st_); });  // U = P T_U
     const int u_new = 1 - b.u_cur;
-    stage(4, [&] { return launch_wpass(s, b, false, first, u_new, st_); });
-    stage(5, [&] { return launch_wfinal(s, b, false, first, st_); });
+    // W = (Delta^T P) T_U + C_old H after the first iteration, as sfr_solve forms it
+    stage(4, [&] { return launch_wpass(s, b, false, first, u_new, st_, !first); });
+    stage(5, [&] { return launch_wfinal(s, b, false, first, st_, !first); });
     stage(6, [&] { return launch_rxr(s, b, true, st_, false); });    // T_V, B, T_C
     stage(7, [&] { return launch_apply_v(s, b, false, st_); });
     stage(8, [&] { return launch_sweep(s, b, false, u_new, st_); });

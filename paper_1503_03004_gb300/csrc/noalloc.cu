@@ -68,8 +68,9 @@ void iteration(const Shape& s, Buffers& b, bool fp64, bool first, cudaStream_t s
   NA_CUDA(launch_rxr(s, b, false, st));
   NA_CUDA(launch_apply_u(s, b, fp64, first, st));
   const int u_new = 1 - b.u_cur;
-  NA_CUDA(launch_wpass(s, b, fp64, first, u_new, st));
-  NA_CUDA(launch_wfinal(s, b, fp64, first, st));
+  const bool wp = !first && mx_path(s, fp64);  // W = (Delta^T P) T_U + C_old H, as sfr_solve forms it
+  NA_CUDA(launch_wpass(s, b, fp64, first, u_new, st, wp));
+  NA_CUDA(launch_wfinal(s, b, fp64, first, st, wp));
   NA_CUDA(launch_rxr(s, b, true, st));
   NA_CUDA(launch_apply_v(s, b, fp64, st));
   NA_CUDA(launch_sweep(s, b, fp64, u_new, st));

@@ -155,7 +155,9 @@ cudaError_t launch_rxr(const Shape& s, const Buffers& b, bool v_side, cudaStream
 cudaError_t launch_reduce_parts(const double* parts, int count, int rpsq, double* out, const DevState* dst,
                                 cudaStream_t st);
 cudaError_t launch_apply_u(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st);
-cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first, int u_new, cudaStream_t st);
+// wp: the mixed SIMT path's partials of Delta^T P instead of Delta^T U_new (W = (Delta^T P) T_U + C H)
+cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first, int u_new, cudaStream_t st,
+                         bool wp = false);
 cudaError_t launch_wfinal(const Shape& s, const Buffers& b, bool fp64, bool first, cudaStream_t st, bool wp = false);
 cudaError_t launch_apply_v(const Shape& s, const Buffers& b, bool fp64, cudaStream_t st);
 cudaError_t launch_sweep(const Shape& s, const Buffers& b, bool fp64, int u_cur, cudaStream_t st);

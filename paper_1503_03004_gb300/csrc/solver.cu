@@ -444,11 +444,25 @@ struct Solver {
       SFR_CUDA(launch_gram_p(s, b, fp64, false, st));
       kernels += 2;
     }
-    timed_launch(slot, 2, [&] { return launch_rxr(s, b, false, st, fp64); });  // T_U = B (B G_P B)^{-1/2}
-    SFR_CUDA(launch_apply_u(s, b, fp64, first, st));                          // U_bar = P T_U
     const int u_new = 1 - b.u_cur;
-    timed_launch(slot, 1, [&] { return launch_wpass(s, b, fp64, first, u_new, st); });  // X^T U_bar partials
-    SFR_CUDA(launch_wfinal(s, b, fp64, first, st));                           // W, G_W partials
+    if (!first && mx_path(s, fp64)) {
+      // as on the tensor-core path: the W pass forms Delta^T P beside the U-side projector, and
+      // W = (Delta^T P) T_U + C_old H after both
+      ensure_side();
+      SFR_CUDA(cudaEventRecord(fork_ev, st));
+      SFR_CUDA(cudaStreamWaitEvent(side, fork_ev, 0));
+      timed_launch_on(side, slot, 1, [&] { return launch_wpass(s, b, fp64, false, u_new, side, true); });
+      SFR_CUDA(cudaEventRecord(join_ev, side));
+      timed_launch(slot, 2, [&] { return launch_rxr(s, b, false, st, fp64); });  // T_U
+      SFR_CUDA(launch_apply_u(s, b, fp64, false, st));                          // U_bar = P T_U, H partials
+      SFR_CUDA(cudaStreamWaitEvent(st, join_ev, 0));
+      SFR_CUDA(launch_wfinal(s, b, fp64, false, st, true));                     // W, G_W partials
+    } else {
+      timed_launch(slot, 2, [&] { return launch_rxr(s, b, false, st, fp64); });  // T_U = B (B G_P B)^{-1/2}
+      SFR_CUDA(launch_apply_u(s, b, fp64, first, st));                          // U_bar = P T_U
+      timed_launch(slot, 1, [&] { return launch_wpass(s, b, fp64, first, u_new, st); });  // X^T U_bar partials
+      SFR_CUDA(launch_wfinal(s, b, fp64, first, st));                           // W, G_W partials
+    }
     timed_launch(slot, 3, [&] { return launch_rxr(s, b, true, st, fp64); });   // T_V, B_bar, T_C
     SFR_CUDA(launch_apply_v(s, b, fp64, st));                                 // V_bar, C
     timed_launch(slot, 0, [&] { return launch_sweep(s, b, fp64, u_new, st); });  // S/Y steps, Delta, next P

@@ -1614,7 +1614,8 @@ cudaError_t launch_apply_u(const Shape& s, const Buffers& b, bool fp64, bool fir
   });
 }
 
-cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first, int u_new, cudaStream_t st) {
+cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first, int u_new, cudaStream_t st,
+                         bool wp) {
   dim3 grid(s.wpass_grid_x, s.nchunk);
   if (mx_path(s, fp64)) {
     const bool vec = first ? mx_vec(s, b) : b.ldy % 4 == 0;
@@ -1623,7 +1624,8 @@ cudaError_t launch_wpass(const Shape& s, const Buffers& b, bool fp64, bool first
       if constexpr (RP > 32) {
         return cudaErrorInvalidValue;
       } else {
-        const float* U = static_cast<const float*>(b.U[u_new]);
+        // wp (after the first iteration): Delta^T P, the operand that does not wait for T_U
+        const float* U = static_cast<const float*>(wp && !first ? b.P : b.U[u_new]);
         float* Wp = static_cast<float*>(b.Wpart);
         auto go = [&](auto tag, auto src, int64_t lds) {
           return launch_k<decltype(tag)::value, 256>(grid, 256, 0, st, src, lds, s.m, s.n, s.rows_per_chunk, U, Wp,
