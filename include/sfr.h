@@ -81,8 +81,9 @@ typedef struct {
   void* cuda_stream;        /* cudaStream_t for sfr_solve; NULL = a stream the ctx creates */
   int profile;              /* 1: time the sweep (or P pass), W-pass and r x r kernels of
                                sfr_solve / sfr_fixed_rank_opt_full with CUDA events on the
-                               solve stream (see sfr_stats); 2: time the sweep (or P pass) only
-                               (fewer event records inside the iteration); 0: no timing    */
+                               solve stream (see sfr_stats); 2: time the sweep (or P pass) only,
+                               in the first iteration and every fourth after it (an event
+                               record splits the iteration's launch chain); 0: no timing  */
   int max_batch;            /* > 0: sfr_submit runs requests on the mixed-precision SIMT path
                                (FR-ADM, device buffers, r <= 32) in a grouped engine with up to
                                this many live problems: every step advances each of them by one

@@ -135,6 +135,19 @@ size_t static_smem() {
   return v;
 }
 
+// The highest stream priority of the device (queried once).
+inline int top_priority() {
+  static const int v = [] {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return greatest;
+  }();
+  return v;
+}
+
 // Opts the kernel in to `smem` bytes of dynamic shared memory where static + dynamic exceed the
 // default 48 KB (a grouped kernel adds a few bytes of its own to the body's static use).
 template <auto Kern>
@@ -185,15 +198,19 @@ template <typename... T> struct BodyTraits<void (*)(const VGrid&, T...)> {
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute at[2];
+    cudaLaunchAttribute at[3];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = cluster;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // see pdl_enter
     at[1].val.programmaticStreamSerializationAllowed = 1;
+    // the highest scheduling priority: a cluster needs a group of free SMs at once, which
+    // kernels of other streams would otherwise take as they free up
+    at[2].id = cudaLaunchAttributePriority;
+    at[2].val.priority = top_priority();
     cfg.attrs = at;
-    cfg.numAttrs = 2;
+    cfg.numAttrs = 3;
     return cudaLaunchKernelEx(&cfg, k, static_cast<T>(a)...);
   }
   template <auto Body, int NT>

@@ -58,11 +58,37 @@ template <typename TMs>
 __global__ void norm_m_kernel(const TMs* __restrict__ M, int64_t m, int64_t n, int64_t ldm, double* part) {
   pdl_enter();
   __shared__ double red[32];
+  constexpr int64_t V = 16 / sizeof(TMs);  // elements per 16-byte load
   double acc = 0.0;
   for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
+    const TMs* row = M + i * ldm;
+    // the elements before the row's first 16-byte boundary, whole 16-byte chunks, the tail
+    const int64_t head = min(n, (int64_t)(((16 - ((uintptr_t)row & 15)) & 15) / sizeof(TMs)));
+    const int64_t nv = (n - head) / V;
     float a = 0.f;
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-      float v = ld_as<float, TMs>(M + i * ldm + j);
+    for (int64_t j = threadIdx.x; j < head; j += blockDim.x) {
+      const float v = ld_as<float, TMs>(row + j);
+      a = fmaf(v, v, a);
+    }
+    const uint4* vrow = reinterpret_cast<const uint4*>(row + head);
+#pragma unroll 4
+    for (int64_t c = threadIdx.x; c < nv; c += blockDim.x) {
+      const uint4 w = __ldg(vrow + c);
+      const uint32_t q[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if constexpr (sizeof(TMs) == 2) {  // two bfloat16 values: their bits are a float's top half
+          const float lo = __uint_as_float(q[k] << 16), hi = __uint_as_float(q[k] & 0xffff0000u);
+          a = fmaf(lo, lo, a);
+          a = fmaf(hi, hi, a);
+        } else {
+          const float v = __uint_as_float(q[k]);
+          a = fmaf(v, v, a);
+        }
+      }
+    }
+    for (int64_t j = head + nv * V + threadIdx.x; j < n; j += blockDim.x) {
+      const float v = ld_as<float, TMs>(row + j);
       a = fmaf(v, v, a);
     }
     acc += (double)a;
@@ -347,11 +373,15 @@ __device__ __forceinline__ void thin_gram_body(const VGrid& vg__, const TC* __re
 // Sum of `count` partials of rpsq values into out, in a fixed order: warp w of a CTA of nw warps
 // adds the partials w, w + nw, w + 2 nw, ... of 32 consecutive entries (four loads in flight),
 // then the warp sums are added in warp order.  out may be the first partial (each entry is read
-// and written by one CTA).  nw = blockDim.x / 32 <= 32.
-template <typename T>
+// and written by one CTA).  nw = blockDim.x / 32 <= 32.  EARLY: the following kernel may be
+// scheduled before this one's wait (pdl_enter_early).
+template <typename T, bool EARLY = false>
 __device__ __forceinline__ void reduce_sq_body(const VGrid& vg__, const T* parts, int64_t count, int64_t rpsq, T* out,
                                                          const DevState* st) {
-  pdl_enter();
+  if constexpr (EARLY)
+    pdl_enter_early();
+  else
+    pdl_enter();
   SFR_VGRID(vg__);
   if (stopped(st)) return;
   __shared__ T red[32][32];
@@ -1329,8 +1359,14 @@ __device__ __forceinline__ void iter_end_body(const VGrid& vg__, const double* _
   double v = 0.0;
 #pragma unroll 8
   for (int c = threadIdx.x; c < count; c += blockDim.x) v += resid_part[c];
-  v = block_sum(v, red);
+  // warp sums, then thread 0 adds them in warp order (the float64 pipe is narrow on this part:
+  // the other threads do not repeat that sum)
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
   if (threadIdx.x == 0) {
+    v = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) v += red[w];
     const double mu = st->mu;
     const double res = sqrt(v) / mu / st->norm_m;
     st->res = res;
@@ -1545,9 +1581,12 @@ cudaError_t launch_copy_m(const Shape& s, const void* M, int64_t ldm, void* Mc, 
 // threads of the partial-sum kernel: 8 warps, 32 when there are many partials to walk
 inline int reduce_threads(int64_t count) { return count >= 256 ? 1024 : 256; }
 
+// The projector's Gram sum: its successor, the projector's cluster, is queued early (see
+// pdl_enter_early) so that it is placed before the W pass that the other stream starts when the
+// Gram kernel ends.
 cudaError_t launch_reduce_parts(const double* parts, int count, int rpsq, double* out, const DevState* dst,
                                 cudaStream_t st) {
-  launch_k<&reduce_sq_body<double>, 1024>(cdiv(rpsq, 32), reduce_threads(count), 0, st, parts, (int64_t)count,
+  launch_k<&reduce_sq_body<double, true>, 1024>(cdiv(rpsq, 32), reduce_threads(count), 0, st, parts, (int64_t)count,
                                            (int64_t)rpsq, out, dst);
   return cudaGetLastError();
 }

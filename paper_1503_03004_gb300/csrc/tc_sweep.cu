@@ -34,8 +34,9 @@ constexpr int NSTAGE = 2;
 constexpr int NCB = 3;  // C tile buffers (they come from L2 about 3 us after issue)
 constexpr uint32_t OFF_C = 0;           // C tiles, NCB buffers x 32 KB: hi (2 K-atoms x 64 rows x 128 B) then lo
 constexpr uint32_t C_BUF = 32768;
-constexpr uint32_t OFF_ST = NCB * 32768;      // input stages, 3 x 32 KB: M tile (128 x 64 bf16), Y tile; each epilogue
-constexpr uint32_t ST_BYTES = 32768;    // warp releases a stage as soon as it has its M and Y values in registers
+constexpr uint32_t OFF_ST = NCB * 32768;      // input stages, NSTAGE x 32 KB: M tile (128 x 64 bf16), Y tile; each
+constexpr uint32_t ST_BYTES = 32768;    // epilogue warp releases a stage once it has its M and Y values in registers
+                                        // and the previous tile's bulk stores have read their source
 constexpr uint32_t ST_Y = 16384;
 constexpr int NVT = 4;                  // V^T tiles (64 x 64 bf16), a ring of 4: held until Delta V_bar is done
 constexpr uint32_t OFF_VT = OFF_ST + NSTAGE * ST_BYTES;
@@ -439,7 +440,6 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
         ywr[cc] = *reinterpret_cast<const uint4*>(ms + ST_Y + off);
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&B.stage_empty[s]);  // this warp is done with the stage
       tc_fence_after();
       float L[kEpiCols];
 #pragma unroll
@@ -463,6 +463,12 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_tc_kernel(const __grid
       if (t >= 1) mbar_wait(&B.d_empty, (t - 1) & 1, abort);
       if (tid == 0 && t >= 1) tma_store_wait_read0();
       named_bar(1, kEpiThreads);
+      // the stage goes back to the producer only now, after the bulk stores of tile t - 1 have
+      // read their shared-memory source: with the release right after the stage reads, the
+      // stage's next TMA load could overlap those stores' reads, and on GB300 about 450 of the
+      // 67 M values that one 8192^2 sweep stored (upper 16-byte halves of 32-byte sectors in the
+      // first rows of odd tiles) then differed from run to run
+      if (lane == 0) mbar_arrive(&B.stage_empty[s]);
 #pragma unroll
       for (int cc = 0; cc < kEpiChunks; ++cc) {
         const uint32_t off = sw128(row, grp * kEpiChunks + cc);

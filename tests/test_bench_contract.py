@@ -1,6 +1,6 @@
 """CPU checks of bench.py's contract: the reference arm (the float64 oracle on the host cores)
-prints the JSON line the driver reads, and the committed ncu traffic summary still matches the
-sweep kernel's source (bench.py reports roofline.traffic only while it does)."""
+prints the JSON line the driver reads, and bench.py reports the committed ncu traffic figure of
+the sweep kernel only while the kernel's source is the one the counters were taken from."""
 import json
 import os
 import subprocess
@@ -26,8 +26,42 @@ def test_reference_arm_prints_the_contract_line():
     assert line["config"]["workload"] == "square16384_r64_bf16_mixed"
 
 
-def test_committed_sweep_traffic_matches_the_kernel_source():
+def _summary():
+    keys = ("traffic_bytes_per_element", "source", "source_until", "source_sha256", "helpers", "helpers_sha256")
+    with open(os.path.join(ROOT, "profiles", "sweep_tc_square8192_r64_bf16.md")) as f:
+        kv = dict(line.strip().split(": ", 1) for line in f if line.startswith("    ") and ": " in line
+                  and line.strip().split(": ", 1)[0] in keys)
+    assert set(kv) == set(keys), "the traffic summary lost one of its fields"
+    return kv
+
+
+def test_sweep_traffic_is_reported_only_for_the_captured_kernel_source():
+    import hashlib
+    kv = _summary()
+    with open(os.path.join(ROOT, kv["source"]), encoding="utf-8") as f:
+        text = f.read()
+    region = text[:text.index(kv["source_until"])]
+    with open(os.path.join(ROOT, kv["helpers"]), "rb") as f:
+        helpers = f.read()
+    same = (hashlib.sha256(region.encode("utf-8")).hexdigest() == kv["source_sha256"]
+            and hashlib.sha256(helpers).hexdigest() == kv["helpers_sha256"])
     t = bench.sweep_traffic(16384, 16384)
-    assert t is not None, "profiles/sweep_tc_square8192_r64_bf16.md no longer matches the sweep kernel source"
-    # DRAM traffic per launch is close to the 8 bytes per element the sweep must move
-    assert 7.0 * 16384 ** 2 <= t <= 8.5 * 16384 ** 2
+    if same:
+        # DRAM traffic per launch is close to the 8 bytes per element the sweep must move
+        assert t is not None and 7.0 * 16384 ** 2 <= t <= 8.5 * 16384 ** 2
+    else:
+        # the kernel changed after the counters were taken: no traffic figure is reported
+        assert t is None
+
+
+def test_sweep_traffic_is_withheld_when_the_kernel_source_changes(tmp_path, monkeypatch):
+    # a copy of the tree whose sweep source differs by one comment line
+    kv = _summary()
+    for rel in ("profiles/sweep_tc_square8192_r64_bf16.md", kv["source"], kv["helpers"]):
+        dst = tmp_path / rel
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        dst.write_bytes(open(os.path.join(ROOT, rel), "rb").read())
+    src = tmp_path / kv["source"]
+    src.write_text("// changed\n" + src.read_text(encoding="utf-8"), encoding="utf-8")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.sweep_traffic(16384, 16384) is None
