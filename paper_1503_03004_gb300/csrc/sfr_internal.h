@@ -29,17 +29,6 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// As pdl_enter, but lets the following kernel be scheduled before the wait.  For a short kernel
-// whose successor needs whole SMs (the projector's cluster): the successor is then queued while
-// this kernel's predecessor still runs, ahead of work another stream releases when that
-// predecessor ends.  This kernel's CTAs all run before the trigger takes effect, and its
-// predecessor's CTAs all ran before this kernel was scheduled, so no waiting kernel holds
-// resources that an earlier one still needs.
-__device__ __forceinline__ void pdl_enter_early() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
 // kern<<<grid, block, smem, st>>>(args...) with the programmatic-serialization attribute.
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,

@@ -373,15 +373,11 @@ __device__ __forceinline__ void thin_gram_body(const VGrid& vg__, const TC* __re
 // Sum of `count` partials of rpsq values into out, in a fixed order: warp w of a CTA of nw warps
 // adds the partials w, w + nw, w + 2 nw, ... of 32 consecutive entries (four loads in flight),
 // then the warp sums are added in warp order.  out may be the first partial (each entry is read
-// and written by one CTA).  nw = blockDim.x / 32 <= 32.  EARLY: the following kernel may be
-// scheduled before this one's wait (pdl_enter_early).
-template <typename T, bool EARLY = false>
+// and written by one CTA).  nw = blockDim.x / 32 <= 32.
+template <typename T>
 __device__ __forceinline__ void reduce_sq_body(const VGrid& vg__, const T* parts, int64_t count, int64_t rpsq, T* out,
                                                          const DevState* st) {
-  if constexpr (EARLY)
-    pdl_enter_early();
-  else
-    pdl_enter();
+  pdl_enter();
   SFR_VGRID(vg__);
   if (stopped(st)) return;
   __shared__ T red[32][32];
@@ -1581,12 +1577,9 @@ cudaError_t launch_copy_m(const Shape& s, const void* M, int64_t ldm, void* Mc, 
 // threads of the partial-sum kernel: 8 warps, 32 when there are many partials to walk
 inline int reduce_threads(int64_t count) { return count >= 256 ? 1024 : 256; }
 
-// The projector's Gram sum: its successor, the projector's cluster, is queued early (see
-// pdl_enter_early) so that it is placed before the W pass that the other stream starts when the
-// Gram kernel ends.
 cudaError_t launch_reduce_parts(const double* parts, int count, int rpsq, double* out, const DevState* dst,
                                 cudaStream_t st) {
-  launch_k<&reduce_sq_body<double, true>, 1024>(cdiv(rpsq, 32), reduce_threads(count), 0, st, parts, (int64_t)count,
+  launch_k<&reduce_sq_body<double>, 1024>(cdiv(rpsq, 32), reduce_threads(count), 0, st, parts, (int64_t)count,
                                            (int64_t)rpsq, out, dst);
   return cudaGetLastError();
 }
