@@ -17,7 +17,6 @@
 // and kept; a device reset (cudaDeviceReset) reloads the module at a new address, so the
 // entry point must not be used in a process after it reset a device.
 #include <cstring>
-#include <mutex>
 
 #include "sfr_internal.h"
 
@@ -25,28 +24,13 @@ namespace sfr {
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB per device
-constexpr int kMaxDevices = 64;
-
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_static_scratch on `device` (which must be current).  In host code
-// the symbol's name is only a host-side stand-in, not a device address, so it is looked up
-// once per device with cudaGetSymbolAddress and cached (valid until a device reset).
-cudaError_t scratch_base(int device, void** out) {
-  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_addr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[device] = p;
-  }
-  *out = g_scratch_addr[device];
-  return cudaSuccess;
-}
+// Device address of g_static_scratch on the current device.  In host code the symbol's name is
+// only a host-side stand-in, not a device address, so it is looked up on every call: the lookup
+// is a host query, not a stream operation, and a cached address would outlive a device reset
+// (the module reloads and the array may move).
+cudaError_t scratch_base(void** out) { return cudaGetSymbolAddress(out, g_static_scratch); }
 
 struct NoAllocFail {
   sfr_status code;
@@ -111,7 +95,7 @@ extern "C" sfr_status sfr_solve_noalloc(sfr_ctx* ctx, const sfr_problem* prob, s
       throw NoAllocFail{SFR_E_NOMEM, buf};
     }
     void* base = nullptr;
-    NA_CUDA(scratch_base(device, &base));
+    NA_CUDA(scratch_base(&base));
     Buffers b{};
     carve(s, fp64, base, &b);
     b.M = p.M;
