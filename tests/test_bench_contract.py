@@ -1,5 +1,5 @@
 """CPU checks of bench.py's contract: the reference arm (the float64 oracle on the host cores)
-prints the JSON line the driver reads, and bench.py reports the committed ncu traffic figure of
+prints its one-line JSON result, and bench.py reports the committed ncu traffic figure of
 the sweep kernel only while the kernel's source is the one the counters were taken from."""
 import json
 import os
