@@ -225,8 +225,8 @@ sfr_status sfr_stats(sfr_ctx* ctx, sfr_kernel_stat* out, int32_t count, int32_t 
  *     The workspace is about 24 bytes (float64 path) or 12 bytes (mixed path)
  *     per element of M plus the thin and r x r buffers; 500 x 500 at r = 25
  *     in float64 needs about 10 MiB.
- *   - The first call on a device looks up the array's device address and keeps
- *     it; do not call this entry point after a cudaDeviceReset in the process.
+ *   - Every call looks up the array's device address (a host query), so a
+ *     cudaDeviceReset earlier in the process leaves no stale address behind.
  *   - All calls share the array and it keeps the previous call's contents (the
  *     solve clears what must start at zero).  Calls whose GPU work overlaps --
  *     from two host threads, or two contexts on one device -- race on it.
