@@ -82,3 +82,35 @@ def test_create_without_a_gpu_fails_cleanly(libpath):
     st = lib.sfr_create(ctypes.byref(h), ctypes.byref(cfg))
     assert st < 0
     assert lib.sfr_last_error(None)
+
+
+def test_struct_offsets_match_the_c_compiler(tmp_path):
+    # the ctypes mirrors' sizes and field offsets against what a C compiler lays out for the header
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = (("sfr_config", binding.Config), ("sfr_problem", binding.Problem), ("sfr_result", binding.Result),
+               ("sfr_kernel_stat", binding.KernelStat), ("sfr_opt_full_problem", binding.OptFullProblem),
+               ("sfr_opt_full_result", binding.OptFullResult))
+    lines = ['#include <stdio.h>', '#include "sfr.h"', "int main(void) {"]
+    for name, py in structs:
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = str(tmp_path / "layout")
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", exe],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    got = {}
+    for line in subprocess.run([exe], capture_output=True, text=True, timeout=60).stdout.splitlines():
+        parts = line.split()
+        got[(parts[0], parts[1])] = int(parts[-1])
+    for name, py in structs:
+        assert got[(name, "size")] == ctypes.sizeof(py), name
+        for f, _ in py._fields_:
+            assert got[(name, f)] == getattr(py, f).offset, (name, f)
