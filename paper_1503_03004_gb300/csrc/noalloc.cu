@@ -13,9 +13,8 @@
 // kStaticScratchBytes of it until the process exits.  All calls share it and it keeps the
 // previous call's contents; the solve clears what must start at zero.  Calls whose work
 // overlaps on the GPU (two host threads, or two contexts on one device) race on it.
-// The array's device address is looked up once per device (on that device's first call)
-// and kept; a device reset (cudaDeviceReset) reloads the module at a new address, so the
-// entry point must not be used in a process after it reset a device.
+// The array's device address is looked up on every call, so a device reset
+// (cudaDeviceReset), which reloads the module at a new address, leaves no stale address.
 #include <cstring>
 
 #include "sfr_internal.h"
